@@ -1,0 +1,260 @@
+/*
+ * md.h — C ABI of surfmd: constrained Langevin molecular dynamics on implicit
+ * surfaces, one GB300 GPU (sm_103a).
+ *
+ * Method (Paquay & Kusters, "A method for molecular dynamics on curved
+ * surfaces"):
+ *   - Constrained Hamiltonian, Eq. (1); equations of motion Eqs. (2)-(4):
+ *       dx/dt = p/m,  dp/dt = f - lambda * n,  n = grad g (unnormalised).
+ *   - Algorithm 1 (RATTLE for particles on manifolds): a position half that
+ *     solves for (x^{m+1}, lambda) by Newton iteration and a momentum half that
+ *     solves for (p^{m+1}, mu) so that n(x^{m+1}) . p^{m+1} = 0.
+ *   - Algorithm S1 (RATTLE with the Gronbech-Jensen/Farago Langevin form):
+ *       f_r^{n+1} = sqrt(2 m kT / (tau dt)) * (r_x, r_y, r_z),  r ~ N(0,1)
+ *       F^{m+1}   = [f^{m+1} - p^{m+1/2}/tau + (f_r^{n+1} + f_r^n)/2] / (1 + dt/(2 tau))
+ *     followed by the momentum half of Algorithm 1 with F^{m+1}.
+ *   - Pair potential: truncated and shifted Lennard-Jones, Eq. (S1); WCA is
+ *     the cut at 2^{1/6} sigma (Section 3.2).
+ *   - Harmonic bond V = k (r - r0)^2 (no factor 1/2) and the repulsive
+ *     Lennard-Jones wall V_w (SI Section S3.2, virus capsid set-up).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an int status (MD_OK = 0 or an MD_ERR_* code).
+ *     md_last_error() returns a NUL-terminated description of the last
+ *     failure on that handle (owned by the handle, valid until the next call).
+ *   - Host arrays passed in are owned by the caller and are copied during the
+ *     call; host arrays passed out are written during the call. Device
+ *     pointers (the *_device variants) must point to memory on the handle's
+ *     device and stay valid until the call returns.
+ *   - The library owns every device buffer it allocates; md_destroy frees
+ *     them. All GPU work is enqueued on the handle's stream (md_set_stream).
+ *   - Per-particle arrays are in user order. In a batch (md_create_batch) the
+ *     systems are concatenated in system order: system s owns particles
+ *     [off_s, off_s + n_s), off_s = n_0 + ... + n_{s-1}.
+ *   - Positions/velocities/forces are row-major [n][3] float64 (x, y, z of
+ *     particle 0, then particle 1, ...).
+ *   - Units are Lennard-Jones units (sigma, epsilon, m, tau_LJ).
+ *
+ * Error behaviour
+ *   - Argument errors are detected on the host before any GPU work and return
+ *     MD_ERR_INVALID_ARG with the state unchanged.
+ *   - Errors raised inside kernels (Newton non-convergence, non-finite
+ *     values, a particle leaving the cell grid) are latched in a device status
+ *     word and reported by the next synchronising call (md_sync, md_get_state,
+ *     md_forces, md_constraint_residual, md_observables). The status word is
+ *     cleared when it is reported. The kernels never trap and never spin
+ *     without a bound.
+ */
+#ifndef SURFMD_MD_H
+#define SURFMD_MD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define MD_OK                  0
+#define MD_ERR_INVALID_ARG     1  /* bad argument; nothing was changed            */
+#define MD_ERR_CUDA            2  /* a CUDA runtime call failed                    */
+#define MD_ERR_RATTLE_DIVERGED 3  /* Newton of Algorithm 1 missed the tolerance    */
+#define MD_ERR_NONFINITE       4  /* NaN/Inf in a position or momentum             */
+#define MD_ERR_OUT_OF_GRID     5  /* a particle left the cell grid of its system   */
+#define MD_ERR_TIMEOUT         6  /* a bounded device-side wait ran out            */
+#define MD_ERR_NO_DEVICE       7  /* no CUDA device is visible                     */
+
+/* Bits of the device status word (md_status); a set bit maps to the code
+ * given beside it, lowest code first. */
+#define MD_FLAG_RATTLE_DIVERGED 0x1u
+#define MD_FLAG_NONFINITE       0x2u
+#define MD_FLAG_OUT_OF_GRID     0x4u
+#define MD_FLAG_TIMEOUT         0x8u
+
+#define MD_MAX_TYPES 8
+
+/* ---- surfaces g(x) = 0 ------------------------------------------------- */
+/* The constraint function g and its unnormalised gradient n = grad g.
+ *   PLANE      g = a(x-x0) + b(y-y0) + c(z-z0), p = (a, b, c)   (SI S3.1)
+ *   SPHERE     g = |x-c|^2 - R^2,                p[0] = R        (Eq. 1 text)
+ *   ELLIPSOID  g = sum_d (x_d-c_d)^2 / p[d]^2 - 1, p = semi-axes
+ *   TORUS      g = (rho - R)^2 + (z-c_z)^2 - r^2, rho = |(x-c_x, y-c_y)|,
+ *              p = (R, r); the connector form of SI S3.1 with its axis on z
+ *   GAUSSIAN_BUMP  g = (z-c_z) - A exp(-rho^2 / (2 w^2)), p = (A, w); rho is
+ *              taken with the minimum image in periodic x, y
+ *   CYLINDER   g = sum_{d != axis} (x_d-c_d)^2 - R^2, p = (R, axis 0|1|2)
+ *              (SI S3.1 with the axis coefficient 0 and the others 1)
+ * The Newton stopping test works on |g| / |grad g|, a length, so one
+ * tolerance means the same thing on every surface. */
+typedef enum {
+  MD_SURF_NONE = 0,
+  MD_SURF_PLANE = 1,
+  MD_SURF_SPHERE = 2,
+  MD_SURF_ELLIPSOID = 3,
+  MD_SURF_TORUS = 4,
+  MD_SURF_GAUSSIAN_BUMP = 5,
+  MD_SURF_CYLINDER = 6
+} md_surface_kind;
+
+typedef struct md_surface {
+  int32_t kind;      /* md_surface_kind                                    */
+  int32_t reserved;  /* must be 0                                          */
+  double center[3];  /* (x0, y0, z0) of the plane / centre of the others   */
+  double p[4];       /* shape parameters, see above                        */
+} md_surface;
+
+/* ---- parameters of one system ------------------------------------------ */
+#define MD_PREC_FP64  0  /* every step in float64                              */
+#define MD_PREC_MIXED 1  /* float32 pair forces and noise; float64 state,
+                            Newton solve, projection and position update      */
+
+typedef struct md_params {
+  double dt;            /* time step                                          */
+  double kT;            /* thermal energy                                     */
+  double gamma;         /* 1/tau, Langevin friction rate; 0 gives NVE          */
+  double rattle_tol;    /* eta: stop when |g|/|grad g| < eta (length units)   */
+  int32_t max_newton;   /* iteration cap of the position half (e.g. 30)        */
+  int32_t frozen_normal;/* 1: keep n = grad g(x^m) in the Newton Jacobian     */
+  int32_t precision;    /* MD_PREC_FP64 | MD_PREC_MIXED                        */
+  int32_t ntypes;       /* 1..MD_MAX_TYPES                                     */
+  double mass[MD_MAX_TYPES];
+  double eps[MD_MAX_TYPES][MD_MAX_TYPES];    /* symmetric                    */
+  double sigma[MD_MAX_TYPES][MD_MAX_TYPES];  /* symmetric                    */
+  double rcut[MD_MAX_TYPES][MD_MAX_TYPES];   /* symmetric; 0 = no pair term  */
+  double box_lo[3];     /* cell-grid bounds; periodic dims wrap at these      */
+  double box_hi[3];     /* all zero: bounds derived from the surface          */
+  int32_t periodic[3];  /* 1 = periodic along that axis                       */
+  int32_t beads_per_mol;/* > 1: particles [k*B, (k+1)*B) of a system form one
+                           linear chain with harmonic bonds between neighbours */
+  double bond_k;        /* V = bond_k (r - bond_r0)^2                         */
+  double bond_r0;
+  int32_t exclude_intramol; /* 1: no pair term between beads of one molecule  */
+  int32_t wall_enable;  /* 1: V_w on unconstrained particles at two z faces   */
+  double wall_lo_z, wall_hi_z, wall_eps, wall_sigma;
+  uint64_t seed;        /* Philox key word 0 = low 32 bits of seed            */
+  uint32_t replica;     /* Philox key word 1                                  */
+  int32_t reserved;     /* must be 0                                          */
+  double cell_size;     /* 0: largest rcut (plus a 2^-12 relative margin)     */
+} md_params;
+
+/* Per-system observables (Section 3.1: kT = 2K/N_dof with 2 degrees of
+ * freedom per constrained and 3 per free particle; MSD closed forms of
+ * SI Section S1.3). */
+typedef struct md_obs {
+  uint64_t step;
+  int64_t n;
+  int64_t ndof;
+  double kinetic;          /* K = sum p^2 / 2m at the integer step            */
+  double potential;        /* U: pair + bond + wall                           */
+  double kT;               /* 2 K / ndof                                      */
+  double max_g_over_gradg; /* max over constrained particles of |g|/|grad g|  */
+  double max_n_dot_v;      /* max |n.v| / |n|                                 */
+  double msd;              /* mean |x - x_ref|^2, x unwrapped                 */
+  double r0_dot_rt;        /* mean (x_ref-c).(x-c)/R^2 (sphere), else 0      */
+} md_obs;
+
+typedef struct md_handle md_handle;
+
+/* Library version, (major << 16) | minor. */
+int md_version(void);
+
+/* Create one system of n particles held on `surf` (kind MD_SURF_NONE: all
+ * particles free). Allocates all device memory for n particles on the
+ * current CUDA device. n = 0 is valid and gives a handle whose steps do
+ * nothing. Returns MD_ERR_INVALID_ARG for inconsistent parameters, e.g.
+ * dt <= 0, a periodic axis shorter than 3 cells, a bump without periodic x,y. */
+int md_create(const md_surface* surf, const md_params* prm, int64_t n,
+              md_handle** out);
+
+/* Create nsys independent systems advanced together (ensembles of replicas).
+ * surfs[s], prms[s], n_per_sys[s] describe system s. All systems must share
+ * precision, ntypes, mass, eps, sigma, rcut and cell_size; the other fields
+ * may differ. Systems never interact. */
+int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms,
+                    const int64_t* n_per_sys, md_handle** out);
+
+/* Enqueue all later GPU work on `cuda_stream` (a cudaStream_t, e.g. taken
+ * from torch.cuda.current_stream().cuda_stream). NULL = the legacy stream. */
+int md_set_stream(md_handle* h, void* cuda_stream);
+
+/* Set the state at step counter step0. x: positions [n][3]; v: velocities
+ * [n][3] (NULL = zero); type: [n] in [0, ntypes) (NULL = 0); mol: [n]
+ * molecule ids for exclusions (NULL = derived from beads_per_mol);
+ * constrained: [n] 0/1 (NULL = 1 where the system has a surface).
+ * Each constrained x must satisfy |g|/|grad g| < 1e-6 (else
+ * MD_ERR_INVALID_ARG); its velocity is projected on the tangent plane,
+ * v <- v - (n.v / n.n) n, before p = m v is stored. The positions also
+ * become the reference of md_obs.msd. The first md_step after this call
+ * forms F^{step0} = f(x) - gamma p + f_r^{step0}, i.e. Algorithm S1 with no
+ * noise average and no 1/(1+dt/2tau) factor on its first force. */
+int md_set_state(md_handle* h, const double* x, const double* v,
+                 const int32_t* type, const int32_t* mol,
+                 const uint8_t* constrained, uint64_t step0);
+
+/* As md_set_state, with x, v and the optional arrays in device memory. */
+int md_set_state_device(md_handle* h, const double* d_x, const double* d_v,
+                        const int32_t* d_type, const int32_t* d_mol,
+                        const uint8_t* d_constrained, uint64_t step0);
+
+/* Restore a checkpoint written by md_get_state: positions x^k, the
+ * half-step momenta p^{k-1/2} and the step counter k. Types, molecules and
+ * the constrained flags stay as last set. Because the noise is a pure
+ * function of (seed, replica, particle, step), a restored run repeats the
+ * uninterrupted trajectory bit for bit. */
+int md_restore(md_handle* h, const double* x, const double* p_half,
+               uint64_t step);
+
+/* Advance every system by nsteps steps of Algorithm S1 (asynchronous: the
+ * work is enqueued on the stream; kernel-side errors surface at the next
+ * synchronising call). */
+int md_step(md_handle* h, int64_t nsteps);
+
+/* Wait for the stream and report (then clear) the device status word. */
+int md_sync(md_handle* h);
+
+/* Device status bits (MD_FLAG_*) since the last report; synchronises. */
+int md_status(md_handle* h, uint32_t* flags);
+
+/* Read the state at the current step counter k: x^k, v^k = p^k/m (the
+ * momentum half of step k is evaluated on demand from p^{k-1/2} and the
+ * forces at x^k), p^{k-1/2} and k. Any output may be NULL. */
+int md_get_state(md_handle* h, double* x, double* v, double* p_half,
+                 uint64_t* step);
+
+/* As md_get_state, outputs in device memory (any may be NULL). */
+int md_get_state_device(md_handle* h, double* d_x, double* d_v, double* d_p_half);
+
+/* Conservative force f = -grad V (pair + bond + wall) at the current
+ * positions, [n][3], and the per-particle potential energy u [n] (pair and
+ * bond energies split equally between the two particles). Either may be
+ * NULL. In MD_PREC_MIXED the pair part is computed in float32. */
+int md_forces(md_handle* h, double* f_out, double* u_out);
+
+/* Constraint residuals at the current step (Section 2.2: g(x)=0 and
+ * v.n = 0): max |g|/|grad g|, max |g| and max |n.v|/|n| over constrained
+ * particles of all systems. */
+int md_constraint_residual(md_handle* h, double* max_g_over_gradg,
+                           double* max_abs_g, double* max_n_dot_v);
+
+/* Observables of every system at the current step: out[nsys]. */
+int md_observables(md_handle* h, md_obs* out, int32_t max_systems,
+                   int32_t* n_written);
+
+/* Counts: total particles, systems, current step. Any output may be NULL. */
+int md_info(md_handle* h, int64_t* n, int32_t* nsys, uint64_t* step);
+
+/* Number of kernel launches issued by the last md_step call. */
+int md_last_launch_count(md_handle* h, int64_t* launches);
+
+/* Description of the last error on h (or of the last md_create failure
+ * when h is NULL). Never NULL. */
+const char* md_last_error(md_handle* h);
+
+/* Free all device memory of the handle. NULL is ignored. */
+void md_destroy(md_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SURFMD_MD_H */

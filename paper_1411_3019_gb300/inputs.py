@@ -1,0 +1,421 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module serves both the CUDA path and the oracle and therefore holds
+none of the method's arithmetic: no Newton solve, no force, no noise, no
+projection. It only draws positions uniformly (by area) on a surface or in a
+volume with overlaps rejected (random sequential addition), Maxwell
+velocities, and the parameter dictionaries of the workloads. Surfaces are
+sampled from their parametrisations, never from g(x).
+
+Every generator takes a seed and uses numpy's counter-based Philox bit
+generator, so a given seed gives the same arrays on every machine.
+
+Area fraction (Section 3.2): phi = N A_p / A with A_p = pi d0^2 / 4 and
+d0 = 2^{1/6} sigma, the WCA cutoff.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+D0 = 2.0 ** (1.0 / 6.0)
+A_P = math.pi * D0 * D0 / 4.0
+WCA_RC = D0
+
+
+def rng(seed: int, stream: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=[seed & 0xFFFFFFFFFFFFFFFF, stream]))
+
+
+# ---------------------------------------------------------------------------
+# parameters
+# ---------------------------------------------------------------------------
+def wca_params(ntypes: int = 1, **over) -> dict:
+    """WCA particles (eps = sigma = m = 1, cutoff 2^{1/6} sigma), kT = gamma = 1."""
+    eps = np.zeros((ntypes, ntypes))
+    sig = np.zeros((ntypes, ntypes))
+    rc = np.zeros((ntypes, ntypes))
+    eps[:, :] = 1.0
+    sig[:, :] = 1.0
+    rc[:, :] = WCA_RC
+    prm = dict(dt=0.002, kT=1.0, gamma=1.0, rattle_tol=1e-10, max_newton=30,
+               frozen_normal=0, precision="mixed", ntypes=ntypes, mass=[1.0] * ntypes,
+               eps=eps, sigma=sig, rcut=rc, box_lo=(0.0, 0.0, 0.0), box_hi=(0.0, 0.0, 0.0),
+               periodic=(0, 0, 0), beads_per_mol=0, bond_k=0.0, bond_r0=0.0,
+               exclude_intramol=0, wall_enable=0, wall_lo_z=0.0, wall_hi_z=0.0,
+               wall_eps=1.0, wall_sigma=1.0, seed=1, replica=0, cell_size=0.0)
+    prm.update(over)
+    return prm
+
+
+def noninteracting(prm: dict) -> dict:
+    """The same parameters with every pair term switched off."""
+    out = dict(prm)
+    nt = prm["ntypes"]
+    out["eps"] = np.zeros((nt, nt))
+    out["rcut"] = np.zeros((nt, nt))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# surface areas (for the area fraction only)
+# ---------------------------------------------------------------------------
+def ellipsoid_area(a: float, b: float, c: float, n: int = 2000) -> float:
+    """Area of the ellipsoid by midpoint quadrature over the sphere angles."""
+    th = (np.arange(n) + 0.5) * math.pi / n
+    ph = (np.arange(2 * n) + 0.5) * math.pi / n
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    st, ct, sp, cp = np.sin(T), np.cos(T), np.sin(P), np.cos(P)
+    nx, ny, nz = b * c * st * st * cp, a * c * st * st * sp, a * b * st * ct
+    dA = np.sqrt(nx * nx + ny * ny + nz * nz)
+    return float(dA.sum() * (math.pi / n) * (math.pi / n))
+
+
+def torus_area(R: float, r: float) -> float:
+    return 4.0 * math.pi ** 2 * R * r
+
+
+def bump_area(L: float, A: float, w: float, n: int = 1500) -> float:
+    h = L / n
+    u = (np.arange(n) + 0.5) * h - L / 2
+    X, Y = np.meshgrid(u, u, indexing="ij")
+    e = A * np.exp(-(X * X + Y * Y) / (2 * w * w))
+    gx, gy = -e * X / (w * w), -e * Y / (w * w)
+    return float(np.sqrt(1 + gx * gx + gy * gy).sum() * h * h)
+
+
+# ---------------------------------------------------------------------------
+# uniform-by-area samplers (parametrisations + rejection on the area element)
+# ---------------------------------------------------------------------------
+def sample_surface(surf: dict, n: int, g: np.random.Generator, box=None) -> np.ndarray:
+    kind = surf["kind"]
+    c = np.asarray(surf.get("center", (0.0, 0.0, 0.0)), dtype=np.float64)
+    p = surf.get("p", ())
+    if kind == "sphere":
+        v = g.standard_normal((n, 3))
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        return c + p[0] * v
+    if kind == "ellipsoid":
+        a, b, cc = p[0], p[1], p[2]
+        out = np.empty((0, 3))
+        mx = max(b * cc, a * cc, a * b)
+        while out.shape[0] < n:
+            m = 2 * (n - out.shape[0]) + 64
+            v = g.standard_normal((m, 3))
+            v /= np.linalg.norm(v, axis=1, keepdims=True)
+            w = np.sqrt((b * cc * v[:, 0]) ** 2 + (a * cc * v[:, 1]) ** 2 + (a * b * v[:, 2]) ** 2)
+            keep = g.random(m) < w / mx
+            out = np.vstack([out, v[keep] * np.array([a, b, cc])])
+        return c + out[:n]
+    if kind == "torus":
+        R, r = p[0], p[1]
+        out = np.empty((0, 3))
+        while out.shape[0] < n:
+            m = 2 * (n - out.shape[0]) + 64
+            th = g.random(m) * 2 * math.pi
+            keep = g.random(m) < (R + r * np.cos(th)) / (R + r)
+            th = th[keep]
+            ph = g.random(th.shape[0]) * 2 * math.pi
+            rr = R + r * np.cos(th)
+            out = np.vstack([out, np.stack([rr * np.cos(ph), rr * np.sin(ph), r * np.sin(th)], 1)])
+        return c + out[:n]
+    if kind == "gaussian_bump":
+        A, w = p[0], p[1]
+        lo, hi = np.asarray(box[0], float), np.asarray(box[1], float)
+        L = hi - lo
+        out = np.empty((0, 3))
+        while out.shape[0] < n:
+            m = 2 * (n - out.shape[0]) + 64
+            xy = lo[:2] + g.random((m, 2)) * L[:2]
+            d = xy - c[:2]
+            d -= L[:2] * np.floor(d / L[:2] + 0.5)
+            e = A * np.exp(-(d ** 2).sum(1) / (2 * w * w))
+            slope2 = (e / (w * w)) ** 2 * (d ** 2).sum(1)
+            mx = 1.0 + (A / (w * math.sqrt(math.e))) ** 2
+            keep = g.random(m) < np.sqrt(1 + slope2) / math.sqrt(mx)
+            z = c[2] + e[keep]
+            out = np.vstack([out, np.column_stack([xy[keep], z])])
+        return out[:n]
+    if kind == "plane":
+        lo, hi = np.asarray(box[0], float), np.asarray(box[1], float)
+        nrm = np.asarray(p[:3], float)
+        if not (nrm[0] == 0 and nrm[1] == 0):
+            raise ValueError("the plane sampler covers planes normal to z")
+        xy = lo[:2] + g.random((n, 2)) * (hi - lo)[:2]
+        return np.column_stack([xy, np.full(n, c[2])])
+    if kind == "cylinder":
+        R, ax = p[0], int(p[1])
+        lo, hi = np.asarray(box[0], float), np.asarray(box[1], float)
+        t = lo[ax] + g.random(n) * (hi - lo)[ax]
+        ph = g.random(n) * 2 * math.pi
+        other = [k for k in range(3) if k != ax]
+        out = np.empty((n, 3))
+        out[:, ax] = t
+        out[:, other[0]] = c[other[0]] + R * np.cos(ph)
+        out[:, other[1]] = c[other[1]] + R * np.sin(ph)
+        return out
+    raise ValueError(f"no sampler for surface {kind!r}")
+
+
+# ---------------------------------------------------------------------------
+# random sequential addition with a hashed grid (groups never conflict)
+# ---------------------------------------------------------------------------
+def _keys(cells: np.ndarray, group: np.ndarray) -> np.ndarray:
+    c = cells.astype(np.int64) + 32768
+    return (group.astype(np.int64) << 48) | (c[:, 0] << 32) | (c[:, 1] << 16) | c[:, 2]
+
+
+def _conflicts(cand, cgrp, ref, rgrp, dmin, periodic, L, lo, exclude_self=False):
+    """For each candidate: does it lie closer than dmin to a reference point
+    of the same group? (exclude_self: cand and ref are the same array and a
+    point conflicts only with an earlier index.)"""
+    n = cand.shape[0]
+    bad = np.zeros(n, bool)
+    if ref.shape[0] == 0 or n == 0:
+        return bad
+    cs = dmin
+    ncell = np.where(periodic, np.maximum(np.floor(L / cs), 1), 1 << 14).astype(np.int64)
+
+    def cell_of(pts):
+        rel = pts - lo
+        c = np.floor(rel / cs).astype(np.int64)
+        for k in range(3):
+            if periodic[k]:
+                c[:, k] = np.mod(np.floor(rel[:, k] / (L[k] / ncell[k])).astype(np.int64), ncell[k])
+        return c
+
+    rc, cc = cell_of(ref), cell_of(cand)
+    rk = _keys(rc, rgrp)
+    order = np.argsort(rk, kind="stable")
+    rk_s, ref_s, ridx_s = rk[order], ref[order], order
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                nc = cc + np.array([dx, dy, dz])
+                for k in range(3):
+                    if periodic[k]:
+                        nc[:, k] = np.mod(nc[:, k], ncell[k])
+                nk = _keys(nc, cgrp)
+                a = np.searchsorted(rk_s, nk, "left")
+                b = np.searchsorted(rk_s, nk, "right")
+                occ = int((b - a).max()) if n else 0
+                for t in range(occ):
+                    idx = a + t
+                    ok = idx < b
+                    if not ok.any():
+                        continue
+                    j = np.where(ok, idx, 0)
+                    d = cand - ref_s[j]
+                    for k in range(3):
+                        if periodic[k]:
+                            d[:, k] -= L[k] * np.floor(d[:, k] / L[k] + 0.5)
+                    close = ok & ((d * d).sum(1) < dmin * dmin)
+                    if exclude_self:
+                        close &= ridx_s[j] < np.arange(n)
+                    bad |= close
+    return bad
+
+
+def rsa(sampler, counts, dmin, g, periodic=(0, 0, 0), box=None, fixed=None, fixed_group=None,
+        max_rounds=400):
+    """Random sequential addition: group k receives counts[k] points from
+    sampler(k, m) with no two points of one group (nor a point and a fixed
+    point of that group) closer than dmin."""
+    counts = np.asarray(counts, dtype=np.int64)
+    periodic = np.asarray(periodic, bool)
+    if box is None:
+        lo, L = np.zeros(3), np.ones(3)
+    else:
+        lo = np.asarray(box[0], float)
+        L = np.asarray(box[1], float) - lo
+    acc = [np.empty((0, 3)) for _ in counts]
+    pts = np.empty((0, 3)) if fixed is None else np.asarray(fixed, float)
+    grp = np.empty(0, np.int64) if fixed is None else np.asarray(fixed_group, np.int64)
+    for _ in range(max_rounds):
+        need = counts - np.array([a.shape[0] for a in acc])
+        if (need <= 0).all():
+            break
+        cand, cg = [], []
+        for k in np.nonzero(need > 0)[0]:
+            m = int(need[k] * 1.3) + 16
+            cand.append(sampler(int(k), m))
+            cg.append(np.full(m, k, np.int64))
+        cand = np.vstack(cand)
+        cg = np.concatenate(cg)
+        bad = _conflicts(cand, cg, pts, grp, dmin, periodic, L, lo)
+        cand, cg = cand[~bad], cg[~bad]
+        bad = _conflicts(cand, cg, cand, cg, dmin, periodic, L, lo, exclude_self=True)
+        cand, cg = cand[~bad], cg[~bad]
+        new_pts, new_grp = [], []
+        for k in np.unique(cg):
+            take = cand[cg == k][: max(int(need[k]), 0)]
+            acc[k] = np.vstack([acc[k], take])
+            new_pts.append(take)
+            new_grp.append(np.full(take.shape[0], k, np.int64))
+        if new_pts:
+            pts = np.vstack([pts] + new_pts)
+            grp = np.concatenate([grp] + new_grp)
+    for k, a in enumerate(acc):
+        if a.shape[0] < counts[k]:
+            raise RuntimeError(f"RSA could not place {counts[k]} points in group {k}")
+    return acc
+
+
+def maxwell(n: int, kT: float, mass, g: np.random.Generator) -> np.ndarray:
+    m = np.broadcast_to(np.asarray(mass, float), (n,))
+    return g.standard_normal((n, 3)) * np.sqrt(kT / m)[:, None]
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+def _system(name, surface, params, x, v, type_=None, constrained=None):
+    n = x.shape[0]
+    return dict(name=name, surface=surface, params=params, n=n,
+                x=np.ascontiguousarray(x, np.float64), v=np.ascontiguousarray(v, np.float64),
+                type=np.zeros(n, np.int32) if type_ is None else np.ascontiguousarray(type_, np.int32),
+                constrained=(np.ones(n, np.uint8) if surface["kind"] != "none" else np.zeros(n, np.uint8))
+                if constrained is None else np.ascontiguousarray(constrained, np.uint8))
+
+
+def sphere_system(n=1000, R=10.0, seed=1, dmin=0.8, precision="fp64", dt=0.001, tol=1e-12,
+                  replica=0, interacting=True, **over):
+    """Plain-method workload: n WCA particles on a sphere of radius R placed
+    uniformly with overlaps closer than dmin rejected, Maxwell velocities at
+    kT = 1 (projected on the tangent plane by the library / oracle)."""
+    g = rng(seed, 0xFFFFFFFF - replica)
+    surf = {"kind": "sphere", "center": (0.0, 0.0, 0.0), "p": (R, 0.0, 0.0, 0.0)}
+    x = rsa(lambda k, m: sample_surface(surf, m, g), [n], dmin, g)[0]
+    prm = wca_params(precision=precision, dt=dt, rattle_tol=tol, seed=seed, replica=replica, **over)
+    if not interacting:
+        prm = noninteracting(prm)
+    v = maxwell(n, prm["kT"], 1.0, g)
+    return _system(f"sphere_N{n}_R{R:g}", surf, prm, x, v)
+
+
+def c1_plain_sphere():
+    """1,000 WCA particles on a sphere R = 10 sigma, float64 path, dt = 0.001,
+    RATTLE tolerance 1e-12, seed 1; overlaps rejected below 0.8 sigma
+    (phi = 0.787 exceeds the jamming limit of RSA at d0)."""
+    return [sphere_system(1000, 10.0, seed=1, dmin=0.8, precision="fp64", dt=0.001, tol=1e-12)]
+
+
+def ellipsoid_axes_for(n: int, phi: float, base=(150.0, 120.0, 90.0)) -> tuple:
+    """Semi-axes of the base ellipsoid's shape scaled to give area fraction phi."""
+    A0 = ellipsoid_area(*base, n=600)
+    s = math.sqrt(n * A_P / phi / A0)
+    return tuple(s * a for a in base)
+
+
+def c2_ellipsoid_torus(n_ell=200_000, n_tor=50_000, seed=1, dmin=1.0, precision="mixed",
+                       dt=0.002, tol=1e-10, torus=(120.0, 40.0)):
+    """Mixed-precision workload: n_ell WCA particles at area fraction 0.4 on
+    an ellipsoid of the shape (150, 120, 90) sigma (scaled so that the count
+    and the fraction both hold: 200,000 particles need semi-axes
+    (249.0, 199.2, 149.4) sigma), and n_tor on a torus R = 120, r = 40 sigma
+    (phi = 0.261) as a separate system. For smaller n the torus is scaled so
+    that its area fraction stays the same."""
+    g = rng(seed, 2)
+    axes = ellipsoid_axes_for(n_ell, 0.4)
+    ell = {"kind": "ellipsoid", "center": (0.0, 0.0, 0.0), "p": (*axes, 0.0)}
+    phi_t = 50_000 * A_P / torus_area(*torus)
+    s = math.sqrt(n_tor * A_P / phi_t / torus_area(*torus))
+    tor = {"kind": "torus", "center": (0.0, 0.0, 0.0), "p": (torus[0] * s, torus[1] * s, 0.0, 0.0)}
+    xs = rsa(lambda k, m: sample_surface(ell if k == 0 else tor, m, g), [n_ell, n_tor], dmin, g)
+    out = []
+    for k, (surf, x) in enumerate(((ell, xs[0]), (tor, xs[1]))):
+        prm = wca_params(precision=precision, dt=dt, rattle_tol=tol, seed=seed, replica=k)
+        out.append(_system(["ellipsoid", "torus"][k], surf, prm, x, maxwell(x.shape[0], 1.0, 1.0, g)))
+    return out
+
+
+def c3_bump_crowders(n_surf=100_000, n_free=900_000, seed=1, dmin=1.0, precision="mixed",
+                     dt=0.002, tol=1e-10, phi_surf=0.4, phi_vol=0.2):
+    """Mixed constrained/free workload: n_surf particles on a Gaussian bump
+    z = A exp(-rho^2/2w^2) in a periodic square box, plus n_free free
+    crowders in a slab between two V_w walls. The stated box (300 sigma,
+    A = 20, w = 15) cannot hold 100,000 particles, so box, A and w are
+    scaled together to give the surface area fraction phi_surf; the slab
+    height follows from the crowders' volume fraction phi_vol with
+    v_p = pi d0^3 / 6."""
+    L0, A0, w0 = 300.0, 20.0, 15.0
+    a0 = bump_area(L0, A0, w0, n=600)
+    s = math.sqrt(n_surf * A_P / phi_surf / a0)
+    L, A, w = L0 * s, A0 * s, w0 * s
+    v_p = math.pi * D0 ** 3 / 6.0
+    h = n_free * v_p / phi_vol / (L * L)
+    zlo, zhi = -h / 2 - 0.5, A + h / 2 + 0.5
+    box = ((-L / 2, -L / 2, zlo - 2.0), (L / 2, L / 2, zhi + 2.0))
+    g = rng(seed, 3)
+    surf = {"kind": "gaussian_bump", "center": (0.0, 0.0, 0.0), "p": (A, w, 0.0, 0.0)}
+    prm = wca_params(precision=precision, dt=dt, rattle_tol=tol, seed=seed, replica=0,
+                     box_lo=box[0], box_hi=box[1], periodic=(1, 1, 0), wall_enable=1,
+                     wall_lo_z=zlo, wall_hi_z=zhi, wall_eps=1.0, wall_sigma=1.0)
+    xs = rsa(lambda k, m: sample_surface(surf, m, g, box=box), [n_surf], dmin, g,
+             periodic=(1, 1, 0), box=box)[0]
+    wall_rc = D0
+
+    def crowders(k, m):
+        xy = np.asarray(box[0][:2]) + g.random((m, 2)) * L
+        z = zlo + wall_rc + g.random(m) * (zhi - zlo - 2 * wall_rc)
+        return np.column_stack([xy, z])
+    xf = rsa(crowders, [n_free], dmin, g, periodic=(1, 1, 0), box=box,
+             fixed=xs, fixed_group=np.zeros(n_surf, np.int64))[0]
+    x = np.vstack([xs, xf])
+    con = np.concatenate([np.ones(n_surf, np.uint8), np.zeros(n_free, np.uint8)])
+    return [_system("bump_crowders", surf, prm, x, maxwell(x.shape[0], 1.0, 1.0, g), constrained=con)]
+
+
+def c4_replicas(nrep=4096, seed=1, nmin=50, nmax=2000, rmin=5.0, rmax=40.0, phimin=0.05,
+                phimax=0.5, dmin=1.0, precision="mixed", dt=0.002, tol=1e-10):
+    """Batched replicas: nrep independent sphere systems with N ~ U[nmin, nmax]
+    and R ~ U[rmin, rmax], redrawn until phi = N A_p / (4 pi R^2) lies in
+    [phimin, phimax]; WCA, gamma = kT = 1."""
+    g = rng(seed, 4)
+    Ns, Rs = [], []
+    while len(Ns) < nrep:
+        N = int(g.integers(nmin, nmax + 1))
+        R = float(rmin + (rmax - rmin) * g.random())
+        phi = N * A_P / (4 * math.pi * R * R)
+        if phimin <= phi <= phimax:
+            Ns.append(N)
+            Rs.append(R)
+    surfs = [{"kind": "sphere", "center": (0.0, 0.0, 0.0), "p": (R, 0.0, 0.0, 0.0)} for R in Rs]
+    xs = rsa(lambda k, m: sample_surface(surfs[k], m, g), Ns, dmin, g)
+    out = []
+    for k in range(nrep):
+        prm = wca_params(precision=precision, dt=dt, rattle_tol=tol, seed=seed, replica=k)
+        out.append(_system(f"replica{k}", surfs[k], prm, xs[k], maxwell(Ns[k], 1.0, 1.0, g)))
+    return out
+
+
+def c5_bead_molecules(nmol=20_000, beads=5, R=60.0, seed=1, dmin=1.0, precision="mixed",
+                      dt=0.002, tol=1e-10, bond_k=100.0, bond_r0=1.0):
+    """Bead molecules on a spherical template: nmol linear chains of `beads`
+    beads (type = bead index), bead 0 held on a sphere of radius R, beads
+    1..beads-1 free and placed radially outward at bond_r0 spacing; harmonic
+    bonds V = k (r - r0)^2; LJ with eps = 2 and cutoff 2.5 sigma between
+    type-3 beads of different molecules, WCA between all other pairs of
+    different molecules (pairs within a molecule are excluded)."""
+    nt = beads
+    prm = wca_params(ntypes=nt, precision=precision, dt=dt, rattle_tol=tol, seed=seed,
+                     beads_per_mol=beads, bond_k=bond_k, bond_r0=bond_r0, exclude_intramol=1)
+    if nt > 3:
+        prm["eps"][3, 3] = 2.0
+        prm["rcut"][3, 3] = 2.5
+    g = rng(seed, 5)
+    surf = {"kind": "sphere", "center": (0.0, 0.0, 0.0), "p": (R, 0.0, 0.0, 0.0)}
+    x0 = rsa(lambda k, m: sample_surface(surf, m, g), [nmol], dmin, g)[0]
+    u = x0 / np.linalg.norm(x0, axis=1, keepdims=True)
+    x = np.empty((nmol, beads, 3))
+    for b in range(beads):
+        x[:, b, :] = u * (R + b * bond_r0)
+    x = x.reshape(-1, 3)
+    ext = R + beads * bond_r0 + 10.0
+    prm["box_lo"] = (-ext, -ext, -ext)
+    prm["box_hi"] = (ext, ext, ext)
+    type_ = np.tile(np.arange(beads, dtype=np.int32), nmol)
+    con = (type_ == 0).astype(np.uint8)
+    return [_system("bead_molecules", surf, prm, x, maxwell(x.shape[0], 1.0, 1.0, g),
+                    type_=type_, constrained=con)]
