@@ -243,8 +243,32 @@ int md_observables(md_handle* h, md_obs* out, int32_t max_systems,
 /* Counts: total particles, systems, current step. Any output may be NULL. */
 int md_info(md_handle* h, int64_t* n, int32_t* nsys, uint64_t* step);
 
-/* Number of kernel launches issued by the last md_step call. */
+/* Advance nsteps steps launching each kernel of a step on its own (no
+ * graph), timed with CUDA events on the handle's stream; kernel_ms[i] is the
+ * mean duration of kernel i of a step (i < *n_kernels, names from
+ * md_profile_kernel_name). Synchronises. The trajectory is the same as with
+ * md_step. */
+int md_profile_step(md_handle* h, int64_t nsteps, double* kernel_ms, int32_t max_kernels,
+                    int32_t* n_kernels);
+const char* md_profile_kernel_name(md_handle* h, int32_t i);
+
+/* Number of kernel launches issued by the last md_step (or md_profile_step)
+ * call. */
 int md_last_launch_count(md_handle* h, int64_t* launches);
+
+/* Diagnostics of the cell list (the index work of the pair step), for
+ * tests. md_grid_info: grid of system `sys`: origin lo[3], cell edge cs[3],
+ * cells per axis nc[3] and the id of its first cell (cell ids of system s
+ * are base_s + cx + nc0 (cy + nc1 cz), cx = floor((x_wrapped - lo)/cs)).
+ * hashed: 0 when a bucket is a cell id, else log2 of the bucket count.
+ * md_cell_list: after the last step, sorted_ids[n] lists the particles
+ * bucket by bucket, ascending id inside a bucket; sorted_cells[n] their cell
+ * ids; bucket_start[nbucket + 1] the bucket ranges. Arrays may be NULL
+ * (then only *nbucket is written). */
+int md_grid_info(md_handle* h, int32_t sys, double lo[3], double cs[3], int32_t nc[3],
+                 uint32_t* base, int32_t* hashed);
+int md_cell_list(md_handle* h, uint32_t* sorted_ids, uint32_t* sorted_cells,
+                 uint32_t* bucket_start, uint32_t* nbucket);
 
 /* Description of the last error on h (or of the last md_create failure
  * when h is NULL). Never NULL. */

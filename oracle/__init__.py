@@ -117,6 +117,12 @@ def lib():
             L.orc_wall_violation.argtypes = [C.c_void_p]
             L.orc_sys_forces.restype = C.c_int
             L.orc_sys_forces.argtypes = [C.c_void_p]
+            L.orc_force_on.argtypes = [C.POINTER(Params), C.c_int64, _dp, _ip, _ip, C.c_void_p,
+                                       C.c_int64, _dp, C.POINTER(C.c_double)]
+            L.orc_particle_advance.restype = C.c_int
+            L.orc_particle_advance.argtypes = [C.POINTER(Surface), C.POINTER(Params), C.c_int64, _dp,
+                                               _ip, _ip, C.c_void_p, C.c_int64, _dp, C.c_uint64,
+                                               C.c_int, _dp, _dp, _dp]
             _lib = L
     return _lib
 
@@ -248,6 +254,43 @@ def bond_wall_forces(prm, x, constrained=None):
     bad = lib().orc_bond_wall_forces(C.byref(P), n, x,
                                      None if con is None else con.ctypes.data, f, u)
     return f, u, bad
+
+
+def _arrays(x, type_, mol, constrained, surf, prm):
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    t = np.zeros(n, np.int32) if type_ is None else np.ascontiguousarray(type_, np.int32)
+    if mol is None:
+        bpm = prm.get("beads_per_mol", 0)
+        mo = (np.arange(n) // bpm if bpm > 1 else np.arange(n)).astype(np.int32)
+    else:
+        mo = np.ascontiguousarray(mol, np.int32)
+    if constrained is None:
+        kind = (surf or {}).get("kind", "none")
+        con = np.full(n, 0 if kind == "none" else 1, np.uint8)
+    else:
+        con = np.ascontiguousarray(constrained, np.uint8)
+    return x, t, mo, con
+
+
+def force_on(prm, x, i, type_=None, mol=None, constrained=None, surf=None):
+    """Force and energy on particle i only (all pairs with i, its bonds and walls)."""
+    x, t, mo, con = _arrays(x, type_, mol, constrained, surf, prm)
+    f = np.zeros(3)
+    u = C.c_double()
+    P = make_params(prm)
+    lib().orc_force_on(C.byref(P), x.shape[0], x, t, mo, con.ctypes.data, int(i), f, C.byref(u))
+    return f, u.value
+
+
+def particle_advance(surf, prm, x, i, p_in, step, first, type_=None, mol=None, constrained=None):
+    """Algorithm S1 for particle i: (p^k, x^{k+1}, p^{k+1/2}, status)."""
+    x, t, mo, con = _arrays(x, type_, mol, constrained, surf, prm)
+    S, P = make_surface(surf), make_params(prm)
+    pk, xn, phn = np.zeros(3), np.zeros(3), np.zeros(3)
+    st = lib().orc_particle_advance(C.byref(S), C.byref(P), x.shape[0], x, t, mo, con.ctypes.data,
+                                    int(i), _f64(p_in), int(step), int(first), pk, xn, phn)
+    return pk, xn, phn, st
 
 
 # ---------------------------------------------------------------------------

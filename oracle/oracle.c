@@ -842,3 +842,90 @@ void orc_newton_stats(const orc_sys* s, int64_t out[3]) {
 }
 
 int32_t orc_wall_violation(const orc_sys* s) { return s->wall_bad; }
+
+/* ------------------------------------------------------------------------ */
+/* One particle at a time (sampled checks of large systems)                  */
+/* ------------------------------------------------------------------------ */
+/* Conservative force and energy on particle i of a system of n particles:
+ * every pair (i, j) of Eq. (S1) with the minimum image, plus its bonds and
+ * walls (readings R5, R6). O(n). */
+void orc_force_on(const orc_params* P, int64_t n, const double* x, const int32_t* type,
+                  const int32_t* mol, const uint8_t* con, int64_t i, double f[3], double* u) {
+  f[0] = f[1] = f[2] = 0.0;
+  double ui = 0.0;
+  for (int64_t j = 0; j < n; ++j) {
+    if (j == i || same_molecule(P, mol, i, j)) continue;
+    double d[3] = {x[3 * i] - x[3 * j], x[3 * i + 1] - x[3 * j + 1], x[3 * i + 2] - x[3 * j + 2]};
+    min_image(P, d);
+    ui += 0.5 * lj_pair(P, type[i], type[j], d, f);
+  }
+  if (P->beads_per_mol > 1) {
+    int64_t B = P->beads_per_mol;
+    for (int side = 0; side < 2; ++side) {
+      int64_t j = side == 0 ? i - 1 : i + 1;
+      if (side == 0 && (i % B) == 0) continue;
+      if (side == 1 && ((i % B) == B - 1 || j >= n)) continue;
+      double d[3] = {x[3 * i] - x[3 * j], x[3 * i + 1] - x[3 * j + 1], x[3 * i + 2] - x[3 * j + 2]};
+      min_image(P, d);
+      double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      double dr = r - P->bond_r0;
+      for (int k = 0; k < 3; ++k) f[k] += -2.0 * P->bond_k * dr / r * d[k];
+      ui += 0.5 * P->bond_k * dr * dr;
+    }
+  }
+  if (P->wall_enable && !(con && con[i])) {
+    double sw = P->wall_sigma, ew = P->wall_eps;
+    double rcw = pow(2.0, 1.0 / 6.0) * sw;
+    double dist[2] = {x[3 * i + 2] - P->wall_lo_z, P->wall_hi_z - x[3 * i + 2]};
+    double sign[2] = {+1.0, -1.0};
+    for (int w = 0; w < 2; ++w) {
+      double r = dist[w];
+      if (r <= 0.0 || r >= rcw) continue;
+      double s6 = pow(sw / r, 6.0);
+      ui += 4.0 * ew * (s6 * s6 - s6 + 0.25);
+      f[2] += sign[w] * 24.0 * ew * (2.0 * s6 * s6 - s6) / r;
+    }
+  }
+  if (u) *u = ui;
+}
+
+/* Algorithm S1 for one particle i whose neighbours sit at x (all n):
+ * from p_in (p^k when first = 1, else p^{k-1/2}) at step counter k, form the
+ * force f^k, the random force and the combined force F^k (reading R2 when
+ * first = 1), the momentum half (when first = 0) giving p^k, then the
+ * position half of the next step giving x^{k+1} and p^{k+1/2}. Returns the
+ * position-half status of orc_position_half (0 for a free particle). */
+int orc_particle_advance(const orc_surface* S, const orc_params* P, int64_t n, const double* x,
+                         const int32_t* type, const int32_t* mol, const uint8_t* con, int64_t i,
+                         const double p_in[3], uint64_t k, int first, double p_k[3],
+                         double x_new[3], double p_half_new[3]) {
+  double m = P->mass[type[i]];
+  double f[3];
+  orc_force_on(P, n, x, type, mol, con, i, f, NULL);
+  double amp = sqrt(2.0 * m * P->kT * P->gamma / P->dt);
+  double xk[3], xkm1[3];
+  orc_gauss3(P->seed, P->replica, (uint32_t)i, k, xk);
+  double F[3];
+  if (first) {
+    for (int c = 0; c < 3; ++c) {
+      F[c] = f[c] - P->gamma * p_in[c] + amp * xk[c];
+      p_k[c] = p_in[c];
+    }
+  } else {
+    orc_gauss3(P->seed, P->replica, (uint32_t)i, k - 1, xkm1);
+    for (int c = 0; c < 3; ++c)
+      F[c] = (f[c] - P->gamma * p_in[c] + 0.5 * amp * (xk[c] + xkm1[c])) / (1.0 + 0.5 * P->dt * P->gamma);
+    if (con && con[i]) {
+      if (orc_momentum_half(S, P, &x[3 * i], p_in, F, m, p_k, NULL, NULL) < 0) return -1;
+    } else {
+      for (int c = 0; c < 3; ++c) p_k[c] = p_in[c] + 0.5 * P->dt * F[c];
+    }
+  }
+  if (con && con[i])
+    return orc_position_half(S, P, &x[3 * i], p_k, F, m, x_new, p_half_new, NULL, NULL);
+  for (int c = 0; c < 3; ++c) {
+    p_half_new[c] = p_k[c] + 0.5 * P->dt * F[c];
+    x_new[c] = x[3 * i + c] + P->dt / m * p_half_new[c];
+  }
+  return 0;
+}

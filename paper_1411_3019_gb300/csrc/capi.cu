@@ -1,0 +1,876 @@
+// capi.cu -- the C ABI of include/md.h on top of the kernels of kernels.cu.
+//
+// A handle owns every device buffer it allocates (cudaMalloc in md_create,
+// cudaFree in md_destroy). One md_step enqueues, per time step, the kernels
+// pair -> integrate -> scan (3) -> scatter -> bucket build; the step is
+// captured once into a CUDA graph (the step counter and the first-step flag
+// live in device memory, so one graph serves every step) and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/md.h"
+#include "engine.h"
+
+using namespace surfmd;
+
+struct md_handle {
+  int dev = 0;
+  cudaStream_t user_stream = nullptr;  // set by md_set_stream (nullptr: own stream)
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int precision = 1;
+  int64_t n = 0;
+  int nsys = 0;
+  int has_pairs = 0, bonds = 0, walls = 0, excl = 0;
+  bool state_set = false;
+  std::vector<SysDev> sys;
+  std::vector<int64_t> first;
+  TypeTable types{};
+  DevArrays A{};
+  int64_t* d_first = nullptr;
+  double* d_stage = nullptr;   // 9n doubles
+  int32_t* d_stage_i = nullptr;  // 2n int32 (type, mol)
+  uint8_t* d_stage_u8 = nullptr; // n
+  unsigned long long* d_resid = nullptr;
+  double* d_obs = nullptr;
+  uint32_t* h_status = nullptr;  // pinned
+  unsigned long long* h_resid = nullptr;  // pinned
+  cudaGraphExec_t graph = nullptr;
+  int64_t last_launches = 0;
+  int kernels_per_step = 0;
+  std::vector<void*> allocs;
+  std::string err;
+
+  cudaStream_t stream() const { return user_stream ? user_stream : own_stream; }
+};
+
+static std::string g_create_err;
+
+namespace {
+
+int fail(md_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_err = msg;
+  return code;
+}
+
+int cuda_fail(md_handle* h, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(h, MD_ERR_CUDA, m);
+}
+
+#define CK(h, call)                                   \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(md_handle* h, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+  if (e == cudaSuccess) {
+    h->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+  }
+  return e;
+}
+
+bool symmetric_ok(const double t[MD_MAX_TYPES][MD_MAX_TYPES], int nt) {
+  for (int a = 0; a < nt; ++a)
+    for (int b = 0; b < nt; ++b)
+      if (!(t[a][b] == t[b][a]) || !std::isfinite(t[a][b]) || t[a][b] < 0.0) return false;
+  return true;
+}
+
+// Validate one system's parameters and fill its SysDev (grid left to the caller).
+int check_system(const md_surface& s, const md_params& p, SysDev& S, std::string& why) {
+  auto bad = [&](const char* m) {
+    why = m;
+    return MD_ERR_INVALID_ARG;
+  };
+  if (!(p.dt > 0.0) || !std::isfinite(p.dt)) return bad("dt must be > 0");
+  if (!(p.kT >= 0.0) || !(p.gamma >= 0.0)) return bad("kT and gamma must be >= 0");
+  if (!(p.rattle_tol > 0.0)) return bad("rattle_tol must be > 0");
+  if (p.max_newton < 0 || p.max_newton > 10000) return bad("max_newton out of range");
+  if (p.precision != MD_PREC_FP64 && p.precision != MD_PREC_MIXED) return bad("unknown precision");
+  if (p.ntypes < 1 || p.ntypes > MD_MAX_TYPES) return bad("ntypes must be in 1..8");
+  for (int a = 0; a < p.ntypes; ++a)
+    if (!(p.mass[a] > 0.0)) return bad("masses must be > 0");
+  if (!symmetric_ok(p.eps, p.ntypes) || !symmetric_ok(p.sigma, p.ntypes) || !symmetric_ok(p.rcut, p.ntypes))
+    return bad("eps, sigma and rcut must be symmetric, finite and >= 0");
+  for (int a = 0; a < p.ntypes; ++a)
+    for (int b = 0; b < p.ntypes; ++b)
+      if (p.rcut[a][b] > 0.0 && !(p.sigma[a][b] > 0.0)) return bad("sigma must be > 0 where rcut > 0");
+  if (s.kind < MD_SURF_NONE || s.kind > MD_SURF_CYLINDER) return bad("unknown surface kind");
+  if (s.reserved != 0 || p.reserved != 0) return bad("reserved fields must be 0");
+  for (int d = 0; d < 3; ++d)
+    if (p.periodic[d] && !(p.box_hi[d] > p.box_lo[d])) return bad("a periodic axis needs box_hi > box_lo");
+  if (p.beads_per_mol > 1 && !(p.bond_k >= 0.0 && p.bond_r0 >= 0.0)) return bad("bond_k, bond_r0 >= 0");
+  if (p.wall_enable && !(p.wall_hi_z > p.wall_lo_z && p.wall_sigma > 0.0 && p.wall_eps >= 0.0))
+    return bad("wall needs wall_hi_z > wall_lo_z and wall_sigma > 0");
+  std::memset(&S, 0, sizeof(S));
+  S.kind = s.kind;
+  for (int d = 0; d < 3; ++d) S.c[d] = s.center[d];
+  for (int d = 0; d < 4; ++d) S.p[d] = s.p[d];
+  switch (s.kind) {
+    case MD_SURF_PLANE:
+      if (!(s.p[0] * s.p[0] + s.p[1] * s.p[1] + s.p[2] * s.p[2] > 0.0)) return bad("plane normal is zero");
+      break;
+    case MD_SURF_SPHERE:
+      if (!(s.p[0] > 0.0)) return bad("sphere radius must be > 0");
+      break;
+    case MD_SURF_ELLIPSOID:
+      for (int d = 0; d < 3; ++d) {
+        if (!(s.p[d] > 0.0)) return bad("ellipsoid semi-axes must be > 0");
+        S.inv_a2[d] = 1.0 / (s.p[d] * s.p[d]);
+      }
+      break;
+    case MD_SURF_TORUS:
+      if (!(s.p[0] > s.p[1] && s.p[1] > 0.0)) return bad("torus needs R > r > 0");
+      break;
+    case MD_SURF_GAUSSIAN_BUMP:
+      if (!(s.p[1] > 0.0)) return bad("bump width must be > 0");
+      if (!p.periodic[0] || !p.periodic[1]) return bad("the bump needs periodic x and y");
+      break;
+    case MD_SURF_CYLINDER:
+      if (!(s.p[0] > 0.0)) return bad("cylinder radius must be > 0");
+      if (!(s.p[1] == 0.0 || s.p[1] == 1.0 || s.p[1] == 2.0)) return bad("cylinder axis must be 0, 1 or 2");
+      S.axis = (int)s.p[1];
+      break;
+    default:
+      break;
+  }
+  S.dt = p.dt;
+  S.half_dt = 0.5 * p.dt;
+  S.kT = p.kT;
+  S.gamma = p.gamma;
+  S.comb = 1.0 / (1.0 + 0.5 * p.gamma * p.dt);
+  S.noise_unit = std::sqrt(2.0 * p.kT * p.gamma / p.dt);
+  S.tol = p.rattle_tol;
+  S.max_newton = p.max_newton;
+  S.frozen = p.frozen_normal ? 1 : 0;
+  for (int d = 0; d < 3; ++d) {
+    S.box_lo[d] = p.box_lo[d];
+    S.box_len[d] = p.box_hi[d] - p.box_lo[d];
+    S.periodic[d] = p.periodic[d] ? 1 : 0;
+  }
+  S.bpm = p.beads_per_mol;
+  S.excl = p.exclude_intramol ? 1 : 0;
+  S.bond_k = p.bond_k;
+  S.bond_r0 = p.bond_r0;
+  S.wall = p.wall_enable ? 1 : 0;
+  S.wall_lo = p.wall_lo_z;
+  S.wall_hi = p.wall_hi_z;
+  S.wall_eps = p.wall_eps;
+  S.wall_sigma = p.wall_sigma;
+  S.wall_rc = std::pow(2.0, 1.0 / 6.0) * p.wall_sigma;
+  S.seed_lo = (uint32_t)(p.seed & 0xffffffffu);
+  S.replica = p.replica;
+  return MD_OK;
+}
+
+// Extent of the surface along axis d: returns false if unbounded.
+bool surface_extent(const md_surface& s, int d, double& lo, double& hi) {
+  const double c = s.center[d];
+  switch (s.kind) {
+    case MD_SURF_SPHERE: lo = c - s.p[0]; hi = c + s.p[0]; return true;
+    case MD_SURF_ELLIPSOID: lo = c - s.p[d]; hi = c + s.p[d]; return true;
+    case MD_SURF_TORUS: {
+      const double e = (d < 2) ? s.p[0] + s.p[1] : s.p[1];
+      lo = c - e; hi = c + e;
+      return true;
+    }
+    case MD_SURF_CYLINDER:
+      if (d == (int)s.p[1]) return false;
+      lo = c - s.p[0]; hi = c + s.p[0];
+      return true;
+    case MD_SURF_GAUSSIAN_BUMP:
+      if (d < 2) return false;
+      lo = c + std::min(0.0, s.p[0]); hi = c + std::max(0.0, s.p[0]);
+      return true;
+    case MD_SURF_PLANE: {
+      const int o1 = (d + 1) % 3, o2 = (d + 2) % 3;
+      if (s.p[o1] == 0.0 && s.p[o2] == 0.0) {
+        lo = hi = c;
+        return true;
+      }
+      return false;
+    }
+    default:
+      return false;
+  }
+}
+
+void fill_types(const md_params& p, TypeTable& T) {
+  std::memset(&T, 0, sizeof(T));
+  for (int a = 0; a < kMaxTypes; ++a) {
+    const double m = a < p.ntypes ? p.mass[a] : 1.0;
+    T.mass[a] = m;
+    T.inv_mass[a] = 1.0 / m;
+    T.sqrt_mass[a] = std::sqrt(m);
+    for (int b = 0; b < kMaxTypes; ++b) {
+      if (a >= p.ntypes || b >= p.ntypes) continue;
+      const double rc = p.rcut[a][b], sg = p.sigma[a][b], ep = p.eps[a][b];
+      T.eps[a][b] = ep;
+      T.sig2[a][b] = sg * sg;
+      T.rc2[a][b] = rc * rc;
+      double shift = 0.0;
+      if (rc > 0.0) {
+        const double s6 = std::pow(sg / rc, 6.0);
+        shift = 4.0 * ep * (s6 * s6 - s6);
+      }
+      T.shift[a][b] = shift;
+      T.eps_f[a][b] = (float)ep;
+      T.sig2_f[a][b] = (float)(sg * sg);
+      T.rc2_f[a][b] = (float)(rc * rc);
+      T.shift_f[a][b] = (float)shift;
+    }
+  }
+}
+
+bool same_interactions(const md_params& a, const md_params& b) {
+  if (a.precision != b.precision || a.ntypes != b.ntypes || a.cell_size != b.cell_size) return false;
+  for (int i = 0; i < a.ntypes; ++i) {
+    if (a.mass[i] != b.mass[i]) return false;
+    for (int j = 0; j < a.ntypes; ++j)
+      if (a.eps[i][j] != b.eps[i][j] || a.sigma[i][j] != b.sigma[i][j] || a.rcut[i][j] != b.rcut[i][j])
+        return false;
+  }
+  return true;
+}
+
+int check_device_status(md_handle* h) {
+  CK(h, cudaMemcpyAsync(h->h_status, h->A.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream()));
+  CK(h, cudaStreamSynchronize(h->stream()));
+  const uint32_t st = *h->h_status;
+  if (st == 0) return MD_OK;
+  CK(h, cudaMemsetAsync(h->A.status, 0, sizeof(uint32_t), h->stream()));
+  CK(h, cudaStreamSynchronize(h->stream()));
+  if (st & kFlagRattle) return fail(h, MD_ERR_RATTLE_DIVERGED, "RATTLE Newton iteration missed the tolerance");
+  if (st & kFlagNonfinite) return fail(h, MD_ERR_NONFINITE, "non-finite position or momentum");
+  if (st & kFlagOutOfGrid) return fail(h, MD_ERR_OUT_OF_GRID, "a particle left its cell grid or crossed a wall");
+  if (st & kFlagTimeout) return fail(h, MD_ERR_TIMEOUT, "a bounded device wait ran out");
+  if (st & kFlagOffSurface)
+    return fail(h, MD_ERR_INVALID_ARG, "a constrained particle is off its surface, or bad input values");
+  return MD_OK;
+}
+
+// Cell list of the current positions (no step advance).
+int rebuild_cells(md_handle* h) {
+  if (!h->has_pairs) return MD_OK;
+  CK(h, launch_bin(h->A, h->stream()));
+  CK(h, launch_cells_after_bin(h->A, 0, h->stream()));
+  CK(h, launch_bucket_build(h->A, h->precision, h->stream()));
+  return MD_OK;
+}
+
+// The kernels of one time step, in launch order.
+struct StepKernel {
+  const char* name;
+  cudaError_t (*fn)(md_handle*, cudaStream_t);
+};
+
+cudaError_t k_pair_step(md_handle* h, cudaStream_t st) {
+  return launch_pair(h->A, h->precision, h->has_pairs, h->bonds, h->walls, h->excl, st);
+}
+cudaError_t k_integrate_step(md_handle* h, cudaStream_t st) {
+  return launch_integrate(h->A, h->precision, h->has_pairs, st);
+}
+cudaError_t k_reduce_step(md_handle* h, cudaStream_t st) { return launch_scan_reduce(h->A, st); }
+cudaError_t k_blocks_step(md_handle* h, cudaStream_t st) { return launch_scan_blocks(h->A, 1, st); }
+cudaError_t k_apply_step(md_handle* h, cudaStream_t st) { return launch_scan_apply(h->A, st); }
+cudaError_t k_scatter_step(md_handle* h, cudaStream_t st) { return launch_scatter(h->A, st); }
+cudaError_t k_bucket_step(md_handle* h, cudaStream_t st) {
+  return launch_bucket_build(h->A, h->precision, st);
+}
+cudaError_t k_advance_step(md_handle* h, cudaStream_t st) { return launch_advance(h->A, st); }
+
+const StepKernel kStepWithCells[] = {{"pair", k_pair_step},          {"integrate", k_integrate_step},
+                                     {"scan_reduce", k_reduce_step}, {"scan_blocks", k_blocks_step},
+                                     {"scan_apply", k_apply_step},   {"scatter", k_scatter_step},
+                                     {"bucket_build", k_bucket_step}};
+const StepKernel kStepNoCells[] = {{"pair", k_pair_step}, {"integrate", k_integrate_step},
+                                   {"advance", k_advance_step}};
+
+int step_kernels(const md_handle* h, const StepKernel** list) {
+  if (h->has_pairs) {
+    *list = kStepWithCells;
+    return 7;
+  }
+  *list = kStepNoCells;
+  return 3;
+}
+
+// One time step, enqueued on stream st.
+cudaError_t enqueue_step(md_handle* h, cudaStream_t st) {
+  const StepKernel* ks;
+  const int nk = step_kernels(h, &ks);
+  for (int i = 0; i < nk; ++i) {
+    cudaError_t e = ks[i].fn(h, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int build_graph(md_handle* h) {
+  if (h->graph) return MD_OK;
+  cudaGraph_t g = nullptr;
+  CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = enqueue_step(h, h->cap_stream);
+  cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+  if (e != cudaSuccess) return cuda_fail(h, e, "capture of one step");
+  if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+  return MD_OK;
+}
+
+int forces_now(md_handle* h) {
+  CK(h, launch_pair(h->A, h->precision, h->has_pairs, h->bonds, h->walls, h->excl, h->stream()));
+  return MD_OK;
+}
+
+int momenta_now(md_handle* h) {
+  int rc = forces_now(h);
+  if (rc) return rc;
+  CK(h, launch_finish(h->A, h->precision, h->stream()));
+  return MD_OK;
+}
+
+int require_state(md_handle* h) {
+  if (!h) return MD_ERR_INVALID_ARG;
+  if (!h->state_set) return fail(h, MD_ERR_INVALID_ARG, "no state: call md_set_state first");
+  if (cudaSetDevice(h->dev) != cudaSuccess) return fail(h, MD_ERR_CUDA, "cudaSetDevice failed");
+  return MD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int md_version(void) { return (1 << 16) | 0; }
+
+int md_create(const md_surface* surf, const md_params* prm, int64_t n, md_handle** out) {
+  if (!surf || !prm) return fail(nullptr, MD_ERR_INVALID_ARG, "surf and prm must not be NULL");
+  return md_create_batch(1, surf, prm, &n, out);
+}
+
+int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms, const int64_t* n_per_sys,
+                    md_handle** out) {
+  if (!out) return fail(nullptr, MD_ERR_INVALID_ARG, "out must not be NULL");
+  *out = nullptr;
+  if (nsys < 1 || !surfs || !prms || !n_per_sys) return fail(nullptr, MD_ERR_INVALID_ARG, "bad batch arguments");
+  if (nsys > (1 << 27)) return fail(nullptr, MD_ERR_INVALID_ARG, "too many systems");
+  md_handle* h = new md_handle();
+  std::string why;
+  int64_t total = 0;
+  h->sys.resize(nsys);
+  h->first.resize(nsys);
+  for (int s = 0; s < nsys; ++s) {
+    if (n_per_sys[s] < 0) {
+      delete h;
+      return fail(nullptr, MD_ERR_INVALID_ARG, "n must be >= 0");
+    }
+    if (check_system(surfs[s], prms[s], h->sys[s], why) != MD_OK) {
+      delete h;
+      return fail(nullptr, MD_ERR_INVALID_ARG, "system " + std::to_string(s) + ": " + why);
+    }
+    if (!same_interactions(prms[0], prms[s])) {
+      delete h;
+      return fail(nullptr, MD_ERR_INVALID_ARG,
+                  "systems of a batch must share precision, ntypes, mass, eps, sigma, rcut, cell_size");
+    }
+    h->first[s] = total;
+    h->sys[s].first = total;
+    h->sys[s].n = n_per_sys[s];
+    total += n_per_sys[s];
+  }
+  if (total >= (int64_t(1) << 31)) {
+    delete h;
+    return fail(nullptr, MD_ERR_INVALID_ARG, "at most 2^31 - 1 particles");
+  }
+  const md_params& P0 = prms[0];
+  h->n = total;
+  h->nsys = nsys;
+  h->precision = P0.precision;
+  fill_types(P0, h->types);
+  double rcmax = 0.0;
+  for (int a = 0; a < P0.ntypes; ++a)
+    for (int b = 0; b < P0.ntypes; ++b) rcmax = std::max(rcmax, P0.rcut[a][b]);
+  h->has_pairs = rcmax > 0.0;
+  for (int s = 0; s < nsys; ++s) {
+    if (prms[s].beads_per_mol > 1) h->bonds = 1;
+    if (prms[s].wall_enable) h->walls = 1;
+    if (prms[s].exclude_intramol) h->excl = 1;
+  }
+  // cell grids
+  const double rc_eff = std::max(rcmax, P0.cell_size) * (1.0 + 1.0 / 4096.0);
+  uint64_t cell_total = 0;
+  for (int s = 0; s < nsys; ++s) {
+    SysDev& S = h->sys[s];
+    const md_params& p = prms[s];
+    for (int d = 0; d < 3; ++d) {
+      if (!h->has_pairs) {
+        S.nc[d] = 1;
+        S.cs[d] = 1.0;
+        S.grid_lo[d] = 0.0;
+      } else if (p.periodic[d]) {
+        const double L = p.box_hi[d] - p.box_lo[d];
+        const int nc = (int)std::floor(L / rc_eff);
+        if (nc < 3) {
+          delete h;
+          return fail(nullptr, MD_ERR_INVALID_ARG, "a periodic axis must be at least 3 cells long");
+        }
+        S.nc[d] = nc;
+        S.cs[d] = L / nc;
+        S.grid_lo[d] = p.box_lo[d];
+      } else {
+        double lo, hi;
+        if (p.box_hi[d] > p.box_lo[d]) {
+          lo = p.box_lo[d];
+          hi = p.box_hi[d];
+        } else if (surface_extent(surfs[s], d, lo, hi)) {
+          lo -= 2.0 * rc_eff;
+          hi += 2.0 * rc_eff;
+        } else {
+          delete h;
+          return fail(nullptr, MD_ERR_INVALID_ARG,
+                      "system " + std::to_string(s) + ": give box_lo/box_hi for an axis the surface does not bound");
+        }
+        const double span = hi - lo;
+        const double ncd = std::ceil(span / rc_eff);
+        if (ncd > 1e6) {
+          delete h;
+          return fail(nullptr, MD_ERR_INVALID_ARG, "cell grid too large along one axis");
+        }
+        S.nc[d] = std::max(1, (int)ncd);
+        S.cs[d] = rc_eff;
+        S.grid_lo[d] = lo;
+      }
+      S.inv_cs[d] = 1.0 / S.cs[d];
+      S.cs_f[d] = (float)S.cs[d];
+    }
+    S.cell_base = (uint32_t)cell_total;
+    cell_total += (uint64_t)S.nc[0] * (uint64_t)S.nc[1] * (uint64_t)S.nc[2];
+    if (cell_total >= 0xFFFFFFF0ull) {
+      delete h;
+      return fail(nullptr, MD_ERR_INVALID_ARG, "more than 2^32 cells in the batch");
+    }
+  }
+  // buckets: the cell id itself when the grid is small, else a hash table of 2^k >= 4n buckets
+  uint64_t t_hash = 16;
+  int log_t = 4;
+  while (t_hash < (uint64_t)std::max<int64_t>(4 * total, 16) && log_t < 30) {
+    t_hash <<= 1;
+    ++log_t;
+  }
+  DevArrays& A = h->A;
+  A.n = total;
+  A.nsys = nsys;
+  if (h->has_pairs && cell_total <= t_hash) {
+    A.hashed = 0;
+    A.nbucket = (uint32_t)cell_total;
+    A.log_t = 0;
+  } else {
+    A.hashed = 1;
+    A.nbucket = (uint32_t)t_hash;
+    A.log_t = log_t;
+  }
+  if (!h->has_pairs) A.nbucket = 1;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    delete h;
+    return fail(nullptr, MD_ERR_NO_DEVICE, "no CUDA device is visible");
+  }
+  cudaGetDevice(&h->dev);
+  const size_t n = (size_t)total;
+  const int nblk = (int)((A.nbucket + kScanPerBlock - 1) / kScanPerBlock);
+  cudaError_t e = cudaSuccess;
+  auto al = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  al(dalloc(h, &A.x, 3 * n));
+  al(dalloc(h, &A.ph, 3 * n));
+  al(dalloc(h, &A.pk, 3 * n));
+  al(dalloc(h, &A.xref, 3 * n));
+  {
+    void* f = nullptr;
+    al(h->precision == MD_PREC_FP64 ? dalloc(h, reinterpret_cast<double4_32a**>(&f), n)
+                                    : dalloc(h, reinterpret_cast<float4**>(&f), n));
+    A.f = f;
+    void* r = nullptr;
+    al(h->precision == MD_PREC_FP64 ? dalloc(h, reinterpret_cast<double4_32a**>(&r), n)
+                                    : dalloc(h, reinterpret_cast<float4**>(&r), n));
+    A.rec = r;
+  }
+  al(dalloc(h, &A.meta, n));
+  if (h->excl) al(dalloc(h, &A.mol, n));
+  al(dalloc(h, &A.cell, n));
+  al(dalloc(h, &A.rank, n));
+  al(dalloc(h, &A.count, A.nbucket));
+  al(dalloc(h, &A.start, (size_t)A.nbucket + 1));
+  al(dalloc(h, &A.blocksum, (size_t)nblk));
+  al(dalloc(h, &A.stag, n));
+  al(dalloc(h, &A.scell, n));
+  SysDev* d_sys = nullptr;
+  al(dalloc(h, &d_sys, (size_t)nsys));
+  A.sys = d_sys;
+  TypeTable* d_types = nullptr;
+  al(dalloc(h, &d_types, 1));
+  A.types = d_types;
+  al(dalloc(h, &A.status, 1));
+  al(dalloc(h, &A.step, 1));
+  al(dalloc(h, &A.mode, 1));
+  al(dalloc(h, &h->d_first, (size_t)nsys));
+  al(dalloc(h, &h->d_stage, 9 * n));
+  al(dalloc(h, &h->d_stage_i, 2 * n));
+  al(dalloc(h, &h->d_stage_u8, n));
+  al(dalloc(h, &h->d_resid, 3));
+  al(dalloc(h, &h->d_obs, 8 * (size_t)nsys));
+  if (e == cudaSuccess) e = cudaMallocHost(&h->h_status, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMallocHost(&h->h_resid, 3 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemcpy(d_sys, h->sys.data(), sizeof(SysDev) * nsys, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_types, &h->types, sizeof(TypeTable), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->d_first, h->first.data(), sizeof(int64_t) * nsys, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(A.count, 0, sizeof(uint32_t) * std::max<size_t>(A.nbucket, 1));
+  if (e == cudaSuccess) e = cudaMemset(A.status, 0, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(A.step, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(A.mode, 0, sizeof(int32_t));
+  if (e == cudaSuccess) {
+    const uint32_t nn = (uint32_t)total;
+    e = cudaMemcpy(A.start + A.nbucket, &nn, sizeof(uint32_t), cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    std::string m = std::string("allocation / upload failed: ") + cudaGetErrorString(e);
+    md_destroy(h);
+    return fail(nullptr, MD_ERR_CUDA, m);
+  }
+  h->kernels_per_step = h->has_pairs ? 7 : 3;
+  *out = h;
+  return MD_OK;
+}
+
+int md_set_stream(md_handle* h, void* cuda_stream) {
+  if (!h) return MD_ERR_INVALID_ARG;
+  h->user_stream = static_cast<cudaStream_t>(cuda_stream);
+  return MD_OK;
+}
+
+static int set_state_common(md_handle* h, const double* d_x, const double* d_v, const int32_t* d_type,
+                            const int32_t* d_mol, const uint8_t* d_con, uint64_t step0) {
+  cudaStream_t st = h->stream();
+  CK(h, launch_build_meta(h->A, h->d_first, h->nsys, d_type, d_con, d_mol, 0, st));
+  CK(h, launch_set_state(h->A, d_x, d_v, st));
+  const unsigned long long k = step0;
+  CK(h, cudaMemcpyAsync(h->A.step, &k, sizeof(k), cudaMemcpyHostToDevice, st));
+  CK(h, cudaMemsetAsync(h->A.mode, 0, sizeof(int32_t), st));
+  int rc = rebuild_cells(h);
+  if (rc) return rc;
+  h->state_set = true;
+  rc = check_device_status(h);
+  if (rc != MD_OK) h->state_set = false;
+  return rc;
+}
+
+int md_set_state(md_handle* h, const double* x, const double* v, const int32_t* type, const int32_t* mol,
+                 const uint8_t* constrained, uint64_t step0) {
+  if (!h) return MD_ERR_INVALID_ARG;
+  if (h->n > 0 && !x) return fail(h, MD_ERR_INVALID_ARG, "x must not be NULL");
+  CK(h, cudaSetDevice(h->dev));
+  const size_t n = (size_t)h->n;
+  cudaStream_t st = h->stream();
+  if (n > 0) {
+    CK(h, cudaMemcpyAsync(h->d_stage, x, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (v) CK(h, cudaMemcpyAsync(h->d_stage + 3 * n, v, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (type) CK(h, cudaMemcpyAsync(h->d_stage_i, type, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (mol) CK(h, cudaMemcpyAsync(h->d_stage_i + n, mol, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (constrained) CK(h, cudaMemcpyAsync(h->d_stage_u8, constrained, n, cudaMemcpyHostToDevice, st));
+  }
+  return set_state_common(h, h->d_stage, v ? h->d_stage + 3 * n : nullptr, type ? h->d_stage_i : nullptr,
+                          mol ? h->d_stage_i + n : nullptr, constrained ? h->d_stage_u8 : nullptr, step0);
+}
+
+int md_set_state_device(md_handle* h, const double* d_x, const double* d_v, const int32_t* d_type,
+                        const int32_t* d_mol, const uint8_t* d_con, uint64_t step0) {
+  if (!h) return MD_ERR_INVALID_ARG;
+  if (h->n > 0 && !d_x) return fail(h, MD_ERR_INVALID_ARG, "d_x must not be NULL");
+  CK(h, cudaSetDevice(h->dev));
+  return set_state_common(h, d_x, d_v, d_type, d_mol, d_con, step0);
+}
+
+int md_restore(md_handle* h, const double* x, const double* p_half, uint64_t step) {
+  int rc = require_state(h);
+  if (rc) return rc;
+  if (h->n > 0 && (!x || !p_half)) return fail(h, MD_ERR_INVALID_ARG, "x and p_half must not be NULL");
+  const size_t n = (size_t)h->n;
+  cudaStream_t st = h->stream();
+  if (n > 0) {
+    CK(h, cudaMemcpyAsync(h->d_stage, x, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(h, cudaMemcpyAsync(h->d_stage + 3 * n, p_half, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  CK(h, launch_restore(h->A, h->d_stage, h->d_stage + 3 * n, st));
+  const unsigned long long k = step;
+  const int32_t one = 1;
+  CK(h, cudaMemcpyAsync(h->A.step, &k, sizeof(k), cudaMemcpyHostToDevice, st));
+  CK(h, cudaMemcpyAsync(h->A.mode, &one, sizeof(one), cudaMemcpyHostToDevice, st));
+  rc = rebuild_cells(h);
+  if (rc) return rc;
+  return check_device_status(h);
+}
+
+int md_step(md_handle* h, int64_t nsteps) {
+  int rc = require_state(h);
+  if (rc) return rc;
+  if (nsteps < 0) return fail(h, MD_ERR_INVALID_ARG, "nsteps must be >= 0");
+  h->last_launches = 0;
+  if (nsteps == 0) return MD_OK;
+  rc = build_graph(h);
+  if (rc) return rc;
+  for (int64_t s = 0; s < nsteps; ++s) CK(h, cudaGraphLaunch(h->graph, h->stream()));
+  h->last_launches = nsteps * h->kernels_per_step;
+  return MD_OK;
+}
+
+int md_profile_step(md_handle* h, int64_t nsteps, double* kernel_ms, int32_t max_kernels,
+                    int32_t* n_kernels) {
+  int rc = require_state(h);
+  if (rc) return rc;
+  if (nsteps < 1 || !kernel_ms || max_kernels < 1) return fail(h, MD_ERR_INVALID_ARG, "bad profile arguments");
+  const StepKernel* ks;
+  const int nk = step_kernels(h, &ks);
+  std::vector<cudaEvent_t> ev((size_t)nk + 1);
+  for (auto& e : ev) CK(h, cudaEventCreate(&e));
+  std::vector<double> acc((size_t)nk, 0.0);
+  cudaStream_t st = h->stream();
+  int status = MD_OK;
+  for (int64_t s = 0; s < nsteps && status == MD_OK; ++s) {
+    for (int i = 0; i < nk; ++i) {
+      cudaError_t e = cudaEventRecord(ev[i], st);
+      if (e == cudaSuccess) e = ks[i].fn(h, st);
+      if (e != cudaSuccess) {
+        status = cuda_fail(h, e, ks[i].name);
+        break;
+      }
+    }
+    if (status != MD_OK) break;
+    cudaError_t e = cudaEventRecord(ev[nk], st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[nk]);
+    if (e != cudaSuccess) {
+      status = cuda_fail(h, e, "profile event");
+      break;
+    }
+    for (int i = 0; i < nk; ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+      acc[i] += ms;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (status != MD_OK) return status;
+  const int m = std::min<int>(nk, max_kernels);
+  for (int i = 0; i < m; ++i) kernel_ms[i] = acc[i] / (double)nsteps;
+  if (n_kernels) *n_kernels = nk;
+  h->last_launches = nsteps * nk;
+  return check_device_status(h);
+}
+
+const char* md_profile_kernel_name(md_handle* h, int32_t i) {
+  if (!h) return "";
+  const StepKernel* ks;
+  const int nk = step_kernels(h, &ks);
+  return (i >= 0 && i < nk) ? ks[i].name : "";
+}
+
+int md_sync(md_handle* h) {
+  if (!h) return MD_ERR_INVALID_ARG;
+  CK(h, cudaSetDevice(h->dev));
+  return check_device_status(h);
+}
+
+int md_status(md_handle* h, uint32_t* flags) {
+  if (!h || !flags) return MD_ERR_INVALID_ARG;
+  CK(h, cudaSetDevice(h->dev));
+  CK(h, cudaMemcpyAsync(h->h_status, h->A.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream()));
+  CK(h, cudaStreamSynchronize(h->stream()));
+  *flags = *h->h_status & 0xffu;
+  CK(h, cudaMemsetAsync(h->A.status, 0, sizeof(uint32_t), h->stream()));
+  CK(h, cudaStreamSynchronize(h->stream()));
+  return MD_OK;
+}
+
+int md_get_state_device(md_handle* h, double* d_x, double* d_v, double* d_p_half) {
+  int rc = require_state(h);
+  if (rc) return rc;
+  if (d_v) {
+    rc = momenta_now(h);
+    if (rc) return rc;
+  }
+  CK(h, launch_get_state(h->A, d_x, d_v, d_p_half, h->stream()));
+  return check_device_status(h);
+}
+
+int md_get_state(md_handle* h, double* x, double* v, double* p_half, uint64_t* step) {
+  int rc = require_state(h);
+  if (rc) return rc;
+  const size_t n = (size_t)h->n;
+  cudaStream_t st = h->stream();
+  double* sx = h->d_stage;
+  double* sv = h->d_stage + 3 * n;
+  double* sp = h->d_stage + 6 * n;
+  if (v) {
+    rc = momenta_now(h);
+    if (rc) return rc;
+  }
+  CK(h, launch_get_state(h->A, x ? sx : nullptr, v ? sv : nullptr, p_half ? sp : nullptr, st));
+  if (x && n) CK(h, cudaMemcpyAsync(x, sx, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (v && n) CK(h, cudaMemcpyAsync(v, sv, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (p_half && n) CK(h, cudaMemcpyAsync(p_half, sp, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  unsigned long long k = 0;
+  CK(h, cudaMemcpyAsync(&k, h->A.step, sizeof(k), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  if (step) *step = k;
+  return check_device_status(h);
+}
+
+int md_forces(md_handle* h, double* f_out, double* u_out) {
+  int rc = require_state(h);
+  if (rc) return rc;
+  const size_t n = (size_t)h->n;
+  cudaStream_t st = h->stream();
+  rc = forces_now(h);
+  if (rc) return rc;
+  CK(h, launch_get_forces(h->A, h->precision, h->d_stage, h->d_stage + 3 * n, st));
+  if (f_out && n) CK(h, cudaMemcpyAsync(f_out, h->d_stage, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (u_out && n) CK(h, cudaMemcpyAsync(u_out, h->d_stage + 3 * n, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  return check_device_status(h);
+}
+
+int md_constraint_residual(md_handle* h, double* max_g_over_gradg, double* max_abs_g, double* max_n_dot_v) {
+  int rc = require_state(h);
+  if (rc) return rc;
+  rc = momenta_now(h);
+  if (rc) return rc;
+  cudaStream_t st = h->stream();
+  CK(h, launch_residual(h->A, h->d_resid, st));
+  CK(h, cudaMemcpyAsync(h->h_resid, h->d_resid, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  double r[3];
+  std::memcpy(r, h->h_resid, sizeof(r));
+  if (max_g_over_gradg) *max_g_over_gradg = r[0];
+  if (max_abs_g) *max_abs_g = r[1];
+  if (max_n_dot_v) *max_n_dot_v = r[2];
+  return check_device_status(h);
+}
+
+int md_observables(md_handle* h, md_obs* out, int32_t max_systems, int32_t* n_written) {
+  int rc = require_state(h);
+  if (rc) return rc;
+  if (!out || max_systems < 0) return fail(h, MD_ERR_INVALID_ARG, "out must not be NULL");
+  rc = momenta_now(h);
+  if (rc) return rc;
+  cudaStream_t st = h->stream();
+  CK(h, launch_observables(h->A, h->precision, h->d_obs, st));
+  std::vector<double> o(8 * (size_t)h->nsys);
+  unsigned long long k = 0;
+  CK(h, cudaMemcpyAsync(o.data(), h->d_obs, o.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaMemcpyAsync(&k, h->A.step, sizeof(k), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  const int m = std::min<int>(max_systems, h->nsys);
+  for (int s = 0; s < m; ++s) {
+    const double* q = &o[8 * (size_t)s];
+    md_obs& r = out[s];
+    r.step = k;
+    r.n = (int64_t)q[7];
+    r.ndof = (int64_t)q[4];
+    r.kinetic = q[0];
+    r.potential = q[1];
+    r.kT = q[4] > 0 ? 2.0 * q[0] / q[4] : 0.0;
+    r.max_g_over_gradg = q[5];
+    r.max_n_dot_v = q[6];
+    r.msd = q[7] > 0 ? q[2] / q[7] : 0.0;
+    r.r0_dot_rt = (h->sys[s].kind == MD_SURF_SPHERE && q[7] > 0) ? q[3] / q[7] : 0.0;
+  }
+  if (n_written) *n_written = m;
+  return check_device_status(h);
+}
+
+int md_info(md_handle* h, int64_t* n, int32_t* nsys, uint64_t* step) {
+  if (!h) return MD_ERR_INVALID_ARG;
+  if (n) *n = h->n;
+  if (nsys) *nsys = h->nsys;
+  if (step) {
+    CK(h, cudaSetDevice(h->dev));
+    unsigned long long k = 0;
+    CK(h, cudaMemcpyAsync(&k, h->A.step, sizeof(k), cudaMemcpyDeviceToHost, h->stream()));
+    CK(h, cudaStreamSynchronize(h->stream()));
+    *step = k;
+  }
+  return MD_OK;
+}
+
+int md_last_launch_count(md_handle* h, int64_t* launches) {
+  if (!h || !launches) return MD_ERR_INVALID_ARG;
+  *launches = h->last_launches;
+  return MD_OK;
+}
+
+int md_grid_info(md_handle* h, int32_t sys, double lo[3], double cs[3], int32_t nc[3], uint32_t* base,
+                 int32_t* hashed) {
+  if (!h || sys < 0 || sys >= h->nsys) return MD_ERR_INVALID_ARG;
+  const SysDev& S = h->sys[sys];
+  for (int d = 0; d < 3; ++d) {
+    if (lo) lo[d] = S.grid_lo[d];
+    if (cs) cs[d] = S.cs[d];
+    if (nc) nc[d] = S.nc[d];
+  }
+  if (base) *base = S.cell_base;
+  if (hashed) *hashed = h->A.hashed ? h->A.log_t : 0;
+  return MD_OK;
+}
+
+int md_cell_list(md_handle* h, uint32_t* sorted_ids, uint32_t* sorted_cells, uint32_t* bucket_start,
+                 uint32_t* nbucket) {
+  int rc = require_state(h);
+  if (rc) return rc;
+  if (nbucket) *nbucket = h->has_pairs ? h->A.nbucket : 0;
+  if (!h->has_pairs) return MD_OK;
+  cudaStream_t st = h->stream();
+  const size_t n = (size_t)h->n;
+  if (sorted_ids && n) CK(h, cudaMemcpyAsync(sorted_ids, h->A.stag, n * 4, cudaMemcpyDeviceToHost, st));
+  if (sorted_cells && n) CK(h, cudaMemcpyAsync(sorted_cells, h->A.scell, n * 4, cudaMemcpyDeviceToHost, st));
+  if (bucket_start)
+    CK(h, cudaMemcpyAsync(bucket_start, h->A.start, ((size_t)h->A.nbucket + 1) * 4, cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  return check_device_status(h);
+}
+
+const char* md_last_error(md_handle* h) {
+  if (!h) return g_create_err.c_str();
+  return h->err.c_str();
+}
+
+void md_destroy(md_handle* h) {
+  if (!h) return;
+  cudaSetDevice(h->dev);
+  if (h->own_stream) cudaStreamSynchronize(h->own_stream);
+  if (h->user_stream) cudaStreamSynchronize(h->user_stream);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->h_status) cudaFreeHost(h->h_status);
+  if (h->h_resid) cudaFreeHost(h->h_resid);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,66 @@
+// engine.h -- host-side launchers of the surfmd kernels (kernels.cu) used by
+// the C ABI (capi.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "surfmd.cuh"
+
+namespace surfmd {
+
+constexpr int kScanPerBlock = 4096;  // bucket counters scanned by one CTA
+
+// Build the meta word of every particle (type, constrained bit, system id)
+// and the molecule ids. type/con/mol may be null (defaults of md_set_state).
+cudaError_t launch_build_meta(const DevArrays& A, const int64_t* d_first, int nsys,
+                              const int32_t* d_type, const uint8_t* d_con, const int32_t* d_mol,
+                              int has_mol_default, cudaStream_t st);
+
+// x, v ([n][3] device) -> SoA state; validate g, project v, p = m v.
+cudaError_t launch_set_state(const DevArrays& A, const double* d_x_aos, const double* d_v_aos,
+                             cudaStream_t st);
+
+// x, p_half ([n][3] device) -> SoA state (checkpoint restore).
+cudaError_t launch_restore(const DevArrays& A, const double* d_x_aos, const double* d_ph_aos,
+                           cudaStream_t st);
+
+// Cell list of the current positions: bin, scan, scatter, canonical sort.
+// `advance` = 1 also moves the step counter on by one (inside md_step).
+cudaError_t launch_bin(const DevArrays& A, cudaStream_t st);
+cudaError_t launch_bucket_build(const DevArrays& A, int precision, cudaStream_t st);
+cudaError_t launch_cells_after_bin(const DevArrays& A, int advance, cudaStream_t st);
+cudaError_t launch_scan_reduce(const DevArrays& A, cudaStream_t st);
+cudaError_t launch_scan_blocks(const DevArrays& A, int advance, cudaStream_t st);
+cudaError_t launch_scan_apply(const DevArrays& A, cudaStream_t st);
+cudaError_t launch_scatter(const DevArrays& A, cudaStream_t st);
+
+// Conservative forces at the current positions into A.f.
+cudaError_t launch_pair(const DevArrays& A, int precision, int has_pairs, int bonds, int walls,
+                        int excl, cudaStream_t st);
+
+// Combine + momentum half + position half (+ binning when has_pairs).
+cudaError_t launch_integrate(const DevArrays& A, int precision, int has_pairs, cudaStream_t st);
+
+// Step counter on by one, mode = 1 (used when there is no cell list).
+cudaError_t launch_advance(const DevArrays& A, cudaStream_t st);
+
+// p^k into A.pk from the state and A.f (momentum half only).
+cudaError_t launch_finish(const DevArrays& A, int precision, cudaStream_t st);
+
+// SoA -> [n][3] for x, v = p^k / m and p^{k-1/2}; outputs may be null.
+cudaError_t launch_get_state(const DevArrays& A, double* d_x_aos, double* d_v_aos, double* d_ph_aos,
+                             cudaStream_t st);
+
+// Forces A.f -> [n][3] float64 and per-particle energies.
+cudaError_t launch_get_forces(const DevArrays& A, int precision, double* d_f_aos, double* d_u,
+                              cudaStream_t st);
+
+// Residuals: out[0] = max |g|/|grad g|, out[1] = max |g|, out[2] = max |n.v|/|n|
+// (stored as the bit patterns of non-negative doubles; zeroed inside).
+cudaError_t launch_residual(const DevArrays& A, unsigned long long* d_out, cudaStream_t st);
+
+// Per-system sums: 8 doubles per system (K, U, msd, r0.rt/R^2, ndof, max g/|n|,
+// max |n.v|/|n|, n), zeroed inside.
+cudaError_t launch_observables(const DevArrays& A, int precision, double* d_obs, cudaStream_t st);
+
+}  // namespace surfmd

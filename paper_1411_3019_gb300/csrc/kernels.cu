@@ -1,0 +1,1015 @@
+// kernels.cu -- CUDA kernels of the constrained Langevin time step
+// (Paquay & Kusters, Algorithm 1 and Algorithm S1) for sm_103a.
+//
+// One step (md_step) is, in launch order:
+//   pair          f^k = -grad V(x^k): truncated-shifted LJ (Eq. S1) over the
+//                 27 neighbour cells, harmonic bonds and walls (SI S3.2)
+//   integrate     Algorithm S1 force combination with Philox noise, the
+//                 momentum half of step k and the position half of step k+1
+//                 (Algorithm 1), then the cell of x^{k+1} and its bucket rank
+//   scan x3       exclusive scan of the bucket counters
+//   scatter       particles to their bucket slots
+//   bucket build  canonical (particle-id) order inside each bucket and the
+//                 cell-relative records the pair kernel reads
+// The momentum half of step k and the position half of step k+1 share one
+// kernel: between steps the state is (x^k, p^{k-1/2}) and the combined force
+// never leaves registers; p^k is rebuilt on demand (launch_finish).
+#include <cfloat>
+#include <cmath>
+
+#include "engine.h"
+
+namespace surfmd {
+
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds, each two
+// 32x32 -> 64-bit products with the published multipliers; the key is bumped
+// by the published Weyl increments between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// Three normals of particle pid at step k: key (seed, replica), counter
+// (pid, k_lo, k_hi, 0); Box-Muller on words (0,1) -> x, y and (2,3) -> z
+// (cosine branch); u = ((w >> 9) + 1/2) 2^-23 is exact in float and double.
+__device__ __forceinline__ void gauss3(uint32_t seed, uint32_t rep, uint32_t pid, uint64_t k,
+                                       float& gx, float& gy, float& gz) {
+  const uint4 w = philox4x32_10(make_uint4(pid, (uint32_t)k, (uint32_t)(k >> 32), 0u),
+                                make_uint2(seed, rep));
+  const float s = 1.0f / 8388608.0f;
+  const float u0 = ((float)(w.x >> 9) + 0.5f) * s, u1 = ((float)(w.y >> 9) + 0.5f) * s;
+  const float u2 = ((float)(w.z >> 9) + 0.5f) * s, u3 = ((float)(w.w >> 9) + 0.5f) * s;
+  const float r01 = sqrtf(-2.0f * logf(u0));
+  const float r23 = sqrtf(-2.0f * logf(u2));
+  float sn, cs;
+  sincospif(2.0f * u1, &sn, &cs);
+  gx = r01 * cs;
+  gy = r01 * sn;
+  gz = r23 * cospif(2.0f * u3);
+}
+
+__device__ __forceinline__ void gauss3(uint32_t seed, uint32_t rep, uint32_t pid, uint64_t k,
+                                       double& gx, double& gy, double& gz) {
+  const uint4 w = philox4x32_10(make_uint4(pid, (uint32_t)k, (uint32_t)(k >> 32), 0u),
+                                make_uint2(seed, rep));
+  const double s = 1.0 / 8388608.0;
+  const double u0 = ((double)(w.x >> 9) + 0.5) * s, u1 = ((double)(w.y >> 9) + 0.5) * s;
+  const double u2 = ((double)(w.z >> 9) + 0.5) * s, u3 = ((double)(w.w >> 9) + 0.5) * s;
+  const double r01 = sqrt(-2.0 * log(u0));
+  const double r23 = sqrt(-2.0 * log(u2));
+  double sn, cs;
+  sincospi(2.0 * u1, &sn, &cs);
+  gx = r01 * cs;
+  gy = r01 * sn;
+  gz = r23 * cospi(2.0 * u3);
+}
+
+// ---------------------------------------------------------------------------
+// Surfaces: g(x) and n = grad g (unnormalised), float64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double wrap_min_image(double d, double L) { return d - L * rint(d / L); }
+
+__device__ __forceinline__ double surf_eval(const SysDev& S, double x, double y, double z,
+                                            double& nx, double& ny, double& nz) {
+  double dx = x - S.c[0], dy = y - S.c[1], dz = z - S.c[2];
+  switch (S.kind) {
+    case kPlane:
+      nx = S.p[0]; ny = S.p[1]; nz = S.p[2];
+      return fma(S.p[0], dx, fma(S.p[1], dy, S.p[2] * dz));
+    case kSphere:
+      nx = 2.0 * dx; ny = 2.0 * dy; nz = 2.0 * dz;
+      return fma(dx, dx, fma(dy, dy, fma(dz, dz, -S.p[0] * S.p[0])));
+    case kEllipsoid: {
+      const double ax = dx * S.inv_a2[0], ay = dy * S.inv_a2[1], az = dz * S.inv_a2[2];
+      nx = 2.0 * ax; ny = 2.0 * ay; nz = 2.0 * az;
+      return fma(ax, dx, fma(ay, dy, fma(az, dz, -1.0)));
+    }
+    case kTorus: {
+      const double rho = sqrt(fma(dx, dx, dy * dy));
+      const double t = rho - S.p[0];
+      const double q = 2.0 * t / rho;
+      nx = q * dx; ny = q * dy; nz = 2.0 * dz;
+      return fma(t, t, fma(dz, dz, -S.p[1] * S.p[1]));
+    }
+    case kBump: {
+      if (S.periodic[0]) dx = wrap_min_image(dx, S.box_len[0]);
+      if (S.periodic[1]) dy = wrap_min_image(dy, S.box_len[1]);
+      const double w2 = S.p[1] * S.p[1];
+      const double e = S.p[0] * exp(-fma(dx, dx, dy * dy) / (2.0 * w2));
+      nx = e * dx / w2; ny = e * dy / w2; nz = 1.0;
+      return dz - e;
+    }
+    case kCylinder: {
+      const int ax = S.axis;
+      if (ax == 0) dx = 0.0;
+      else if (ax == 1) dy = 0.0;
+      else dz = 0.0;
+      nx = 2.0 * dx; ny = 2.0 * dy; nz = 2.0 * dz;
+      return fma(dx, dx, fma(dy, dy, fma(dz, dz, -S.p[0] * S.p[0])));
+    }
+    default:
+      nx = ny = nz = 0.0;
+      return 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cell grid
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t bucket_of(uint32_t cell, int hashed, int log_t) {
+  if (!hashed) return cell;
+  const uint32_t h = ((cell >> 3) * 0x9E3779B1u) >> (35 - log_t);
+  return (h << 3) | (cell & 7u);
+}
+
+// Coordinate wrapped into the periodic box (unchanged on open axes). The
+// binning arithmetic is written with round-to-nearest intrinsics (no FMA
+// contraction) so that the cell of a particle is reproducible on the host.
+__device__ __forceinline__ double wrap_coord(const SysDev& S, int d, double v) {
+  if (!S.periodic[d]) return v;
+  const double L = S.box_len[d];
+  const double r = __dsub_rn(v, S.box_lo[d]);
+  return __dadd_rn(S.box_lo[d], __dsub_rn(r, __dmul_rn(L, floor(__ddiv_rn(r, L)))));
+}
+
+__device__ __forceinline__ int cell_coord(const SysDev& S, int d, double v, bool& out) {
+  const double t = __dmul_rn(__dsub_rn(v, S.grid_lo[d]), S.inv_cs[d]);
+  int c = (int)floor(t);
+  if (c < 0) {
+    if (!S.periodic[d]) out = true;
+    c = 0;
+  } else if (c >= S.nc[d]) {
+    if (!S.periodic[d] || c > S.nc[d]) out = true;
+    c = S.nc[d] - 1;
+  }
+  if (!(t == t)) {
+    out = true;
+    c = 0;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint32_t cell_of(const SysDev& S, double x, double y, double z,
+                                            bool& out) {
+  const int cx = cell_coord(S, 0, wrap_coord(S, 0, x), out);
+  const int cy = cell_coord(S, 1, wrap_coord(S, 1, y), out);
+  const int cz = cell_coord(S, 2, wrap_coord(S, 2, z), out);
+  return S.cell_base + (uint32_t)cx + (uint32_t)S.nc[0] * ((uint32_t)cy + (uint32_t)S.nc[1] * (uint32_t)cz);
+}
+
+__device__ __forceinline__ void cell_decode(const SysDev& S, uint32_t cell, int& cx, int& cy, int& cz) {
+  uint32_t r = cell - S.cell_base;
+  cx = (int)(r % (uint32_t)S.nc[0]);
+  r /= (uint32_t)S.nc[0];
+  cy = (int)(r % (uint32_t)S.nc[1]);
+  cz = (int)(r / (uint32_t)S.nc[1]);
+}
+
+__device__ __forceinline__ void flag(uint32_t* status, uint32_t bit) { atomicOr(status, bit); }
+
+__device__ __forceinline__ bool finite3(double a, double b, double c) {
+  return isfinite(a) && isfinite(b) && isfinite(c);
+}
+
+// ---------------------------------------------------------------------------
+// meta / set state / restore
+// ---------------------------------------------------------------------------
+__global__ void k_build_meta(DevArrays A, const int64_t* __restrict__ first, int nsys,
+                             const int32_t* __restrict__ type, const uint8_t* __restrict__ con,
+                             const int32_t* __restrict__ mol) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  int lo = 0, hi = nsys - 1;  // last system with first <= i
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  const SysDev& S = A.sys[lo];
+  int t = type ? type[i] : 0;
+  if (t < 0 || t >= kMaxTypes) {
+    flag(A.status, kFlagOffSurface);
+    t = 0;
+  }
+  const uint32_t c = con ? (con[i] ? 1u : 0u) : (S.kind != kNone ? 1u : 0u);
+  A.meta[i] = meta_pack((uint32_t)t, (S.kind != kNone) ? c : 0u, (uint32_t)lo);
+  if (A.mol) {
+    const int64_t pid = i - S.first;
+    A.mol[i] = mol ? mol[i] : (int32_t)(S.bpm > 1 ? pid / S.bpm : pid);
+  }
+}
+
+__global__ void k_set_state(DevArrays A, const double* __restrict__ xa, const double* __restrict__ va) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = A.n;
+  if (i >= n) return;
+  const uint32_t m = A.meta[i];
+  const SysDev& S = A.sys[meta_sys(m)];
+  const double x = xa[3 * i], y = xa[3 * i + 1], z = xa[3 * i + 2];
+  double vx = va ? va[3 * i] : 0.0, vy = va ? va[3 * i + 1] : 0.0, vz = va ? va[3 * i + 2] : 0.0;
+  if (!finite3(x, y, z) || !finite3(vx, vy, vz)) flag(A.status, kFlagOffSurface);
+  if (meta_con(m)) {
+    double nx, ny, nz;
+    const double g = surf_eval(S, x, y, z, nx, ny, nz);
+    const double n2 = nx * nx + ny * ny + nz * nz;
+    if (!(fabs(g) < 1e-6 * sqrt(n2))) flag(A.status, kFlagOffSurface);
+    const double s = (nx * vx + ny * vy + nz * vz) / n2;
+    vx -= s * nx; vy -= s * ny; vz -= s * nz;
+  }
+  const double mass = A.types->mass[meta_type(m)];
+  A.x[i] = x; A.x[n + i] = y; A.x[2 * n + i] = z;
+  A.xref[i] = x; A.xref[n + i] = y; A.xref[2 * n + i] = z;
+  A.ph[i] = mass * vx; A.ph[n + i] = mass * vy; A.ph[2 * n + i] = mass * vz;
+  A.pk[i] = mass * vx; A.pk[n + i] = mass * vy; A.pk[2 * n + i] = mass * vz;
+}
+
+__global__ void k_restore(DevArrays A, const double* __restrict__ xa, const double* __restrict__ pa) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = A.n;
+  if (i >= n) return;
+  for (int d = 0; d < 3; ++d) {
+    A.x[d * n + i] = xa[3 * i + d];
+    A.ph[d * n + i] = pa[3 * i + d];
+  }
+  if (!finite3(xa[3 * i], xa[3 * i + 1], xa[3 * i + 2])) flag(A.status, kFlagNonfinite);
+}
+
+// ---------------------------------------------------------------------------
+// cell list
+// ---------------------------------------------------------------------------
+__global__ void k_bin(DevArrays A) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = A.n;
+  if (i >= n) return;
+  const SysDev& S = A.sys[meta_sys(A.meta[i])];
+  bool out = false;
+  const uint32_t cell = cell_of(S, A.x[i], A.x[n + i], A.x[2 * n + i], out);
+  if (out) flag(A.status, kFlagOutOfGrid);
+  A.cell[i] = cell;
+  A.rank[i] = atomicAdd(&A.count[bucket_of(cell, A.hashed, A.log_t)], 1u);
+}
+
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = kScanPerBlock / kScanThreads;  // 8
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot,
+                                                         uint32_t& block_total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) warp_tot[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    uint32_t w = lane < nw ? warp_tot[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < nw) warp_tot[lane] = wi - w;
+    if (lane == nw - 1) warp_tot[32] = wi;
+  }
+  __syncthreads();
+  block_total = warp_tot[32];
+  return warp_tot[wid] + inc - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ count,
+                                                              uint32_t T, uint32_t* blocksum) {
+  __shared__ uint32_t red[kScanThreads / 32];
+  const uint32_t base = blockIdx.x * (uint32_t)kScanPerBlock + threadIdx.x * kScanItems;
+  uint32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j)
+    if (base + j < T) s += count[base + j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < kScanThreads / 32 ? red[threadIdx.x] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) blocksum[blockIdx.x] = s;
+  }
+}
+
+// One CTA: exclusive scan of the block sums in place; optionally advance the
+// step counter (it runs once per step, after the integrator).
+__global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* blocksum, int nblk,
+                                                      unsigned long long* step, int32_t* mode,
+                                                      int advance) {
+  __shared__ uint32_t warp_tot[33];
+  const int per = (nblk + 1023) / 1024;
+  const int b0 = threadIdx.x * per;
+  uint32_t local = 0;
+  for (int j = 0; j < per; ++j)
+    if (b0 + j < nblk) local += blocksum[b0 + j];
+  uint32_t total;
+  uint32_t run = block_exclusive_scan(local, warp_tot, total);
+  for (int j = 0; j < per; ++j)
+    if (b0 + j < nblk) {
+      const uint32_t v = blocksum[b0 + j];
+      blocksum[b0 + j] = run;
+      run += v;
+    }
+  if (advance && threadIdx.x == 0) {
+    *step += 1ull;
+    *mode = 1;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(uint32_t* __restrict__ count, uint32_t T,
+                                                             const uint32_t* __restrict__ blocksum,
+                                                             uint32_t* __restrict__ start) {
+  __shared__ uint32_t warp_tot[33];
+  const uint32_t base = blockIdx.x * (uint32_t)kScanPerBlock + threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    v[j] = (base + j < T) ? count[base + j] : 0u;
+    s += v[j];
+  }
+  uint32_t total;
+  uint32_t run = block_exclusive_scan(s, warp_tot, total) + blocksum[blockIdx.x];
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j)
+    if (base + j < T) {
+      start[base + j] = run;
+      run += v[j];
+      count[base + j] = 0u;
+    }
+}
+
+__global__ void k_scatter(DevArrays A) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  const uint32_t b = bucket_of(A.cell[i], A.hashed, A.log_t);
+  A.stag[A.start[b] + A.rank[i]] = (uint32_t)i;
+}
+
+template <typename R> __device__ __forceinline__ void put_rec(void* rec, uint32_t s, double ox, double oy,
+                                                              double oz, uint32_t bits);
+template <> __device__ __forceinline__ void put_rec<float>(void* rec, uint32_t s, double ox, double oy,
+                                                           double oz, uint32_t bits) {
+  reinterpret_cast<float4*>(rec)[s] = make_float4((float)ox, (float)oy, (float)oz, __uint_as_float(bits));
+}
+template <> __device__ __forceinline__ void put_rec<double>(void* rec, uint32_t s, double ox, double oy,
+                                                            double oz, uint32_t bits) {
+  reinterpret_cast<double4_32a*>(rec)[s] =
+      make_double4_32a(ox, oy, oz, __longlong_as_double((long long)bits));
+}
+
+// One thread per bucket: order the bucket's particles by id (so that every
+// force sum has one fixed order and runs repeat bit for bit), then write for
+// each slot its cell id and its cell-relative offset (formed in float64).
+template <typename R>
+__global__ void k_bucket_build(DevArrays A) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= A.nbucket) return;
+  const uint32_t s0 = A.start[b], s1 = A.start[b + 1];
+  if (s0 == s1) return;
+  for (uint32_t s = s0 + 1; s < s1; ++s) {  // insertion sort (buckets hold a few particles)
+    const uint32_t t = A.stag[s];
+    uint32_t q = s;
+    while (q > s0 && A.stag[q - 1] > t) {
+      A.stag[q] = A.stag[q - 1];
+      --q;
+    }
+    A.stag[q] = t;
+  }
+  const int64_t n = A.n;
+  for (uint32_t s = s0; s < s1; ++s) {
+    const uint32_t tag = A.stag[s];
+    const uint32_t cell = A.cell[tag];
+    const uint32_t m = A.meta[tag];
+    const SysDev& S = A.sys[meta_sys(m)];
+    int c[3];
+    cell_decode(S, cell, c[0], c[1], c[2]);
+    double o[3];
+    const double xv[3] = {A.x[tag], A.x[n + tag], A.x[2 * n + tag]};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) o[d] = wrap_coord(S, d, xv[d]) - fma((double)c[d], S.cs[d], S.grid_lo[d]);
+    const uint32_t mol = A.mol ? (uint32_t)A.mol[tag] : 0u;
+    A.scell[s] = cell;
+    put_rec<R>(A.rec, s, o[0], o[1], o[2], meta_type(m) | (mol << 3));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pair forces
+// ---------------------------------------------------------------------------
+template <typename R> struct RecT;
+template <> struct RecT<float> {
+  using T = float4;
+  static __device__ __forceinline__ uint32_t bits(const float4& r) { return __float_as_uint(r.w); }
+};
+template <> struct RecT<double> {
+  using T = double4_32a;
+  static __device__ __forceinline__ uint32_t bits(const double4_32a& r) {
+    return (uint32_t)__double_as_longlong(r.w);
+  }
+};
+
+template <typename R> struct PairTab {
+  R eps[kMaxTypes * kMaxTypes], sig2[kMaxTypes * kMaxTypes], rc2[kMaxTypes * kMaxTypes],
+      shift[kMaxTypes * kMaxTypes];
+};
+
+template <typename R> __device__ __forceinline__ void load_tab(PairTab<R>& t, const TypeTable* T);
+template <> __device__ __forceinline__ void load_tab<float>(PairTab<float>& t, const TypeTable* T) {
+  for (int q = threadIdx.x; q < kMaxTypes * kMaxTypes; q += blockDim.x) {
+    const int a = q / kMaxTypes, b = q % kMaxTypes;
+    t.eps[q] = T->eps_f[a][b];
+    t.sig2[q] = T->sig2_f[a][b];
+    t.rc2[q] = T->rc2_f[a][b];
+    t.shift[q] = T->shift_f[a][b];
+  }
+}
+template <> __device__ __forceinline__ void load_tab<double>(PairTab<double>& t, const TypeTable* T) {
+  for (int q = threadIdx.x; q < kMaxTypes * kMaxTypes; q += blockDim.x) {
+    const int a = q / kMaxTypes, b = q % kMaxTypes;
+    t.eps[q] = T->eps[a][b];
+    t.sig2[q] = T->sig2[a][b];
+    t.rc2[q] = T->rc2[a][b];
+    t.shift[q] = T->shift[a][b];
+  }
+}
+
+template <typename R> __device__ __forceinline__ R rcp(R v);
+template <> __device__ __forceinline__ float rcp<float>(float v) { return __frcp_rn(v); }
+template <> __device__ __forceinline__ double rcp<double>(double v) { return 1.0 / v; }
+
+template <typename R> __device__ __forceinline__ void store_f(void* f, uint32_t i, R fx, R fy, R fz, R u);
+template <> __device__ __forceinline__ void store_f<float>(void* f, uint32_t i, float fx, float fy, float fz,
+                                                           float u) {
+  reinterpret_cast<float4*>(f)[i] = make_float4(fx, fy, fz, u);
+}
+template <> __device__ __forceinline__ void store_f<double>(void* f, uint32_t i, double fx, double fy,
+                                                            double fz, double u) {
+  reinterpret_cast<double4_32a*>(f)[i] = make_double4_32a(fx, fy, fz, u);
+}
+
+// Bond (V = k (r - r0)^2, no factor 1/2) and wall (V_w) terms of particle
+// `tag`; displacements in float64, force arithmetic in R.
+template <typename R>
+__device__ __forceinline__ void bonded_terms(const DevArrays& A, const SysDev& S, uint32_t tag, uint32_t m,
+                                             bool bonds, bool walls, R& fx, R& fy, R& fz, R& u) {
+  const int64_t n = A.n;
+  const double xi = A.x[tag], yi = A.x[n + tag], zi = A.x[2 * n + tag];
+  if (bonds && S.bpm > 1) {
+    const int64_t pid = (int64_t)tag - S.first;
+    const int64_t B = S.bpm;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      int64_t j;
+      if (side == 0) {
+        if (pid % B == 0) continue;
+        j = (int64_t)tag - 1;
+      } else {
+        if (pid % B == B - 1 || pid + 1 >= S.n) continue;
+        j = (int64_t)tag + 1;
+      }
+      double dx = xi - A.x[j], dy = yi - A.x[n + j], dz = zi - A.x[2 * n + j];
+      if (S.periodic[0]) dx = wrap_min_image(dx, S.box_len[0]);
+      if (S.periodic[1]) dy = wrap_min_image(dy, S.box_len[1]);
+      if (S.periodic[2]) dz = wrap_min_image(dz, S.box_len[2]);
+      const R rx = (R)dx, ry = (R)dy, rz = (R)dz;
+      const R r = sqrt(rx * rx + ry * ry + rz * rz);
+      const R dr = r - (R)S.bond_r0;
+      const R fo = (R)(-2.0 * S.bond_k) * dr / r;
+      fx += fo * rx; fy += fo * ry; fz += fo * rz;
+      u += (R)(0.5 * S.bond_k) * dr * dr;
+    }
+  }
+  if (walls && S.wall && !meta_con(m)) {
+    const double dist[2] = {zi - S.wall_lo, S.wall_hi - zi};
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      const double r = dist[w];
+      if (!(r > 0.0)) {
+        flag(A.status, kFlagOutOfGrid);
+        continue;
+      }
+      if (r >= S.wall_rc) continue;
+      const R rr = (R)r;
+      const R s2 = (R)(S.wall_sigma * S.wall_sigma) / (rr * rr);
+      const R s6 = s2 * s2 * s2;
+      const R e = (R)S.wall_eps;
+      const R fr = (R)24 * e * ((R)2 * s6 * s6 - s6) / rr;
+      fz += (w == 0) ? fr : -fr;
+      u += (R)4 * e * (s6 * s6 - s6 + (R)0.25);
+    }
+  }
+}
+
+template <typename R, bool BONDS, bool WALLS, bool EXCL>
+__global__ void __launch_bounds__(256) k_pair(DevArrays A) {
+  __shared__ PairTab<R> tab;
+  load_tab<R>(tab, A.types);
+  __syncthreads();
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= (uint32_t)A.n) return;
+  using Rec = typename RecT<R>::T;
+  const Rec* __restrict__ rec = reinterpret_cast<const Rec*>(A.rec);
+  const uint32_t* __restrict__ scell = A.scell;
+  const uint32_t* __restrict__ start = A.start;
+  const uint32_t tag = A.stag[s];
+  const uint32_t cell = scell[s];
+  const Rec ri = rec[s];
+  const uint32_t bi = RecT<R>::bits(ri);
+  const uint32_t ti = bi & 7u, moli = bi >> 3;
+  const uint32_t m = A.meta[tag];
+  const SysDev& S = A.sys[meta_sys(m)];
+  int c[3];
+  cell_decode(S, cell, c[0], c[1], c[2]);
+  R fx = 0, fy = 0, fz = 0, u = 0;
+  const R csx = (R)S.cs[0], csy = (R)S.cs[1], csz = (R)S.cs[2];
+  for (int dz = -1; dz <= 1; ++dz) {
+    int z = c[2] + dz;
+    if (z < 0 || z >= S.nc[2]) {
+      if (!S.periodic[2]) continue;
+      z = (z + S.nc[2]) % S.nc[2];
+    }
+    for (int dy = -1; dy <= 1; ++dy) {
+      int y = c[1] + dy;
+      if (y < 0 || y >= S.nc[1]) {
+        if (!S.periodic[1]) continue;
+        y = (y + S.nc[1]) % S.nc[1];
+      }
+      for (int dx = -1; dx <= 1; ++dx) {
+        int x = c[0] + dx;
+        if (x < 0 || x >= S.nc[0]) {
+          if (!S.periodic[0]) continue;
+          x = (x + S.nc[0]) % S.nc[0];
+        }
+        const uint32_t nb = S.cell_base + (uint32_t)x +
+                            (uint32_t)S.nc[0] * ((uint32_t)y + (uint32_t)S.nc[1] * (uint32_t)z);
+        const uint32_t b = bucket_of(nb, A.hashed, A.log_t);
+        const uint32_t t1 = start[b + 1];
+        const R shx = (R)dx * csx, shy = (R)dy * csy, shz = (R)dz * csz;
+        for (uint32_t t = start[b]; t < t1; ++t) {
+          if (scell[t] != nb || t == s) continue;
+          const Rec rj = rec[t];
+          const uint32_t bj = RecT<R>::bits(rj);
+          if (EXCL && (bj >> 3) == moli) continue;
+          const uint32_t q = ti * kMaxTypes + (bj & 7u);
+          const R ddx = ri.x - rj.x - shx, ddy = ri.y - rj.y - shy, ddz = ri.z - rj.z - shz;
+          const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+          if (r2 < tab.rc2[q]) {
+            const R inv_r2 = rcp<R>(r2);
+            const R s2 = tab.sig2[q] * inv_r2;
+            const R s6 = s2 * s2 * s2;
+            const R e = tab.eps[q];
+            const R fr = (R)24 * e * s6 * ((R)2 * s6 - (R)1) * inv_r2;
+            fx += fr * ddx; fy += fr * ddy; fz += fr * ddz;
+            u += (R)0.5 * ((R)4 * e * s6 * (s6 - (R)1) - tab.shift[q]);
+          }
+        }
+      }
+    }
+  }
+  if (BONDS || WALLS) bonded_terms<R>(A, S, tag, m, BONDS, WALLS, fx, fy, fz, u);
+  store_f<R>(A.f, tag, fx, fy, fz, u);
+}
+
+// No pair term anywhere: only bonds and walls, in particle order.
+template <typename R>
+__global__ void k_nopair(DevArrays A, int bonds, int walls) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  const uint32_t m = A.meta[i];
+  const SysDev& S = A.sys[meta_sys(m)];
+  R fx = 0, fy = 0, fz = 0, u = 0;
+  if (bonds || walls) bonded_terms<R>(A, S, (uint32_t)i, m, bonds, walls, fx, fy, fz, u);
+  store_f<R>(A.f, (uint32_t)i, fx, fy, fz, u);
+}
+
+// ---------------------------------------------------------------------------
+// integrator
+// ---------------------------------------------------------------------------
+template <typename R> __device__ __forceinline__ void load_f(const void* f, int64_t i, double& fx, double& fy,
+                                                             double& fz);
+template <> __device__ __forceinline__ void load_f<float>(const void* f, int64_t i, double& fx, double& fy,
+                                                          double& fz) {
+  const float4 v = reinterpret_cast<const float4*>(f)[i];
+  fx = v.x; fy = v.y; fz = v.z;
+}
+template <> __device__ __forceinline__ void load_f<double>(const void* f, int64_t i, double& fx, double& fy,
+                                                           double& fz) {
+  const double4_32a v = reinterpret_cast<const double4_32a*>(f)[i];
+  fx = v.x; fy = v.y; fz = v.z;
+}
+
+// Algorithm S1 force combination at step k for particle i (in double):
+//   first step after a set state:  F = f - gamma p + f_r^k
+//   otherwise:  F = [f - gamma p^{k-1/2} + (f_r^k + f_r^{k-1})/2] / (1 + gamma dt/2)
+// with f_r = sqrt(2 m kT gamma / dt) xi, xi from Philox (noise in R).
+template <typename R>
+__device__ __forceinline__ void combine(const SysDev& S, uint32_t pid, unsigned long long k, int mode,
+                                        double sqm, double fx, double fy, double fz, double px,
+                                        double py, double pz, double& Fx, double& Fy, double& Fz) {
+  double nx = 0.0, ny = 0.0, nz = 0.0;
+  if (S.noise_unit > 0.0) {
+    R gx, gy, gz;
+    gauss3(S.seed_lo, S.replica, pid, k, gx, gy, gz);
+    if (mode == 0) {
+      nx = (double)gx; ny = (double)gy; nz = (double)gz;
+    } else {
+      R hx, hy, hz;
+      gauss3(S.seed_lo, S.replica, pid, k - 1ull, hx, hy, hz);
+      nx = 0.5 * ((double)gx + (double)hx);
+      ny = 0.5 * ((double)gy + (double)hy);
+      nz = 0.5 * ((double)gz + (double)hz);
+    }
+    const double a = S.noise_unit * sqm;
+    nx *= a; ny *= a; nz *= a;
+  }
+  if (mode == 0) {
+    Fx = fx - S.gamma * px + nx;
+    Fy = fy - S.gamma * py + ny;
+    Fz = fz - S.gamma * pz + nz;
+  } else {
+    Fx = S.comb * (fx - S.gamma * px + nx);
+    Fy = S.comb * (fy - S.gamma * py + ny);
+    Fz = S.comb * (fz - S.gamma * pz + nz);
+  }
+}
+
+template <typename R, bool BIN>
+__global__ void __launch_bounds__(256) k_integrate(DevArrays A) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = A.n;
+  if (i >= n) return;
+  const unsigned long long k = *A.step;
+  const int mode = *A.mode;
+  const uint32_t m = A.meta[i];
+  const SysDev& S = A.sys[meta_sys(m)];
+  const uint32_t ty = meta_type(m);
+  const double inv_m = A.types->inv_mass[ty];
+  const double x = A.x[i], y = A.x[n + i], z = A.x[2 * n + i];
+  double px = A.ph[i], py = A.ph[n + i], pz = A.ph[2 * n + i];
+  double fx, fy, fz;
+  load_f<R>(A.f, i, fx, fy, fz);
+  double Fx, Fy, Fz;
+  combine<R>(S, (uint32_t)(i - S.first), k, mode, A.types->sqrt_mass[ty], fx, fy, fz, px, py, pz, Fx, Fy,
+             Fz);
+  const double h = S.half_dt;
+  const bool con = meta_con(m);
+  double n0x = 0.0, n0y = 0.0, n0z = 0.0;
+  if (con) surf_eval(S, x, y, z, n0x, n0y, n0z);
+  if (mode != 0) {
+    // momentum half of Algorithm 1 at x^k: p^k = p^{k-1/2} + h (F - mu n)
+    // with n.p^k = 0; the residual is linear in (p, mu), so the Newton
+    // iteration ends after one exact step: a tangent-plane projection.
+    px += h * Fx; py += h * Fy; pz += h * Fz;
+    if (con) {
+      const double sc = (n0x * px + n0y * py + n0z * pz) / (n0x * n0x + n0y * n0y + n0z * n0z);
+      px -= sc * n0x; py -= sc * n0y; pz -= sc * n0z;
+    }
+  }
+  // position half of Algorithm 1 for step k+1. With r_x = 0 after the first
+  // update, the 4x4 Newton of Algorithm 1 reduces to a scalar Newton on
+  // lambda: x(lambda) = y - a lambda n0, lambda += g(x) / (a n1.n0).
+  double qx = px + h * Fx, qy = py + h * Fy, qz = pz + h * Fz;  // p^{k+1/2} before the constraint
+  const double dtm = S.dt * inv_m;
+  double xn = fma(dtm, qx, x), yn = fma(dtm, qy, y), zn = fma(dtm, qz, z);
+  if (con) {
+    const double a = h * dtm;  // dt^2 / (2m)
+    const double yx = xn, yy = yn, yz = zn;
+    double lam = 0.0;
+    bool ok = false;
+    for (int it = 0; it <= S.max_newton; ++it) {
+      double n1x, n1y, n1z;
+      const double g = surf_eval(S, xn, yn, zn, n1x, n1y, n1z);
+      const double gn = sqrt(n1x * n1x + n1y * n1y + n1z * n1z);
+      if (fabs(g) < S.tol * gn) {
+        ok = true;
+        break;
+      }
+      if (it == S.max_newton) break;
+      if (S.frozen) {
+        n1x = n0x; n1y = n0y; n1z = n0z;
+      }
+      const double dl = g / (a * (n1x * n0x + n1y * n0y + n1z * n0z));
+      lam += dl;
+      xn = fma(-a * lam, n0x, yx);
+      yn = fma(-a * lam, n0y, yy);
+      zn = fma(-a * lam, n0z, yz);
+      const double stepmax = fabs(dl) * a * fmax(fabs(n0x), fmax(fabs(n0y), fabs(n0z)));
+      const double xm = fmax(fabs(xn), fmax(fabs(yn), fabs(zn)));
+      if (stepmax <= 4.0 * xm * DBL_EPSILON) {  // round-off floor (4 ulp)
+        ok = true;
+        break;
+      }
+    }
+    if (!ok) flag(A.status, kFlagRattle);
+    qx -= h * lam * n0x; qy -= h * lam * n0y; qz -= h * lam * n0z;
+  }
+  if (!finite3(xn, yn, zn) || !finite3(qx, qy, qz)) flag(A.status, kFlagNonfinite);
+  A.x[i] = xn; A.x[n + i] = yn; A.x[2 * n + i] = zn;
+  A.ph[i] = qx; A.ph[n + i] = qy; A.ph[2 * n + i] = qz;
+  if (BIN) {
+    bool out = false;
+    const uint32_t cell = cell_of(S, xn, yn, zn, out);
+    if (out) flag(A.status, kFlagOutOfGrid);
+    A.cell[i] = cell;
+    A.rank[i] = atomicAdd(&A.count[bucket_of(cell, A.hashed, A.log_t)], 1u);
+  }
+}
+
+__global__ void k_advance(unsigned long long* step, int32_t* mode) {
+  *step += 1ull;
+  *mode = 1;
+}
+
+// p^k = momentum half of Algorithm 1 from p^{k-1/2} and F^k (state unchanged).
+template <typename R>
+__global__ void k_finish(DevArrays A) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = A.n;
+  if (i >= n) return;
+  const int mode = *A.mode;
+  if (mode == 0) {
+    A.pk[i] = A.ph[i]; A.pk[n + i] = A.ph[n + i]; A.pk[2 * n + i] = A.ph[2 * n + i];
+    return;
+  }
+  const unsigned long long k = *A.step;
+  const uint32_t m = A.meta[i];
+  const SysDev& S = A.sys[meta_sys(m)];
+  const uint32_t ty = meta_type(m);
+  double px = A.ph[i], py = A.ph[n + i], pz = A.ph[2 * n + i];
+  double fx, fy, fz;
+  load_f<R>(A.f, i, fx, fy, fz);
+  double Fx, Fy, Fz;
+  combine<R>(S, (uint32_t)(i - S.first), k, 1, A.types->sqrt_mass[ty], fx, fy, fz, px, py, pz, Fx, Fy, Fz);
+  const double h = S.half_dt;
+  px += h * Fx; py += h * Fy; pz += h * Fz;
+  if (meta_con(m)) {
+    double nx, ny, nz;
+    surf_eval(S, A.x[i], A.x[n + i], A.x[2 * n + i], nx, ny, nz);
+    const double sc = (nx * px + ny * py + nz * pz) / (nx * nx + ny * ny + nz * nz);
+    px -= sc * nx; py -= sc * ny; pz -= sc * nz;
+  }
+  A.pk[i] = px; A.pk[n + i] = py; A.pk[2 * n + i] = pz;
+}
+
+// ---------------------------------------------------------------------------
+// read-out
+// ---------------------------------------------------------------------------
+__global__ void k_get_state(DevArrays A, double* xa, double* va, double* pa) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = A.n;
+  if (i >= n) return;
+  const double inv_m = A.types->inv_mass[meta_type(A.meta[i])];
+  for (int d = 0; d < 3; ++d) {
+    if (xa) xa[3 * i + d] = A.x[d * n + i];
+    if (va) va[3 * i + d] = A.pk[d * n + i] * inv_m;
+    if (pa) pa[3 * i + d] = A.ph[d * n + i];
+  }
+}
+
+template <typename R>
+__global__ void k_get_forces(DevArrays A, double* fa, double* ua) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  using V = typename V4<R>::T;
+  const V v = reinterpret_cast<const V*>(A.f)[i];
+  if (fa) {
+    fa[3 * i] = (double)v.x;
+    fa[3 * i + 1] = (double)v.y;
+    fa[3 * i + 2] = (double)v.z;
+  }
+  if (ua) ua[i] = (double)v.w;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* a, double v) {
+  atomicMax(a, (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void k_residual(DevArrays A, unsigned long long* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = A.n;
+  if (i >= n) return;
+  const uint32_t m = A.meta[i];
+  if (!meta_con(m)) return;
+  const SysDev& S = A.sys[meta_sys(m)];
+  double nx, ny, nz;
+  const double g = surf_eval(S, A.x[i], A.x[n + i], A.x[2 * n + i], nx, ny, nz);
+  const double gn = sqrt(nx * nx + ny * ny + nz * nz);
+  const double inv_m = A.types->inv_mass[meta_type(m)];
+  const double nv = (nx * A.pk[i] + ny * A.pk[n + i] + nz * A.pk[2 * n + i]) * inv_m;
+  atomic_max_nonneg(&out[0], fabs(g) / gn);
+  atomic_max_nonneg(&out[1], fabs(g));
+  atomic_max_nonneg(&out[2], fabs(nv) / gn);
+}
+
+template <typename R>
+__global__ void k_observables(DevArrays A, double* obs) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = A.n;
+  if (i >= n) return;
+  const uint32_t m = A.meta[i];
+  const uint32_t sid = meta_sys(m);
+  const SysDev& S = A.sys[sid];
+  const uint32_t ty = meta_type(m);
+  const double inv_m = A.types->inv_mass[ty];
+  const double px = A.pk[i], py = A.pk[n + i], pz = A.pk[2 * n + i];
+  const double x = A.x[i], y = A.x[n + i], z = A.x[2 * n + i];
+  const double dx = x - A.xref[i], dy = y - A.xref[n + i], dz = z - A.xref[2 * n + i];
+  using V = typename V4<R>::T;
+  const V f = reinterpret_cast<const V*>(A.f)[i];
+  double* o = obs + 8 * (int64_t)sid;
+  atomicAdd(&o[0], 0.5 * (px * px + py * py + pz * pz) * inv_m);
+  atomicAdd(&o[1], (double)f.w);
+  atomicAdd(&o[2], dx * dx + dy * dy + dz * dz);
+  if (S.kind == kSphere) {
+    const double R2 = S.p[0] * S.p[0];
+    const double dot = (A.xref[i] - S.c[0]) * (x - S.c[0]) + (A.xref[n + i] - S.c[1]) * (y - S.c[1]) +
+                       (A.xref[2 * n + i] - S.c[2]) * (z - S.c[2]);
+    atomicAdd(&o[3], dot / R2);
+  }
+  const bool con = meta_con(m);
+  atomicAdd(&o[4], con ? 2.0 : 3.0);
+  if (con) {
+    double nx, ny, nz;
+    const double g = surf_eval(S, x, y, z, nx, ny, nz);
+    const double gn = sqrt(nx * nx + ny * ny + nz * nz);
+    atomic_max_nonneg(reinterpret_cast<unsigned long long*>(&o[5]), fabs(g) / gn);
+    atomic_max_nonneg(reinterpret_cast<unsigned long long*>(&o[6]),
+                      fabs((nx * px + ny * py + nz * pz) * inv_m) / gn);
+  }
+  atomicAdd(&o[7], 1.0);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+cudaError_t launch_build_meta(const DevArrays& A, const int64_t* d_first, int nsys, const int32_t* d_type,
+                              const uint8_t* d_con, const int32_t* d_mol, int, cudaStream_t st) {
+  if (A.n == 0) return cudaSuccess;
+  k_build_meta<<<grid_for(A.n, 256), 256, 0, st>>>(A, d_first, nsys, d_type, d_con, d_mol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_state(const DevArrays& A, const double* d_x, const double* d_v, cudaStream_t st) {
+  if (A.n == 0) return cudaSuccess;
+  k_set_state<<<grid_for(A.n, 256), 256, 0, st>>>(A, d_x, d_v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restore(const DevArrays& A, const double* d_x, const double* d_ph, cudaStream_t st) {
+  if (A.n == 0) return cudaSuccess;
+  k_restore<<<grid_for(A.n, 256), 256, 0, st>>>(A, d_x, d_ph);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin(const DevArrays& A, cudaStream_t st) {
+  if (A.n == 0) return cudaSuccess;
+  k_bin<<<grid_for(A.n, 256), 256, 0, st>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_reduce(const DevArrays& A, cudaStream_t st) {
+  const int nblk = (int)((A.nbucket + kScanPerBlock - 1) / kScanPerBlock);
+  k_scan_reduce<<<nblk, kScanThreads, 0, st>>>(A.count, A.nbucket, A.blocksum);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_blocks(const DevArrays& A, int advance, cudaStream_t st) {
+  const int nblk = (int)((A.nbucket + kScanPerBlock - 1) / kScanPerBlock);
+  k_scan_blocks<<<1, 1024, 0, st>>>(A.blocksum, nblk, A.step, A.mode, advance);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_apply(const DevArrays& A, cudaStream_t st) {
+  const int nblk = (int)((A.nbucket + kScanPerBlock - 1) / kScanPerBlock);
+  k_scan_apply<<<nblk, kScanThreads, 0, st>>>(A.count, A.nbucket, A.blocksum, A.start);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const DevArrays& A, cudaStream_t st) {
+  if (A.n == 0) return cudaSuccess;
+  k_scatter<<<grid_for(A.n, 256), 256, 0, st>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cells_after_bin(const DevArrays& A, int advance, cudaStream_t st) {
+  cudaError_t e = launch_scan_reduce(A, st);
+  if (e == cudaSuccess) e = launch_scan_blocks(A, advance, st);
+  if (e == cudaSuccess) e = launch_scan_apply(A, st);
+  if (e == cudaSuccess) e = launch_scatter(A, st);
+  return e;
+}
+
+cudaError_t launch_bucket_build(const DevArrays& A, int precision, cudaStream_t st) {
+  if (A.n == 0) return cudaSuccess;
+  if (precision == 0) k_bucket_build<double><<<grid_for(A.nbucket, 256), 256, 0, st>>>(A);
+  else k_bucket_build<float><<<grid_for(A.nbucket, 256), 256, 0, st>>>(A);
+  return cudaGetLastError();
+}
+
+template <typename R>
+static void pair_dispatch(const DevArrays& A, int bonds, int walls, int excl, cudaStream_t st) {
+  const unsigned g = grid_for(A.n, 256);
+  const int key = (bonds ? 4 : 0) | (walls ? 2 : 0) | (excl ? 1 : 0);
+  switch (key) {
+    case 0: k_pair<R, false, false, false><<<g, 256, 0, st>>>(A); break;
+    case 1: k_pair<R, false, false, true><<<g, 256, 0, st>>>(A); break;
+    case 2: k_pair<R, false, true, false><<<g, 256, 0, st>>>(A); break;
+    case 3: k_pair<R, false, true, true><<<g, 256, 0, st>>>(A); break;
+    case 4: k_pair<R, true, false, false><<<g, 256, 0, st>>>(A); break;
+    case 5: k_pair<R, true, false, true><<<g, 256, 0, st>>>(A); break;
+    case 6: k_pair<R, true, true, false><<<g, 256, 0, st>>>(A); break;
+    default: k_pair<R, true, true, true><<<g, 256, 0, st>>>(A); break;
+  }
+}
+
+cudaError_t launch_pair(const DevArrays& A, int precision, int has_pairs, int bonds, int walls, int excl,
+                        cudaStream_t st) {
+  if (A.n == 0) return cudaSuccess;
+  if (!has_pairs) {
+    if (precision == 0) k_nopair<double><<<grid_for(A.n, 256), 256, 0, st>>>(A, bonds, walls);
+    else k_nopair<float><<<grid_for(A.n, 256), 256, 0, st>>>(A, bonds, walls);
+  } else if (precision == 0) {
+    pair_dispatch<double>(A, bonds, walls, excl, st);
+  } else {
+    pair_dispatch<float>(A, bonds, walls, excl, st);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_integrate(const DevArrays& A, int precision, int has_pairs, cudaStream_t st) {
+  if (A.n == 0) return cudaSuccess;
+  const unsigned g = grid_for(A.n, 256);
+  if (precision == 0) {
+    if (has_pairs) k_integrate<double, true><<<g, 256, 0, st>>>(A);
+    else k_integrate<double, false><<<g, 256, 0, st>>>(A);
+  } else {
+    if (has_pairs) k_integrate<float, true><<<g, 256, 0, st>>>(A);
+    else k_integrate<float, false><<<g, 256, 0, st>>>(A);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance(const DevArrays& A, cudaStream_t st) {
+  k_advance<<<1, 1, 0, st>>>(A.step, A.mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const DevArrays& A, int precision, cudaStream_t st) {
+  if (A.n == 0) return cudaSuccess;
+  if (precision == 0) k_finish<double><<<grid_for(A.n, 256), 256, 0, st>>>(A);
+  else k_finish<float><<<grid_for(A.n, 256), 256, 0, st>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_state(const DevArrays& A, double* xa, double* va, double* pa, cudaStream_t st) {
+  if (A.n == 0) return cudaSuccess;
+  k_get_state<<<grid_for(A.n, 256), 256, 0, st>>>(A, xa, va, pa);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_forces(const DevArrays& A, int precision, double* fa, double* ua, cudaStream_t st) {
+  if (A.n == 0) return cudaSuccess;
+  if (precision == 0) k_get_forces<double><<<grid_for(A.n, 256), 256, 0, st>>>(A, fa, ua);
+  else k_get_forces<float><<<grid_for(A.n, 256), 256, 0, st>>>(A, fa, ua);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const DevArrays& A, unsigned long long* d_out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(d_out, 0, 3 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess || A.n == 0) return e;
+  k_residual<<<grid_for(A.n, 256), 256, 0, st>>>(A, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_observables(const DevArrays& A, int precision, double* d_obs, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(d_obs, 0, 8 * sizeof(double) * (size_t)A.nsys, st);
+  if (e != cudaSuccess || A.n == 0) return e;
+  if (precision == 0) k_observables<double><<<grid_for(A.n, 256), 256, 0, st>>>(A, d_obs);
+  else k_observables<float><<<grid_for(A.n, 256), 256, 0, st>>>(A, d_obs);
+  return cudaGetLastError();
+}
+
+}  // namespace surfmd

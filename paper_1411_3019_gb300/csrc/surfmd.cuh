@@ -1,0 +1,111 @@
+// surfmd.cuh -- device-side types and helpers of the constrained Langevin
+// step (Paquay & Kusters, Algorithm 1 and Algorithm S1) on sm_103a.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace surfmd {
+
+constexpr int kMaxTypes = 8;
+
+// Bits of the device status word (match MD_FLAG_* of md.h).
+constexpr uint32_t kFlagRattle = 0x1u;
+constexpr uint32_t kFlagNonfinite = 0x2u;
+constexpr uint32_t kFlagOutOfGrid = 0x4u;
+constexpr uint32_t kFlagTimeout = 0x8u;
+constexpr uint32_t kFlagOffSurface = 0x100u;  // set-state validation only
+
+enum SurfKind : int32_t {
+  kNone = 0, kPlane = 1, kSphere = 2, kEllipsoid = 3, kTorus = 4, kBump = 5, kCylinder = 6
+};
+
+// Per-particle meta word: type (bits 0-2), constrained (bit 3), system (bits 4-31).
+__host__ __device__ inline uint32_t meta_pack(uint32_t type, uint32_t con, uint32_t sys) {
+  return (type & 7u) | ((con & 1u) << 3) | (sys << 4);
+}
+__host__ __device__ inline uint32_t meta_type(uint32_t m) { return m & 7u; }
+__host__ __device__ inline bool meta_con(uint32_t m) { return (m >> 3) & 1u; }
+__host__ __device__ inline uint32_t meta_sys(uint32_t m) { return m >> 4; }
+
+// One system's constants as the kernels read them.
+struct SysDev {
+  // surface g(x) = 0
+  int32_t kind;
+  int32_t axis;              // cylinder axis
+  double c[3];               // centre / plane point
+  double p[4];               // shape parameters
+  double inv_a2[3];          // ellipsoid 1/a_d^2
+  // integration
+  double dt, half_dt, kT, gamma;
+  double comb;               // 1 / (1 + gamma dt / 2)
+  double noise_unit;         // sqrt(2 kT gamma / dt); times sqrt(m) per particle
+  double tol;
+  int32_t max_newton, frozen;
+  // box and cell grid
+  double box_lo[3], box_len[3];
+  int32_t periodic[3];
+  int32_t pad0;
+  double grid_lo[3], cs[3], inv_cs[3];
+  float cs_f[3];
+  int32_t nc[3];
+  uint32_t cell_base;
+  // bonds, exclusions, walls
+  int32_t bpm;
+  int32_t excl;
+  double bond_k, bond_r0;
+  int32_t wall;
+  int32_t pad1;
+  double wall_lo, wall_hi, wall_eps, wall_sigma, wall_rc;
+  // noise key, particle range
+  uint32_t seed_lo, replica;
+  int64_t first, n;
+};
+
+// Pair tables shared by all systems of a handle (symmetric).
+struct TypeTable {
+  double eps[kMaxTypes][kMaxTypes];
+  double sig2[kMaxTypes][kMaxTypes];
+  double rc2[kMaxTypes][kMaxTypes];
+  double shift[kMaxTypes][kMaxTypes];  // phi(r_c)
+  float eps_f[kMaxTypes][kMaxTypes];
+  float sig2_f[kMaxTypes][kMaxTypes];
+  float rc2_f[kMaxTypes][kMaxTypes];
+  float shift_f[kMaxTypes][kMaxTypes];
+  double mass[kMaxTypes], inv_mass[kMaxTypes], sqrt_mass[kMaxTypes];
+};
+
+template <typename R> struct V4;
+template <> struct V4<float> { using T = float4; };
+template <> struct V4<double> { using T = double4_32a; };
+
+// Arrays of one handle, passed by value to the kernels.
+struct DevArrays {
+  int64_t n;            // particles
+  int32_t nsys;
+  uint32_t nbucket;     // T
+  int32_t hashed;       // 0: bucket = cell id; 1: hashed buckets
+  int32_t log_t;
+  double* x;            // [3][n] positions (unwrapped), SoA
+  double* ph;           // [3][n] p^{k-1/2} (or p^k before the first step)
+  double* pk;           // [3][n] p^k scratch
+  double* xref;         // [3][n] MSD reference
+  void* f;              // [n] float4 / double4_32a: conservative force + energy
+  uint32_t* meta;       // [n]
+  int32_t* mol;         // [n] molecule ids (exclusions) or null
+  uint32_t* cell;       // [n] cell id of each particle
+  uint32_t* rank;       // [n] rank inside its bucket (atomic order)
+  uint32_t* count;      // [T] bucket occupancy
+  uint32_t* start;      // [T+1] bucket start
+  uint32_t* blocksum;   // [scan blocks]
+  uint32_t* stag;       // [n] sorted slot -> particle
+  uint32_t* scell;      // [n] sorted slot -> cell id
+  void* rec;            // [n] float4 / double4_32a cell-relative offsets + type/mol bits
+  const SysDev* sys;    // [nsys]
+  const TypeTable* types;  // pair and mass tables shared by the systems
+  uint32_t* status;     // device status word
+  unsigned long long* step;  // device step counter k
+  int32_t* mode;        // 0: state holds p^k (first step pending); 1: holds p^{k-1/2}
+};
+
+}  // namespace surfmd

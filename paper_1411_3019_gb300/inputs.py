@@ -218,10 +218,11 @@ def _conflicts(cand, cgrp, ref, rgrp, dmin, periodic, L, lo, exclude_self=False)
 
 
 def rsa(sampler, counts, dmin, g, periodic=(0, 0, 0), box=None, fixed=None, fixed_group=None,
-        max_rounds=400):
+        max_rounds=400, sampler_multi=None):
     """Random sequential addition: group k receives counts[k] points from
-    sampler(k, m) with no two points of one group (nor a point and a fixed
-    point of that group) closer than dmin."""
+    sampler(k, m) (or sampler_multi(group_ids) for all groups at once) with no
+    two points of one group (nor a point and a fixed point of that group)
+    closer than dmin."""
     counts = np.asarray(counts, dtype=np.int64)
     periodic = np.asarray(periodic, bool)
     if box is None:
@@ -229,37 +230,46 @@ def rsa(sampler, counts, dmin, g, periodic=(0, 0, 0), box=None, fixed=None, fixe
     else:
         lo = np.asarray(box[0], float)
         L = np.asarray(box[1], float) - lo
-    acc = [np.empty((0, 3)) for _ in counts]
+    have = np.zeros(counts.shape[0], np.int64)
+    acc_pts, acc_grp = [], []
     pts = np.empty((0, 3)) if fixed is None else np.asarray(fixed, float)
     grp = np.empty(0, np.int64) if fixed is None else np.asarray(fixed_group, np.int64)
     for _ in range(max_rounds):
-        need = counts - np.array([a.shape[0] for a in acc])
+        need = counts - have
         if (need <= 0).all():
             break
-        cand, cg = [], []
-        for k in np.nonzero(need > 0)[0]:
-            m = int(need[k] * 1.3) + 16
-            cand.append(sampler(int(k), m))
-            cg.append(np.full(m, k, np.int64))
-        cand = np.vstack(cand)
-        cg = np.concatenate(cg)
-        bad = _conflicts(cand, cg, pts, grp, dmin, periodic, L, lo)
+        ks = np.nonzero(need > 0)[0]
+        m = (need[ks] * 1.3).astype(np.int64) + 16
+        cg = np.repeat(ks, m)
+        if sampler_multi is not None:
+            cand = sampler_multi(cg)
+        else:
+            cand = np.vstack([sampler(int(k), int(mk)) for k, mk in zip(ks, m)])
+        active = need[grp] > 0  # points of finished groups can no longer conflict
+        bad = _conflicts(cand, cg, pts[active], grp[active], dmin, periodic, L, lo)
         cand, cg = cand[~bad], cg[~bad]
         bad = _conflicts(cand, cg, cand, cg, dmin, periodic, L, lo, exclude_self=True)
         cand, cg = cand[~bad], cg[~bad]
-        new_pts, new_grp = [], []
-        for k in np.unique(cg):
-            take = cand[cg == k][: max(int(need[k]), 0)]
-            acc[k] = np.vstack([acc[k], take])
-            new_pts.append(take)
-            new_grp.append(np.full(take.shape[0], k, np.int64))
-        if new_pts:
-            pts = np.vstack([pts] + new_pts)
-            grp = np.concatenate([grp] + new_grp)
-    for k, a in enumerate(acc):
-        if a.shape[0] < counts[k]:
-            raise RuntimeError(f"RSA could not place {counts[k]} points in group {k}")
-    return acc
+        order = np.argsort(cg, kind="stable")
+        cand, cg = cand[order], cg[order]
+        first = np.searchsorted(cg, cg, "left")
+        rank = np.arange(cg.shape[0]) - first
+        keep = rank < need[cg]
+        cand, cg = cand[keep], cg[keep]
+        have += np.bincount(cg, minlength=counts.shape[0])
+        acc_pts.append(cand)
+        acc_grp.append(cg)
+        pts = np.vstack([pts, cand])
+        grp = np.concatenate([grp, cg])
+    if (have < counts).any():
+        k = int(np.nonzero(have < counts)[0][0])
+        raise RuntimeError(f"RSA could not place {counts[k]} points in group {k}")
+    allp = np.vstack(acc_pts) if acc_pts else np.empty((0, 3))
+    allg = np.concatenate(acc_grp) if acc_grp else np.empty(0, np.int64)
+    order = np.argsort(allg, kind="stable")
+    allp, allg = allp[order], allg[order]
+    bounds = np.concatenate([[0], np.cumsum(counts)])
+    return [allp[bounds[k]:bounds[k + 1]] for k in range(counts.shape[0])]
 
 
 def maxwell(n: int, kT: float, mass, g: np.random.Generator) -> np.ndarray:
@@ -367,11 +377,29 @@ def c3_bump_crowders(n_surf=100_000, n_free=900_000, seed=1, dmin=1.0, precision
     return [_system("bump_crowders", surf, prm, x, maxwell(x.shape[0], 1.0, 1.0, g), constrained=con)]
 
 
+_C4_CHUNK = 256  # replicas per placement chunk (fixed, so results do not depend on workers)
+
+
+def _c4_chunk(args):
+    seed, chunk, Rs, Ns, dmin = args
+    g = rng(seed, 0x40000 + chunk)
+    Rarr = np.asarray(Rs)
+
+    def on_spheres(groups):
+        v = g.standard_normal((groups.shape[0], 3))
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        return v * Rarr[groups][:, None]
+    xs = rsa(None, Ns, dmin, g, sampler_multi=on_spheres)
+    vs = [maxwell(n, 1.0, 1.0, g) for n in Ns]
+    return xs, vs
+
+
 def c4_replicas(nrep=4096, seed=1, nmin=50, nmax=2000, rmin=5.0, rmax=40.0, phimin=0.05,
-                phimax=0.5, dmin=1.0, precision="mixed", dt=0.002, tol=1e-10):
+                phimax=0.5, dmin=1.0, precision="mixed", dt=0.002, tol=1e-10, workers=None):
     """Batched replicas: nrep independent sphere systems with N ~ U[nmin, nmax]
     and R ~ U[rmin, rmax], redrawn until phi = N A_p / (4 pi R^2) lies in
-    [phimin, phimax]; WCA, gamma = kT = 1."""
+    [phimin, phimax]; WCA, gamma = kT = 1. Placement runs in chunks of 256
+    replicas, each with its own seeded stream (in parallel when workers > 1)."""
     g = rng(seed, 4)
     Ns, Rs = [], []
     while len(Ns) < nrep:
@@ -381,12 +409,26 @@ def c4_replicas(nrep=4096, seed=1, nmin=50, nmax=2000, rmin=5.0, rmax=40.0, phim
         if phimin <= phi <= phimax:
             Ns.append(N)
             Rs.append(R)
-    surfs = [{"kind": "sphere", "center": (0.0, 0.0, 0.0), "p": (R, 0.0, 0.0, 0.0)} for R in Rs]
-    xs = rsa(lambda k, m: sample_surface(surfs[k], m, g), Ns, dmin, g)
+    jobs = [(seed, c, Rs[c * _C4_CHUNK:(c + 1) * _C4_CHUNK], Ns[c * _C4_CHUNK:(c + 1) * _C4_CHUNK], dmin)
+            for c in range((nrep + _C4_CHUNK - 1) // _C4_CHUNK)]
+    if workers is None:
+        import os
+        workers = min(len(jobs), os.cpu_count() or 1)
+    if workers > 1 and len(jobs) > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(_c4_chunk, jobs))
+    else:
+        parts = [_c4_chunk(j) for j in jobs]
     out = []
-    for k in range(nrep):
-        prm = wca_params(precision=precision, dt=dt, rattle_tol=tol, seed=seed, replica=k)
-        out.append(_system(f"replica{k}", surfs[k], prm, xs[k], maxwell(Ns[k], 1.0, 1.0, g)))
+    k = 0
+    for xs, vs in parts:
+        for x, v in zip(xs, vs):
+            surf = {"kind": "sphere", "center": (0.0, 0.0, 0.0), "p": (Rs[k], 0.0, 0.0, 0.0)}
+            prm = wca_params(precision=precision, dt=dt, rattle_tol=tol, seed=seed, replica=k)
+            out.append(_system(f"replica{k}", surf, prm, x, v))
+            k += 1
     return out
 
 

@@ -1,0 +1,58 @@
+"""Shared helpers of the GPU parity tests: run a list of system dicts on the
+GPU (through the C ABI) and on the oracle (one oracle system per system),
+and compare."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+from paper_1411_3019_gb300 import md
+
+# Tolerances (derived in the design doc): float64 path and mixed path.
+FORCE_REL = {"fp64": 1e-11, "mixed": 1e-5}
+POS_100 = {"fp64": 1e-8, "mixed": 1e-6}
+
+
+def force_err(f_gpu, f_ref):
+    """max |df| / max(|f|, 1) per particle (1 eps/sigma floor for near-zero forces)."""
+    scale = np.maximum(np.linalg.norm(f_ref, axis=1), 1.0)
+    return float(np.max(np.linalg.norm(f_gpu - f_ref, axis=1) / scale)) if len(f_ref) else 0.0
+
+
+def gpu_run(systems, nsteps, step0=0, chunks=None):
+    sim = md.Simulation(systems)
+    sim.set_state(step0)
+    for k in (chunks or [nsteps]):
+        if k:
+            sim.step(k)
+    sim.sync()
+    st = sim.state()
+    f, u = sim.forces()
+    res = sim.residual()
+    obs = sim.observables()
+    sim.close()
+    return st, f, u, res, obs
+
+
+def oracle_run(systems, nsteps, step0=0, force_mode="auto"):
+    xs, vs, phs, fs, us, res, obs = [], [], [], [], [], [], []
+    for s in systems:
+        o = oracle.System(s["surface"], s["params"], s["n"], force_mode=force_mode)
+        o.set_state(s["x"], s["v"], s["type"], s.get("mol"), s["constrained"], step0)
+        o.step(nsteps)
+        st = o.state()
+        f, u = o.forces()
+        xs.append(st["x"])
+        vs.append(st["v"])
+        phs.append(st["p_half"])
+        fs.append(f)
+        us.append(u)
+        res.append(o.residual())
+        obs.append(o.observables())
+    cat = np.concatenate
+    return {"x": cat(xs), "v": cat(vs), "p_half": cat(phs)}, cat(fs), cat(us), res, obs
+
+
+def precision_of(systems):
+    p = systems[0]["params"]["precision"]
+    return p if isinstance(p, str) else ("fp64" if p == 0 else "mixed")

@@ -149,3 +149,25 @@ def test_wall_known_value(orc):
     x = np.array([[0.0, 0.0, 2 ** (1 / 6)]])
     f, u, _ = orc.bond_wall_forces(prm, x, np.zeros(1, np.uint8))
     assert abs(u[0]) < 1e-12 and abs(f[0, 2]) < 1e-10
+
+
+def test_periodic_forces_equal_explicit_image_sum(orc):
+    """Periodic x, y: the minimum-image forces equal the forces of the
+    central copy in an open system built from the 3x3 replicated box."""
+    box = ((-4.5, -4.0, -3.0), (4.5, 4.0, 3.0))
+    L = np.subtract(box[1], box[0])
+    g = np.random.default_rng(21)
+    n = 60
+    x = I.rsa(lambda k, m: box[0] + g.random((m, 3)) * L, [n], 0.9, g,
+              periodic=(1, 1, 0), box=box)[0]
+    prm = I.wca_params(ntypes=1, box_lo=box[0], box_hi=box[1], periodic=(1, 1, 0))
+    prm["eps"][0, 0] = 2.0
+    prm["rcut"][0, 0] = 2.5
+    f_per, u_per = orc.pair_forces(prm, x)
+    reps = [x + np.array([i * L[0], j * L[1], 0.0]) for i in (-1, 0, 1) for j in (-1, 0, 1)]
+    big = np.vstack(reps)
+    open_prm = dict(prm, periodic=(0, 0, 0))
+    f_big, u_big = orc.pair_forces(open_prm, big)
+    centre = slice(4 * n, 5 * n)
+    np.testing.assert_allclose(f_per, f_big[centre], rtol=1e-12, atol=1e-10)
+    np.testing.assert_allclose(u_per, u_big[centre], rtol=1e-12, atol=1e-12)
