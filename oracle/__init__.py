@@ -119,6 +119,7 @@ def lib():
             L.orc_sys_forces.argtypes = [C.c_void_p]
             L.orc_force_on.argtypes = [C.POINTER(Params), C.c_int64, _dp, _ip, _ip, C.c_void_p,
                                        C.c_int64, _dp, C.POINTER(C.c_double)]
+            L.orc_force_scale.argtypes = [C.POINTER(Params), C.c_int64, _dp, _ip, _ip, C.c_void_p, _dp]
             L.orc_particle_advance.restype = C.c_int
             L.orc_particle_advance.argtypes = [C.POINTER(Surface), C.POINTER(Params), C.c_int64, _dp,
                                                _ip, _ip, C.c_void_p, C.c_int64, _dp, C.c_uint64,
@@ -281,6 +282,15 @@ def force_on(prm, x, i, type_=None, mol=None, constrained=None, surf=None):
     P = make_params(prm)
     lib().orc_force_on(C.byref(P), x.shape[0], x, t, mo, con.ctypes.data, int(i), f, C.byref(u))
     return f, u.value
+
+
+def force_scale(prm, x, type_=None, mol=None, constrained=None, surf=None):
+    """Per particle, the sum of the force magnitudes of its pair, bond and wall terms."""
+    x, t, mo, con = _arrays(x, type_, mol, constrained, surf, prm)
+    out = np.zeros(x.shape[0])
+    P = make_params(prm)
+    lib().orc_force_scale(C.byref(P), x.shape[0], x, t, mo, con.ctypes.data, out)
+    return out
 
 
 def particle_advance(surf, prm, x, i, p_in, step, first, type_=None, mol=None, constrained=None):

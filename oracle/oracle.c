@@ -929,3 +929,50 @@ int orc_particle_advance(const orc_surface* S, const orc_params* P, int64_t n, c
   }
   return 0;
 }
+
+/* Force scale of every particle: sum over its pair, bond and wall terms of
+ * the magnitude of each term's force (the size of the numbers whose sum is
+ * the particle's force). Brute force over all pairs. */
+void orc_force_scale(const orc_params* P, int64_t n, const double* x, const int32_t* type,
+                     const int32_t* mol, const uint8_t* con, double* scale) {
+  memset(scale, 0, sizeof(double) * (size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i || same_molecule(P, mol, i, j)) continue;
+      double d[3] = {x[3 * i] - x[3 * j], x[3 * i + 1] - x[3 * j + 1], x[3 * i + 2] - x[3 * j + 2]};
+      min_image(P, d);
+      double fi[3] = {0.0, 0.0, 0.0};
+      lj_pair(P, type[i], type[j], d, fi);
+      scale[i] += sqrt(fi[0] * fi[0] + fi[1] * fi[1] + fi[2] * fi[2]);
+    }
+  }
+  /* bonds and walls: add |f| of each term */
+  if (P->beads_per_mol > 1 || P->wall_enable) {
+    for (int64_t i = 0; i < n; ++i) {
+      if (P->beads_per_mol > 1) {
+        int64_t B = P->beads_per_mol;
+        for (int side = 0; side < 2; ++side) {
+          int64_t j = side == 0 ? i - 1 : i + 1;
+          if (side == 0 && (i % B) == 0) continue;
+          if (side == 1 && ((i % B) == B - 1 || j >= n)) continue;
+          double d[3] = {x[3 * i] - x[3 * j], x[3 * i + 1] - x[3 * j + 1], x[3 * i + 2] - x[3 * j + 2]};
+          min_image(P, d);
+          double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+          scale[i] += fabs(2.0 * P->bond_k * (r - P->bond_r0));
+        }
+      }
+    }
+    if (P->wall_enable) {
+      for (int64_t i = 0; i < n; ++i) {
+        if (con && con[i]) continue;
+        double fw[3] = {0.0, 0.0, 0.0};
+        double xi[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+        orc_params Q = *P;
+        Q.beads_per_mol = 0;
+        double dummy;
+        orc_force_on(&Q, 1, xi, &type[i], &mol[i], NULL, 0, fw, &dummy);
+        scale[i] += fabs(fw[2]);
+      }
+    }
+  }
+}

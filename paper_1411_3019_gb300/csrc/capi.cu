@@ -152,6 +152,10 @@ int check_system(const md_surface& s, const md_params& p, SysDev& S, std::string
   S.comb = 1.0 / (1.0 + 0.5 * p.gamma * p.dt);
   S.noise_unit = std::sqrt(2.0 * p.kT * p.gamma / p.dt);
   S.tol = p.rattle_tol;
+  S.tol2 = p.rattle_tol * p.rattle_tol;
+  S.gamma_f = (float)p.gamma;
+  S.comb_f = (float)S.comb;
+  S.noise_unit_f = (float)S.noise_unit;
   S.max_newton = p.max_newton;
   S.frozen = p.frozen_normal ? 1 : 0;
   for (int d = 0; d < 3; ++d) {
@@ -213,6 +217,7 @@ void fill_types(const md_params& p, TypeTable& T) {
     T.mass[a] = m;
     T.inv_mass[a] = 1.0 / m;
     T.sqrt_mass[a] = std::sqrt(m);
+    T.sqrt_mass_f[a] = (float)std::sqrt(m);
     for (int b = 0; b < kMaxTypes; ++b) {
       if (a >= p.ntypes || b >= p.ntypes) continue;
       const double rc = p.rcut[a][b], sg = p.sigma[a][b], ep = p.eps[a][b];
@@ -263,7 +268,7 @@ int check_device_status(md_handle* h) {
 // Cell list of the current positions (no step advance).
 int rebuild_cells(md_handle* h) {
   if (!h->has_pairs) return MD_OK;
-  CK(h, launch_bin(h->A, h->stream()));
+  CK(h, launch_bin(h->A, h->precision, h->stream()));
   CK(h, launch_cells_after_bin(h->A, 0, h->stream()));
   CK(h, launch_bucket_build(h->A, h->precision, h->stream()));
   return MD_OK;
@@ -410,7 +415,10 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
     if (prms[s].exclude_intramol) h->excl = 1;
   }
   // cell grids
-  const double rc_eff = std::max(rcmax, P0.cell_size) * (1.0 + 1.0 / 4096.0);
+  // cell edge: the largest cutoff plus a 2^-12 margin, rounded up to a float
+  // so that the stencil shift is exact in the float32 pair kernel
+  const double rc_eff = (double)std::nextafter((float)(std::max(rcmax, P0.cell_size) * (1.0 + 1.0 / 4096.0)),
+                                               INFINITY);
   uint64_t cell_total = 0;
   for (int s = 0; s < nsys; ++s) {
     SysDev& S = h->sys[s];
@@ -455,6 +463,10 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
       }
       S.inv_cs[d] = 1.0 / S.cs[d];
       S.cs_f[d] = (float)S.cs[d];
+      S.grid_lo_f[d] = (float)S.grid_lo[d];
+      S.inv_cs_f[d] = (float)S.inv_cs[d];
+      S.box_lo_f[d] = (float)S.box_lo[d];
+      S.box_len_f[d] = (float)S.box_len[d];
     }
     S.cell_base = (uint32_t)cell_total;
     cell_total += (uint64_t)S.nc[0] * (uint64_t)S.nc[1] * (uint64_t)S.nc[2];
@@ -473,7 +485,7 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
   DevArrays& A = h->A;
   A.n = total;
   A.nsys = nsys;
-  if (h->has_pairs && cell_total <= t_hash) {
+  if (h->has_pairs && cell_total <= std::max<uint64_t>(t_hash, uint64_t(1) << 20)) {
     A.hashed = 0;
     A.nbucket = (uint32_t)cell_total;
     A.log_t = 0;
@@ -517,6 +529,7 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
   al(dalloc(h, &A.start, (size_t)A.nbucket + 1));
   al(dalloc(h, &A.blocksum, (size_t)nblk));
   al(dalloc(h, &A.stag, n));
+  al(dalloc(h, &A.stag_tmp, n));
   al(dalloc(h, &A.scell, n));
   SysDev* d_sys = nullptr;
   al(dalloc(h, &d_sys, (size_t)nsys));

@@ -26,7 +26,7 @@ cudaError_t launch_restore(const DevArrays& A, const double* d_x_aos, const doub
 
 // Cell list of the current positions: bin, scan, scatter, canonical sort.
 // `advance` = 1 also moves the step counter on by one (inside md_step).
-cudaError_t launch_bin(const DevArrays& A, cudaStream_t st);
+cudaError_t launch_bin(const DevArrays& A, int precision, cudaStream_t st);
 cudaError_t launch_bucket_build(const DevArrays& A, int precision, cudaStream_t st);
 cudaError_t launch_cells_after_bin(const DevArrays& A, int advance, cudaStream_t st);
 cudaError_t launch_scan_reduce(const DevArrays& A, cudaStream_t st);

@@ -161,12 +161,53 @@ __device__ __forceinline__ int cell_coord(const SysDev& S, int d, double v, bool
   return c;
 }
 
-__device__ __forceinline__ uint32_t cell_of(const SysDev& S, double x, double y, double z,
-                                            bool& out) {
+__device__ __forceinline__ uint32_t cell_id(const SysDev& S, int cx, int cy, int cz) {
+  return S.cell_base + (uint32_t)cx + (uint32_t)S.nc[0] * ((uint32_t)cy + (uint32_t)S.nc[1] * (uint32_t)cz);
+}
+
+// Cell of a position, float64 binning (float64 path).
+__device__ __forceinline__ uint32_t cell_of_d(const SysDev& S, double x, double y, double z, bool& out) {
   const int cx = cell_coord(S, 0, wrap_coord(S, 0, x), out);
   const int cy = cell_coord(S, 1, wrap_coord(S, 1, y), out);
   const int cz = cell_coord(S, 2, wrap_coord(S, 2, z), out);
-  return S.cell_base + (uint32_t)cx + (uint32_t)S.nc[0] * ((uint32_t)cy + (uint32_t)S.nc[1] * (uint32_t)cz);
+  return cell_id(S, cx, cy, cz);
+}
+
+// Cell of a position, float32 binning (mixed path): the coordinate is rounded
+// to float, wrapped and scaled in float with round-to-nearest intrinsics. The
+// cell edge carries a 2^-12 margin over the cutoff, far more than the float
+// rounding of a coordinate, so a neighbour within the cutoff is still at most
+// one cell away.
+__device__ __forceinline__ int cell_coord_f(const SysDev& S, int d, double v, bool& out) {
+  float u = (float)v;
+  if (S.periodic[d]) {
+    const float L = S.box_len_f[d];
+    const float r = __fsub_rn(u, S.box_lo_f[d]);
+    u = __fadd_rn(S.box_lo_f[d], __fsub_rn(r, __fmul_rn(L, floorf(__fdiv_rn(r, L)))));
+  }
+  const float t = __fmul_rn(__fsub_rn(u, S.grid_lo_f[d]), S.inv_cs_f[d]);
+  int c = (int)floorf(t);
+  if (c < 0) {
+    if (!S.periodic[d]) out = true;
+    c = 0;
+  } else if (c >= S.nc[d]) {
+    if (!S.periodic[d] || c > S.nc[d]) out = true;
+    c = S.nc[d] - 1;
+  }
+  if (!(t == t)) {
+    out = true;
+    c = 0;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint32_t cell_of_f(const SysDev& S, double x, double y, double z, bool& out) {
+  return cell_id(S, cell_coord_f(S, 0, x, out), cell_coord_f(S, 1, y, out), cell_coord_f(S, 2, z, out));
+}
+
+template <typename R>
+__device__ __forceinline__ uint32_t cell_of(const SysDev& S, double x, double y, double z, bool& out) {
+  return sizeof(R) == 4 ? cell_of_f(S, x, y, z, out) : cell_of_d(S, x, y, z, out);
 }
 
 __device__ __forceinline__ void cell_decode(const SysDev& S, uint32_t cell, int& cx, int& cy, int& cz) {
@@ -248,13 +289,14 @@ __global__ void k_restore(DevArrays A, const double* __restrict__ xa, const doub
 // ---------------------------------------------------------------------------
 // cell list
 // ---------------------------------------------------------------------------
+template <typename R>
 __global__ void k_bin(DevArrays A) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = A.n;
   if (i >= n) return;
   const SysDev& S = A.sys[meta_sys(A.meta[i])];
   bool out = false;
-  const uint32_t cell = cell_of(S, A.x[i], A.x[n + i], A.x[2 * n + i], out);
+  const uint32_t cell = cell_of<R>(S, A.x[i], A.x[n + i], A.x[2 * n + i], out);
   if (out) flag(A.status, kFlagOutOfGrid);
   A.cell[i] = cell;
   A.rank[i] = atomicAdd(&A.count[bucket_of(cell, A.hashed, A.log_t)], 1u);
@@ -363,7 +405,7 @@ __global__ void k_scatter(DevArrays A) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
   const uint32_t b = bucket_of(A.cell[i], A.hashed, A.log_t);
-  A.stag[A.start[b] + A.rank[i]] = (uint32_t)i;
+  A.stag_tmp[A.start[b] + A.rank[i]] = (uint32_t)i;
 }
 
 template <typename R> __device__ __forceinline__ void put_rec(void* rec, uint32_t s, double ox, double oy,
@@ -378,40 +420,38 @@ template <> __device__ __forceinline__ void put_rec<double>(void* rec, uint32_t 
       make_double4_32a(ox, oy, oz, __longlong_as_double((long long)bits));
 }
 
-// One thread per bucket: order the bucket's particles by id (so that every
-// force sum has one fixed order and runs repeat bit for bit), then write for
-// each slot its cell id and its cell-relative offset (formed in float64).
+// One thread per slot: a particle's place inside its bucket is the number of
+// bucket members with a smaller id, which gives every bucket one canonical
+// order (so every force sum has one fixed order and runs repeat bit for bit).
+// The thread writes the slot's particle id, cell id and its offset from the
+// cell centre (formed in float64, stored in R).
 template <typename R>
 __global__ void k_bucket_build(DevArrays A) {
-  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= A.nbucket) return;
-  const uint32_t s0 = A.start[b], s1 = A.start[b + 1];
-  if (s0 == s1) return;
-  for (uint32_t s = s0 + 1; s < s1; ++s) {  // insertion sort (buckets hold a few particles)
-    const uint32_t t = A.stag[s];
-    uint32_t q = s;
-    while (q > s0 && A.stag[q - 1] > t) {
-      A.stag[q] = A.stag[q - 1];
-      --q;
-    }
-    A.stag[q] = t;
-  }
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = A.n;
-  for (uint32_t s = s0; s < s1; ++s) {
-    const uint32_t tag = A.stag[s];
-    const uint32_t cell = A.cell[tag];
-    const uint32_t m = A.meta[tag];
-    const SysDev& S = A.sys[meta_sys(m)];
-    int c[3];
-    cell_decode(S, cell, c[0], c[1], c[2]);
-    double o[3];
-    const double xv[3] = {A.x[tag], A.x[n + tag], A.x[2 * n + tag]};
+  if (s >= n) return;
+  const uint32_t tag = A.stag_tmp[s];
+  const uint32_t cell = A.cell[tag];
+  const uint32_t b = bucket_of(cell, A.hashed, A.log_t);
+  const uint32_t s0 = A.start[b], s1 = A.start[b + 1];
+  uint32_t rank = 0;
+  for (uint32_t t = s0; t < s1; ++t) rank += (A.stag_tmp[t] < tag) ? 1u : 0u;
+  const uint32_t d = s0 + rank;
+  const uint32_t m = A.meta[tag];
+  const SysDev& S = A.sys[meta_sys(m)];
+  int c[3];
+  cell_decode(S, cell, c[0], c[1], c[2]);
+  const double xv[3] = {A.x[tag], A.x[n + tag], A.x[2 * n + tag]};
+  double o[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) o[d] = wrap_coord(S, d, xv[d]) - fma((double)c[d], S.cs[d], S.grid_lo[d]);
-    const uint32_t mol = A.mol ? (uint32_t)A.mol[tag] : 0u;
-    A.scell[s] = cell;
-    put_rec<R>(A.rec, s, o[0], o[1], o[2], meta_type(m) | (mol << 3));
+  for (int k = 0; k < 3; ++k) {  // offset from the cell centre: |o| <= cs/2 keeps float32 rounding small
+    o[k] = xv[k] - fma((double)c[k] + 0.5, S.cs[k], S.grid_lo[k]);
+    if (S.periodic[k]) o[k] = wrap_min_image(o[k], S.box_len[k]);  // the image the binning chose
   }
+  const uint32_t mol = A.mol ? (uint32_t)A.mol[tag] : 0u;
+  A.stag[d] = tag;
+  A.scell[d] = cell;
+  put_rec<R>(A.rec, d, o[0], o[1], o[2], meta_type(m) | (mol << 3));
 }
 
 // ---------------------------------------------------------------------------
@@ -606,54 +646,183 @@ __global__ void k_nopair(DevArrays A, int bonds, int walls) {
 // ---------------------------------------------------------------------------
 // integrator
 // ---------------------------------------------------------------------------
-template <typename R> __device__ __forceinline__ void load_f(const void* f, int64_t i, double& fx, double& fy,
-                                                             double& fz);
-template <> __device__ __forceinline__ void load_f<float>(const void* f, int64_t i, double& fx, double& fy,
-                                                          double& fz) {
-  const float4 v = reinterpret_cast<const float4*>(f)[i];
-  fx = v.x; fy = v.y; fz = v.z;
-}
-template <> __device__ __forceinline__ void load_f<double>(const void* f, int64_t i, double& fx, double& fy,
-                                                           double& fz) {
-  const double4_32a v = reinterpret_cast<const double4_32a*>(f)[i];
-  fx = v.x; fy = v.y; fz = v.z;
+// float64 reciprocal and inverse square root without the long divide/sqrt
+// sequences: a float32 hardware estimate refined by Newton-Raphson steps
+// (Newton's method on 1/e - v = 0 and on 1/e^2 - v = 0), each step doubling
+// the correct bits (2^-22 -> 2^-44 -> full float64). v must be a positive
+// normal number inside the float32 range; otherwise the float64 operator is
+// used.
+__device__ __forceinline__ double nr_rcp(double v) {
+  const float vf = (float)v;
+  if (!(vf > 1.0e-37f && vf < 1.0e37f)) return 1.0 / v;
+  double e = (double)__frcp_rn(vf);
+  e = fma(e, fma(-v, e, 1.0), e);
+  e = fma(e, fma(-v, e, 1.0), e);
+  return e;
 }
 
-// Algorithm S1 force combination at step k for particle i (in double):
+__device__ __forceinline__ double nr_rsqrt(double v) {
+  const float vf = (float)v;
+  if (!(vf > 1.0e-37f && vf < 1.0e37f)) return 1.0 / sqrt(v);
+  double r = (double)rsqrtf(vf);
+  const double hv = 0.5 * v;
+  r = r * fma(-hv * r, r, 1.5);
+  r = r * fma(-hv * r, r, 1.5);
+  return r;
+}
+
+// g at a point, keeping what the gradient needs (the gradient is formed only
+// when a Newton update needs it).
+struct GEval {
+  double g, ux, uy, uz, q;
+};
+
+__device__ __forceinline__ GEval surf_g(const SysDev& S, double x, double y, double z) {
+  GEval e;
+  double dx = x - S.c[0], dy = y - S.c[1], dz = z - S.c[2];
+  e.q = 0.0;
+  switch (S.kind) {
+    case kPlane:
+      e.g = fma(S.p[0], dx, fma(S.p[1], dy, S.p[2] * dz));
+      break;
+    case kSphere:
+      e.g = fma(dx, dx, fma(dy, dy, fma(dz, dz, -S.p[0] * S.p[0])));
+      break;
+    case kEllipsoid:
+      dx *= S.inv_a2[0];  // keep a_d^-2 (x_d - c_d)
+      dy *= S.inv_a2[1];
+      dz *= S.inv_a2[2];
+      e.g = fma(dx, x - S.c[0], fma(dy, y - S.c[1], fma(dz, z - S.c[2], -1.0)));
+      break;
+    case kTorus: {
+      const double rho2 = fma(dx, dx, dy * dy);
+      const double ir = nr_rsqrt(rho2);
+      const double t = fma(rho2, ir, -S.p[0]);  // rho - R
+      e.q = 2.0 * t * ir;
+      e.g = fma(t, t, fma(dz, dz, -S.p[1] * S.p[1]));
+      break;
+    }
+    case kBump: {
+      if (S.periodic[0]) dx = wrap_min_image(dx, S.box_len[0]);
+      if (S.periodic[1]) dy = wrap_min_image(dy, S.box_len[1]);
+      const double w2 = S.p[1] * S.p[1];
+      const double ex = S.p[0] * exp(-fma(dx, dx, dy * dy) / (2.0 * w2));
+      e.q = ex / w2;
+      e.g = dz - ex;
+      break;
+    }
+    case kCylinder:
+      if (S.axis == 0) dx = 0.0;
+      else if (S.axis == 1) dy = 0.0;
+      else dz = 0.0;
+      e.g = fma(dx, dx, fma(dy, dy, fma(dz, dz, -S.p[0] * S.p[0])));
+      break;
+    default:
+      e.g = 0.0;
+  }
+  e.ux = dx; e.uy = dy; e.uz = dz;
+  return e;
+}
+
+__device__ __forceinline__ void surf_n(const SysDev& S, const GEval& e, double& nx, double& ny, double& nz) {
+  switch (S.kind) {
+    case kPlane: nx = S.p[0]; ny = S.p[1]; nz = S.p[2]; break;
+    case kTorus: nx = e.q * e.ux; ny = e.q * e.uy; nz = 2.0 * e.uz; break;
+    case kBump: nx = e.q * e.ux; ny = e.q * e.uy; nz = 1.0; break;
+    case kSphere:
+    case kEllipsoid:
+    case kCylinder: nx = 2.0 * e.ux; ny = 2.0 * e.uy; nz = 2.0 * e.uz; break;
+    default: nx = ny = nz = 0.0;
+  }
+}
+
+template <typename R> struct Force3 { R x, y, z; };
+
+template <typename R> __device__ __forceinline__ Force3<R> load_f3(const void* f, int64_t i);
+template <> __device__ __forceinline__ Force3<float> load_f3<float>(const void* f, int64_t i) {
+  const float4 v = reinterpret_cast<const float4*>(f)[i];
+  return {v.x, v.y, v.z};
+}
+template <> __device__ __forceinline__ Force3<double> load_f3<double>(const void* f, int64_t i) {
+  const double4_32a v = reinterpret_cast<const double4_32a*>(f)[i];
+  return {v.x, v.y, v.z};
+}
+
+template <typename R> __device__ __forceinline__ R sys_gamma(const SysDev& S);
+template <> __device__ __forceinline__ float sys_gamma<float>(const SysDev& S) { return S.gamma_f; }
+template <> __device__ __forceinline__ double sys_gamma<double>(const SysDev& S) { return S.gamma; }
+template <typename R> __device__ __forceinline__ R sys_comb(const SysDev& S);
+template <> __device__ __forceinline__ float sys_comb<float>(const SysDev& S) { return S.comb_f; }
+template <> __device__ __forceinline__ double sys_comb<double>(const SysDev& S) { return S.comb; }
+template <typename R> __device__ __forceinline__ R noise_amp(const SysDev& S, const TypeTable* T, uint32_t ty);
+template <> __device__ __forceinline__ float noise_amp<float>(const SysDev& S, const TypeTable* T, uint32_t ty) {
+  return S.noise_unit_f * T->sqrt_mass_f[ty];
+}
+template <> __device__ __forceinline__ double noise_amp<double>(const SysDev& S, const TypeTable* T, uint32_t ty) {
+  return S.noise_unit * T->sqrt_mass[ty];
+}
+
+// Algorithm S1 force combination at step k for one particle, in R:
 //   first step after a set state:  F = f - gamma p + f_r^k
 //   otherwise:  F = [f - gamma p^{k-1/2} + (f_r^k + f_r^{k-1})/2] / (1 + gamma dt/2)
-// with f_r = sqrt(2 m kT gamma / dt) xi, xi from Philox (noise in R).
+// with f_r = sqrt(2 m kT gamma / dt) xi, xi drawn from Philox in R.
 template <typename R>
-__device__ __forceinline__ void combine(const SysDev& S, uint32_t pid, unsigned long long k, int mode,
-                                        double sqm, double fx, double fy, double fz, double px,
-                                        double py, double pz, double& Fx, double& Fy, double& Fz) {
-  double nx = 0.0, ny = 0.0, nz = 0.0;
-  if (S.noise_unit > 0.0) {
+__device__ __forceinline__ Force3<R> combine(const SysDev& S, const TypeTable* T, uint32_t ty, uint32_t pid,
+                                             unsigned long long k, int mode, Force3<R> f, double px, double py,
+                                             double pz) {
+  R nx = 0, ny = 0, nz = 0;
+  const R amp = noise_amp<R>(S, T, ty);
+  if (amp > (R)0) {
     R gx, gy, gz;
     gauss3(S.seed_lo, S.replica, pid, k, gx, gy, gz);
     if (mode == 0) {
-      nx = (double)gx; ny = (double)gy; nz = (double)gz;
+      nx = amp * gx; ny = amp * gy; nz = amp * gz;
     } else {
       R hx, hy, hz;
       gauss3(S.seed_lo, S.replica, pid, k - 1ull, hx, hy, hz);
-      nx = 0.5 * ((double)gx + (double)hx);
-      ny = 0.5 * ((double)gy + (double)hy);
-      nz = 0.5 * ((double)gz + (double)hz);
+      const R ha = (R)0.5 * amp;
+      nx = ha * (gx + hx); ny = ha * (gy + hy); nz = ha * (gz + hz);
     }
-    const double a = S.noise_unit * sqm;
-    nx *= a; ny *= a; nz *= a;
   }
-  if (mode == 0) {
-    Fx = fx - S.gamma * px + nx;
-    Fy = fy - S.gamma * py + ny;
-    Fz = fz - S.gamma * pz + nz;
-  } else {
-    Fx = S.comb * (fx - S.gamma * px + nx);
-    Fy = S.comb * (fy - S.gamma * py + ny);
-    Fz = S.comb * (fz - S.gamma * pz + nz);
+  const R gam = sys_gamma<R>(S);
+  Force3<R> F;
+  F.x = f.x - gam * (R)px + nx;
+  F.y = f.y - gam * (R)py + ny;
+  F.z = f.z - gam * (R)pz + nz;
+  if (mode != 0) {
+    const R c = sys_comb<R>(S);
+    F.x *= c; F.y *= c; F.z *= c;
+  }
+  return F;
+}
+
+// Momentum half of Algorithm 1 at x^k: p^k = p^{k-1/2} + h (F - mu n) with
+// n.p^k = 0. The residual is linear in (p, mu), so the Newton iteration ends
+// after one exact step: the projection p - (n.p / n.n) n.
+__device__ __forceinline__ void momentum_half(double h, double Fx, double Fy, double Fz, bool con, double nx,
+                                              double ny, double nz, double inv_nn, double& px, double& py,
+                                              double& pz) {
+  px = fma(h, Fx, px); py = fma(h, Fy, py); pz = fma(h, Fz, pz);
+  if (con) {
+    const double sc = fma(nx, px, fma(ny, py, nz * pz)) * inv_nn;
+    px = fma(-sc, nx, px); py = fma(-sc, ny, py); pz = fma(-sc, nz, pz);
   }
 }
 
+__device__ __forceinline__ bool finite_bits(double v) {
+  return (__double2hiint(v) & 0x7ff00000) != 0x7ff00000;
+}
+
+// Combine (R) + momentum half of step k + position half of step k+1 (float64),
+// then the cell of x^{k+1} and its rank in the bucket counter.
+//
+// Position half of Algorithm 1: with y = x + (dt/m)(p + h F) and
+// a = dt^2/(2m), x^{k+1} = y - a lambda n0 with n0 = grad g(x^k). After its
+// first update the residual r_x of Algorithm 1 is zero, and the 4x4 Newton
+// step reduces to lambda += g(x) / (a n1.n0), n1 = grad g(x) at the iterate
+// (n1 = n0 for the frozen-normal variant). Stop when |g| < eta |n|, with
+// |n| = |n0| (the two differ by |x - x^k| times the curvature), or when the
+// update falls under 4 ulp of the position (round-off floor).
 template <typename R, bool BIN>
 __global__ void __launch_bounds__(256) k_integrate(DevArrays A) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -663,73 +832,69 @@ __global__ void __launch_bounds__(256) k_integrate(DevArrays A) {
   const int mode = *A.mode;
   const uint32_t m = A.meta[i];
   const SysDev& S = A.sys[meta_sys(m)];
+  const TypeTable* T = A.types;
   const uint32_t ty = meta_type(m);
-  const double inv_m = A.types->inv_mass[ty];
   const double x = A.x[i], y = A.x[n + i], z = A.x[2 * n + i];
   double px = A.ph[i], py = A.ph[n + i], pz = A.ph[2 * n + i];
-  double fx, fy, fz;
-  load_f<R>(A.f, i, fx, fy, fz);
-  double Fx, Fy, Fz;
-  combine<R>(S, (uint32_t)(i - S.first), k, mode, A.types->sqrt_mass[ty], fx, fy, fz, px, py, pz, Fx, Fy,
-             Fz);
+  const Force3<R> Fr = combine<R>(S, T, ty, (uint32_t)(i - S.first), k, mode, load_f3<R>(A.f, i), px, py, pz);
+  const double Fx = (double)Fr.x, Fy = (double)Fr.y, Fz = (double)Fr.z;
   const double h = S.half_dt;
   const bool con = meta_con(m);
-  double n0x = 0.0, n0y = 0.0, n0z = 0.0;
-  if (con) surf_eval(S, x, y, z, n0x, n0y, n0z);
-  if (mode != 0) {
-    // momentum half of Algorithm 1 at x^k: p^k = p^{k-1/2} + h (F - mu n)
-    // with n.p^k = 0; the residual is linear in (p, mu), so the Newton
-    // iteration ends after one exact step: a tangent-plane projection.
-    px += h * Fx; py += h * Fy; pz += h * Fz;
-    if (con) {
-      const double sc = (n0x * px + n0y * py + n0z * pz) / (n0x * n0x + n0y * n0y + n0z * n0z);
-      px -= sc * n0x; py -= sc * n0y; pz -= sc * n0z;
-    }
+  double n0x = 0.0, n0y = 0.0, n0z = 0.0, nn = 1.0, inv_nn = 0.0;
+  if (con) {
+    surf_n(S, surf_g(S, x, y, z), n0x, n0y, n0z);
+    nn = fma(n0x, n0x, fma(n0y, n0y, n0z * n0z));
+    inv_nn = nr_rcp(nn);
   }
-  // position half of Algorithm 1 for step k+1. With r_x = 0 after the first
-  // update, the 4x4 Newton of Algorithm 1 reduces to a scalar Newton on
-  // lambda: x(lambda) = y - a lambda n0, lambda += g(x) / (a n1.n0).
-  double qx = px + h * Fx, qy = py + h * Fy, qz = pz + h * Fz;  // p^{k+1/2} before the constraint
-  const double dtm = S.dt * inv_m;
+  if (mode != 0) momentum_half(h, Fx, Fy, Fz, con, n0x, n0y, n0z, inv_nn, px, py, pz);
+  double qx = fma(h, Fx, px), qy = fma(h, Fy, py), qz = fma(h, Fz, pz);  // p^{k+1/2} before the constraint
+  const double dtm = S.dt * T->inv_mass[ty];
   double xn = fma(dtm, qx, x), yn = fma(dtm, qy, y), zn = fma(dtm, qz, z);
   if (con) {
     const double a = h * dtm;  // dt^2 / (2m)
     const double yx = xn, yy = yn, yz = zn;
+    const double tol2nn = S.tol2 * nn;
+    const double inv_a_nn = S.frozen ? inv_nn * nr_rcp(a) : 0.0;
     double lam = 0.0;
     bool ok = false;
     for (int it = 0; it <= S.max_newton; ++it) {
-      double n1x, n1y, n1z;
-      const double g = surf_eval(S, xn, yn, zn, n1x, n1y, n1z);
-      const double gn = sqrt(n1x * n1x + n1y * n1y + n1z * n1z);
-      if (fabs(g) < S.tol * gn) {
+      const GEval e = surf_g(S, xn, yn, zn);
+      if (e.g * e.g < tol2nn) {
         ok = true;
         break;
       }
       if (it == S.max_newton) break;
+      double dl;
       if (S.frozen) {
-        n1x = n0x; n1y = n0y; n1z = n0z;
+        dl = e.g * inv_a_nn;
+      } else {
+        double n1x, n1y, n1z;
+        surf_n(S, e, n1x, n1y, n1z);
+        dl = e.g * nr_rcp(a * fma(n1x, n0x, fma(n1y, n0y, n1z * n0z)));
       }
-      const double dl = g / (a * (n1x * n0x + n1y * n0y + n1z * n0z));
       lam += dl;
-      xn = fma(-a * lam, n0x, yx);
-      yn = fma(-a * lam, n0y, yy);
-      zn = fma(-a * lam, n0z, yz);
-      const double stepmax = fabs(dl) * a * fmax(fabs(n0x), fmax(fabs(n0y), fabs(n0z)));
-      const double xm = fmax(fabs(xn), fmax(fabs(yn), fabs(zn)));
-      if (stepmax <= 4.0 * xm * DBL_EPSILON) {  // round-off floor (4 ulp)
-        ok = true;
-        break;
+      const double al = a * lam;
+      xn = fma(-al, n0x, yx); yn = fma(-al, n0y, yy); zn = fma(-al, n0z, yz);
+      if (it > 0) {  // round-off floor: the update is below 4 ulp of the position
+        const double step = fabs(dl) * a * fmax(fabs(n0x), fmax(fabs(n0y), fabs(n0z)));
+        if (step <= 4.0 * DBL_EPSILON * fmax(fabs(xn), fmax(fabs(yn), fabs(zn)))) {
+          ok = true;
+          break;
+        }
       }
     }
     if (!ok) flag(A.status, kFlagRattle);
-    qx -= h * lam * n0x; qy -= h * lam * n0y; qz -= h * lam * n0z;
+    const double hl = h * lam;
+    qx = fma(-hl, n0x, qx); qy = fma(-hl, n0y, qy); qz = fma(-hl, n0z, qz);
   }
-  if (!finite3(xn, yn, zn) || !finite3(qx, qy, qz)) flag(A.status, kFlagNonfinite);
+  if (!(finite_bits(xn) && finite_bits(yn) && finite_bits(zn) && finite_bits(qx) && finite_bits(qy) &&
+        finite_bits(qz)))
+    flag(A.status, kFlagNonfinite);
   A.x[i] = xn; A.x[n + i] = yn; A.x[2 * n + i] = zn;
   A.ph[i] = qx; A.ph[n + i] = qy; A.ph[2 * n + i] = qz;
   if (BIN) {
     bool out = false;
-    const uint32_t cell = cell_of(S, xn, yn, zn, out);
+    const uint32_t cell = cell_of<R>(S, xn, yn, zn, out);
     if (out) flag(A.status, kFlagOutOfGrid);
     A.cell[i] = cell;
     A.rank[i] = atomicAdd(&A.count[bucket_of(cell, A.hashed, A.log_t)], 1u);
@@ -741,7 +906,8 @@ __global__ void k_advance(unsigned long long* step, int32_t* mode) {
   *mode = 1;
 }
 
-// p^k = momentum half of Algorithm 1 from p^{k-1/2} and F^k (state unchanged).
+// p^k = momentum half of Algorithm 1 from p^{k-1/2} and F^k (state unchanged),
+// with the same arithmetic as k_integrate.
 template <typename R>
 __global__ void k_finish(DevArrays A) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -756,19 +922,16 @@ __global__ void k_finish(DevArrays A) {
   const uint32_t m = A.meta[i];
   const SysDev& S = A.sys[meta_sys(m)];
   const uint32_t ty = meta_type(m);
+  const double x = A.x[i], y = A.x[n + i], z = A.x[2 * n + i];
   double px = A.ph[i], py = A.ph[n + i], pz = A.ph[2 * n + i];
-  double fx, fy, fz;
-  load_f<R>(A.f, i, fx, fy, fz);
-  double Fx, Fy, Fz;
-  combine<R>(S, (uint32_t)(i - S.first), k, 1, A.types->sqrt_mass[ty], fx, fy, fz, px, py, pz, Fx, Fy, Fz);
-  const double h = S.half_dt;
-  px += h * Fx; py += h * Fy; pz += h * Fz;
-  if (meta_con(m)) {
-    double nx, ny, nz;
-    surf_eval(S, A.x[i], A.x[n + i], A.x[2 * n + i], nx, ny, nz);
-    const double sc = (nx * px + ny * py + nz * pz) / (nx * nx + ny * ny + nz * nz);
-    px -= sc * nx; py -= sc * ny; pz -= sc * nz;
+  const Force3<R> Fr = combine<R>(S, A.types, ty, (uint32_t)(i - S.first), k, 1, load_f3<R>(A.f, i), px, py, pz);
+  const bool con = meta_con(m);
+  double nx = 0.0, ny = 0.0, nz = 0.0, inv_nn = 0.0;
+  if (con) {
+    surf_n(S, surf_g(S, x, y, z), nx, ny, nz);
+    inv_nn = nr_rcp(fma(nx, nx, fma(ny, ny, nz * nz)));
   }
+  momentum_half(S.half_dt, (double)Fr.x, (double)Fr.y, (double)Fr.z, con, nx, ny, nz, inv_nn, px, py, pz);
   A.pk[i] = px; A.pk[n + i] = py; A.pk[2 * n + i] = pz;
 }
 
@@ -801,63 +964,105 @@ __global__ void k_get_forces(DevArrays A, double* fa, double* ua) {
   if (ua) ua[i] = (double)v.w;
 }
 
+
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* a, double v) {
   atomicMax(a, (unsigned long long)__double_as_longlong(v));
 }
 
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Residuals of Section 2.2 (g = 0, n.v = 0): per-warp maxima, one atomic per warp.
 __global__ void k_residual(DevArrays A, unsigned long long* out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = A.n;
-  if (i >= n) return;
-  const uint32_t m = A.meta[i];
-  if (!meta_con(m)) return;
-  const SysDev& S = A.sys[meta_sys(m)];
-  double nx, ny, nz;
-  const double g = surf_eval(S, A.x[i], A.x[n + i], A.x[2 * n + i], nx, ny, nz);
-  const double gn = sqrt(nx * nx + ny * ny + nz * nz);
-  const double inv_m = A.types->inv_mass[meta_type(m)];
-  const double nv = (nx * A.pk[i] + ny * A.pk[n + i] + nz * A.pk[2 * n + i]) * inv_m;
-  atomic_max_nonneg(&out[0], fabs(g) / gn);
-  atomic_max_nonneg(&out[1], fabs(g));
-  atomic_max_nonneg(&out[2], fabs(nv) / gn);
+  double r0 = 0.0, r1 = 0.0, r2 = 0.0;
+  if (i < n) {
+    const uint32_t m = A.meta[i];
+    if (meta_con(m)) {
+      const SysDev& S = A.sys[meta_sys(m)];
+      double nx, ny, nz;
+      const double g = surf_eval(S, A.x[i], A.x[n + i], A.x[2 * n + i], nx, ny, nz);
+      const double gn = sqrt(nx * nx + ny * ny + nz * nz);
+      const double inv_m = A.types->inv_mass[meta_type(m)];
+      const double nv = (nx * A.pk[i] + ny * A.pk[n + i] + nz * A.pk[2 * n + i]) * inv_m;
+      r0 = fabs(g) / gn;
+      r1 = fabs(g);
+      r2 = fabs(nv) / gn;
+    }
+  }
+  r0 = warp_max(r0);
+  r1 = warp_max(r1);
+  r2 = warp_max(r2);
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg(&out[0], r0);
+    atomic_max_nonneg(&out[1], r1);
+    atomic_max_nonneg(&out[2], r2);
+  }
 }
 
+// Per-system sums and maxima; a warp whose particles belong to one system
+// reduces in registers and issues one atomic per quantity.
 template <typename R>
 __global__ void k_observables(DevArrays A, double* obs) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = A.n;
-  if (i >= n) return;
-  const uint32_t m = A.meta[i];
-  const uint32_t sid = meta_sys(m);
-  const SysDev& S = A.sys[sid];
-  const uint32_t ty = meta_type(m);
-  const double inv_m = A.types->inv_mass[ty];
-  const double px = A.pk[i], py = A.pk[n + i], pz = A.pk[2 * n + i];
-  const double x = A.x[i], y = A.x[n + i], z = A.x[2 * n + i];
-  const double dx = x - A.xref[i], dy = y - A.xref[n + i], dz = z - A.xref[2 * n + i];
-  using V = typename V4<R>::T;
-  const V f = reinterpret_cast<const V*>(A.f)[i];
+  double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  uint32_t sid = 0xffffffffu;
+  if (i < n) {
+    const uint32_t m = A.meta[i];
+    sid = meta_sys(m);
+    const SysDev& S = A.sys[sid];
+    const double inv_m = A.types->inv_mass[meta_type(m)];
+    const double px = A.pk[i], py = A.pk[n + i], pz = A.pk[2 * n + i];
+    const double x = A.x[i], y = A.x[n + i], z = A.x[2 * n + i];
+    const double dx = x - A.xref[i], dy = y - A.xref[n + i], dz = z - A.xref[2 * n + i];
+    using V = typename V4<R>::T;
+    const V f = reinterpret_cast<const V*>(A.f)[i];
+    v[0] = 0.5 * (px * px + py * py + pz * pz) * inv_m;
+    v[1] = (double)f.w;
+    v[2] = dx * dx + dy * dy + dz * dz;
+    if (S.kind == kSphere) {
+      const double R2 = S.p[0] * S.p[0];
+      v[3] = ((A.xref[i] - S.c[0]) * (x - S.c[0]) + (A.xref[n + i] - S.c[1]) * (y - S.c[1]) +
+              (A.xref[2 * n + i] - S.c[2]) * (z - S.c[2])) / R2;
+    }
+    const bool con = meta_con(m);
+    v[4] = con ? 2.0 : 3.0;
+    if (con) {
+      double nx, ny, nz;
+      const double g = surf_eval(S, x, y, z, nx, ny, nz);
+      const double gn = sqrt(nx * nx + ny * ny + nz * nz);
+      v[5] = fabs(g) / gn;
+      v[6] = fabs((nx * px + ny * py + nz * pz) * inv_m) / gn;
+    }
+    v[7] = 1.0;
+  }
+  const uint32_t s0 = __shfl_sync(0xffffffffu, sid, 0);
+  const bool uniform = __all_sync(0xffffffffu, sid == s0 || sid == 0xffffffffu);
+  if (uniform) {
+    if (s0 == 0xffffffffu) return;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = (q == 5 || q == 6) ? warp_max(v[q]) : warp_sum(v[q]);
+    if ((threadIdx.x & 31) != 0) return;
+    sid = s0;
+  } else if (sid == 0xffffffffu) {
+    return;
+  }
   double* o = obs + 8 * (int64_t)sid;
-  atomicAdd(&o[0], 0.5 * (px * px + py * py + pz * pz) * inv_m);
-  atomicAdd(&o[1], (double)f.w);
-  atomicAdd(&o[2], dx * dx + dy * dy + dz * dz);
-  if (S.kind == kSphere) {
-    const double R2 = S.p[0] * S.p[0];
-    const double dot = (A.xref[i] - S.c[0]) * (x - S.c[0]) + (A.xref[n + i] - S.c[1]) * (y - S.c[1]) +
-                       (A.xref[2 * n + i] - S.c[2]) * (z - S.c[2]);
-    atomicAdd(&o[3], dot / R2);
+  for (int q = 0; q < 8; ++q) {
+    if (q == 5 || q == 6) atomic_max_nonneg(reinterpret_cast<unsigned long long*>(&o[q]), v[q]);
+    else if (v[q] != 0.0) atomicAdd(&o[q], v[q]);
   }
-  const bool con = meta_con(m);
-  atomicAdd(&o[4], con ? 2.0 : 3.0);
-  if (con) {
-    double nx, ny, nz;
-    const double g = surf_eval(S, x, y, z, nx, ny, nz);
-    const double gn = sqrt(nx * nx + ny * ny + nz * nz);
-    atomic_max_nonneg(reinterpret_cast<unsigned long long*>(&o[5]), fabs(g) / gn);
-    atomic_max_nonneg(reinterpret_cast<unsigned long long*>(&o[6]),
-                      fabs((nx * px + ny * py + nz * pz) * inv_m) / gn);
-  }
-  atomicAdd(&o[7], 1.0);
 }
 
 // ---------------------------------------------------------------------------
@@ -884,9 +1089,10 @@ cudaError_t launch_restore(const DevArrays& A, const double* d_x, const double* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_bin(const DevArrays& A, cudaStream_t st) {
+cudaError_t launch_bin(const DevArrays& A, int precision, cudaStream_t st) {
   if (A.n == 0) return cudaSuccess;
-  k_bin<<<grid_for(A.n, 256), 256, 0, st>>>(A);
+  if (precision == 0) k_bin<double><<<grid_for(A.n, 256), 256, 0, st>>>(A);
+  else k_bin<float><<<grid_for(A.n, 256), 256, 0, st>>>(A);
   return cudaGetLastError();
 }
 
@@ -924,8 +1130,8 @@ cudaError_t launch_cells_after_bin(const DevArrays& A, int advance, cudaStream_t
 
 cudaError_t launch_bucket_build(const DevArrays& A, int precision, cudaStream_t st) {
   if (A.n == 0) return cudaSuccess;
-  if (precision == 0) k_bucket_build<double><<<grid_for(A.nbucket, 256), 256, 0, st>>>(A);
-  else k_bucket_build<float><<<grid_for(A.nbucket, 256), 256, 0, st>>>(A);
+  if (precision == 0) k_bucket_build<double><<<grid_for(A.n, 256), 256, 0, st>>>(A);
+  else k_bucket_build<float><<<grid_for(A.n, 256), 256, 0, st>>>(A);
   return cudaGetLastError();
 }
 

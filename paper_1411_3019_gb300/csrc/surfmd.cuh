@@ -40,7 +40,8 @@ struct SysDev {
   double dt, half_dt, kT, gamma;
   double comb;               // 1 / (1 + gamma dt / 2)
   double noise_unit;         // sqrt(2 kT gamma / dt); times sqrt(m) per particle
-  double tol;
+  double tol, tol2;           // RATTLE tolerance and its square
+  float gamma_f, comb_f, noise_unit_f;
   int32_t max_newton, frozen;
   // box and cell grid
   double box_lo[3], box_len[3];
@@ -48,6 +49,7 @@ struct SysDev {
   int32_t pad0;
   double grid_lo[3], cs[3], inv_cs[3];
   float cs_f[3];
+  float grid_lo_f[3], inv_cs_f[3], box_lo_f[3], box_len_f[3];  // float32 binning
   int32_t nc[3];
   uint32_t cell_base;
   // bonds, exclusions, walls
@@ -73,6 +75,7 @@ struct TypeTable {
   float rc2_f[kMaxTypes][kMaxTypes];
   float shift_f[kMaxTypes][kMaxTypes];
   double mass[kMaxTypes], inv_mass[kMaxTypes], sqrt_mass[kMaxTypes];
+  float sqrt_mass_f[kMaxTypes];
 };
 
 template <typename R> struct V4;
@@ -98,7 +101,8 @@ struct DevArrays {
   uint32_t* count;      // [T] bucket occupancy
   uint32_t* start;      // [T+1] bucket start
   uint32_t* blocksum;   // [scan blocks]
-  uint32_t* stag;       // [n] sorted slot -> particle
+  uint32_t* stag;       // [n] sorted slot -> particle (canonical order)
+  uint32_t* stag_tmp;   // [n] slot -> particle in atomic order (before the canonical sort)
   uint32_t* scell;      // [n] sorted slot -> cell id
   void* rec;            // [n] float4 / double4_32a cell-relative offsets + type/mol bits
   const SysDev* sys;    // [nsys]

@@ -22,13 +22,24 @@ def _expected(h, systems, x):
         prm = sy["params"]
         xs = x[off:off + sy["n"]]
         c = np.zeros((sy["n"], 3), np.int64)
+        mixed = prm["precision"] in ("mixed", 1)
         for d in range(3):
-            v = xs[:, d].copy()
-            if prm["periodic"][d]:
-                lo, L = prm["box_lo"][d], prm["box_hi"][d] - prm["box_lo"][d]
-                r = v - lo
-                v = lo + (r - L * np.floor(r / L))
-            t = (v - gi["lo"][d]) * (1.0 / gi["cs"][d])
+            if mixed:  # float32 binning with round-to-nearest operations
+                f32 = np.float32
+                v = xs[:, d].astype(f32)
+                if prm["periodic"][d]:
+                    lo = f32(prm["box_lo"][d])
+                    L = f32(prm["box_hi"][d] - prm["box_lo"][d])
+                    r = (v - lo).astype(f32)
+                    v = (lo + (r - (L * np.floor(r / L)).astype(f32)).astype(f32)).astype(f32)
+                t = ((v - f32(gi["lo"][d])).astype(f32) * f32(1.0 / gi["cs"][d])).astype(f32)
+            else:
+                v = xs[:, d].copy()
+                if prm["periodic"][d]:
+                    lo, L = prm["box_lo"][d], prm["box_hi"][d] - prm["box_lo"][d]
+                    r = v - lo
+                    v = lo + (r - L * np.floor(r / L))
+                t = (v - gi["lo"][d]) * (1.0 / gi["cs"][d])
             c[:, d] = np.clip(np.floor(t), 0, gi["nc"][d] - 1)
         nc = gi["nc"].astype(np.int64)
         cells[off:off + sy["n"]] = gi["base"] + c[:, 0] + nc[0] * (c[:, 1] + nc[1] * c[:, 2])
@@ -47,7 +58,9 @@ def test_cell_list_is_the_definition(case):
     if case == "dense_sphere":
         systems = [I.sphere_system(n=1000, R=10.0, seed=1, dmin=0.8, precision="fp64")]
     elif case == "hashed_batch":
-        systems = I.c2_ellipsoid_torus(n_ell=3000, n_tor=1000, seed=3)
+        # sparse particles on large surfaces: a grid of ~10^8 cells, so buckets are hashed
+        systems = [I.sphere_system(n=3000, R=150.0, seed=3, dmin=1.0, precision="mixed", replica=0),
+                   I.sphere_system(n=1000, R=60.0, seed=4, dmin=1.0, precision="mixed", replica=1)]
     else:
         systems = I.c3_bump_crowders(n_surf=500, n_free=1200, seed=6)
     sim = md.Simulation(systems)

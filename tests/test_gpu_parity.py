@@ -7,7 +7,7 @@ import pytest
 
 from paper_1411_3019_gb300 import inputs as I
 
-from parity_util import FORCE_REL, POS_100, force_err, gpu_run, oracle_run, precision_of
+from parity_util import POS_100, assert_forces, gpu_run, oracle_run
 
 pytestmark = pytest.mark.gpu
 
@@ -22,7 +22,7 @@ def test_forces_match_oracle_on_the_plain_workload(precision):
     systems = _c1(precision)
     st, f, u, res, _ = gpu_run(systems, 0)
     _, f_ref, u_ref, _, _ = oracle_run(systems, 0)
-    assert force_err(f, f_ref) <= FORCE_REL[precision]
+    assert_forces(systems, st["x"], f, precision)
     np.testing.assert_allclose(u.sum(), u_ref.sum(), rtol=1e-10 if precision == "fp64" else 1e-5)
     assert np.abs(f_ref).max() > 10.0  # overlapping start: a real test of the pair kernel
 
@@ -43,7 +43,7 @@ def test_trajectory_matches_oracle(precision, nsteps):
     tol = systems[0]["params"]["rattle_tol"]
     assert res["max_g_over_gradg"] < tol
     assert res["max_n_dot_v"] < 1e-9
-    assert force_err(f, f_ref) <= 10 * FORCE_REL[precision]
+    assert_forces(systems, st["x"], f, precision)
     assert obs[0]["ndof"] == 2 * systems[0]["n"]
     assert obs[0]["kT"] == pytest.approx(obs_ref[0]["kT"], rel=1e-6)
 
@@ -61,7 +61,7 @@ SURFACES = {
 }
 
 
-def _surface_system(name, precision, n=600, seed=3):
+def _surface_system(name, precision, n=300, seed=3):
     surf, extra = SURFACES[name]
     prm = I.wca_params(precision=precision, dt=0.002, rattle_tol=1e-12 if precision == "fp64" else 1e-10,
                        seed=seed, **extra)
@@ -79,7 +79,7 @@ def test_every_surface_matches_oracle(name, precision):
     st, f, u, res, _ = gpu_run(systems, 50)
     ref, f_ref, _, res_ref, _ = oracle_run(systems, 50)
     assert np.abs(st["x"] - ref["x"]).max() <= POS_100[precision]
-    assert force_err(f, f_ref) <= 10 * FORCE_REL[precision]
+    assert_forces(systems, st["x"], f, precision)
     assert res["max_g_over_gradg"] < systems[0]["params"]["rattle_tol"]
 
 
@@ -90,7 +90,7 @@ def test_batch_of_replicas_matches_independent_oracles(precision):
     st, f, u, res, obs = gpu_run(systems, 40)
     ref, f_ref, _, _, obs_ref = oracle_run(systems, 40)
     assert np.abs(st["x"] - ref["x"]).max() <= POS_100[precision]
-    assert force_err(f, f_ref) <= 10 * FORCE_REL[precision]
+    assert_forces(systems, st["x"], f, precision)
     assert len(obs) == 6
     for a, b, sy in zip(obs, obs_ref, systems):
         assert a["n"] == sy["n"]
@@ -105,7 +105,7 @@ def test_bead_molecules_match_oracle(precision):
     st, f, u, res, obs = gpu_run(systems, 60)
     ref, f_ref, u_ref, _, obs_ref = oracle_run(systems, 60)
     assert np.abs(st["x"] - ref["x"]).max() <= POS_100[precision]
-    assert force_err(f, f_ref) <= 10 * FORCE_REL[precision]
+    assert_forces(systems, st["x"], f, precision)
     np.testing.assert_allclose(u.sum(), u_ref.sum(), rtol=1e-9 if precision == "fp64" else 1e-5)
     con = systems[0]["constrained"].astype(bool)
     assert obs[0]["ndof"] == 2 * con.sum() + 3 * (~con).sum()
@@ -118,7 +118,7 @@ def test_constrained_and_free_with_walls_match_oracle(precision):
     st, f, u, res, _ = gpu_run(systems, 40)
     ref, f_ref, _, _, _ = oracle_run(systems, 40)
     assert np.abs(st["x"] - ref["x"]).max() <= POS_100[precision]
-    assert force_err(f, f_ref) <= 10 * FORCE_REL[precision]
+    assert_forces(systems, st["x"], f, precision)
 
 
 def test_mixed_tracks_fp64_within_tolerance():

@@ -37,7 +37,7 @@ def test_runs_are_bitwise_repeatable_and_resumable(precision):
 
 def test_torch_device_buffers_and_stream():
     torch = pytest.importorskip("torch")
-    systems = [I.sphere_system(n=800, R=9.0, seed=4, dmin=0.9, precision="mixed")]
+    systems = [I.sphere_system(n=500, R=9.0, seed=4, dmin=0.9, precision="mixed")]
     s = systems[0]
     with md.Simulation(systems) as ref:
         ref.set_state()
