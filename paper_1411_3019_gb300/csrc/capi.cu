@@ -145,6 +145,11 @@ int check_system(const md_surface& s, const md_params& p, SysDev& S, std::string
     default:
       break;
   }
+  for (int d = 0; d < 3; ++d) {
+    S.c_f[d] = (float)S.c[d];
+    S.inv_a2_f[d] = (float)S.inv_a2[d];
+  }
+  for (int d = 0; d < 4; ++d) S.p_f[d] = (float)S.p[d];
   S.dt = p.dt;
   S.half_dt = 0.5 * p.dt;
   S.kT = p.kT;
@@ -468,6 +473,28 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
       S.box_lo_f[d] = (float)S.box_lo[d];
       S.box_len_f[d] = (float)S.box_len[d];
     }
+    // Stencil pruning for surface-bound particles: a neighbour within rc on a
+    // surface of curvature <= kappa lies within rc^2 kappa / 2 of the
+    // particle's tangent plane; the slab is taken twice that plus 1e-3.
+    {
+      const md_surface& sf = surfs[s];
+      double kappa = -1.0;
+      switch (sf.kind) {
+        case MD_SURF_PLANE: kappa = 0.0; break;
+        case MD_SURF_SPHERE: kappa = 1.0 / sf.p[0]; break;
+        case MD_SURF_CYLINDER: kappa = 1.0 / sf.p[0]; break;
+        case MD_SURF_ELLIPSOID: {
+          const double amax = std::max(sf.p[0], std::max(sf.p[1], sf.p[2]));
+          const double amin = std::min(sf.p[0], std::min(sf.p[1], sf.p[2]));
+          kappa = amax / (amin * amin);
+          break;
+        }
+        case MD_SURF_TORUS: kappa = 1.0 / sf.p[1] + 1.0 / (sf.p[0] - sf.p[1]); break;
+        case MD_SURF_GAUSSIAN_BUMP: kappa = 2.0 * std::fabs(sf.p[0]) / (sf.p[1] * sf.p[1]); break;
+        default: break;
+      }
+      S.slab = (h->has_pairs && kappa >= 0.0 && rcmax * kappa < 0.5) ? (float)(rcmax * rcmax * kappa + 1e-3) : 0.0f;
+    }
     S.cell_base = (uint32_t)cell_total;
     cell_total += (uint64_t)S.nc[0] * (uint64_t)S.nc[1] * (uint64_t)S.nc[2];
     if (cell_total >= 0xFFFFFFF0ull) {
@@ -541,6 +568,7 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
   al(dalloc(h, &A.step, 1));
   al(dalloc(h, &A.mode, 1));
   al(dalloc(h, &h->d_first, (size_t)nsys));
+  al(dalloc(h, &A.sys_free, (size_t)nsys));
   al(dalloc(h, &h->d_stage, 9 * n));
   al(dalloc(h, &h->d_stage_i, 2 * n));
   al(dalloc(h, &h->d_stage_u8, n));
@@ -581,6 +609,7 @@ int md_set_stream(md_handle* h, void* cuda_stream) {
 static int set_state_common(md_handle* h, const double* d_x, const double* d_v, const int32_t* d_type,
                             const int32_t* d_mol, const uint8_t* d_con, uint64_t step0) {
   cudaStream_t st = h->stream();
+  CK(h, cudaMemsetAsync(h->A.sys_free, 0, sizeof(int32_t) * (size_t)h->nsys, st));
   CK(h, launch_build_meta(h->A, h->d_first, h->nsys, d_type, d_con, d_mol, 0, st));
   CK(h, launch_set_state(h->A, d_x, d_v, st));
   const unsigned long long k = step0;

@@ -36,6 +36,7 @@ struct SysDev {
   double c[3];               // centre / plane point
   double p[4];               // shape parameters
   double inv_a2[3];          // ellipsoid 1/a_d^2
+  float c_f[3], p_f[4], inv_a2_f[3];  // float32 copies for surface directions
   // integration
   double dt, half_dt, kT, gamma;
   double comb;               // 1 / (1 + gamma dt / 2)
@@ -50,6 +51,7 @@ struct SysDev {
   double grid_lo[3], cs[3], inv_cs[3];
   float cs_f[3];
   float grid_lo_f[3], inv_cs_f[3], box_lo_f[3], box_len_f[3];  // float32 binning
+  float slab;                // tangent-slab half thickness for stencil pruning (0: off)
   int32_t nc[3];
   uint32_t cell_base;
   // bonds, exclusions, walls
@@ -107,6 +109,7 @@ struct DevArrays {
   void* rec;            // [n] float4 / double4_32a cell-relative offsets + type/mol bits
   const SysDev* sys;    // [nsys]
   const TypeTable* types;  // pair and mass tables shared by the systems
+  int32_t* sys_free;    // [nsys] unconstrained particles per system (set with the state)
   uint32_t* status;     // device status word
   unsigned long long* step;  // device step counter k
   int32_t* mode;        // 0: state holds p^k (first step pending); 1: holds p^{k-1/2}
