@@ -127,6 +127,9 @@ class ClockSampler:
 def algorithmic_bytes(kernel: str, n: int, nbucket: int, precision: str) -> float:
     v4 = 16 if precision == "mixed" else 32
     per = {
+        # fused: pair reads (sorted id, cell, own record, meta) + update reads x, p and writes
+        # x, p, cell, rank (+ bucket starts once, counters read-modify-write)
+        "pair_integrate": n * (4 + 4 + v4 + 4 + 24 + 24 + 24 + 24 + 4 + 4) + 4 * (nbucket + 1) + 8 * nbucket,
         # reads: sorted id, cell id, own record, meta; write: force vec4 (+ bucket starts once)
         "pair": n * (4 + 4 + v4 + 4 + v4) + 4 * (nbucket + 1),
         # reads: meta, x, p_half, force vec4; writes: x, p_half, cell, rank; counter RMW

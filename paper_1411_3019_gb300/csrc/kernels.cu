@@ -628,13 +628,11 @@ __device__ __forceinline__ void bonded_terms(const DevArrays& A, const SysDev& S
 // particles, a cell whose box lies farther than the tangent slab from the
 // particle's tangent plane cannot hold a neighbour and is skipped. The bucket
 // ranges of one stencil row are loaded together before its candidates.
+template <typename R> struct Force4 { R x, y, z, u; };
+
 template <typename R, bool BONDS, bool WALLS, bool EXCL>
-__global__ void __launch_bounds__(256) k_pair(DevArrays A) {
-  __shared__ PairTab<R> tab;
-  load_tab<R>(tab, A.types);
-  __syncthreads();
-  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= (uint32_t)A.n) return;
+__device__ __forceinline__ Force4<R> pair_force(const DevArrays& A, const PairTab<R>& tab, uint32_t s,
+                                                uint32_t& tag_out) {
   using Rec = typename RecT<R>::T;
   const Rec* __restrict__ rec = reinterpret_cast<const Rec*>(A.rec);
   const uint32_t* __restrict__ scell = A.scell;
@@ -732,7 +730,20 @@ __global__ void __launch_bounds__(256) k_pair(DevArrays A) {
     }
   }
   if (BONDS || WALLS) bonded_terms<R>(A, S, tag, m, BONDS, WALLS, fx, fy, fz, u);
-  store_f<R>(A.f, tag, fx, fy, fz, u);
+  tag_out = tag;
+  return {fx, fy, fz, u};
+}
+
+template <typename R, bool BONDS, bool WALLS, bool EXCL>
+__global__ void __launch_bounds__(256) k_pair(DevArrays A) {
+  __shared__ PairTab<R> tab;
+  load_tab<R>(tab, A.types);
+  __syncthreads();
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= (uint32_t)A.n) return;
+  uint32_t tag;
+  const Force4<R> f = pair_force<R, BONDS, WALLS, EXCL>(A, tab, s, tag);
+  store_f<R>(A.f, tag, f.x, f.y, f.z, f.u);
 }
 
 // No pair term anywhere: only bonds and walls, in particle order.
@@ -924,10 +935,8 @@ __device__ __forceinline__ bool finite_bits(double v) {
 // |n| = |n0| (the two differ by |x - x^k| times the curvature), or when the
 // update falls under 4 ulp of the position (round-off floor).
 template <typename R, bool BIN>
-__global__ void __launch_bounds__(256) k_integrate(DevArrays A) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void integrate_particle(const DevArrays& A, int64_t i, Force3<R> fr_in) {
   const int64_t n = A.n;
-  if (i >= n) return;
   const unsigned long long k = *A.step;
   const int mode = *A.mode;
   const uint32_t m = A.meta[i];
@@ -936,7 +945,7 @@ __global__ void __launch_bounds__(256) k_integrate(DevArrays A) {
   const uint32_t ty = meta_type(m);
   const double x = A.x[i], y = A.x[n + i], z = A.x[2 * n + i];
   double px = A.ph[i], py = A.ph[n + i], pz = A.ph[2 * n + i];
-  const Force3<R> Fr = combine<R>(S, T, ty, (uint32_t)(i - S.first), k, mode, load_f3<R>(A.f, i), px, py, pz);
+  const Force3<R> Fr = combine<R>(S, T, ty, (uint32_t)(i - S.first), k, mode, fr_in, px, py, pz);
   const double Fx = (double)Fr.x, Fy = (double)Fr.y, Fz = (double)Fr.z;
   const double h = S.half_dt;
   const bool con = meta_con(m);
@@ -1015,6 +1024,13 @@ __global__ void __launch_bounds__(256) k_integrate(DevArrays A) {
     A.cell[i] = cell;
     A.rank[i] = atomicAdd(&A.count[bucket_of(cell, A.hashed, A.log_t)], 1u);
   }
+}
+
+template <typename R, bool BIN>
+__global__ void __launch_bounds__(256) k_integrate(DevArrays A) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  integrate_particle<R, BIN>(A, i, load_f3<R>(A.f, i));
 }
 
 __global__ void k_advance(unsigned long long* step, int32_t* mode) {
