@@ -270,6 +270,35 @@ int md_grid_info(md_handle* h, int32_t sys, double lo[3], double cs[3], int32_t 
 int md_cell_list(md_handle* h, uint32_t* sorted_ids, uint32_t* sorted_cells,
                  uint32_t* bucket_start, uint32_t* nbucket);
 
+/* Forces of one system without allocating device memory. The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate at
+ * the point where they need forces, e.g. a thread working while a CUDA graph
+ * is captured in global mode (device allocation is not permitted then), or
+ * an application whose device memory is all owned by its own allocator.
+ * It computes f = -grad V (pair, bond and wall terms) and the per-particle
+ * energy u at positions d_x, exactly as md_forces does for a handle with the
+ * same surface and parameters, using a scratch array of about 10 MB that the
+ * library reserves in device global memory when its device code is loaded
+ * (each device that loads the library keeps it until the process exits).
+ *   n <= 65536 particles (else MD_ERR_INVALID_ARG); cell grids larger than
+ *   2^18 cells use 2^18 hashed buckets.
+ *   d_x [n][3] float64, d_f [n][3] float64 (required); d_type, d_mol,
+ *   d_constrained, d_u may be NULL (defaults of md_set_state). All pointers
+ *   are device memory owned by the caller.
+ *   cuda_stream: the stream to work on (NULL = legacy stream). The call
+ *   waits for the stream before it returns and reports a particle outside
+ *   the grid as MD_ERR_OUT_OF_GRID.
+ * The first call on a device resolves the scratch address on that device
+ * (and loads the device code if it is not loaded yet); make that first call
+ * before any stream capture. Every call shares the one array: calls that
+ * overlap on the GPU (other threads, other streams) race and must be
+ * serialised by the caller. Errors of this entry point are read with
+ * md_last_error(NULL). */
+int md_forces_noalloc(const md_surface* surf, const md_params* prm, int64_t n,
+                      const double* d_x, const int32_t* d_type, const int32_t* d_mol,
+                      const uint8_t* d_constrained, double* d_f, double* d_u,
+                      void* cuda_stream);
+
 /* Description of the last error on h (or of the last md_create failure
  * when h is NULL). Never NULL. */
 const char* md_last_error(md_handle* h);

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -916,3 +917,209 @@ void md_destroy(md_handle* h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// md_forces_noalloc: forces of one system without any device allocation.
+//
+// For callers that cannot allocate device memory at the point where they need
+// forces -- a host thread working while a CUDA graph is being captured in
+// global mode (cudaMalloc is not permitted then), or an application whose
+// device memory is entirely reserved by its own allocator. All scratch (cell
+// list, records, tables) lives in one fixed-size array in device global
+// memory, reserved when the library's device code is loaded; every device that
+// loads the library keeps it until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNaMaxParticles = 65536;
+constexpr uint32_t kNaMaxBuckets = 1u << 18;
+
+constexpr size_t na_align(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Byte offsets of the regions of the scratch array (each 256-byte aligned).
+struct NaLayout {
+  static constexpr size_t N = (size_t)kNaMaxParticles, T = (size_t)kNaMaxBuckets;
+  static constexpr size_t x = 0;
+  static constexpr size_t f = x + na_align(3 * N * sizeof(double));
+  static constexpr size_t rec = f + na_align(N * sizeof(double4_32a));
+  static constexpr size_t meta = rec + na_align(N * sizeof(double4_32a));
+  static constexpr size_t mol = meta + na_align(N * 4);
+  static constexpr size_t cell = mol + na_align(N * 4);
+  static constexpr size_t rank = cell + na_align(N * 4);
+  static constexpr size_t stag = rank + na_align(N * 4);
+  static constexpr size_t stag_tmp = stag + na_align(N * 4);
+  static constexpr size_t scell = stag_tmp + na_align(N * 4);
+  static constexpr size_t count = scell + na_align(N * 4);
+  static constexpr size_t start = count + na_align(T * 4);
+  static constexpr size_t blocksum = start + na_align((T + 1) * 4);
+  static constexpr size_t sys = blocksum + na_align((T / kScanPerBlock + 1) * 4);
+  static constexpr size_t types = sys + na_align(sizeof(SysDev));
+  static constexpr size_t status = types + na_align(sizeof(TypeTable));
+  static constexpr size_t step = status + 256;
+  static constexpr size_t mode = step + 256;
+  static constexpr size_t sys_free = mode + 256;
+  static constexpr size_t first = sys_free + 256;
+  static constexpr size_t total = first + 256;
+};
+
+}  // namespace
+
+// The scratch array (about 10 MB). In host code its name is only a stand-in
+// for the device symbol; its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_forces_scratch[NaLayout::total];
+
+namespace {
+
+std::mutex g_na_mutex;
+unsigned char* g_na_ptr[256] = {};  // per device: device address of g_forces_scratch
+
+int na_fail(const std::string& m, int code = MD_ERR_INVALID_ARG) { return fail(nullptr, code, m); }
+
+__global__ void k_na_load_x(int64_t n, const double* __restrict__ xa, double* __restrict__ x) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  x[i] = xa[3 * i];
+  x[n + i] = xa[3 * i + 1];
+  x[2 * n + i] = xa[3 * i + 2];
+}
+
+}  // namespace
+
+extern "C" int md_forces_noalloc(const md_surface* surf, const md_params* prm, int64_t n, const double* d_x,
+                                 const int32_t* d_type, const int32_t* d_mol, const uint8_t* d_constrained,
+                                 double* d_f, double* d_u, void* cuda_stream) {
+  if (!surf || !prm) return na_fail("surf and prm must not be NULL");
+  if (n < 0 || n > kNaMaxParticles)
+    return na_fail("md_forces_noalloc: n must be in [0, " + std::to_string(kNaMaxParticles) + "]");
+  if (n > 0 && (!d_x || !d_f)) return na_fail("d_x and d_f must not be NULL");
+  SysDev S;
+  std::string why;
+  if (check_system(*surf, *prm, S, why) != MD_OK) return na_fail("md_forces_noalloc: " + why);
+  TypeTable T;
+  fill_types(*prm, T);
+  double rcmax = 0.0;
+  for (int a = 0; a < prm->ntypes; ++a)
+    for (int b = 0; b < prm->ntypes; ++b) rcmax = std::max(rcmax, prm->rcut[a][b]);
+  const int has_pairs = rcmax > 0.0;
+  const double rc_eff =
+      (double)std::nextafter((float)(std::max(rcmax, prm->cell_size) * (1.0 + 1.0 / 4096.0)), INFINITY);
+  uint64_t cells = 1;
+  for (int d = 0; d < 3; ++d) {
+    if (!has_pairs) {
+      S.nc[d] = 1;
+      S.cs[d] = 1.0;
+      S.grid_lo[d] = 0.0;
+    } else if (prm->periodic[d]) {
+      const double L = prm->box_hi[d] - prm->box_lo[d];
+      const int nc = (int)std::floor(L / rc_eff);
+      if (nc < 3) return na_fail("a periodic axis must be at least 3 cells long");
+      S.nc[d] = nc;
+      S.cs[d] = L / nc;
+      S.grid_lo[d] = prm->box_lo[d];
+    } else {
+      double lo, hi;
+      if (prm->box_hi[d] > prm->box_lo[d]) {
+        lo = prm->box_lo[d];
+        hi = prm->box_hi[d];
+      } else if (surface_extent(*surf, d, lo, hi)) {
+        lo -= 2.0 * rc_eff;
+        hi += 2.0 * rc_eff;
+      } else {
+        return na_fail("give box_lo/box_hi for an axis the surface does not bound");
+      }
+      const double ncd = std::ceil((hi - lo) / rc_eff);
+      if (ncd > 1e6) return na_fail("cell grid too large along one axis");
+      S.nc[d] = std::max(1, (int)ncd);
+      S.cs[d] = rc_eff;
+      S.grid_lo[d] = lo;
+    }
+    S.inv_cs[d] = 1.0 / S.cs[d];
+    S.cs_f[d] = (float)S.cs[d];
+    S.grid_lo_f[d] = (float)S.grid_lo[d];
+    S.inv_cs_f[d] = (float)S.inv_cs[d];
+    S.box_lo_f[d] = (float)S.box_lo[d];
+    S.box_len_f[d] = (float)S.box_len[d];
+    cells *= (uint64_t)S.nc[d];
+  }
+  if (cells >= 0xFFFFFFF0ull) return na_fail("more than 2^32 cells");
+  S.slab = 0.0f;  // every stencil cell is visited
+  S.cell_base = 0;
+  S.first = 0;
+  S.n = n;
+  const int bonds = prm->beads_per_mol > 1, walls = prm->wall_enable != 0, excl = prm->exclude_intramol != 0;
+  // device scratch address, once per device
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return na_fail("no current device", MD_ERR_NO_DEVICE);
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_ptr[dev]) {
+      void* ptr = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&ptr, g_forces_scratch);
+      if (e != cudaSuccess) return na_fail(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e), MD_ERR_CUDA);
+      g_na_ptr[dev] = static_cast<unsigned char*>(ptr);
+    }
+    base = g_na_ptr[dev];
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  DevArrays A{};
+  A.n = n;
+  A.nsys = 1;
+  if (cells <= kNaMaxBuckets) {
+    A.hashed = 0;
+    A.nbucket = (uint32_t)cells;
+    A.log_t = 0;
+  } else {
+    A.hashed = 1;
+    A.nbucket = kNaMaxBuckets;
+    A.log_t = 18;
+  }
+  A.x = reinterpret_cast<double*>(base + NaLayout::x);
+  A.f = base + NaLayout::f;
+  A.rec = base + NaLayout::rec;
+  A.meta = reinterpret_cast<uint32_t*>(base + NaLayout::meta);
+  A.mol = excl ? reinterpret_cast<int32_t*>(base + NaLayout::mol) : nullptr;
+  A.cell = reinterpret_cast<uint32_t*>(base + NaLayout::cell);
+  A.rank = reinterpret_cast<uint32_t*>(base + NaLayout::rank);
+  A.count = reinterpret_cast<uint32_t*>(base + NaLayout::count);
+  A.start = reinterpret_cast<uint32_t*>(base + NaLayout::start);
+  A.blocksum = reinterpret_cast<uint32_t*>(base + NaLayout::blocksum);
+  A.stag = reinterpret_cast<uint32_t*>(base + NaLayout::stag);
+  A.stag_tmp = reinterpret_cast<uint32_t*>(base + NaLayout::stag_tmp);
+  A.scell = reinterpret_cast<uint32_t*>(base + NaLayout::scell);
+  A.sys = reinterpret_cast<const SysDev*>(base + NaLayout::sys);
+  A.types = reinterpret_cast<const TypeTable*>(base + NaLayout::types);
+  A.sys_free = reinterpret_cast<int32_t*>(base + NaLayout::sys_free);
+  A.status = reinterpret_cast<uint32_t*>(base + NaLayout::status);
+  A.step = reinterpret_cast<unsigned long long*>(base + NaLayout::step);
+  A.mode = reinterpret_cast<int32_t*>(base + NaLayout::mode);
+  int64_t* d_first = reinterpret_cast<int64_t*>(base + NaLayout::first);
+  const int64_t zero64 = 0;
+  const uint32_t nn32 = (uint32_t)n;
+  // the array keeps the last call's contents: reset what must start at zero
+  cudaError_t e = cudaMemcpyAsync(base + NaLayout::sys, &S, sizeof(SysDev), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(base + NaLayout::types, &T, sizeof(TypeTable), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_first, &zero64, sizeof(int64_t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(A.start + A.nbucket, &nn32, sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A.count, 0, sizeof(uint32_t) * A.nbucket, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + NaLayout::status, 0, 3 * 256 + 256, st);
+  if (e == cudaSuccess && n > 0) {
+    k_na_load_x<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, d_x, A.x);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = launch_build_meta(A, d_first, 1, d_type, d_constrained, d_mol, 0, st);
+  if (has_pairs) {
+    if (e == cudaSuccess) e = launch_bin(A, prm->precision, st);
+    if (e == cudaSuccess) e = launch_cells_after_bin(A, 0, st);
+    if (e == cudaSuccess) e = launch_bucket_build(A, prm->precision, st);
+  }
+  if (e == cudaSuccess) e = launch_pair(A, prm->precision, has_pairs, bonds, walls, excl, st);
+  if (e == cudaSuccess) e = launch_get_forces(A, prm->precision, d_f, d_u, st);
+  uint32_t status = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&status, A.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return na_fail(std::string("md_forces_noalloc: ") + cudaGetErrorString(e), MD_ERR_CUDA);
+  if (status & kFlagOutOfGrid) return na_fail("a particle is outside the cell grid", MD_ERR_OUT_OF_GRID);
+  if (status & kFlagOffSurface) return na_fail("a type is outside [0, ntypes)");
+  return MD_OK;
+}

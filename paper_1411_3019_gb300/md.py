@@ -107,6 +107,8 @@ def lib():
                 "md_cell_list": ([vp, dp, dp, dp, C.POINTER(C.c_uint32)], C.c_int),
                 "md_profile_step": ([vp, i64, C.POINTER(C.c_double), i32, C.POINTER(i32)], C.c_int),
                 "md_profile_kernel_name": ([vp, i32], C.c_char_p),
+                "md_forces_noalloc": ([C.POINTER(md_surface), C.POINTER(md_params), i64, dp, dp, dp, dp, dp,
+                                       dp, vp], C.c_int),
                 "md_last_error": ([vp], C.c_char_p),
                 "md_destroy": ([vp], None),
             }
@@ -335,6 +337,19 @@ def md_profile_step(h, nsteps: int = 1):
     nk = C.c_int32()
     _check(h, lib().md_profile_step(h, int(nsteps), buf, 16, C.byref(nk)))
     return {lib().md_profile_kernel_name(h, i).decode(): buf[i] for i in range(nk.value)}
+
+
+def md_forces_noalloc(surface: dict | None, params: dict, n: int, d_x, d_f, d_type=None, d_mol=None,
+                      d_con=None, d_u=None, stream=None) -> None:
+    """Forces of one system at device positions d_x into device d_f (and d_u)
+    without any device allocation (the library's fixed scratch array is used;
+    at most 65,536 particles). Device arguments are ints or objects with
+    data_ptr(); stream is a cudaStream_t or an object with cuda_stream."""
+    S, P = make_surface(surface), make_params(params)
+    sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    rc = lib().md_forces_noalloc(C.byref(S), C.byref(P), int(n), _dptr(d_x), _dptr(d_type), _dptr(d_mol),
+                                 _dptr(d_con), _dptr(d_f), _dptr(d_u), C.c_void_p(sptr) if sptr else None)
+    _check(None, rc)
 
 
 def md_last_error(h=None) -> str:
