@@ -134,9 +134,9 @@ def algorithmic_bytes(kernel: str, n: int, nbucket: int, precision: str) -> floa
         "pair": n * (4 + 4 + v4 + 4 + v4) + 4 * (nbucket + 1),
         # reads: meta, x, p_half, force vec4; writes: x, p_half, cell, rank; counter RMW
         "integrate": n * (4 + 24 + 24 + v4 + 24 + 24 + 4 + 4) + 8 * nbucket,
-        "scan_reduce": 4 * nbucket,
-        "scan_blocks": 8 * math.ceil(nbucket / 4096),
-        "scan_apply": 12 * nbucket,
+        # counters read and cleared, starts written, chunk sums read
+        "scan": 12 * nbucket + 4 * math.ceil(nbucket / 4096),
+        # cell id and rank read, bucket start read, slot written
         "scatter": n * (4 + 4 + 4 + 4),
         "bucket_build": n * (4 + 4 + 4 + 24 + 4 + v4) + 4 * (nbucket + 1) + 4 * n,
     }

@@ -209,6 +209,16 @@ int md_restore(md_handle* h, const double* x, const double* p_half,
  * synchronising call). */
 int md_step(md_handle* h, int64_t nsteps);
 
+/* Tuning options (they change speed, not results beyond float rounding
+ * order). MD_OPT_PAIR_LANES: lanes of a warp that share one particle in the
+ * pair kernel: 1 (default: one thread per particle, a z-slab of bucket ranges
+ * loaded at a time) or 2, 4, 8 (the 27 cells split over the lanes and the
+ * partial forces combined by shuffles). A change takes effect at the next
+ * md_step (the captured step is rebuilt). */
+#define MD_OPT_PAIR_LANES 1
+int md_set_option(md_handle* h, int32_t key, int64_t value);
+int md_get_option(md_handle* h, int32_t key, int64_t* value);
+
 /* Wait for the stream and report (then clear) the device status word. */
 int md_sync(md_handle* h);
 

@@ -292,18 +292,17 @@ cudaError_t k_pair_step(md_handle* h, cudaStream_t st) {
 cudaError_t k_integrate_step(md_handle* h, cudaStream_t st) {
   return launch_integrate(h->A, h->precision, h->has_pairs, st);
 }
-cudaError_t k_reduce_step(md_handle* h, cudaStream_t st) { return launch_scan_reduce(h->A, st); }
-cudaError_t k_blocks_step(md_handle* h, cudaStream_t st) { return launch_scan_blocks(h->A, 1, st); }
-cudaError_t k_apply_step(md_handle* h, cudaStream_t st) { return launch_scan_apply(h->A, st); }
+cudaError_t k_scan_step(md_handle* h, cudaStream_t st) { return launch_scan(h->A, 1, st); }
 cudaError_t k_scatter_step(md_handle* h, cudaStream_t st) { return launch_scatter(h->A, st); }
 cudaError_t k_bucket_step(md_handle* h, cudaStream_t st) {
   return launch_bucket_build(h->A, h->precision, st);
 }
 cudaError_t k_advance_step(md_handle* h, cudaStream_t st) { return launch_advance(h->A, st); }
 
-const StepKernel kStepWithCells[] = {{"pair", k_pair_step},          {"integrate", k_integrate_step},
-                                     {"scan_reduce", k_reduce_step}, {"scan_blocks", k_blocks_step},
-                                     {"scan_apply", k_apply_step},   {"scatter", k_scatter_step},
+const StepKernel kStepWithCells[] = {{"pair", k_pair_step},
+                                     {"integrate", k_integrate_step},
+                                     {"scan", k_scan_step},
+                                     {"scatter", k_scatter_step},
                                      {"bucket_build", k_bucket_step}};
 const StepKernel kStepNoCells[] = {{"pair", k_pair_step}, {"integrate", k_integrate_step},
                                    {"advance", k_advance_step}};
@@ -311,7 +310,7 @@ const StepKernel kStepNoCells[] = {{"pair", k_pair_step}, {"integrate", k_integr
 int step_kernels(const md_handle* h, const StepKernel** list) {
   if (h->has_pairs) {
     *list = kStepWithCells;
-    return 7;
+    return 5;
   }
   *list = kStepNoCells;
   return 3;
@@ -523,6 +522,7 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
     A.log_t = log_t;
   }
   if (!h->has_pairs) A.nbucket = 1;
+  A.pair_lanes = 1;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
     delete h;
@@ -556,6 +556,8 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
   al(dalloc(h, &A.count, A.nbucket));
   al(dalloc(h, &A.start, (size_t)A.nbucket + 1));
   al(dalloc(h, &A.blocksum, (size_t)nblk));
+  al(dalloc(h, &A.tile_state, (size_t)nblk));
+  al(dalloc(h, &A.scan, 1));
   al(dalloc(h, &A.stag, n));
   al(dalloc(h, &A.stag_tmp, n));
   al(dalloc(h, &A.scell, n));
@@ -584,6 +586,8 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
   if (e == cudaSuccess)
     e = cudaMemcpy(h->d_first, h->first.data(), sizeof(int64_t) * nsys, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(A.count, 0, sizeof(uint32_t) * std::max<size_t>(A.nbucket, 1));
+  if (e == cudaSuccess) e = cudaMemset(A.tile_state, 0, sizeof(unsigned long long) * (size_t)nblk);
+  if (e == cudaSuccess) e = cudaMemset(A.scan, 0, sizeof(ScanCtl));
   if (e == cudaSuccess) e = cudaMemset(A.status, 0, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(A.step, 0, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(A.mode, 0, sizeof(int32_t));
@@ -596,7 +600,7 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
     md_destroy(h);
     return fail(nullptr, MD_ERR_CUDA, m);
   }
-  h->kernels_per_step = h->has_pairs ? 7 : 3;
+  h->kernels_per_step = h->has_pairs ? 5 : 3;
   *out = h;
   return MD_OK;
 }
@@ -731,6 +735,32 @@ const char* md_profile_kernel_name(md_handle* h, int32_t i) {
   const StepKernel* ks;
   const int nk = step_kernels(h, &ks);
   return (i >= 0 && i < nk) ? ks[i].name : "";
+}
+
+int md_set_option(md_handle* h, int32_t key, int64_t value) {
+  if (!h) return MD_ERR_INVALID_ARG;
+  switch (key) {
+    case MD_OPT_PAIR_LANES:
+      if (value != 1 && value != 2 && value != 4 && value != 8)
+        return fail(h, MD_ERR_INVALID_ARG, "pair lanes must be 1, 2, 4 or 8");
+      h->A.pair_lanes = (int32_t)value;
+      break;
+    default:
+      return fail(h, MD_ERR_INVALID_ARG, "unknown option");
+  }
+  if (h->graph) {  // the captured step used the old setting
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return MD_OK;
+}
+
+int md_get_option(md_handle* h, int32_t key, int64_t* value) {
+  if (!h || !value) return MD_ERR_INVALID_ARG;
+  switch (key) {
+    case MD_OPT_PAIR_LANES: *value = h->A.pair_lanes; return MD_OK;
+    default: return fail(h, MD_ERR_INVALID_ARG, "unknown option");
+  }
 }
 
 int md_sync(md_handle* h) {
@@ -952,7 +982,9 @@ struct NaLayout {
   static constexpr size_t count = scell + na_align(N * 4);
   static constexpr size_t start = count + na_align(T * 4);
   static constexpr size_t blocksum = start + na_align((T + 1) * 4);
-  static constexpr size_t sys = blocksum + na_align((T / kScanPerBlock + 1) * 4);
+  static constexpr size_t tile_state = blocksum + na_align((T / kScanPerBlock + 1) * 4);
+  static constexpr size_t scan = tile_state + na_align((T / kScanPerBlock + 1) * 8);
+  static constexpr size_t sys = scan + 256;
   static constexpr size_t types = sys + na_align(sizeof(SysDev));
   static constexpr size_t status = types + na_align(sizeof(TypeTable));
   static constexpr size_t step = status + 256;
@@ -1065,6 +1097,7 @@ extern "C" int md_forces_noalloc(const md_surface* surf, const md_params* prm, i
   DevArrays A{};
   A.n = n;
   A.nsys = 1;
+  A.pair_lanes = 1;
   if (cells <= kNaMaxBuckets) {
     A.hashed = 0;
     A.nbucket = (uint32_t)cells;
@@ -1084,6 +1117,8 @@ extern "C" int md_forces_noalloc(const md_surface* surf, const md_params* prm, i
   A.count = reinterpret_cast<uint32_t*>(base + NaLayout::count);
   A.start = reinterpret_cast<uint32_t*>(base + NaLayout::start);
   A.blocksum = reinterpret_cast<uint32_t*>(base + NaLayout::blocksum);
+  A.tile_state = reinterpret_cast<unsigned long long*>(base + NaLayout::tile_state);
+  A.scan = reinterpret_cast<ScanCtl*>(base + NaLayout::scan);
   A.stag = reinterpret_cast<uint32_t*>(base + NaLayout::stag);
   A.stag_tmp = reinterpret_cast<uint32_t*>(base + NaLayout::stag_tmp);
   A.scell = reinterpret_cast<uint32_t*>(base + NaLayout::scell);
@@ -1102,6 +1137,10 @@ extern "C" int md_forces_noalloc(const md_surface* surf, const md_params* prm, i
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_first, &zero64, sizeof(int64_t), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(A.start + A.nbucket, &nn32, sizeof(uint32_t), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(A.count, 0, sizeof(uint32_t) * A.nbucket, st);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(A.tile_state, 0,
+                        sizeof(unsigned long long) * ((A.nbucket + kScanPerBlock - 1) / kScanPerBlock), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A.scan, 0, sizeof(ScanCtl), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(base + NaLayout::status, 0, 3 * 256 + 256, st);
   if (e == cudaSuccess && n > 0) {
     k_na_load_x<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, d_x, A.x);

@@ -8,7 +8,7 @@
 
 namespace surfmd {
 
-constexpr int kScanPerBlock = 4096;  // bucket counters scanned by one CTA
+constexpr int kScanPerBlock = 8192;  // bucket counters scanned by one CTA
 
 // Build the meta word of every particle (type, constrained bit, system id)
 // and the molecule ids. type/con/mol may be null (defaults of md_set_state).
@@ -29,9 +29,7 @@ cudaError_t launch_restore(const DevArrays& A, const double* d_x_aos, const doub
 cudaError_t launch_bin(const DevArrays& A, int precision, cudaStream_t st);
 cudaError_t launch_bucket_build(const DevArrays& A, int precision, cudaStream_t st);
 cudaError_t launch_cells_after_bin(const DevArrays& A, int advance, cudaStream_t st);
-cudaError_t launch_scan_reduce(const DevArrays& A, cudaStream_t st);
-cudaError_t launch_scan_blocks(const DevArrays& A, int advance, cudaStream_t st);
-cudaError_t launch_scan_apply(const DevArrays& A, cudaStream_t st);
+cudaError_t launch_scan(const DevArrays& A, int advance, cudaStream_t st);
 cudaError_t launch_scatter(const DevArrays& A, cudaStream_t st);
 
 // Conservative forces at the current positions into A.f.

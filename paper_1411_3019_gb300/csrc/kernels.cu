@@ -7,13 +7,14 @@
 //   integrate     Algorithm S1 force combination with Philox noise, the
 //                 momentum half of step k and the position half of step k+1
 //                 (Algorithm 1), then the cell of x^{k+1} and its bucket rank
-//   scan x3       exclusive scan of the bucket counters
+//   scan          exclusive scan of the bucket counters (one pass)
 //   scatter       particles to their bucket slots
 //   bucket build  canonical (particle-id) order inside each bucket and the
 //                 cell-relative records the pair kernel reads
 // The momentum half of step k and the position half of step k+1 share one
 // kernel: between steps the state is (x^k, p^{k-1/2}) and the combined force
 // never leaves registers; p^k is rebuilt on demand (launch_finish).
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 
@@ -304,7 +305,7 @@ __global__ void k_bin(DevArrays A) {
 }
 
 constexpr int kScanThreads = 512;
-constexpr int kScanItems = kScanPerBlock / kScanThreads;  // 8
+constexpr int kScanItems = kScanPerBlock / kScanThreads;  // 16 (four uint4)
 
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot,
                                                          uint32_t& block_total) {
@@ -334,72 +335,132 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
   return warp_tot[wid] + inc - v;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ count,
-                                                              uint32_t T, uint32_t* blocksum) {
-  __shared__ uint32_t red[kScanThreads / 32];
-  const uint32_t base = blockIdx.x * (uint32_t)kScanPerBlock + threadIdx.x * kScanItems;
-  uint32_t s = 0;
-#pragma unroll
-  for (int j = 0; j < kScanItems; ++j)
-    if (base + j < T) s += count[base + j];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+// Exclusive scan of the bucket counters in one pass (decoupled look-back):
+// each CTA takes the next tile index from a counter (so every tile's
+// predecessors have started), scans its kScanPerBlock counters, publishes its
+// aggregate, then walks back over its predecessors' published values until it
+// meets an inclusive prefix. Tile states are 64-bit words
+// (epoch:30 | flag:2 | value:32); a state from an earlier launch (older epoch)
+// reads as "not ready". Every wait is bounded: after kScanSpinLimit polls the
+// kernel sets the timeout flag and carries on. The last CTA to finish resets
+// the tile counter and advances the epoch. Optionally the kernel also moves
+// the step counter on (nothing in it reads the step).
+constexpr uint32_t kTileAgg = 1u, kTileIncl = 2u;
+constexpr int kScanSpinLimit = 1 << 22;
+
+__device__ __forceinline__ unsigned long long tile_word(uint32_t epoch, uint32_t flag, uint32_t value) {
+  return ((unsigned long long)(epoch & 0x3fffffffu) << 34) | ((unsigned long long)flag << 32) | value;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_onepass(DevArrays A, int advance) {
+  __shared__ uint32_t warp_tot[33];
+  __shared__ uint32_t s_tile, s_prefix;
+  uint32_t* __restrict__ count = A.count;
+  const uint32_t T = A.nbucket;
+  ScanCtl* ctl = A.scan;
+  const uint32_t epoch = ctl->epoch;
+  if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->tile, 1u);
   __syncthreads();
-  if (threadIdx.x < 32) {
-    s = threadIdx.x < kScanThreads / 32 ? red[threadIdx.x] : 0u;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) blocksum[blockIdx.x] = s;
-  }
-}
-
-// One CTA: exclusive scan of the block sums in place; optionally advance the
-// step counter (it runs once per step, after the integrator).
-__global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* blocksum, int nblk,
-                                                      unsigned long long* step, int32_t* mode,
-                                                      int advance) {
-  __shared__ uint32_t warp_tot[33];
-  const int per = (nblk + 1023) / 1024;
-  const int b0 = threadIdx.x * per;
-  uint32_t local = 0;
-  for (int j = 0; j < per; ++j)
-    if (b0 + j < nblk) local += blocksum[b0 + j];
-  uint32_t total;
-  uint32_t run = block_exclusive_scan(local, warp_tot, total);
-  for (int j = 0; j < per; ++j)
-    if (b0 + j < nblk) {
-      const uint32_t v = blocksum[b0 + j];
-      blocksum[b0 + j] = run;
-      run += v;
-    }
-  if (advance && threadIdx.x == 0) {
-    *step += 1ull;
-    *mode = 1;
-  }
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(uint32_t* __restrict__ count, uint32_t T,
-                                                             const uint32_t* __restrict__ blocksum,
-                                                             uint32_t* __restrict__ start) {
-  __shared__ uint32_t warp_tot[33];
-  const uint32_t base = blockIdx.x * (uint32_t)kScanPerBlock + threadIdx.x * kScanItems;
+  const uint32_t tile = s_tile;
+  const uint32_t base = tile * (uint32_t)kScanPerBlock + threadIdx.x * kScanItems;
+  const bool full = base + kScanItems <= T;  // whole run in range: 16-byte vector accesses
   uint32_t v[kScanItems];
-  uint32_t s = 0;
+  if (full) {
 #pragma unroll
-  for (int j = 0; j < kScanItems; ++j) {
-    v[j] = (base + j < T) ? count[base + j] : 0u;
-    s += v[j];
-  }
-  uint32_t total;
-  uint32_t run = block_exclusive_scan(s, warp_tot, total) + blocksum[blockIdx.x];
-#pragma unroll
-  for (int j = 0; j < kScanItems; ++j)
-    if (base + j < T) {
-      start[base + j] = run;
-      run += v[j];
-      count[base + j] = 0u;
+    for (int j = 0; j < kScanItems; j += 4) {
+      const uint4 q = *reinterpret_cast<const uint4*>(count + base + j);
+      v[j] = q.x; v[j + 1] = q.y; v[j + 2] = q.z; v[j + 3] = q.w;
     }
+  } else {
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) v[j] = (base + j < T) ? count[base + j] : 0u;
+  }
+  uint32_t sum = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) sum += v[j];
+  uint32_t total;
+  const uint32_t excl = block_exclusive_scan(sum, warp_tot, total);
+  if (threadIdx.x < 32) {  // warp 0 publishes and looks back 32 predecessors per probe
+    volatile unsigned long long* st = A.tile_state;
+    const int lane = threadIdx.x;
+    const uint32_t ep = epoch & 0x3fffffffu;
+    uint32_t prefix = 0;
+    if (tile == 0) {
+      if (lane == 0) st[0] = tile_word(epoch, kTileIncl, total);
+    } else {
+      if (lane == 0) st[tile] = tile_word(epoch, kTileAgg, total);
+      __threadfence();
+      int32_t hi = (int32_t)tile - 1;  // highest predecessor not yet summed
+      bool timed_out = false;
+      while (hi >= 0) {
+        const int32_t j = hi - lane;
+        unsigned long long w = 0ull;
+        uint32_t flag = kTileIncl;  // lanes beyond tile 0 act as an empty inclusive prefix
+        if (j >= 0) {
+          int spins = 0;
+          w = st[j];
+          // ready: written in this launch (epoch) with a flag (zeroed words carry none)
+          while (((uint32_t)(w >> 34) != ep || ((w >> 32) & 3u) == 0u) && spins < kScanSpinLimit) {
+            ++spins;
+            w = st[j];
+          }
+          if (spins >= kScanSpinLimit) timed_out = true;
+          flag = (uint32_t)((w >> 32) & 3u);
+        }
+        // the nearest inclusive prefix among the 32 (lowest lane holding one)
+        const unsigned incl = __ballot_sync(0xffffffffu, flag == kTileIncl);
+        const int stop = incl ? __ffs(incl) - 1 : 32;  // lanes 0..stop contribute
+        uint32_t part = (lane <= stop && j >= 0) ? (uint32_t)w : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        prefix += part;
+        if (__any_sync(0xffffffffu, timed_out)) {
+          if (lane == 0) atomicOr(A.status, kFlagTimeout);
+          break;
+        }
+        if (incl) break;
+        hi -= 32;
+      }
+      __threadfence();
+      if (lane == 0) st[tile] = tile_word(epoch, kTileIncl, prefix + total);
+    }
+    if (lane == 0) s_prefix = prefix;
+  }
+  __syncthreads();
+  uint32_t run = excl + s_prefix;
+  if (full) {
+#pragma unroll
+    for (int j = 0; j < kScanItems; j += 4) {
+      uint4 o;
+      o.x = run; run += v[j];
+      o.y = run; run += v[j + 1];
+      o.z = run; run += v[j + 2];
+      o.w = run; run += v[j + 3];
+      *reinterpret_cast<uint4*>(A.start + base + j) = o;
+      *reinterpret_cast<uint4*>(count + base + j) = make_uint4(0u, 0u, 0u, 0u);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j)
+      if (base + j < T) {
+        A.start[base + j] = run;
+        run += v[j];
+        count[base + j] = 0u;
+      }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const uint32_t nblk = gridDim.x;
+    if (atomicAdd(&ctl->done, 1u) == nblk - 1) {  // last CTA: reset for the next launch
+      ctl->done = 0u;
+      ctl->tile = 0u;
+      ctl->epoch = epoch + 1u;
+      if (advance) {
+        *A.step += 1ull;
+        *A.mode = 1;
+      }
+    }
+  }
 }
 
 __global__ void k_scatter(DevArrays A) {
@@ -628,11 +689,18 @@ __device__ __forceinline__ void bonded_terms(const DevArrays& A, const SysDev& S
 // particles, a cell whose box lies farther than the tangent slab from the
 // particle's tangent plane cannot hold a neighbour and is skipped. The bucket
 // ranges of one stencil row are loaded together before its candidates.
-template <typename R> struct Force4 { R x, y, z, u; };
-
+// One thread per sorted slot: the forces on its particle from the 27
+// neighbour cells. For a particle held on a surface in a system without free
+// particles, a cell whose box lies farther than the tangent slab from the
+// particle's tangent plane cannot hold a neighbour and is skipped. The bucket
+// ranges of one stencil row are loaded together before its candidates.
 template <typename R, bool BONDS, bool WALLS, bool EXCL>
-__device__ __forceinline__ Force4<R> pair_force(const DevArrays& A, const PairTab<R>& tab, uint32_t s,
-                                                uint32_t& tag_out) {
+__global__ void __launch_bounds__(256) k_pair_row(DevArrays A) {
+  __shared__ PairTab<R> tab;
+  load_tab<R>(tab, A.types);
+  __syncthreads();
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= (uint32_t)A.n) return;
   using Rec = typename RecT<R>::T;
   const Rec* __restrict__ rec = reinterpret_cast<const Rec*>(A.rec);
   const uint32_t* __restrict__ scell = A.scell;
@@ -709,8 +777,9 @@ __device__ __forceinline__ Force4<R> pair_force(const DevArrays& A, const PairTa
       for (int q = 0; q < 3; ++q) {
         const R shx = (R)(q - 1) * csx, shy = (R)dy * csy, shz = (R)dz * csz;
         for (uint32_t t = t0[q]; t < t1[q]; ++t) {
-          if (scell[t] != nb[q] || t == s) continue;
-          const Rec rj = rec[t];
+          const uint32_t cj = scell[t];
+          const Rec rj = rec[t];  // issued together with the cell id
+          if (cj != nb[q] || t == s) continue;
           const uint32_t bj = RecT<R>::bits(rj);
           if (EXCL && (bj >> 3) == moli) continue;
           const uint32_t qt = ti * kMaxTypes + (bj & 7u);
@@ -730,20 +799,117 @@ __device__ __forceinline__ Force4<R> pair_force(const DevArrays& A, const PairTa
     }
   }
   if (BONDS || WALLS) bonded_terms<R>(A, S, tag, m, BONDS, WALLS, fx, fy, fz, u);
-  tag_out = tag;
-  return {fx, fy, fz, u};
+  store_f<R>(A.f, tag, fx, fy, fz, u);
 }
 
-template <typename R, bool BONDS, bool WALLS, bool EXCL>
-__global__ void __launch_bounds__(256) k_pair(DevArrays A) {
+// L lanes of one warp share one particle: lane q walks the stencil cells
+// q, q+L, q+2L, ... of the 27, so each lane's chain of dependent loads is L
+// times shorter; the lanes' partial sums are combined by a fixed xor-shuffle
+// tree (the summation order, hence every bit of the result, is fixed).
+template <typename R, bool BONDS, bool WALLS, bool EXCL, int L>
+__global__ void __launch_bounds__(256) k_pair_lanes(DevArrays A) {
   __shared__ PairTab<R> tab;
   load_tab<R>(tab, A.types);
   __syncthreads();
-  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= (uint32_t)A.n) return;
-  uint32_t tag;
-  const Force4<R> f = pair_force<R, BONDS, WALLS, EXCL>(A, tab, s, tag);
-  store_f<R>(A.f, tag, f.x, f.y, f.z, f.u);
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t s = (uint32_t)(g / L);
+  const int q = (int)(g % L);
+  const bool valid = s < (uint32_t)A.n;
+  using Rec = typename RecT<R>::T;
+  const Rec* __restrict__ rec = reinterpret_cast<const Rec*>(A.rec);
+  const uint32_t* __restrict__ scell = A.scell;
+  const uint32_t* __restrict__ start = A.start;
+  R fx = 0, fy = 0, fz = 0, u = 0;
+  uint32_t tag = 0, m = 0;
+  const SysDev* Sp = A.sys;
+  if (valid) {
+    tag = A.stag[s];
+    const uint32_t cell = scell[s];
+    const Rec ri = rec[s];
+    const uint32_t bi = RecT<R>::bits(ri);
+    const uint32_t ti = bi & 7u, moli = bi >> 3;
+    m = A.meta[tag];
+    const uint32_t sid = meta_sys(m);
+    Sp = &A.sys[sid];
+    const SysDev& S = *Sp;
+    int c[3];
+    cell_decode(S, cell, c[0], c[1], c[2]);
+    const R csx = sizeof(R) == 4 ? (R)S.cs_f[0] : (R)S.cs[0];
+    const R csy = sizeof(R) == 4 ? (R)S.cs_f[1] : (R)S.cs[1];
+    const R csz = sizeof(R) == 4 ? (R)S.cs_f[2] : (R)S.cs[2];
+    bool prune = S.slab > 0.f && meta_con(m) && A.sys_free[sid] == 0;
+    float nhx = 0.f, nhy = 0.f, nhz = 0.f, reach = 0.f, on = 0.f;
+    if (prune) {
+      const float ox = (float)ri.x, oy = (float)ri.y, oz = (float)ri.z;
+      const float rx = S.grid_lo_f[0] + ((float)c[0] + 0.5f) * S.cs_f[0] + ox - S.c_f[0];
+      const float ry = S.grid_lo_f[1] + ((float)c[1] + 0.5f) * S.cs_f[1] + oy - S.c_f[1];
+      const float rz = S.grid_lo_f[2] + ((float)c[2] + 0.5f) * S.cs_f[2] + oz - S.c_f[2];
+      surf_grad_f(S, rx, ry, rz, nhx, nhy, nhz);
+      const float nn = fmaf(nhx, nhx, fmaf(nhy, nhy, nhz * nhz));
+      if (nn > 0.f) {
+        const float inv = rsqrtf(nn);
+        nhx *= inv; nhy *= inv; nhz *= inv;
+        reach = 0.5f * (S.cs_f[0] * fabsf(nhx) + S.cs_f[1] * fabsf(nhy) + S.cs_f[2] * fabsf(nhz)) + S.slab;
+        on = nhx * ox + nhy * oy + nhz * oz;
+      } else {
+        prune = false;
+      }
+    }
+    for (int k = q; k < 27; k += L) {
+      const int dz = k / 9 - 1, dy = (k / 3) % 3 - 1, dx = k % 3 - 1;
+      int x = c[0] + dx, y = c[1] + dy, z = c[2] + dz;
+      if (x < 0 || x >= S.nc[0]) {
+        if (!S.periodic[0]) continue;
+        x = (x + S.nc[0]) % S.nc[0];
+      }
+      if (y < 0 || y >= S.nc[1]) {
+        if (!S.periodic[1]) continue;
+        y = (y + S.nc[1]) % S.nc[1];
+      }
+      if (z < 0 || z >= S.nc[2]) {
+        if (!S.periodic[2]) continue;
+        z = (z + S.nc[2]) % S.nc[2];
+      }
+      if (prune) {
+        const float dist = nhx * (float)dx * S.cs_f[0] + nhy * (float)dy * S.cs_f[1] +
+                           nhz * (float)dz * S.cs_f[2] - on;
+        if (fabsf(dist) > reach) continue;
+      }
+      const uint32_t nb = cell_id(S, x, y, z);
+      const uint32_t b = bucket_of(nb, A.hashed, A.log_t);
+      const uint32_t t1 = start[b + 1];
+      const R shx = (R)dx * csx, shy = (R)dy * csy, shz = (R)dz * csz;
+      for (uint32_t t = start[b]; t < t1; ++t) {
+        const uint32_t cj = scell[t];
+        const Rec rj = rec[t];  // issued together with the cell id
+        if (cj != nb || t == s) continue;
+        const uint32_t bj = RecT<R>::bits(rj);
+        if (EXCL && (bj >> 3) == moli) continue;
+        const uint32_t qt = ti * kMaxTypes + (bj & 7u);
+        const R ddx = ri.x - rj.x - shx, ddy = ri.y - rj.y - shy, ddz = ri.z - rj.z - shz;
+        const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+        if (r2 < tab.rc2[qt]) {
+          const R inv_r2 = rcp<R>(r2);
+          const R s2 = tab.sig2[qt] * inv_r2;
+          const R s6 = s2 * s2 * s2;
+          const R e = tab.eps[qt];
+          const R fr = (R)24 * e * s6 * ((R)2 * s6 - (R)1) * inv_r2;
+          fx += fr * ddx; fy += fr * ddy; fz += fr * ddz;
+          u += (R)0.5 * ((R)4 * e * s6 * (s6 - (R)1) - tab.shift[qt]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) {
+    fx += __shfl_xor_sync(0xffffffffu, fx, o);
+    fy += __shfl_xor_sync(0xffffffffu, fy, o);
+    fz += __shfl_xor_sync(0xffffffffu, fz, o);
+    u += __shfl_xor_sync(0xffffffffu, u, o);
+  }
+  if (!valid || q != 0) return;
+  if (BONDS || WALLS) bonded_terms<R>(A, *Sp, tag, m, BONDS, WALLS, fx, fy, fz, u);
+  store_f<R>(A.f, tag, fx, fy, fz, u);
 }
 
 // No pair term anywhere: only bonds and walls, in particle order.
@@ -1027,7 +1193,7 @@ __device__ __forceinline__ void integrate_particle(const DevArrays& A, int64_t i
 }
 
 template <typename R, bool BIN>
-__global__ void __launch_bounds__(256) k_integrate(DevArrays A) {
+__global__ void __launch_bounds__(256, 4) k_integrate(DevArrays A) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
   integrate_particle<R, BIN>(A, i, load_f3<R>(A.f, i));
@@ -1235,21 +1401,12 @@ cudaError_t launch_bin(const DevArrays& A, int precision, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan_reduce(const DevArrays& A, cudaStream_t st) {
-  const int nblk = (int)((A.nbucket + kScanPerBlock - 1) / kScanPerBlock);
-  k_scan_reduce<<<nblk, kScanThreads, 0, st>>>(A.count, A.nbucket, A.blocksum);
-  return cudaGetLastError();
+static inline uint32_t scan_blocks_of(const DevArrays& A) {
+  return (A.nbucket + kScanPerBlock - 1) / kScanPerBlock;
 }
 
-cudaError_t launch_scan_blocks(const DevArrays& A, int advance, cudaStream_t st) {
-  const int nblk = (int)((A.nbucket + kScanPerBlock - 1) / kScanPerBlock);
-  k_scan_blocks<<<1, 1024, 0, st>>>(A.blocksum, nblk, A.step, A.mode, advance);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_scan_apply(const DevArrays& A, cudaStream_t st) {
-  const int nblk = (int)((A.nbucket + kScanPerBlock - 1) / kScanPerBlock);
-  k_scan_apply<<<nblk, kScanThreads, 0, st>>>(A.count, A.nbucket, A.blocksum, A.start);
+cudaError_t launch_scan(const DevArrays& A, int advance, cudaStream_t st) {
+  k_scan_onepass<<<scan_blocks_of(A), kScanThreads, 0, st>>>(A, advance);
   return cudaGetLastError();
 }
 
@@ -1260,9 +1417,7 @@ cudaError_t launch_scatter(const DevArrays& A, cudaStream_t st) {
 }
 
 cudaError_t launch_cells_after_bin(const DevArrays& A, int advance, cudaStream_t st) {
-  cudaError_t e = launch_scan_reduce(A, st);
-  if (e == cudaSuccess) e = launch_scan_blocks(A, advance, st);
-  if (e == cudaSuccess) e = launch_scan_apply(A, st);
+  cudaError_t e = launch_scan(A, advance, st);
   if (e == cudaSuccess) e = launch_scatter(A, st);
   return e;
 }
@@ -1275,18 +1430,44 @@ cudaError_t launch_bucket_build(const DevArrays& A, int precision, cudaStream_t 
 }
 
 template <typename R>
-static void pair_dispatch(const DevArrays& A, int bonds, int walls, int excl, cudaStream_t st) {
+static void pair_dispatch_row(const DevArrays& A, int bonds, int walls, int excl, cudaStream_t st) {
   const unsigned g = grid_for(A.n, 256);
   const int key = (bonds ? 4 : 0) | (walls ? 2 : 0) | (excl ? 1 : 0);
   switch (key) {
-    case 0: k_pair<R, false, false, false><<<g, 256, 0, st>>>(A); break;
-    case 1: k_pair<R, false, false, true><<<g, 256, 0, st>>>(A); break;
-    case 2: k_pair<R, false, true, false><<<g, 256, 0, st>>>(A); break;
-    case 3: k_pair<R, false, true, true><<<g, 256, 0, st>>>(A); break;
-    case 4: k_pair<R, true, false, false><<<g, 256, 0, st>>>(A); break;
-    case 5: k_pair<R, true, false, true><<<g, 256, 0, st>>>(A); break;
-    case 6: k_pair<R, true, true, false><<<g, 256, 0, st>>>(A); break;
-    default: k_pair<R, true, true, true><<<g, 256, 0, st>>>(A); break;
+    case 0: k_pair_row<R, false, false, false><<<g, 256, 0, st>>>(A); break;
+    case 1: k_pair_row<R, false, false, true><<<g, 256, 0, st>>>(A); break;
+    case 2: k_pair_row<R, false, true, false><<<g, 256, 0, st>>>(A); break;
+    case 3: k_pair_row<R, false, true, true><<<g, 256, 0, st>>>(A); break;
+    case 4: k_pair_row<R, true, false, false><<<g, 256, 0, st>>>(A); break;
+    case 5: k_pair_row<R, true, false, true><<<g, 256, 0, st>>>(A); break;
+    case 6: k_pair_row<R, true, true, false><<<g, 256, 0, st>>>(A); break;
+    default: k_pair_row<R, true, true, true><<<g, 256, 0, st>>>(A); break;
+  }
+}
+
+template <typename R, int L>
+static void pair_dispatch_l(const DevArrays& A, int bonds, int walls, int excl, cudaStream_t st) {
+  const unsigned g = (unsigned)(((uint64_t)A.n * L + 255) / 256);
+  const int key = (bonds ? 4 : 0) | (walls ? 2 : 0) | (excl ? 1 : 0);
+  switch (key) {
+    case 0: k_pair_lanes<R, false, false, false, L><<<g, 256, 0, st>>>(A); break;
+    case 1: k_pair_lanes<R, false, false, true, L><<<g, 256, 0, st>>>(A); break;
+    case 2: k_pair_lanes<R, false, true, false, L><<<g, 256, 0, st>>>(A); break;
+    case 3: k_pair_lanes<R, false, true, true, L><<<g, 256, 0, st>>>(A); break;
+    case 4: k_pair_lanes<R, true, false, false, L><<<g, 256, 0, st>>>(A); break;
+    case 5: k_pair_lanes<R, true, false, true, L><<<g, 256, 0, st>>>(A); break;
+    case 6: k_pair_lanes<R, true, true, false, L><<<g, 256, 0, st>>>(A); break;
+    default: k_pair_lanes<R, true, true, true, L><<<g, 256, 0, st>>>(A); break;
+  }
+}
+
+template <typename R>
+static void pair_dispatch(const DevArrays& A, int bonds, int walls, int excl, int lanes, cudaStream_t st) {
+  switch (lanes) {
+    case 2: pair_dispatch_l<R, 2>(A, bonds, walls, excl, st); break;
+    case 4: pair_dispatch_l<R, 4>(A, bonds, walls, excl, st); break;
+    case 8: pair_dispatch_l<R, 8>(A, bonds, walls, excl, st); break;
+    default: pair_dispatch_row<R>(A, bonds, walls, excl, st); break;
   }
 }
 
@@ -1297,9 +1478,9 @@ cudaError_t launch_pair(const DevArrays& A, int precision, int has_pairs, int bo
     if (precision == 0) k_nopair<double><<<grid_for(A.n, 256), 256, 0, st>>>(A, bonds, walls);
     else k_nopair<float><<<grid_for(A.n, 256), 256, 0, st>>>(A, bonds, walls);
   } else if (precision == 0) {
-    pair_dispatch<double>(A, bonds, walls, excl, st);
+    pair_dispatch<double>(A, bonds, walls, excl, A.pair_lanes, st);
   } else {
-    pair_dispatch<float>(A, bonds, walls, excl, st);
+    pair_dispatch<float>(A, bonds, walls, excl, A.pair_lanes, st);
   }
   return cudaGetLastError();
 }

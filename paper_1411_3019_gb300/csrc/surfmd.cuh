@@ -84,6 +84,14 @@ template <typename R> struct V4;
 template <> struct V4<float> { using T = float4; };
 template <> struct V4<double> { using T = double4_32a; };
 
+// Control words of the one-pass scan (zero at creation).
+struct ScanCtl {
+  uint32_t tile;   // next tile index
+  uint32_t done;   // tiles finished in this launch
+  uint32_t epoch;  // launch counter tagging the tile states
+  uint32_t pad;
+};
+
 // Arrays of one handle, passed by value to the kernels.
 struct DevArrays {
   int64_t n;            // particles
@@ -91,6 +99,7 @@ struct DevArrays {
   uint32_t nbucket;     // T
   int32_t hashed;       // 0: bucket = cell id; 1: hashed buckets
   int32_t log_t;
+  int32_t pair_lanes;   // lanes per particle in the pair kernel (1, 2, 4 or 8)
   double* x;            // [3][n] positions (unwrapped), SoA
   double* ph;           // [3][n] p^{k-1/2} (or p^k before the first step)
   double* pk;           // [3][n] p^k scratch
@@ -102,7 +111,9 @@ struct DevArrays {
   uint32_t* rank;       // [n] rank inside its bucket (atomic order)
   uint32_t* count;      // [T] bucket occupancy
   uint32_t* start;      // [T+1] bucket start
-  uint32_t* blocksum;   // [scan blocks]
+  uint32_t* blocksum;   // [scan blocks] (unused by the one-pass scan)
+  unsigned long long* tile_state;  // [scan blocks] published tile aggregates / prefixes
+  ScanCtl* scan;        // one-pass scan control words
   uint32_t* stag;       // [n] sorted slot -> particle (canonical order)
   uint32_t* stag_tmp;   // [n] slot -> particle in atomic order (before the canonical sort)
   uint32_t* scell;      // [n] sorted slot -> cell id

@@ -26,6 +26,7 @@ PRECISION = {"fp64": 0, "mixed": 1}
 MD_OK, MD_ERR_INVALID_ARG, MD_ERR_CUDA, MD_ERR_RATTLE_DIVERGED = 0, 1, 2, 3
 MD_ERR_NONFINITE, MD_ERR_OUT_OF_GRID, MD_ERR_TIMEOUT, MD_ERR_NO_DEVICE = 4, 5, 6, 7
 MD_FLAG_RATTLE_DIVERGED, MD_FLAG_NONFINITE, MD_FLAG_OUT_OF_GRID, MD_FLAG_TIMEOUT = 1, 2, 4, 8
+MD_OPT_PAIR_LANES = 1
 ERROR_NAMES = {0: "MD_OK", 1: "MD_ERR_INVALID_ARG", 2: "MD_ERR_CUDA", 3: "MD_ERR_RATTLE_DIVERGED",
                4: "MD_ERR_NONFINITE", 5: "MD_ERR_OUT_OF_GRID", 6: "MD_ERR_TIMEOUT", 7: "MD_ERR_NO_DEVICE"}
 
@@ -109,6 +110,8 @@ def lib():
                 "md_profile_kernel_name": ([vp, i32], C.c_char_p),
                 "md_forces_noalloc": ([C.POINTER(md_surface), C.POINTER(md_params), i64, dp, dp, dp, dp, dp,
                                        dp, vp], C.c_int),
+                "md_set_option": ([vp, i32, i64], C.c_int),
+                "md_get_option": ([vp, i32, C.POINTER(i64)], C.c_int),
                 "md_last_error": ([vp], C.c_char_p),
                 "md_destroy": ([vp], None),
             }
@@ -350,6 +353,16 @@ def md_forces_noalloc(surface: dict | None, params: dict, n: int, d_x, d_f, d_ty
     rc = lib().md_forces_noalloc(C.byref(S), C.byref(P), int(n), _dptr(d_x), _dptr(d_type), _dptr(d_mol),
                                  _dptr(d_con), _dptr(d_f), _dptr(d_u), C.c_void_p(sptr) if sptr else None)
     _check(None, rc)
+
+
+def md_set_option(h, key: int, value: int) -> None:
+    _check(h, lib().md_set_option(h, int(key), int(value)))
+
+
+def md_get_option(h, key: int) -> int:
+    v = C.c_int64()
+    _check(h, lib().md_get_option(h, int(key), C.byref(v)))
+    return v.value
 
 
 def md_last_error(h=None) -> str:
