@@ -2,23 +2,25 @@
 """Throughput of the constrained Langevin time step (Algorithm S1 with
 RATTLE, Algorithm 1) on one GB300, in particle-steps per second.
 
-Workload (default): 200,000 WCA particles at area fraction 0.4 on an
-ellipsoid of shape (150, 120, 90) sigma scaled to semi-axes
-(249.0, 199.2, 149.4) sigma, plus 50,000 on a torus R = 120, r = 40 sigma as a
-separate system of the same batch; kT = gamma = 1, dt = 0.002; float32 pair
-forces and noise, float64 state, Newton solve, projection and position
-update; RATTLE tolerance 1e-10 sigma. One bench step = one time step of
-both systems (every kernel of the hot path).
+Workload (default `ellipsoid_torus`): 200,000 WCA particles at area
+fraction 0.4 on an ellipsoid of shape (150, 120, 90) sigma scaled to
+semi-axes (249.0, 199.2, 149.4) sigma, plus 50,000 on a torus R = 120,
+r = 40 sigma as a separate system of the same batch; kT = gamma = 1,
+dt = 0.002; float32 pair forces and noise, float64 state, constraint value,
+projection and position update; RATTLE tolerance 1e-10 sigma. One bench
+step = one time step of both systems (every kernel of the hot path).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl surfmd|reference]
+                  [--workload NAME] [--precision mixed|fp64]
 
 Prints one JSON line (rank 0). Under torchrun each rank advances its own,
 independently seeded copy of the workload (weak scaling, no collective on
-the data path).
+the data path; the timing uses a barrier and max/sum reductions only).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -36,40 +38,80 @@ METRIC = ("particle-steps/sec on 1 GB300 (FP32-force/FP64-RATTLE vs plain FP64) 
           "≤1e-10")
 UNIT = "particle-steps/s"
 L2_FLUSH_BYTES = 256 << 20  # larger than the 129 MB L2
+WORKLOADS = ("ellipsoid_torus", "plain_sphere", "replicas", "bead_molecules", "bump_crowders")
+# float64 pipe of one GB300: 152 SMs x 2 float64 operations per SM per clock
+FP64_OPS_PER_SM_CLK = 2
+SMS = 152
+SM_MAX_MHZ = 2070.0
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="surfmd", choices=["surfmd", "reference"])
+    ap.add_argument("--workload", default="ellipsoid_torus", choices=WORKLOADS)
+    ap.add_argument("--precision", default=None, choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the float64 comparison leg")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
-def workload(rank: int, precision: str = "mixed"):
+# ---------------------------------------------------------------------------
+# workloads and their sharding over ranks (independent, seeded per rank)
+# ---------------------------------------------------------------------------
+def rank_seed(rank: int) -> int:
+    return 1 + rank
+
+
+def workload(name: str, rank: int, precision: str):
+    """The systems rank `rank` advances: an independently seeded copy of the
+    named workload (weak scaling)."""
     from paper_1411_3019_gb300 import inputs
 
-    systems = inputs.c2_ellipsoid_torus(seed=1 + rank, precision=precision)
-    return systems
+    seed = rank_seed(rank)
+    if name == "ellipsoid_torus":
+        return inputs.c2_ellipsoid_torus(seed=seed, precision=precision)
+    if name == "plain_sphere":
+        return [inputs.sphere_system(1000, 10.0, seed=seed, dmin=0.8, precision=precision, dt=0.001,
+                                     tol=1e-12 if precision == "fp64" else 1e-10)]
+    if name == "replicas":
+        return inputs.c4_replicas(seed=seed, precision=precision)
+    if name == "bead_molecules":
+        return inputs.c5_bead_molecules(seed=seed, precision=precision)
+    if name == "bump_crowders":
+        return inputs.c3_bump_crowders(seed=seed, precision=precision)
+    raise ValueError(name)
 
 
-def workload_config(systems, precision):
-    ell, tor = systems[0]["surface"]["p"], systems[1]["surface"]["p"]
-    return {
-        "workload": (f"ellipsoid+torus: {systems[0]['n']} WCA on ellipsoid semi-axes "
-                     f"({ell[0]:.1f},{ell[1]:.1f},{ell[2]:.1f}) at phi=0.4 + {systems[1]['n']} on torus "
-                     f"R={tor[0]:g} r={tor[1]:g} (separate system); kT=gamma=1, dt=0.002, "
-                     f"tol=1e-10, {precision}"),
-        "particles": int(sum(s["n"] for s in systems)),
-        "systems": len(systems),
-        "precision": precision,
-        "l2": "flushed between timed steps (256 MB write, outside the timed events)",
-    }
+def workload_config(name, systems, precision):
+    n = int(sum(s["n"] for s in systems))
+    if name == "ellipsoid_torus":
+        ell, tor = systems[0]["surface"]["p"], systems[1]["surface"]["p"]
+        desc = (f"ellipsoid+torus: {systems[0]['n']} WCA on ellipsoid semi-axes "
+                f"({ell[0]:.1f},{ell[1]:.1f},{ell[2]:.1f}) at phi=0.4 + {systems[1]['n']} on torus "
+                f"R={tor[0]:g} r={tor[1]:g} (separate system); kT=gamma=1, dt=0.002, tol=1e-10")
+    else:
+        desc = f"{name}: {n} particles in {len(systems)} system(s)"
+    return {"workload": f"{desc}, {precision}", "particles": n, "systems": len(systems),
+            "precision": precision,
+            "l2": "flushed between timed steps (256 MB write, outside the timed events)"}
+
+
+def reduce_over_ranks(dist, ms_local: float, n_local: float, device=None):
+    """(max over ranks of the step time, total particles over ranks)."""
+    if dist is None:
+        return ms_local, n_local
+    import torch
+
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    m = torch.tensor([n_local], dtype=torch.float64, device=device)
+    dist.all_reduce(m, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(m.item())
 
 
 # ---------------------------------------------------------------------------
@@ -122,36 +164,94 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# algorithmic bytes per launch of each kernel
+# rooflines
 # ---------------------------------------------------------------------------
 def algorithmic_bytes(kernel: str, n: int, nbucket: int, precision: str) -> float:
+    """Bytes each kernel must move per launch if every datum is read or written
+    once."""
     v4 = 16 if precision == "mixed" else 32
+    tiles = math.ceil(nbucket / 8192)
     per = {
-        # fused: pair reads (sorted id, cell, own record, meta) + update reads x, p and writes
-        # x, p, cell, rank (+ bucket starts once, counters read-modify-write)
-        "pair_integrate": n * (4 + 4 + v4 + 4 + 24 + 24 + 24 + 24 + 4 + 4) + 4 * (nbucket + 1) + 8 * nbucket,
-        # reads: sorted id, cell id, own record, meta; write: force vec4 (+ bucket starts once)
+        # sorted id, cell id, own record, meta; force vec4; bucket starts once
         "pair": n * (4 + 4 + v4 + 4 + v4) + 4 * (nbucket + 1),
-        # reads: meta, x, p_half, force vec4; writes: x, p_half, cell, rank; counter RMW
+        # meta, x, p_half, force vec4; x, p_half, cell, rank; counters read-modify-write
         "integrate": n * (4 + 24 + 24 + v4 + 24 + 24 + 4 + 4) + 8 * nbucket,
-        # counters read and cleared, starts written, chunk sums read
-        "scan": 12 * nbucket + 4 * math.ceil(nbucket / 4096),
-        # cell id and rank read, bucket start read, slot written
+        # counters read and cleared, starts written, tile states
+        "scan": 12 * nbucket + 16 * tiles,
+        # cell id, rank, bucket start; slot written
         "scatter": n * (4 + 4 + 4 + 4),
-        "bucket_build": n * (4 + 4 + 4 + 24 + 4 + v4) + 4 * (nbucket + 1) + 4 * n,
+        # slot id, cell, meta, x (3 x float64), bucket range; record, sorted id, sorted cell
+        "bucket_build": n * (4 + 4 + 4 + 24 + 8 + v4 + 4 + 4),
     }
     return float(per.get(kernel, 0))
 
 
-def main():
-    args = parse()
+def kernels_source_hash() -> str:
+    path = os.path.join(ROOT, "paper_1411_3019_gb300", "csrc", "kernels.cu")
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()
+
+
+def ncu_counts(workload_name: str, precision: str):
+    """Per-launch ncu counters (float64-pipe thread instructions, DRAM bytes)
+    recorded in profiles/ for this workload, if they were taken from the
+    current kernel source (else {})."""
+    path = os.path.join(ROOT, "profiles", f"ncu_counts_{workload_name}_{precision}.txt")
+    if not os.path.exists(path):
+        return {}
+    out, sha = {}, None
+    with open(path) as fh:
+        for line in fh:
+            parts = line.split()
+            if not parts or parts[0].startswith("#"):
+                continue
+            if parts[0] == "kernels_cu_sha256":
+                sha = parts[1]
+            elif len(parts) == 3:
+                out.setdefault(parts[0], {})[parts[1]] = float(parts[2])
+    return out if sha == kernels_source_hash() else {}
+
+
+def rooflines(prof_ms, n, nbucket, precision, hbm_peak, counts, sm_mhz):
+    fp64_peak = SMS * FP64_OPS_PER_SM_CLK * (sm_mhz or SM_MAX_MHZ) * 1e6  # float64 ops/s
+    table = {}
+    for k, ms in prof_ms.items():
+        b = algorithmic_bytes(k, n, nbucket, precision)
+        row = {"ms": round(ms, 5), "bytes_per_launch": b, "hbm_gbs": b / (ms / 1e3) / 1e9,
+               "hbm_frac": b / (ms / 1e3) / 1e9 / hbm_peak}
+        c = counts.get(k, {})
+        if "fp64_inst" in c:
+            row["fp64_inst_per_launch"] = c["fp64_inst"]
+            row["fp64_frac"] = c["fp64_inst"] / (ms / 1e3) / fp64_peak
+        if "dram_bytes" in c:
+            row["traffic"] = c["dram_bytes"]
+        table[k] = row
+    top = max(prof_ms, key=prof_ms.get)
+    r = table[top]
+    if r.get("fp64_frac", 0.0) > r["hbm_frac"]:
+        main = {"bound": "alu", "kernel": top, "achieved": r["fp64_inst_per_launch"] / (prof_ms[top] / 1e3),
+                "peak": fp64_peak, "unit": "FP64 ops/s", "frac": r["fp64_frac"],
+                "traffic": r.get("traffic"),
+                "peak_source": "derived: 152 SMs x 2 float64 ops/clk x SM clock"}
+    else:
+        main = {"bound": "hbm", "kernel": top, "achieved": r["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": r["hbm_frac"], "traffic": r.get("traffic"), "peak_source": "measured"}
+    main["per_kernel"] = table
+    return main
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def main(argv=None):
+    args = parse(argv)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    precision = args.precision or ("fp64" if args.workload == "plain_sphere" else "mixed")
     if args.impl == "reference":
-        return reference_arm(args, rank, world)
+        return reference_arm(args, rank, world, precision)
 
-    import numpy as np
     import torch
 
     torch.cuda.set_device(local)
@@ -165,20 +265,6 @@ def main():
     def barrier():
         if dist is not None:
             dist.barrier()
-
-    def max_over_ranks(v: float) -> float:
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(v: float) -> float:
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
 
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -199,8 +285,7 @@ def main():
         stream.synchronize()
         return [a.elapsed_time(b) for a, b in evs], launches
 
-    precision = "mixed"
-    systems = workload(rank, precision)
+    systems = workload(args.workload, rank, precision)
     n_local = int(sum(s["n"] for s in systems))
     sim = md.Simulation(systems, stream=stream)
     sim.set_state()
@@ -218,9 +303,7 @@ def main():
     clk = clocks.stop() if clocks else None
     sim.sync()
     res = sim.residual()
-    ms_local = sum(durs) / len(durs)
-    ms = max_over_ranks(ms_local)
-    total_particles = sum_over_ranks(float(n_local))
+    ms, total_particles = reduce_over_ranks(dist, sum(durs) / len(durs), float(n_local), "cuda")
     value = total_particles / (ms / 1e3)
 
     # steady state: back-to-back steps without flushes (state resident in L2)
@@ -230,7 +313,7 @@ def main():
         sim.step(args.steps)
         b.record(stream)
     stream.synchronize()
-    ms_resident = max_over_ranks(a.elapsed_time(b) / args.steps)
+    ms_resident, _ = reduce_over_ranks(dist, a.elapsed_time(b) / args.steps, 0.0, "cuda")
 
     # per-kernel durations (events between kernels, L2 flushed between steps)
     prof = {}
@@ -241,7 +324,6 @@ def main():
             for kname, kms in md.md_profile_step(sim.h, 1).items():
                 prof[kname] = prof.get(kname, 0.0) + kms / nprof
     nbucket = int(md.md_cell_list(sim.h)["bucket_start"].shape[0] - 1)
-    top = max(prof, key=prof.get)
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -249,12 +331,10 @@ def main():
     except OSError:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = algorithmic_bytes(top, n_local, nbucket, precision) / (prof[top] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "kernel_ms": {k: round(v, 5) for k, v in prof.items()},
-                "bytes_per_launch": algorithmic_bytes(top, n_local, nbucket, precision)}
+    roofline = rooflines(prof, n_local, nbucket, precision, hbm_peak, ncu_counts(args.workload, precision),
+                         clk["sm_mhz"] if clk else None)
+    if "hbm_gbs" not in peaks and roofline["bound"] == "hbm":
+        roofline["peak_source"] = "fallback"
 
     # end to end through the C ABI with host buffers (pinned): restore the
     # checkpoint state from the host, one step, read the state back
@@ -279,15 +359,15 @@ def main():
         if rc:
             raise RuntimeError(md.md_last_error(sim.h))
         k_now = step_c.value
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_n)
+    e2e_s, _ = reduce_over_ranks(dist, (time.perf_counter() - t0) / e2e_n, 0.0, "cuda")
     e2e = {"value": total_particles / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 24 * n_local,
            "d2h_bytes_per_step": 2 * 24 * n_local + 8, "ms_per_step": e2e_s * 1e3,
            "path": "md_restore(host x, p_half) + md_step(1) + md_get_state(host x, p_half)"}
     sim.close()
 
     plain = None
-    if not args.no_plain:
-        systems64 = workload(rank, "fp64")
+    if not args.no_plain and precision == "mixed":
+        systems64 = workload(args.workload, rank, "fp64")
         sim64 = md.Simulation(systems64, stream=stream)
         sim64.set_state()
         sim64.step(args.warmup)
@@ -297,7 +377,7 @@ def main():
         d64, _ = timed_steps(sim64, k64)
         sim64.sync()
         res64 = sim64.residual()
-        ms64 = max_over_ranks(sum(d64) / len(d64))
+        ms64, _ = reduce_over_ranks(dist, sum(d64) / len(d64), 0.0, "cuda")
         plain = {"value": total_particles / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "steps": k64,
                  "dtype": "f64", "max_g_over_gradg": res64["max_g_over_gradg"],
                  "mixed_speedup": ms64 / ms}
@@ -305,14 +385,14 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(workload(0, precision), args.cpu_seconds)
+        cpu = cpu_baseline(systems, args.cpu_seconds)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": workload_config(systems, precision),
+            "vs_baseline": None, "dtype": "f32+f64" if precision == "mixed" else "f64", "data": "synthetic",
+            "config": workload_config(args.workload, systems, precision),
             "residual_max_g_over_gradg": res["max_g_over_gradg"],
             "l2_resident": {"value": total_particles / (ms_resident / 1e3), "ms_per_step": ms_resident},
             "wall_s_timed_region": t_wall,
@@ -324,16 +404,21 @@ def main():
         dist.destroy_process_group()
 
 
-def cpu_baseline(systems, seconds: float):
-    """The oracle, as it stands, on the host cores: whole time steps of the same
-    workload for about `seconds` of CPU time (single thread)."""
+def _oracle_systems(systems):
     import oracle
 
     sims = []
     for s in systems:
         o = oracle.System(s["surface"], s["params"], s["n"], force_mode="cells")
-        o.set_state(s["x"], s["v"])
+        o.set_state(s["x"], s["v"], s["type"], s.get("mol"), s["constrained"])
         sims.append(o)
+    return sims
+
+
+def cpu_baseline(systems, seconds: float):
+    """The oracle, as it stands, on the host cores: whole time steps of the same
+    workload for about `seconds` of CPU time (single thread)."""
+    sims = _oracle_systems(systems)
     n = sum(s["n"] for s in systems)
     steps = 0
     t0 = time.perf_counter()
@@ -345,27 +430,22 @@ def cpu_baseline(systems, seconds: float):
         if el >= seconds:
             break
     return {"value": n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} whole time steps of the {n}-particle workload (both systems), "
+            "sample": f"{steps} whole time steps of the {n}-particle workload ({len(systems)} system(s)), "
                       f"{el:.1f} s, single-threaded float64 C oracle with a cell list"}
 
 
-def reference_arm(args, rank: int, world: int):
-    """The reference arm is the oracle on the host cores: rank 0 only."""
+def reference_arm(args, rank: int, world: int, precision: str):
+    """The reference arm is the oracle on the host cores: rank 0 only, whole
+    time steps of the same workload (at most 60 timed steps)."""
     if rank != 0:
         return
-    import oracle
-
-    systems = workload(0, "mixed")
-    sims = []
-    for s in systems:
-        o = oracle.System(s["surface"], s["params"], s["n"], force_mode="cells")
-        o.set_state(s["x"], s["v"])
-        sims.append(o)
+    systems = workload(args.workload, 0, precision)
+    sims = _oracle_systems(systems)
     n = sum(s["n"] for s in systems)
     for _ in range(args.warmup):
         for o in sims:
             o.step(1)
-    steps = min(args.steps, 60)
+    steps = max(1, min(args.steps, 60))
     t0 = time.perf_counter()
     for _ in range(steps):
         for o in sims:
@@ -375,7 +455,7 @@ def reference_arm(args, rank: int, world: int):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
             "warmup": args.warmup, "ms_per_step": el / steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(systems, "mixed"), "impl": "reference",
+            "config": workload_config(args.workload, systems, precision), "impl": "reference",
             "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
                              "sample": f"{steps} whole time steps of the {n}-particle workload"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
