@@ -216,6 +216,10 @@ int md_step(md_handle* h, int64_t nsteps);
  * partial forces combined by shuffles). A change takes effect at the next
  * md_step (the captured step is rebuilt). */
 #define MD_OPT_PAIR_LANES 1
+/* MD_OPT_PAIR_ORDER: 1 (default) = the pair kernel visits particles in a
+ * spatial (Morton) order refreshed every 16 steps, so neighbouring threads
+ * share cache lines; 0 = bucket order. */
+#define MD_OPT_PAIR_ORDER 2
 int md_set_option(md_handle* h, int32_t key, int64_t value);
 int md_get_option(md_handle* h, int32_t key, int64_t* value);
 

@@ -41,6 +41,11 @@ struct md_handle {
   uint32_t* h_status = nullptr;  // pinned
   unsigned long long* h_resid = nullptr;  // pinned
   cudaGraphExec_t graph = nullptr;
+  // visiting order of the pair kernel (refreshed every kOrderEvery steps)
+  DevArrays O{};
+  uint32_t order_coord_shift = 0, order_morton_drop = 0, order_sys_shift = 0;
+  uint32_t* d_order = nullptr;
+  int64_t steps_since_order = 0;
   int64_t last_launches = 0;
   int kernels_per_step = 0;
   std::vector<void*> allocs;
@@ -50,6 +55,7 @@ struct md_handle {
 };
 
 static std::string g_create_err;
+constexpr int64_t kOrderEvery = 16;  // steps between refreshes of the pair visiting order
 
 namespace {
 
@@ -277,6 +283,9 @@ int rebuild_cells(md_handle* h) {
   CK(h, launch_bin(h->A, h->precision, h->stream()));
   CK(h, launch_cells_after_bin(h->A, 0, h->stream()));
   CK(h, launch_bucket_build(h->A, h->precision, h->stream()));
+  CK(h, launch_order(h->A, h->O, h->order_coord_shift, h->order_morton_drop, h->order_sys_shift, h->d_order,
+                     h->stream()));
+  h->steps_since_order = 0;
   return MD_OK;
 }
 
@@ -558,8 +567,35 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
   al(dalloc(h, &A.blocksum, (size_t)nblk));
   al(dalloc(h, &A.tile_state, (size_t)nblk));
   al(dalloc(h, &A.scan, 1));
+  // order keys: (system, Morton code of the cell) packed into at most 2^20 keys
+  {
+    int maxnc = 1;
+    for (int sy = 0; sy < nsys; ++sy)
+      for (int d = 0; d < 3; ++d) maxnc = std::max(maxnc, h->sys[sy].nc[d]);
+    uint32_t cbits = 0;
+    while ((1 << cbits) < maxnc) ++cbits;
+    const uint32_t coord_shift = cbits > 10 ? cbits - 10 : 0;
+    const uint32_t mbits = 3 * std::min<uint32_t>(cbits, 10);
+    uint32_t sbits = 0;
+    while ((1u << sbits) < (uint32_t)nsys) ++sbits;
+    const uint32_t kKeyBits = 20;
+    uint32_t keep = sbits >= kKeyBits ? 0 : std::min(mbits, kKeyBits - sbits);
+    h->order_coord_shift = coord_shift;
+    h->order_morton_drop = mbits - keep;
+    h->order_sys_shift = keep;
+    const uint64_t nkeys = (uint64_t)nsys << keep;
+    h->O = A;
+    h->O.nbucket = (uint32_t)std::min<uint64_t>(nkeys, uint64_t(1) << 31);
+    const size_t ot = (h->O.nbucket + kScanPerBlock - 1) / kScanPerBlock;
+    al(dalloc(h, &h->O.count, h->O.nbucket));
+    al(dalloc(h, &h->O.start, (size_t)h->O.nbucket + 1));
+    al(dalloc(h, &h->O.tile_state, ot));
+    al(dalloc(h, &h->O.scan, 1));
+  }
   al(dalloc(h, &A.stag, n));
   al(dalloc(h, &A.stag_tmp, n));
+  al(dalloc(h, &A.slot_of, n));
+  al(dalloc(h, &h->d_order, n));
   al(dalloc(h, &A.scell, n));
   SysDev* d_sys = nullptr;
   al(dalloc(h, &d_sys, (size_t)nsys));
@@ -588,6 +624,18 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
   if (e == cudaSuccess) e = cudaMemset(A.count, 0, sizeof(uint32_t) * std::max<size_t>(A.nbucket, 1));
   if (e == cudaSuccess) e = cudaMemset(A.tile_state, 0, sizeof(unsigned long long) * (size_t)nblk);
   if (e == cudaSuccess) e = cudaMemset(A.scan, 0, sizeof(ScanCtl));
+  if (e == cudaSuccess) e = cudaMemset(h->O.count, 0, sizeof(uint32_t) * h->O.nbucket);
+  if (e == cudaSuccess)
+    e = cudaMemset(h->O.tile_state, 0,
+                   sizeof(unsigned long long) * ((h->O.nbucket + kScanPerBlock - 1) / kScanPerBlock));
+  if (e == cudaSuccess) e = cudaMemset(h->O.scan, 0, sizeof(ScanCtl));
+  if (e == cudaSuccess) {
+    const uint32_t nn = (uint32_t)total;
+    e = cudaMemcpy(h->O.start + h->O.nbucket, &nn, sizeof(uint32_t), cudaMemcpyHostToDevice);
+  }
+  h->O.status = A.status;  // the order scan reports through the handle's status word
+  h->O.n = A.n;
+  if (h->has_pairs && total > 0) A.order = h->d_order;
   if (e == cudaSuccess) e = cudaMemset(A.status, 0, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(A.step, 0, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(A.mode, 0, sizeof(int32_t));
@@ -682,8 +730,18 @@ int md_step(md_handle* h, int64_t nsteps) {
   if (nsteps == 0) return MD_OK;
   rc = build_graph(h);
   if (rc) return rc;
-  for (int64_t s = 0; s < nsteps; ++s) CK(h, cudaGraphLaunch(h->graph, h->stream()));
-  h->last_launches = nsteps * h->kernels_per_step;
+  int64_t extra = 0;
+  for (int64_t s = 0; s < nsteps; ++s) {
+    CK(h, cudaGraphLaunch(h->graph, h->stream()));
+    if (h->has_pairs && h->A.order && ++h->steps_since_order >= kOrderEvery) {
+      // any permutation is a valid visiting order; a fresh one keeps it spatial
+      CK(h, launch_order(h->A, h->O, h->order_coord_shift, h->order_morton_drop, h->order_sys_shift, h->d_order,
+                     h->stream()));
+      h->steps_since_order = 0;
+      extra += 3;
+    }
+  }
+  h->last_launches = nsteps * h->kernels_per_step + extra;
   return MD_OK;
 }
 
@@ -745,6 +803,15 @@ int md_set_option(md_handle* h, int32_t key, int64_t value) {
         return fail(h, MD_ERR_INVALID_ARG, "pair lanes must be 1, 2, 4 or 8");
       h->A.pair_lanes = (int32_t)value;
       break;
+    case MD_OPT_PAIR_ORDER:
+      if (value != 0 && value != 1) return fail(h, MD_ERR_INVALID_ARG, "pair order must be 0 or 1");
+      h->A.order = (value && h->has_pairs && h->n > 0) ? h->d_order : nullptr;
+      if (h->A.order && h->state_set) {
+        CK(h, launch_order(h->A, h->O, h->order_coord_shift, h->order_morton_drop, h->order_sys_shift,
+                           h->d_order, h->stream()));
+        h->steps_since_order = 0;
+      }
+      break;
     default:
       return fail(h, MD_ERR_INVALID_ARG, "unknown option");
   }
@@ -759,6 +826,7 @@ int md_get_option(md_handle* h, int32_t key, int64_t* value) {
   if (!h || !value) return MD_ERR_INVALID_ARG;
   switch (key) {
     case MD_OPT_PAIR_LANES: *value = h->A.pair_lanes; return MD_OK;
+    case MD_OPT_PAIR_ORDER: *value = h->A.order ? 1 : 0; return MD_OK;
     default: return fail(h, MD_ERR_INVALID_ARG, "unknown option");
   }
 }

@@ -30,6 +30,13 @@ cudaError_t launch_bin(const DevArrays& A, int precision, cudaStream_t st);
 cudaError_t launch_bucket_build(const DevArrays& A, int precision, cudaStream_t st);
 cudaError_t launch_cells_after_bin(const DevArrays& A, int advance, cudaStream_t st);
 cudaError_t launch_scan(const DevArrays& A, int advance, cudaStream_t st);
+// Visiting order of the pair kernel: counting sort of the particles by
+// (system << sys_shift) | (Morton code of (cell coords >> coord_shift)) >>
+// morton_drop. O holds the key counters, starts and scan state (its nbucket =
+// number of keys); A.rank is reused as scratch (call it after the cell list
+// is complete, before the next binning).
+cudaError_t launch_order(const DevArrays& A, const DevArrays& O, uint32_t coord_shift, uint32_t morton_drop,
+                         uint32_t sys_shift, uint32_t* order, cudaStream_t st);
 cudaError_t launch_scatter(const DevArrays& A, cudaStream_t st);
 
 // Conservative forces at the current positions into A.f.

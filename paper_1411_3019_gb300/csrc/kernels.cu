@@ -513,6 +513,7 @@ __global__ void k_bucket_build(DevArrays A) {
   const uint32_t mol = A.mol ? (uint32_t)A.mol[tag] : 0u;
   A.stag[d] = tag;
   A.scell[d] = cell;
+  if (A.slot_of) A.slot_of[tag] = d;
   put_rec<R>(A.rec, d, o[0], o[1], o[2], meta_type(m) | (mol << 3));
 }
 
@@ -573,6 +574,49 @@ __device__ __forceinline__ void surf_grad_f(const SysDev& S, float dx, float dy,
       break;
     default: nx = ny = nz = 0.f;
   }
+}
+
+// Visiting order of the pair kernel: a counting sort of the particles by a
+// spatial key -- the system index in the top bits, then the Morton code of
+// the particle's cell (coordinates interleaved bit by bit, so consecutive
+// keys are compact octree blocks) with its low bits dropped to fit 2^20 keys.
+// The order inside a key is the atomic order: it only decides which thread
+// takes which particle, never a result.
+__device__ __forceinline__ uint32_t part1by2(uint32_t v) {  // spread 10 bits to every third bit
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000ffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+struct OrderKey {
+  uint32_t coord_shift;  // cell coordinates >> this keep 10 bits
+  uint32_t morton_drop;  // low Morton bits dropped
+  uint32_t sys_shift;    // system index << this
+};
+
+__device__ __forceinline__ uint32_t order_key(const DevArrays& A, const OrderKey& K, int64_t i) {
+  const uint32_t sid = meta_sys(A.meta[i]);
+  const SysDev& S = A.sys[sid];
+  int cx, cy, cz;
+  cell_decode(S, A.cell[i], cx, cy, cz);
+  const uint32_t mort = part1by2((uint32_t)cx >> K.coord_shift) | (part1by2((uint32_t)cy >> K.coord_shift) << 1) |
+                        (part1by2((uint32_t)cz >> K.coord_shift) << 2);
+  return (sid << K.sys_shift) | (mort >> K.morton_drop);
+}
+
+__global__ void k_order_hist(DevArrays A, DevArrays O, OrderKey K) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  A.rank[i] = atomicAdd(&O.count[order_key(A, K, i)], 1u);
+}
+
+__global__ void k_order_scatter(DevArrays A, DevArrays O, OrderKey K, uint32_t* order) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  order[O.start[order_key(A, K, i)] + A.rank[i]] = (uint32_t)i;
 }
 
 // ---------------------------------------------------------------------------
@@ -699,8 +743,12 @@ __global__ void __launch_bounds__(256) k_pair_row(DevArrays A) {
   __shared__ PairTab<R> tab;
   load_tab<R>(tab, A.types);
   __syncthreads();
-  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= (uint32_t)A.n) return;
+  const uint32_t t_id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t_id >= (uint32_t)A.n) return;
+  // with a visiting order, neighbouring threads take spatially neighbouring
+  // particles, whose stencils share cache lines; the particle's own slot
+  // follows from the slot map (the arithmetic per particle is unchanged)
+  const uint32_t s = A.order ? A.slot_of[A.order[t_id]] : t_id;
   using Rec = typename RecT<R>::T;
   const Rec* __restrict__ rec = reinterpret_cast<const Rec*>(A.rec);
   const uint32_t* __restrict__ scell = A.scell;
@@ -1413,6 +1461,18 @@ cudaError_t launch_scan(const DevArrays& A, int advance, cudaStream_t st) {
 cudaError_t launch_scatter(const DevArrays& A, cudaStream_t st) {
   if (A.n == 0) return cudaSuccess;
   k_scatter<<<grid_for(A.n, 256), 256, 0, st>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_order(const DevArrays& A, const DevArrays& O, uint32_t coord_shift, uint32_t morton_drop,
+                         uint32_t sys_shift, uint32_t* order, cudaStream_t st) {
+  if (A.n == 0) return cudaSuccess;
+  const OrderKey K{coord_shift, morton_drop, sys_shift};
+  k_order_hist<<<grid_for(A.n, 256), 256, 0, st>>>(A, O, K);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_scan(O, 0, st);
+  if (e != cudaSuccess) return e;
+  k_order_scatter<<<grid_for(A.n, 256), 256, 0, st>>>(A, O, K, order);
   return cudaGetLastError();
 }
 

@@ -114,6 +114,8 @@ struct DevArrays {
   uint32_t* blocksum;   // [scan blocks] (unused by the one-pass scan)
   unsigned long long* tile_state;  // [scan blocks] published tile aggregates / prefixes
   ScanCtl* scan;        // one-pass scan control words
+  uint32_t* slot_of;    // [n] particle -> its sorted slot (written with the records)
+  const uint32_t* order;  // [n] visiting order of the pair kernel (spatially coherent) or null
   uint32_t* stag;       // [n] sorted slot -> particle (canonical order)
   uint32_t* stag_tmp;   // [n] slot -> particle in atomic order (before the canonical sort)
   uint32_t* scell;      // [n] sorted slot -> cell id
