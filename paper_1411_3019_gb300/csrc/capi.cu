@@ -170,9 +170,20 @@ int check_system(const md_surface& s, const md_params& p, SysDev& S, std::string
   S.noise_unit_f = (float)S.noise_unit;
   S.max_newton = p.max_newton;
   S.frozen = p.frozen_normal ? 1 : 0;
+  for (int t = 0; t < kMaxTypes; ++t) {
+    if (!(p.mass[t] > 0.0)) continue;
+    S.dtm[t] = p.dt / p.mass[t];
+    S.inv_dtm[t] = p.mass[t] / p.dt;
+    S.dtm_f[t] = (float)S.dtm[t];
+  }
+  S.half_dt_f = (float)S.half_dt;
+  S.tol_f = (float)p.rattle_tol;
+  if (s.kind == MD_SURF_SPHERE || s.kind == MD_SURF_CYLINDER) S.gconst = -s.p[0] * s.p[0];
+  if (s.kind == MD_SURF_TORUS) S.gconst = -s.p[1] * s.p[1];
   for (int d = 0; d < 3; ++d) {
     S.box_lo[d] = p.box_lo[d];
     S.box_len[d] = p.box_hi[d] - p.box_lo[d];
+    S.inv_box_len[d] = S.box_len[d] > 0.0 ? 1.0 / S.box_len[d] : 0.0;
     S.periodic[d] = p.periodic[d] ? 1 : 0;
   }
   S.bpm = p.beads_per_mol;

@@ -77,6 +77,45 @@ __device__ __forceinline__ void gauss3(uint32_t seed, uint32_t rep, uint32_t pid
   gz = r23 * cospi(2.0 * u3);
 }
 
+// Format conversions on the integer pipe. On this GPU a float64 <-> float32
+// conversion issues on the float64 pipe at the float64 rate (two lanes per SM
+// per clock), as costly as a DFMA; the mixed integrator converts a dozen
+// values per particle. These build the result from the IEEE 754 binary64 and
+// binary32 bit fields (sign, biased exponent with bias 1023 / 127, fraction of
+// 52 / 23 bits) with integer operations. Zero and every normal binary32 result
+// are formed here; binary32 subnormal results, overflow, infinities and NaN
+// take the hardware conversion, so the result is bit-identical to it always.
+//
+// binary64 -> binary32, round to nearest, ties to even: rebias the exponent
+// field in place (1023 - 127 = 896), then drop the low 29 fraction bits with
+// the rounding increment 2^28 - 1 plus the lowest kept bit; a carry out of the
+// fraction moves into the exponent, as rounding up to the next binade must.
+__device__ __forceinline__ float d2f_rn(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned long long a = b & 0x7fffffffffffffffull;
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  // biased binary64 exponent in [897, 1150] <=> binary32 exponent in [1, 254]
+  if (a - (897ull << 52) < (254ull << 52)) {
+    const unsigned long long r = a - (896ull << 52);
+    const unsigned long long q = (r + 0x0fffffffull + ((r >> 29) & 1ull)) >> 29;
+    return __uint_as_float(sign | (uint32_t)q);
+  }
+  if (a == 0ull) return __uint_as_float(sign);
+  return __double2float_rn(v);
+}
+
+// binary32 -> binary64 (exact): exponent + 896, fraction shifted up by 29.
+__device__ __forceinline__ double f2d(float v) {
+  const uint32_t u = __float_as_uint(v);
+  const uint32_t e = (u >> 23) & 0xffu;
+  if (e - 1u < 254u) {
+    const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0x000fffffu);
+    return __hiloint2double((int)hi, (int)(u << 29));
+  }
+  if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  return (double)v;
+}
+
 // ---------------------------------------------------------------------------
 // Surfaces: g(x) and n = grad g (unnormalised), float64.
 // ---------------------------------------------------------------------------
@@ -180,7 +219,7 @@ __device__ __forceinline__ uint32_t cell_of_d(const SysDev& S, double x, double 
 // rounding of a coordinate, so a neighbour within the cutoff is still at most
 // one cell away.
 __device__ __forceinline__ int cell_coord_f(const SysDev& S, int d, double v, bool& out) {
-  float u = (float)v;
+  float u = d2f_rn(v);
   if (S.periodic[d]) {
     const float L = S.box_len_f[d];
     const float r = __fsub_rn(u, S.box_lo_f[d]);
@@ -474,7 +513,7 @@ template <typename R> __device__ __forceinline__ void put_rec(void* rec, uint32_
                                                               double oz, uint32_t bits);
 template <> __device__ __forceinline__ void put_rec<float>(void* rec, uint32_t s, double ox, double oy,
                                                            double oz, uint32_t bits) {
-  reinterpret_cast<float4*>(rec)[s] = make_float4((float)ox, (float)oy, (float)oz, __uint_as_float(bits));
+  reinterpret_cast<float4*>(rec)[s] = make_float4(d2f_rn(ox), d2f_rn(oy), d2f_rn(oz), __uint_as_float(bits));
 }
 template <> __device__ __forceinline__ void put_rec<double>(void* rec, uint32_t s, double ox, double oy,
                                                             double oz, uint32_t bits) {
@@ -507,8 +546,14 @@ __global__ void k_bucket_build(DevArrays A) {
   double o[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {  // offset from the cell centre: |o| <= cs/2 keeps float32 rounding small
-    o[k] = xv[k] - fma((double)c[k] + 0.5, S.cs[k], S.grid_lo[k]);
-    if (S.periodic[k]) o[k] = wrap_min_image(o[k], S.box_len[k]);  // the image the binning chose
+    // c + 1/2 is exact in float32 (c < 2^22), so the centre is the same float64 value either way
+    o[k] = xv[k] - fma(f2d((float)c[k] + 0.5f), S.cs[k], S.grid_lo[k]);
+    // the image the binning chose. With three or more cells on the axis, o lies within cs/2 <= L/6 of a
+    // multiple of the box length L, far from an odd multiple of L/2, so o / L and o * (1 / L) round to
+    // the same integer and the reciprocal form (no float64 divide) picks the same image.
+    if (S.periodic[k])
+      o[k] = S.nc[k] >= 3 ? fma(-S.box_len[k], rint(o[k] * S.inv_box_len[k]), o[k])
+                          : wrap_min_image(o[k], S.box_len[k]);
   }
   const uint32_t mol = A.mol ? (uint32_t)A.mol[tag] : 0u;
   A.stag[d] = tag;
@@ -524,18 +569,18 @@ __global__ void k_bucket_build(DevArrays A) {
 // normal number inside the float32 range; otherwise the float64 operator is
 // used.
 __device__ __forceinline__ double nr_rcp(double v) {
-  const float vf = (float)v;
+  const float vf = d2f_rn(v);
   if (!(vf > 1.0e-37f && vf < 1.0e37f)) return 1.0 / v;
-  double e = (double)__frcp_rn(vf);
+  double e = f2d(__frcp_rn(vf));
   e = fma(e, fma(-v, e, 1.0), e);
   e = fma(e, fma(-v, e, 1.0), e);
   return e;
 }
 
 __device__ __forceinline__ double nr_rsqrt(double v) {
-  const float vf = (float)v;
+  const float vf = d2f_rn(v);
   if (!(vf > 1.0e-37f && vf < 1.0e37f)) return 1.0 / sqrt(v);
-  double r = (double)rsqrtf(vf);
+  double r = f2d(rsqrtf(vf));
   const double hv = 0.5 * v;
   r = r * fma(-hv * r, r, 1.5);
   r = r * fma(-hv * r, r, 1.5);
@@ -1045,18 +1090,18 @@ __device__ __forceinline__ void surf_n_f(const SysDev& S, const GEval& e, float&
   switch (S.kind) {
     case kPlane: nx = S.p_f[0]; ny = S.p_f[1]; nz = S.p_f[2]; break;
     case kTorus: {
-      const float q = (float)e.q;
-      nx = q * (float)e.ux; ny = q * (float)e.uy; nz = 2.f * (float)e.uz;
+      const float q = d2f_rn(e.q);
+      nx = q * d2f_rn(e.ux); ny = q * d2f_rn(e.uy); nz = 2.f * d2f_rn(e.uz);
       break;
     }
     case kBump: {
-      const float q = (float)e.q;
-      nx = q * (float)e.ux; ny = q * (float)e.uy; nz = 1.f;
+      const float q = d2f_rn(e.q);
+      nx = q * d2f_rn(e.ux); ny = q * d2f_rn(e.uy); nz = 1.f;
       break;
     }
     case kSphere:
     case kEllipsoid:
-    case kCylinder: nx = 2.f * (float)e.ux; ny = 2.f * (float)e.uy; nz = 2.f * (float)e.uz; break;
+    case kCylinder: nx = 2.f * d2f_rn(e.ux); ny = 2.f * d2f_rn(e.uy); nz = 2.f * d2f_rn(e.uz); break;
     default: nx = ny = nz = 0.f;
   }
 }
@@ -1093,8 +1138,7 @@ template <> __device__ __forceinline__ double noise_amp<double>(const SysDev& S,
 // with f_r = sqrt(2 m kT gamma / dt) xi, xi drawn from Philox in R.
 template <typename R>
 __device__ __forceinline__ Force3<R> combine(const SysDev& S, const TypeTable* T, uint32_t ty, uint32_t pid,
-                                             unsigned long long k, int mode, Force3<R> f, double px, double py,
-                                             double pz) {
+                                             unsigned long long k, int mode, Force3<R> f, R px, R py, R pz) {
   R nx = 0, ny = 0, nz = 0;
   const R amp = noise_amp<R>(S, T, ty);
   if (amp > (R)0) {
@@ -1111,9 +1155,9 @@ __device__ __forceinline__ Force3<R> combine(const SysDev& S, const TypeTable* T
   }
   const R gam = sys_gamma<R>(S);
   Force3<R> F;
-  F.x = f.x - gam * (R)px + nx;
-  F.y = f.y - gam * (R)py + ny;
-  F.z = f.z - gam * (R)pz + nz;
+  F.x = f.x - gam * px + nx;
+  F.y = f.y - gam * py + ny;
+  F.z = f.z - gam * pz + nz;
   if (mode != 0) {
     const R c = sys_comb<R>(S);
     F.x *= c; F.y *= c; F.z *= c;
@@ -1138,8 +1182,8 @@ __device__ __forceinline__ bool finite_bits(double v) {
   return (__double2hiint(v) & 0x7ff00000) != 0x7ff00000;
 }
 
-// Combine (R) + momentum half of step k + position half of step k+1 (float64),
-// then the cell of x^{k+1} and its rank in the bucket counter.
+// Float64 path: combine + momentum half of step k + position half of step
+// k+1, then the cell of x^{k+1} and its rank in the bucket counter.
 //
 // Position half of Algorithm 1: with y = x + (dt/m)(p + h F) and
 // a = dt^2/(2m), x^{k+1} = y - a lambda n0 with n0 = grad g(x^k). After its
@@ -1148,8 +1192,8 @@ __device__ __forceinline__ bool finite_bits(double v) {
 // (n1 = n0 for the frozen-normal variant). Stop when |g| < eta |n|, with
 // |n| = |n0| (the two differ by |x - x^k| times the curvature), or when the
 // update falls under 4 ulp of the position (round-off floor).
-template <typename R, bool BIN>
-__device__ __forceinline__ void integrate_particle(const DevArrays& A, int64_t i, Force3<R> fr_in) {
+template <bool BIN>
+__device__ __forceinline__ void integrate_particle_fp64(const DevArrays& A, int64_t i, Force3<double> fr_in) {
   const int64_t n = A.n;
   const unsigned long long k = *A.step;
   const int mode = *A.mode;
@@ -1159,25 +1203,15 @@ __device__ __forceinline__ void integrate_particle(const DevArrays& A, int64_t i
   const uint32_t ty = meta_type(m);
   const double x = A.x[i], y = A.x[n + i], z = A.x[2 * n + i];
   double px = A.ph[i], py = A.ph[n + i], pz = A.ph[2 * n + i];
-  const Force3<R> Fr = combine<R>(S, T, ty, (uint32_t)(i - S.first), k, mode, fr_in, px, py, pz);
-  const double Fx = (double)Fr.x, Fy = (double)Fr.y, Fz = (double)Fr.z;
+  const Force3<double> Fr = combine<double>(S, T, ty, (uint32_t)(i - S.first), k, mode, fr_in, px, py, pz);
+  const double Fx = Fr.x, Fy = Fr.y, Fz = Fr.z;
   const double h = S.half_dt;
   const bool con = meta_con(m);
-  constexpr bool kMixed = sizeof(R) == 4;
   double n0x = 0.0, n0y = 0.0, n0z = 0.0, nn = 1.0, inv_nn = 0.0;
-  float n0xf = 0.f, n0yf = 0.f, n0zf = 0.f;
   if (con) {
-    if (kMixed) {
-      surf_grad_f(S, (float)x - S.c_f[0], (float)y - S.c_f[1], (float)z - S.c_f[2], n0xf, n0yf, n0zf);
-      const float nnf = fmaf(n0xf, n0xf, fmaf(n0yf, n0yf, n0zf * n0zf));
-      n0x = n0xf; n0y = n0yf; n0z = n0zf;
-      nn = nnf;
-      inv_nn = (double)(1.0f / nnf);
-    } else {
-      surf_n(S, surf_g(S, x, y, z), n0x, n0y, n0z);
-      nn = fma(n0x, n0x, fma(n0y, n0y, n0z * n0z));
-      inv_nn = nr_rcp(nn);
-    }
+    surf_n(S, surf_g(S, x, y, z), n0x, n0y, n0z);
+    nn = fma(n0x, n0x, fma(n0y, n0y, n0z * n0z));
+    inv_nn = nr_rcp(nn);
   }
   if (mode != 0) momentum_half(h, Fx, Fy, Fz, con, n0x, n0y, n0z, inv_nn, px, py, pz);
   double qx = fma(h, Fx, px), qy = fma(h, Fy, py), qz = fma(h, Fz, pz);  // p^{k+1/2} before the constraint
@@ -1202,10 +1236,6 @@ __device__ __forceinline__ void integrate_particle(const DevArrays& A, int64_t i
       double dl;
       if (S.frozen) {
         dl = e.g * inv_a_nn;
-      } else if (kMixed) {  // Newton denominator a n1.n0 in float32 (the step only needs ~1e-7)
-        float n1x, n1y, n1z;
-        surf_n_f(S, e, n1x, n1y, n1z);
-        dl = e.g * (double)(1.0f / ((float)a * fmaf(n1x, n0xf, fmaf(n1y, n0yf, n1z * n0zf))));
       } else {
         double n1x, n1y, n1z;
         surf_n(S, e, n1x, n1y, n1z);
@@ -1233,7 +1263,221 @@ __device__ __forceinline__ void integrate_particle(const DevArrays& A, int64_t i
   A.ph[i] = qx; A.ph[n + i] = qy; A.ph[2 * n + i] = qz;
   if (BIN) {
     bool out = false;
-    const uint32_t cell = cell_of<R>(S, xn, yn, zn, out);
+    const uint32_t cell = cell_of_d(S, xn, yn, zn, out);
+    if (out) flag(A.status, kFlagOutOfGrid);
+    A.cell[i] = cell;
+    A.rank[i] = atomicAdd(&A.count[bucket_of(cell, A.hashed, A.log_t)], 1u);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Mixed path: float32 forces, noise, surface direction, Newton denominator and
+// stopping tests; float64 positions, momenta, constraint values and updates.
+//
+// Algorithm 1 in multiplier form. The momentum half at x^k and the kick of the
+// position half give q = p^{k-1/2} + dt F^k - s n0, s = n0.(p^{k-1/2} + h F^k)
+// / |n0|^2, n0 = grad g(x^k); the position half then subtracts h lambda n0.
+// Both corrections lie along n0, so with q0 = p^{k-1/2} + dt F^k,
+// y = x^k + (dt/m) q0 and mu = (dt/m)(s + h lambda):
+//   x^{k+1} = y - mu n0,   p^{k+1/2} = q0 - (m/dt) mu n0,   g(y - mu n0) = 0.
+// The projection s only sets where the Newton iteration starts (mu_0 =
+// (dt/m) s, formed in float32), not its root. On the first step after a state
+// is set there is no momentum half: q0 = p^k + h F^k, mu_0 = 0.
+//
+// The position-half Newton update lambda += g / (a n1.n0) of Algorithm 1 reads
+// mu += g(x(mu)) / (n1.n0) on the line x(mu) = y - mu n0 (mu = a lambda,
+// n1 = grad g(x(mu)); n1 = n0 in the frozen-normal variant), and g along that
+// line is evaluated by the surface's line form below. The full-step momentum
+// p^k is not needed by the step and is formed only on read-out.
+// ---------------------------------------------------------------------------
+
+// Quadric surfaces (plane, sphere, ellipsoid, cylinder): g along the line is
+// exactly g(y) - b mu + c mu^2 with b = grad g(y).n0 and c = n0.H n0 / 2 (H the
+// constant Hessian), so n1.n0 = -dg/dmu = b - 2 c mu.
+struct LineQuadric {
+  double g0, b, c;
+  float bf, cf;
+  __device__ __forceinline__ double g(double mu) { return fma(mu, fma(mu, c, -b), g0); }
+  __device__ __forceinline__ float n1n0(float mu) const { return fmaf(-2.f * mu, cf, bf); }
+};
+
+// Torus: with d = y - centre, rho the in-plane radius and z = d_z - mu n0_z,
+// g = (rho - R)^2 + z^2 - r^2 and rho(mu)^2 = rho_y^2 + D(mu), D = -2 A1 mu +
+// A2 mu^2 (A1 = d_xy.n0_xy, A2 = |n0_xy|^2). rho(mu) is advanced from rho_y by
+// the series sqrt(rho_y^2 + D) = rho_y + w - w^2 / (2 rho_y) + ..., w = D /
+// (2 rho_y), whose next term, w^3 / (2 rho_y^2), is below 1e-15 rho_y while
+// |w| < 1e-5 rho_y (a time step moves a particle far less); beyond that bound
+// rho(mu) is taken from its square root directly.
+struct LineTorus {
+  double dz, tY, rho2, a1x2, a2, inv2rho, n0z, R, mr2;
+  float rhoyf, inv2rhof, a1f, a2f, n0zf, Rf;
+  float ttf, zf;  // rho - R and z at the last evaluation (for n1.n0)
+  __device__ __forceinline__ double g(double mu) {
+    const double D = mu * fma(mu, a2, -a1x2);
+    const double w = D * inv2rho;
+    const float wf = d2f_rn(w);
+    double tt;
+    if (fabsf(wf) < 1e-5f * rhoyf) {
+      tt = (tY + w) - f2d(wf * wf * inv2rhof);
+    } else {
+      const double q2 = rho2 + D;
+      tt = q2 * nr_rsqrt(q2) - R;
+    }
+    const double z = fma(-mu, n0z, dz);
+    ttf = d2f_rn(tt);
+    zf = d2f_rn(z);
+    return fma(tt, tt, fma(z, z, mr2));
+  }
+  // n1 = (2 (rho - R) / rho) (d_xy - mu n0_xy, 0) + (0, 0, 2 z)
+  __device__ __forceinline__ float n1n0(float mu) const {
+    return 2.f * ttf / (ttf + Rf) * fmaf(-mu, a2f, a1f) + 2.f * zf * n0zf;
+  }
+};
+
+// Any other surface: g re-evaluated at x(mu).
+struct LineGeneric {
+  const SysDev* S;
+  double yx, yy, yz, n0x, n0y, n0z;
+  float n0xf, n0yf, n0zf;
+  GEval e;
+  __device__ __forceinline__ double g(double mu) {
+    e = surf_g(*S, fma(-mu, n0x, yx), fma(-mu, n0y, yy), fma(-mu, n0z, yz));
+    return e.g;
+  }
+  __device__ __forceinline__ float n1n0(float) const {
+    float n1x, n1y, n1z;
+    surf_n_f(*S, e, n1x, n1y, n1z);
+    return fmaf(n1x, n0xf, fmaf(n1y, n0yf, n1z * n0zf));
+  }
+};
+
+// Newton on the line from mu_0: stop when |g| < tol_n (tolerance times |n0|,
+// with a 1% margin for |n(x^{k+1})| != |n0|) or when an update falls under the
+// round-off floor (4 ulp of the position).
+template <class L>
+__device__ __forceinline__ bool newton_line(L& line, int max_newton, bool frozen, float nnf, float tol_n,
+                                            float floor_mu, float mu0f, double& mu) {
+  mu = f2d(mu0f);
+  double g = line.g(mu);
+  for (int it = 0; it <= max_newton; ++it) {
+    const float gf = d2f_rn(g);
+    if (fabsf(gf) < tol_n) return true;
+    if (it == max_newton) break;
+    const float rden = __frcp_rn(frozen ? nnf : line.n1n0(d2f_rn(mu)));
+    mu = fma(g, f2d(rden), mu);
+    if (it > 0 && fabsf(gf * rden) <= floor_mu) return true;
+    g = line.g(mu);
+  }
+  return false;
+}
+
+template <bool BIN>
+__device__ __forceinline__ void integrate_particle_mixed(const DevArrays& A, int64_t i, Force3<float> fr_in) {
+  const int64_t n = A.n;
+  const unsigned long long k = *A.step;
+  const int mode = *A.mode;
+  const uint32_t m = A.meta[i];
+  const SysDev& S = A.sys[meta_sys(m)];
+  const uint32_t ty = meta_type(m);
+  const double x = A.x[i], y = A.x[n + i], z = A.x[2 * n + i];
+  const double px = A.ph[i], py = A.ph[n + i], pz = A.ph[2 * n + i];
+  const float pxf = d2f_rn(px), pyf = d2f_rn(py), pzf = d2f_rn(pz);
+  const Force3<float> F = combine<float>(S, A.types, ty, (uint32_t)(i - S.first), k, mode, fr_in, pxf, pyf, pzf);
+  const double kick = mode ? S.dt : S.half_dt;
+  double qx = fma(kick, f2d(F.x), px), qy = fma(kick, f2d(F.y), py), qz = fma(kick, f2d(F.z), pz);
+  const double dtm = S.dtm[ty];
+  const double yx = fma(dtm, qx, x), yy = fma(dtm, qy, y), yz = fma(dtm, qz, z);
+  double xn = yx, yn = yy, zn = yz;
+  if (meta_con(m)) {
+    const float xf = d2f_rn(x), yf = d2f_rn(y), zf = d2f_rn(z);
+    float n0xf, n0yf, n0zf;
+    surf_grad_f(S, xf - S.c_f[0], yf - S.c_f[1], zf - S.c_f[2], n0xf, n0yf, n0zf);
+    const float nnf = fmaf(n0xf, n0xf, fmaf(n0yf, n0yf, n0zf * n0zf));
+    float mu0f = 0.f;
+    if (mode) {  // mu_0 = (dt/m) n0.(p + h F) / |n0|^2
+      const float hf = S.half_dt_f;
+      const float sp = fmaf(n0xf, fmaf(hf, F.x, pxf), fmaf(n0yf, fmaf(hf, F.y, pyf), n0zf * fmaf(hf, F.z, pzf)));
+      mu0f = S.dtm_f[ty] * sp / nnf;
+    }
+    const float tol_n = 0.99f * S.tol_f * sqrtf(nnf);
+    const float floor_mu = 4.f * (float)DBL_EPSILON * fmaxf(fabsf(xf), fmaxf(fabsf(yf), fabsf(zf))) /
+                           fmaxf(fabsf(n0xf), fmaxf(fabsf(n0yf), fabsf(n0zf)));
+    const double n0x = f2d(n0xf), n0y = f2d(n0yf), n0z = f2d(n0zf);
+    const double dx = yx - S.c[0], dy = yy - S.c[1], dz = yz - S.c[2];
+    double mu;
+    bool ok;
+    switch (S.kind) {
+      case kSphere:
+      case kCylinder:
+      case kEllipsoid:
+      case kPlane: {
+        LineQuadric L;
+        const double tx = f2d(2.f * n0xf), ty2 = f2d(2.f * n0yf), tz = f2d(2.f * n0zf);  // 2 n0, exact
+        if (S.kind == kEllipsoid) {
+          const double ux = dx * S.inv_a2[0], uy = dy * S.inv_a2[1], uz = dz * S.inv_a2[2];
+          L.g0 = fma(ux, dx, fma(uy, dy, fma(uz, dz, -1.0)));
+          L.b = fma(ux, tx, fma(uy, ty2, uz * tz));
+          L.cf = fmaf(n0xf * n0xf, S.inv_a2_f[0], fmaf(n0yf * n0yf, S.inv_a2_f[1], n0zf * n0zf * S.inv_a2_f[2]));
+        } else if (S.kind == kPlane) {
+          L.g0 = fma(S.p[0], dx, fma(S.p[1], dy, S.p[2] * dz));
+          L.b = fma(S.p[0], n0x, fma(S.p[1], n0y, S.p[2] * n0z));
+          L.cf = 0.f;
+        } else {  // sphere; cylinder with the axis component of d dropped (n0 has none)
+          const double ex = (S.kind == kCylinder && S.axis == 0) ? 0.0 : dx;
+          const double ey = (S.kind == kCylinder && S.axis == 1) ? 0.0 : dy;
+          const double ez = (S.kind == kCylinder && S.axis == 2) ? 0.0 : dz;
+          L.g0 = fma(ex, ex, fma(ey, ey, fma(ez, ez, S.gconst)));
+          L.b = fma(ex, tx, fma(ey, ty2, ez * tz));
+          L.cf = nnf;
+        }
+        L.c = f2d(L.cf);
+        L.bf = d2f_rn(L.b);
+        ok = newton_line(L, S.max_newton, S.frozen, nnf, tol_n, floor_mu, mu0f, mu);
+        break;
+      }
+      case kTorus: {
+        LineTorus L;
+        L.rho2 = fma(dx, dx, dy * dy);
+        const double ir = nr_rsqrt(L.rho2);
+        L.R = S.p[0];
+        L.mr2 = S.gconst;
+        L.tY = fma(L.rho2, ir, -L.R);
+        L.inv2rho = 0.5 * ir;
+        L.dz = dz;
+        L.n0z = n0z;
+        L.a1x2 = fma(dx, f2d(2.f * n0xf), dy * f2d(2.f * n0yf));
+        L.a2f = fmaf(n0xf, n0xf, n0yf * n0yf);
+        L.a2 = f2d(L.a2f);
+        L.a1f = 0.5f * d2f_rn(L.a1x2);
+        L.inv2rhof = d2f_rn(L.inv2rho);
+        L.Rf = S.p_f[0];
+        L.rhoyf = d2f_rn(L.tY) + L.Rf;
+        L.n0zf = n0zf;
+        ok = newton_line(L, S.max_newton, S.frozen, nnf, tol_n, floor_mu, mu0f, mu);
+        break;
+      }
+      default: {
+        LineGeneric L;
+        L.S = &S;
+        L.yx = yx; L.yy = yy; L.yz = yz;
+        L.n0x = n0x; L.n0y = n0y; L.n0z = n0z;
+        L.n0xf = n0xf; L.n0yf = n0yf; L.n0zf = n0zf;
+        ok = newton_line(L, S.max_newton, S.frozen, nnf, tol_n, floor_mu, mu0f, mu);
+      }
+    }
+    if (!ok) flag(A.status, kFlagRattle);
+    xn = fma(-mu, n0x, yx); yn = fma(-mu, n0y, yy); zn = fma(-mu, n0z, yz);
+    const double c = mu * S.inv_dtm[ty];
+    qx = fma(-c, n0x, qx); qy = fma(-c, n0y, qy); qz = fma(-c, n0z, qz);
+  }
+  if (!(finite_bits(xn) && finite_bits(yn) && finite_bits(zn) && finite_bits(qx) && finite_bits(qy) &&
+        finite_bits(qz)))
+    flag(A.status, kFlagNonfinite);
+  A.x[i] = xn; A.x[n + i] = yn; A.x[2 * n + i] = zn;
+  A.ph[i] = qx; A.ph[n + i] = qy; A.ph[2 * n + i] = qz;
+  if (BIN) {
+    bool out = false;
+    const uint32_t cell = cell_of_f(S, xn, yn, zn, out);
     if (out) flag(A.status, kFlagOutOfGrid);
     A.cell[i] = cell;
     A.rank[i] = atomicAdd(&A.count[bucket_of(cell, A.hashed, A.log_t)], 1u);
@@ -1244,7 +1488,8 @@ template <typename R, bool BIN>
 __global__ void __launch_bounds__(256, 4) k_integrate(DevArrays A) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
-  integrate_particle<R, BIN>(A, i, load_f3<R>(A.f, i));
+  if constexpr (sizeof(R) == 4) integrate_particle_mixed<BIN>(A, i, load_f3<float>(A.f, i));
+  else integrate_particle_fp64<BIN>(A, i, load_f3<double>(A.f, i));
 }
 
 __global__ void k_advance(unsigned long long* step, int32_t* mode) {
@@ -1270,7 +1515,8 @@ __global__ void k_finish(DevArrays A) {
   const uint32_t ty = meta_type(m);
   const double x = A.x[i], y = A.x[n + i], z = A.x[2 * n + i];
   double px = A.ph[i], py = A.ph[n + i], pz = A.ph[2 * n + i];
-  const Force3<R> Fr = combine<R>(S, A.types, ty, (uint32_t)(i - S.first), k, 1, load_f3<R>(A.f, i), px, py, pz);
+  const Force3<R> Fr = combine<R>(S, A.types, ty, (uint32_t)(i - S.first), k, 1, load_f3<R>(A.f, i), (R)px, (R)py,
+                                  (R)pz);
   const bool con = meta_con(m);
   double nx = 0.0, ny = 0.0, nz = 0.0, inv_nn = 0.0;
   if (con) {

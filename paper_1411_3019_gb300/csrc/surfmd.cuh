@@ -44,8 +44,13 @@ struct SysDev {
   double tol, tol2;           // RATTLE tolerance and its square
   float gamma_f, comb_f, noise_unit_f;
   int32_t max_newton, frozen;
+  // per particle type: dt/m and m/dt (float64), dt/m (float32)
+  double dtm[kMaxTypes], inv_dtm[kMaxTypes];
+  float dtm_f[kMaxTypes];
+  float half_dt_f, tol_f;
+  double gconst;             // constant term of g: -R^2 (sphere, cylinder), -r^2 (torus)
   // box and cell grid
-  double box_lo[3], box_len[3];
+  double box_lo[3], box_len[3], inv_box_len[3];
   int32_t periodic[3];
   int32_t pad0;
   double grid_lo[3], cs[3], inv_cs[3];

@@ -20,7 +20,8 @@ def _systems(precision):
                          dt=0.002, tol=tol)
 
 
-def _run(systems, nsteps, **opts):
+def _run(systems, nsteps, opts=None):
+    opts = opts or {}
     sim = md.Simulation(systems)
     for key, val in opts.items():
         md.md_set_option(sim.h, key, val)
@@ -39,7 +40,7 @@ def _run(systems, nsteps, **opts):
 @pytest.mark.parametrize("order", [0, 1])
 def test_every_option_setting_matches_oracle(precision, lanes, order):
     systems = _systems(precision)
-    st, f, got = _run(systems, 30, **{md.MD_OPT_PAIR_LANES: lanes, md.MD_OPT_PAIR_ORDER: order})
+    st, f, got = _run(systems, 30, {md.MD_OPT_PAIR_LANES: lanes, md.MD_OPT_PAIR_ORDER: order})
     assert got == {md.MD_OPT_PAIR_LANES: lanes, md.MD_OPT_PAIR_ORDER: order}
     ref = oracle_run(systems, 30)[0]
     assert np.abs(st["x"] - ref["x"]).max() <= POS_100[precision]
@@ -49,8 +50,8 @@ def test_every_option_setting_matches_oracle(precision, lanes, order):
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_visiting_order_changes_no_bit(precision):
     systems = _systems(precision)
-    a = _run(systems, 40, **{md.MD_OPT_PAIR_ORDER: 0})
-    b = _run(systems, 40, **{md.MD_OPT_PAIR_ORDER: 1})
+    a = _run(systems, 40, {md.MD_OPT_PAIR_ORDER: 0})
+    b = _run(systems, 40, {md.MD_OPT_PAIR_ORDER: 1})
     for key in ("x", "v", "p_half"):
         assert np.array_equal(a[0][key], b[0][key]), key
     assert np.array_equal(a[1], b[1])
