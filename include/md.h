@@ -313,6 +313,18 @@ int md_forces_noalloc(const md_surface* surf, const md_params* prm, int64_t n,
                       const uint8_t* d_constrained, double* d_f, double* d_u,
                       void* cuda_stream);
 
+/* Diagnostic (no counterpart in the paper): runs on the current device the
+ * float64 -> float32 (round to nearest, ties to even) and float32 -> float64
+ * format conversions that the mixed-precision kernels perform with integer
+ * operations on the IEEE 754 bit fields, so that they can be checked against
+ * any IEEE 754 implementation.
+ *   in [n] float64, out_f32 [n] = in rounded to float32, out_f64 [n] =
+ *   out_f32 widened to float64; all three are host memory owned by the
+ *   caller; n >= 0 (n = 0 does nothing).
+ * Synchronous; allocates and frees its own device buffers. Errors are read
+ * with md_last_error(NULL). */
+int md_check_conversions(const double* in, int64_t n, float* out_f32, double* out_f64);
+
 /* Description of the last error on h (or of the last md_create failure
  * when h is NULL). Never NULL. */
 const char* md_last_error(md_handle* h);

@@ -1006,6 +1006,27 @@ int md_cell_list(md_handle* h, uint32_t* sorted_ids, uint32_t* sorted_cells, uin
   return check_device_status(h);
 }
 
+int md_check_conversions(const double* in, int64_t n, float* out_f32, double* out_f64) {
+  if (n < 0 || (n > 0 && (!in || !out_f32 || !out_f64))) return fail(nullptr, MD_ERR_INVALID_ARG, "bad arguments");
+  if (n == 0) return MD_OK;
+  double* d_in = nullptr;
+  double* d_d = nullptr;
+  float* d_f = nullptr;
+  const size_t nb = (size_t)n;
+  cudaError_t e = cudaMalloc(&d_in, nb * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_d, nb * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_f, nb * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(d_in, in, nb * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_check_conversions(d_in, n, d_f, d_d, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(out_f32, d_f, nb * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(out_f64, d_d, nb * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d_in);
+  cudaFree(d_d);
+  cudaFree(d_f);
+  if (e != cudaSuccess) return fail(nullptr, MD_ERR_CUDA, std::string("conversion check: ") + cudaGetErrorString(e));
+  return MD_OK;
+}
+
 const char* md_last_error(md_handle* h) {
   if (!h) return g_create_err.c_str();
   return h->err.c_str();

@@ -60,6 +60,10 @@ cudaError_t launch_get_state(const DevArrays& A, double* d_x_aos, double* d_v_ao
 cudaError_t launch_get_forces(const DevArrays& A, int precision, double* d_f_aos, double* d_u,
                               cudaStream_t st);
 
+// out_f[i] = in[i] rounded to float32, out_d[i] = out_f[i] widened to float64,
+// by the integer-pipe conversions of the mixed path.
+cudaError_t launch_check_conversions(const double* in, int64_t n, float* out_f, double* out_d, cudaStream_t st);
+
 // Residuals: out[0] = max |g|/|grad g|, out[1] = max |g|, out[2] = max |n.v|/|n|
 // (stored as the bit patterns of non-negative doubles; zeroed inside).
 cudaError_t launch_residual(const DevArrays& A, unsigned long long* d_out, cudaStream_t st);

@@ -1822,6 +1822,21 @@ cudaError_t launch_get_state(const DevArrays& A, double* xa, double* va, double*
   return cudaGetLastError();
 }
 
+__global__ void k_check_conversions(const double* __restrict__ in, int64_t n, float* __restrict__ out_f,
+                                    double* __restrict__ out_d) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float f = d2f_rn(in[i]);
+  out_f[i] = f;
+  out_d[i] = f2d(f);
+}
+
+cudaError_t launch_check_conversions(const double* in, int64_t n, float* out_f, double* out_d, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_check_conversions<<<grid_for(n, 256), 256, 0, st>>>(in, n, out_f, out_d);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_get_forces(const DevArrays& A, int precision, double* fa, double* ua, cudaStream_t st) {
   if (A.n == 0) return cudaSuccess;
   if (precision == 0) k_get_forces<double><<<grid_for(A.n, 256), 256, 0, st>>>(A, fa, ua);

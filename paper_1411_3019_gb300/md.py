@@ -112,6 +112,7 @@ def lib():
                 "md_forces_noalloc": ([C.POINTER(md_surface), C.POINTER(md_params), i64, dp, dp, dp, dp, dp,
                                        dp, vp], C.c_int),
                 "md_set_option": ([vp, i32, i64], C.c_int),
+                "md_check_conversions": ([vp, i64, vp, vp], C.c_int),
                 "md_get_option": ([vp, i32, C.POINTER(i64)], C.c_int),
                 "md_last_error": ([vp], C.c_char_p),
                 "md_destroy": ([vp], None),
@@ -354,6 +355,16 @@ def md_forces_noalloc(surface: dict | None, params: dict, n: int, d_x, d_f, d_ty
     rc = lib().md_forces_noalloc(C.byref(S), C.byref(P), int(n), _dptr(d_x), _dptr(d_type), _dptr(d_mol),
                                  _dptr(d_con), _dptr(d_f), _dptr(d_u), C.c_void_p(sptr) if sptr else None)
     _check(None, rc)
+
+
+def md_check_conversions(values) -> tuple[np.ndarray, np.ndarray]:
+    """float64 values rounded to float32 and widened back, by the device's
+    integer-pipe conversions (a diagnostic of the mixed path)."""
+    v = np.ascontiguousarray(values, dtype=np.float64)
+    f = np.empty(v.shape, np.float32)
+    d = np.empty(v.shape, np.float64)
+    _check(None, lib().md_check_conversions(v.ctypes.data, v.size, f.ctypes.data, d.ctypes.data))
+    return f, d
 
 
 def md_set_option(h, key: int, value: int) -> None:
