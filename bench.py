@@ -20,6 +20,7 @@ the data path; the timing uses a barrier and max/sum reductions only).
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import math
@@ -48,7 +49,7 @@ SM_MAX_MHZ = 2070.0
 def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="surfmd", choices=["surfmd", "reference"])
     ap.add_argument("--workload", default="ellipsoid_torus", choices=WORKLOADS)
@@ -119,19 +120,54 @@ def reduce_over_ranks(dist, ms_local: float, n_local: float, device=None):
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling every 200 ms from construction to stop(); only the
+    samples whose timestamps fall inside [mark_start, mark_end] are kept."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device_index: int):
         self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.proc = None
+        self.t0 = self.t1 = None
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", "200", "-i", str(device_index)], stdout=self.file, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+
+    def mark_start(self):
+        self.t0 = datetime.datetime.now()
+
+    def mark_end(self):
+        self.t1 = datetime.datetime.now()
+
+    @staticmethod
+    def parse(text: str, t0, t1):
+        sm, smax, reasons, n_all = [], [], set(), 0
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in text.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                mhz, mhz_max = float(parts[2]), float(parts[3])
+            except ValueError:
+                continue
+            n_all += 1
+            if t0 is not None and not (t0 <= ts <= t1):
+                continue
+            sm.append(mhz)
+            smax.append(mhz_max)
+            for nm, val in zip(names, parts[6:10]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "window_s": round((t1 - t0).total_seconds(), 3) if t0 else None}
 
     def stop(self):
         if self.proc is None:
@@ -143,25 +179,9 @@ class ClockSampler:
             self.proc.kill()
         self.file.flush()
         self.file.seek(0)
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.file.read().splitlines():
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, val in zip(names, parts[5:9]):
-                if val.lower() == "active":
-                    reasons.add(nm)
+        text = self.file.read()
         os.unlink(self.file.name)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return self.parse(text, self.t0, self.t1)
 
 
 # ---------------------------------------------------------------------------
@@ -226,6 +246,8 @@ def rooflines(prof_ms, n, nbucket, precision, hbm_peak, counts, sm_mhz):
             row["fp64_frac"] = c["fp64_inst"] / (ms / 1e3) / fp64_peak
         if "dram_bytes" in c:
             row["traffic"] = c["dram_bytes"]
+        if "fma_pct" in c:  # sm__pipe_fma_cycles_active: the float32 pipe's busy fraction (ncu)
+            row["fp32_pipe_frac"] = c["fma_pct"] / 100.0
         table[k] = row
     top = max(prof_ms, key=prof_ms.get)
     r = table[top]
@@ -237,6 +259,8 @@ def rooflines(prof_ms, n, nbucket, precision, hbm_peak, counts, sm_mhz):
     else:
         main = {"bound": "hbm", "kernel": top, "achieved": r["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
                 "frac": r["hbm_frac"], "traffic": r.get("traffic"), "peak_source": "measured"}
+    if "fp32_pipe_frac" in r:
+        main["fp32_pipe_frac"] = r["fp32_pipe_frac"]
     main["per_kernel"] = table
     return main
 
@@ -268,6 +292,7 @@ def main(argv=None):
             dist.barrier()
 
     stream = torch.cuda.Stream()
+    clocks = ClockSampler(local) if rank == 0 else None  # sampling from here; the timed window is marked below
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def timed_steps(sim, k):
@@ -304,12 +329,15 @@ def main(argv=None):
 
     barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.mark_start()
     t_wall0 = time.perf_counter()
     durs, launches = timed_steps(sim, args.steps)
     torch.cuda.synchronize()
     barrier()
     t_wall = time.perf_counter() - t_wall0
+    if clocks:
+        clocks.mark_end()
     clk = clocks.stop() if clocks else None
     sim.sync()
     res = sim.residual()

@@ -1,0 +1,34 @@
+"""Host-side logic of bench.py: the clock record keeps only the samples taken
+inside the timed window and reports throttle reasons seen there."""
+import datetime
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+import bench  # noqa: E402
+
+
+def _row(t, mhz, reasons=("Not Active",) * 4):
+    return (f"{t.strftime('%Y/%m/%d %H:%M:%S.%f')[:-3]}, 0, {mhz}, 2070, 900.5, 0x0, "
+            + ", ".join(reasons))
+
+
+def test_clock_samples_outside_the_window_are_dropped():
+    t = datetime.datetime(2026, 1, 2, 3, 4, 5)
+    ms = datetime.timedelta(milliseconds=200)
+    rows = [_row(t, 1000), _row(t + ms, 2070), _row(t + 2 * ms, 2070),
+            _row(t + 3 * ms, 1900, ("Not Active", "Not Active", "Not Active", "Active")),
+            _row(t + 5 * ms, 500, ("Active", "Not Active", "Not Active", "Not Active"))]
+    out = bench.ClockSampler.parse("\n".join(rows), t + ms / 2, t + 3 * ms + ms / 2)
+    assert out["samples"] == 3
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+    assert abs(out["window_s"] - 0.6) < 1e-9
+
+
+def test_no_sample_in_the_window_gives_none():
+    t = datetime.datetime(2026, 1, 2, 3, 4, 5)
+    assert bench.ClockSampler.parse(_row(t, 2070), t + datetime.timedelta(seconds=1),
+                                    t + datetime.timedelta(seconds=2)) is None
+    assert bench.ClockSampler.parse("garbage line\n", None, None) is None
