@@ -57,6 +57,9 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the float64 comparison leg")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch options")
+    ap.add_argument("--engine", default="auto", choices=["auto", "global", "resident"],
+                    help="auto: the autotuner picks the engine and its options")
+    ap.add_argument("--nrep", type=int, default=4096, help="systems of the replicas workload")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args(argv)
@@ -69,7 +72,7 @@ def rank_seed(rank: int) -> int:
     return 1 + rank
 
 
-def workload(name: str, rank: int, precision: str):
+def workload(name: str, rank: int, precision: str, nrep: int = 4096):
     """The systems rank `rank` advances: an independently seeded copy of the
     named workload (weak scaling)."""
     from paper_1411_3019_gb300 import inputs
@@ -81,7 +84,7 @@ def workload(name: str, rank: int, precision: str):
         return [inputs.sphere_system(1000, 10.0, seed=seed, dmin=0.8, precision=precision, dt=0.001,
                                      tol=1e-12 if precision == "fp64" else 1e-10)]
     if name == "replicas":
-        return inputs.c4_replicas(seed=seed, precision=precision)
+        return inputs.c4_replicas(nrep=nrep, seed=seed, precision=precision)
     if name == "bead_molecules":
         return inputs.c5_bead_molecules(seed=seed, precision=precision)
     if name == "bump_crowders":
@@ -189,7 +192,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 def algorithmic_bytes(kernel: str, n: int, nbucket: int, precision: str) -> float:
     """Bytes each kernel must move per launch if every datum is read or written
-    once."""
+    once (per step for the resident engine's entry)."""
     v4 = 16 if precision == "mixed" else 32
     tiles = math.ceil(nbucket / 8192)
     per = {
@@ -203,6 +206,9 @@ def algorithmic_bytes(kernel: str, n: int, nbucket: int, precision: str) -> floa
         "scatter": n * (4 + 4 + 4 + 4),
         # slot id, cell, meta, x (3 x float64), bucket range; record, sorted id, sorted cell
         "bucket_build": n * (4 + 4 + 4 + 24 + 8 + v4 + 4 + 4),
+        # resident engine, per step: meta, x, p_half read; x, p_half written (the
+        # cell list and forces stay in shared memory)
+        "resident": n * (4 + 24 + 24 + 24 + 24),
     }
     return float(per.get(kernel, 0))
 
@@ -311,7 +317,20 @@ def main(argv=None):
         stream.synchronize()
         return [a.elapsed_time(b) for a, b in evs], launches
 
-    systems = workload(args.workload, rank, precision)
+    def timed_resident(sim, k):
+        """k steps in one md_step call (the resident engine's persistent
+        launches plus its one cell-list rebuild), bracketed by CUDA events;
+        the L2 is flushed before; the state (x and p) is larger than L2."""
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.add_(1.0)
+            a.record(stream)
+            sim.step(k)
+            b.record(stream)
+        stream.synchronize()
+        return [a.elapsed_time(b) / k] * k, md.md_last_launch_count(sim.h)
+
+    systems = workload(args.workload, rank, precision, args.nrep)
     n_local = int(sum(s["n"] for s in systems))
     sim = md.Simulation(systems, stream=stream)
     sim.set_state()
@@ -321,7 +340,10 @@ def main(argv=None):
 
     tuned = {"options": {"pair_order": md.md_get_option(sim.h, md.MD_OPT_PAIR_ORDER),
                          "pair_lanes": md.md_get_option(sim.h, md.MD_OPT_PAIR_LANES)}}
-    if not args.no_tune:
+    if args.engine == "resident":
+        md.md_set_option(sim.h, md.MD_OPT_ENGINE, 1)
+        tuned = {"options": {"engine": 1, "resident_threads": md.md_get_option(sim.h, md.MD_OPT_RESIDENT_THREADS)}}
+    elif args.engine == "auto" and not args.no_tune:
         with torch.cuda.stream(stream):  # launch options chosen by the autotuner during warm-up
             tuned = tune.autotune(sim.h, trials=3, flush=lambda: flush.add_(1.0))
     sim.step(2)
@@ -332,7 +354,8 @@ def main(argv=None):
     if clocks:
         clocks.mark_start()
     t_wall0 = time.perf_counter()
-    durs, launches = timed_steps(sim, args.steps)
+    resident = md.md_get_option(sim.h, md.MD_OPT_ENGINE) == 1
+    durs, launches = (timed_resident if resident else timed_steps)(sim, args.steps)
     torch.cuda.synchronize()
     barrier()
     t_wall = time.perf_counter() - t_wall0
@@ -357,10 +380,14 @@ def main(argv=None):
     prof = {}
     nprof = min(args.steps, 20)
     with torch.cuda.stream(stream):
-        for _ in range(nprof):
+        if resident:  # the resident launches per step and the rebuild of one call spread over its steps
             flush.add_(1.0)
-            for kname, kms in md.md_profile_step(sim.h, 1).items():
-                prof[kname] = prof.get(kname, 0.0) + kms / nprof
+            prof = md.md_profile_step(sim.h, min(args.steps, 100))
+        else:
+            for _ in range(nprof):
+                flush.add_(1.0)
+                for kname, kms in md.md_profile_step(sim.h, 1).items():
+                    prof[kname] = prof.get(kname, 0.0) + kms / nprof
     nbucket = int(md.md_cell_list(sim.h)["bucket_start"].shape[0] - 1)
     peaks = {}
     try:
@@ -405,7 +432,7 @@ def main(argv=None):
 
     plain = None
     if not args.no_plain and precision == "mixed":
-        systems64 = workload(args.workload, rank, "fp64")
+        systems64 = workload(args.workload, rank, "fp64", args.nrep)
         sim64 = md.Simulation(systems64, stream=stream)
         sim64.set_state()
         sim64.step(args.warmup)
@@ -430,7 +457,11 @@ def main(argv=None):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64" if precision == "mixed" else "f64", "data": "synthetic",
-            "config": workload_config(args.workload, systems, precision),
+            "config": dict(workload_config(args.workload, systems, precision),
+                           **({"l2": f"one md_step({args.steps}) call (persistent resident launches), L2 flushed "
+                                     f"before it; the state x, p ({48 * n_local / 1e6:.0f} MB) is larger than "
+                                     f"the 129 MB L2"} if resident else {}),
+                           engine="resident" if resident else "global"),
             "residual_max_g_over_gradg": res["max_g_over_gradg"],
             "l2_resident": {"value": total_particles / (ms_resident / 1e3), "ms_per_step": ms_resident},
             "wall_s_timed_region": t_wall,
@@ -478,7 +509,7 @@ def reference_arm(args, rank: int, world: int, precision: str):
     time steps of the same workload (at most 60 timed steps)."""
     if rank != 0:
         return
-    systems = workload(args.workload, 0, precision)
+    systems = workload(args.workload, 0, precision, args.nrep)
     sims = _oracle_systems(systems)
     n = sum(s["n"] for s in systems)
     for _ in range(args.warmup):
@@ -494,7 +525,11 @@ def reference_arm(args, rank: int, world: int, precision: str):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
             "warmup": args.warmup, "ms_per_step": el / steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.workload, systems, precision), "impl": "reference",
+            "config": dict(workload_config(args.workload, systems, precision),
+                           **({"l2": f"one md_step({args.steps}) call (persistent resident launches), L2 flushed "
+                                     f"before it; the state x, p ({48 * n_local / 1e6:.0f} MB) is larger than "
+                                     f"the 129 MB L2"} if resident else {}),
+                           engine="resident" if resident else "global"), "impl": "reference",
             "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
                              "sample": f"{steps} whole time steps of the {n}-particle workload"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -220,6 +220,25 @@ int md_step(md_handle* h, int64_t nsteps);
  * spatial (Morton) order refreshed every 16 steps, so neighbouring threads
  * share cache lines; 0 = bucket order. */
 #define MD_OPT_PAIR_ORDER 2
+/* MD_OPT_ENGINE: 0 (default) = every step is one graph of five kernels over
+ * the whole batch with the cell list in global memory; 1 = resident engine:
+ * one persistent launch advances every system many steps, one CTA per
+ * system at a time with the system's cell list and forces in shared memory
+ * (x and p stay in global memory). Results are bit-identical to engine 0.
+ * Needs pair interactions and systems small enough for one CTA's shared
+ * memory (at most 65535 particles; about 46 bytes per particle plus 4 per
+ * bucket in mixed precision, 78 in float64); md_set_option returns
+ * MD_ERR_INVALID_ARG with the reason otherwise. md_step(n) then runs
+ * ceil(n / MD_OPT_RESIDENT_STEPS) launches and rebuilds the global cell list
+ * of the final positions once, and md_profile_step reports two entries:
+ * "resident" (the launches, per step) and "rebuild" (per step of the call). */
+#define MD_OPT_ENGINE 3
+/* MD_OPT_RESIDENT_THREADS: threads per CTA of the resident engine, a
+ * multiple of 32 in 64..512 (default 256). */
+#define MD_OPT_RESIDENT_THREADS 4
+/* MD_OPT_RESIDENT_STEPS: most steps one resident launch runs (1..100000,
+ * default 256); longer md_step calls are split into several launches. */
+#define MD_OPT_RESIDENT_STEPS 5
 int md_set_option(md_handle* h, int32_t key, int64_t value);
 int md_get_option(md_handle* h, int32_t key, int64_t* value);
 

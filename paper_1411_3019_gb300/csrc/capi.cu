@@ -48,6 +48,13 @@ struct md_handle {
   int64_t steps_since_order = 0;
   int64_t last_launches = 0;
   int kernels_per_step = 0;
+  // resident engine (MD_OPT_ENGINE = 1): systems largest first, a work counter
+  int engine = 0;
+  int res_threads = 256;
+  int64_t res_steps_per_launch = 256;
+  uint32_t res_nmax = 0, res_tmax = 0;
+  int32_t* d_res_order = nullptr;
+  uint32_t* d_res_next = nullptr;
   std::vector<void*> allocs;
   std::string err;
 
@@ -361,6 +368,40 @@ int build_graph(md_handle* h) {
   return MD_OK;
 }
 
+// Why the resident engine cannot run this handle ("" when it can).
+std::string resident_unfit(md_handle* h, int threads) {
+  if (!h->has_pairs) return "the resident engine needs pair interactions";
+  if (h->res_nmax > 65535) return "the resident engine holds at most 65535 particles per system";
+  if (h->res_nmax == 0) return "the batch has no particles";
+  const int per_sm = resident_blocks_per_sm(h->precision, h->bonds, h->walls, h->excl, h->res_nmax, h->res_tmax,
+                                            threads);
+  if (per_sm < 1)
+    return "the largest system (" + std::to_string(h->res_nmax) + " particles, " +
+           std::to_string(resident_smem_bytes(h->precision, h->res_nmax, h->res_tmax)) +
+           " bytes of shared memory) does not fit one CTA of " + std::to_string(threads) + " threads";
+  return "";
+}
+
+constexpr int64_t kRebuildLaunches = 7;  // bin, scan, scatter, bucket build, visiting order (3)
+
+// nsteps steps of every system by the resident engine, in launches of at most
+// res_steps_per_launch steps, then the global cell list of the new positions
+// (read by md_forces, md_get_state, the global engine and the observables).
+int resident_steps(md_handle* h, int64_t nsteps) {
+  int64_t launches = 0;
+  for (int64_t done = 0; done < nsteps;) {
+    const int64_t chunk = std::min(nsteps - done, h->res_steps_per_launch);
+    ResidentJob J{h->d_res_order, h->d_res_next, h->nsys, (int32_t)chunk, h->res_nmax, h->res_tmax};
+    CK(h, launch_resident(h->A, h->precision, J, h->bonds, h->walls, h->excl, h->res_threads, 0, h->stream()));
+    done += chunk;
+    launches += 2;
+  }
+  int rc = rebuild_cells(h);
+  if (rc) return rc;
+  h->last_launches = launches + kRebuildLaunches;
+  return MD_OK;
+}
+
 int forces_now(md_handle* h) {
   CK(h, launch_pair(h->A, h->precision, h->has_pairs, h->bonds, h->walls, h->excl, h->stream()));
   return MD_OK;
@@ -522,6 +563,30 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
       return fail(nullptr, MD_ERR_INVALID_ARG, "more than 2^32 cells in the batch");
     }
   }
+  // resident engine: per-system buckets in shared memory, the local cell id
+  // when the system's grid has at most 2^k >= 2n (and >= 64) cells, else a
+  // hash table of 2^k buckets
+  for (int s = 0; s < nsys; ++s) {
+    SysDev& S = h->sys[s];
+    uint32_t t = 64;
+    int lg = 6;
+    while ((int64_t)t < 2 * n_per_sys[s] && lg < 16) {
+      t <<= 1;
+      ++lg;
+    }
+    const uint64_t cells = (uint64_t)S.nc[0] * (uint64_t)S.nc[1] * (uint64_t)S.nc[2];
+    if (cells <= t) {
+      S.res_t = (uint32_t)cells;
+      S.res_hashed = 0;
+      S.res_log_t = 0;
+    } else {
+      S.res_t = t;
+      S.res_hashed = 1;
+      S.res_log_t = lg;
+    }
+    h->res_nmax = std::max<uint32_t>(h->res_nmax, (uint32_t)std::min<int64_t>(n_per_sys[s], 0xFFFFFFFF));
+    h->res_tmax = std::max(h->res_tmax, S.res_t);
+  }
   // buckets: the cell id itself when the grid is small, else a hash table of 2^k >= 4n buckets
   uint64_t t_hash = 16;
   int log_t = 4;
@@ -607,6 +672,8 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
   al(dalloc(h, &A.stag_tmp, n));
   al(dalloc(h, &A.slot_of, n));
   al(dalloc(h, &h->d_order, n));
+  al(dalloc(h, &h->d_res_order, (size_t)nsys));
+  al(dalloc(h, &h->d_res_next, 1));
   al(dalloc(h, &A.scell, n));
   SysDev* d_sys = nullptr;
   al(dalloc(h, &d_sys, (size_t)nsys));
@@ -653,6 +720,17 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
   if (e == cudaSuccess) {
     const uint32_t nn = (uint32_t)total;
     e = cudaMemcpy(A.start + A.nbucket, &nn, sizeof(uint32_t), cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    std::string m = std::string("allocation / upload failed: ") + cudaGetErrorString(e);
+    md_destroy(h);
+    return fail(nullptr, MD_ERR_CUDA, m);
+  }
+  if (e == cudaSuccess) {  // resident work list: largest systems first
+    std::vector<int32_t> ord((size_t)nsys);
+    for (int q = 0; q < nsys; ++q) ord[(size_t)q] = q;
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return n_per_sys[a] > n_per_sys[b]; });
+    e = cudaMemcpy(h->d_res_order, ord.data(), sizeof(int32_t) * (size_t)nsys, cudaMemcpyHostToDevice);
   }
   if (e != cudaSuccess) {
     std::string m = std::string("allocation / upload failed: ") + cudaGetErrorString(e);
@@ -739,6 +817,7 @@ int md_step(md_handle* h, int64_t nsteps) {
   if (nsteps < 0) return fail(h, MD_ERR_INVALID_ARG, "nsteps must be >= 0");
   h->last_launches = 0;
   if (nsteps == 0) return MD_OK;
+  if (h->engine == 1) return resident_steps(h, nsteps);
   rc = build_graph(h);
   if (rc) return rc;
   int64_t extra = 0;
@@ -761,6 +840,41 @@ int md_profile_step(md_handle* h, int64_t nsteps, double* kernel_ms, int32_t max
   int rc = require_state(h);
   if (rc) return rc;
   if (nsteps < 1 || !kernel_ms || max_kernels < 1) return fail(h, MD_ERR_INVALID_ARG, "bad profile arguments");
+  if (h->engine == 1) {  // resident engine: its launches per step, then the global cell-list rebuild per call
+    cudaEvent_t ev[3];
+    for (auto& e : ev) CK(h, cudaEventCreate(&e));
+    cudaStream_t st = h->stream();
+    int status = MD_OK;
+    int64_t launches = 0;
+    cudaError_t e = cudaEventRecord(ev[0], st);
+    for (int64_t done = 0; done < nsteps && e == cudaSuccess;) {
+      const int64_t chunk = std::min(nsteps - done, h->res_steps_per_launch);
+      ResidentJob J{h->d_res_order, h->d_res_next, h->nsys, (int32_t)chunk, h->res_nmax, h->res_tmax};
+      e = launch_resident(h->A, h->precision, J, h->bonds, h->walls, h->excl, h->res_threads, 0, st);
+      done += chunk;
+      launches += 2;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+    if (e != cudaSuccess) status = cuda_fail(h, e, "resident");
+    if (status == MD_OK) status = rebuild_cells(h);
+    if (status == MD_OK) {
+      e = cudaEventRecord(ev[2], st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+      if (e != cudaSuccess) status = cuda_fail(h, e, "profile event");
+    }
+    float ms[2] = {0.f, 0.f};
+    if (status == MD_OK) {
+      cudaEventElapsedTime(&ms[0], ev[0], ev[1]);
+      cudaEventElapsedTime(&ms[1], ev[1], ev[2]);
+    }
+    for (auto& ee : ev) cudaEventDestroy(ee);
+    if (status != MD_OK) return status;
+    kernel_ms[0] = ms[0] / (double)nsteps;
+    if (max_kernels > 1) kernel_ms[1] = ms[1] / (double)nsteps;
+    if (n_kernels) *n_kernels = 2;
+    h->last_launches = launches + kRebuildLaunches;
+    return check_device_status(h);
+  }
   const StepKernel* ks;
   const int nk = step_kernels(h, &ks);
   std::vector<cudaEvent_t> ev((size_t)nk + 1);
@@ -801,6 +915,7 @@ int md_profile_step(md_handle* h, int64_t nsteps, double* kernel_ms, int32_t max
 
 const char* md_profile_kernel_name(md_handle* h, int32_t i) {
   if (!h) return "";
+  if (h->engine == 1) return i == 0 ? "resident" : (i == 1 ? "rebuild" : "");
   const StepKernel* ks;
   const int nk = step_kernels(h, &ks);
   return (i >= 0 && i < nk) ? ks[i].name : "";
@@ -823,6 +938,29 @@ int md_set_option(md_handle* h, int32_t key, int64_t value) {
         h->steps_since_order = 0;
       }
       break;
+    case MD_OPT_ENGINE: {
+      if (value != 0 && value != 1) return fail(h, MD_ERR_INVALID_ARG, "engine must be 0 or 1");
+      if (value == 1) {
+        const std::string why = resident_unfit(h, h->res_threads);
+        if (!why.empty()) return fail(h, MD_ERR_INVALID_ARG, why);
+      }
+      h->engine = (int)value;
+      break;
+    }
+    case MD_OPT_RESIDENT_THREADS: {
+      if (value < 64 || value > 512 || value % 32 != 0)
+        return fail(h, MD_ERR_INVALID_ARG, "resident threads must be a multiple of 32 in 64..512");
+      if (h->engine == 1) {
+        const std::string why = resident_unfit(h, (int)value);
+        if (!why.empty()) return fail(h, MD_ERR_INVALID_ARG, why);
+      }
+      h->res_threads = (int)value;
+      break;
+    }
+    case MD_OPT_RESIDENT_STEPS:
+      if (value < 1 || value > 100000) return fail(h, MD_ERR_INVALID_ARG, "steps per launch must be in 1..100000");
+      h->res_steps_per_launch = value;
+      break;
     default:
       return fail(h, MD_ERR_INVALID_ARG, "unknown option");
   }
@@ -838,6 +976,9 @@ int md_get_option(md_handle* h, int32_t key, int64_t* value) {
   switch (key) {
     case MD_OPT_PAIR_LANES: *value = h->A.pair_lanes; return MD_OK;
     case MD_OPT_PAIR_ORDER: *value = h->A.order ? 1 : 0; return MD_OK;
+    case MD_OPT_ENGINE: *value = h->engine; return MD_OK;
+    case MD_OPT_RESIDENT_THREADS: *value = h->res_threads; return MD_OK;
+    case MD_OPT_RESIDENT_STEPS: *value = h->res_steps_per_launch; return MD_OK;
     default: return fail(h, MD_ERR_INVALID_ARG, "unknown option");
   }
 }

@@ -60,6 +60,16 @@ cudaError_t launch_get_state(const DevArrays& A, double* d_x_aos, double* d_v_ao
 cudaError_t launch_get_forces(const DevArrays& A, int precision, double* d_f_aos, double* d_u,
                               cudaStream_t st);
 
+// Resident engine: every system of J advances J.nsteps steps inside one
+// launch (one CTA per system at a time, cell list and forces in shared
+// memory), then the step counter advances by J.nsteps. threads: CTA size
+// (a multiple of 32, <= 512); grid_cap > 0 limits the CTAs.
+size_t resident_smem_bytes(int precision, uint32_t nmax, uint32_t tmax);
+cudaError_t launch_resident(const DevArrays& A, int precision, const ResidentJob& J, int bonds, int walls, int excl,
+                            int threads, int grid_cap, cudaStream_t st);
+// CTAs of the resident kernel that fit on one SM (0: none).
+int resident_blocks_per_sm(int precision, int bonds, int walls, int excl, uint32_t nmax, uint32_t tmax, int threads);
+
 // out_f[i] = in[i] rounded to float32, out_d[i] = out_f[i] widened to float64,
 // by the integer-pipe conversions of the mixed path.
 cudaError_t launch_check_conversions(const double* in, int64_t n, float* out_f, double* out_d, cudaStream_t st);

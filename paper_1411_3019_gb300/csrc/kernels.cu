@@ -16,6 +16,7 @@
 // never leaves registers; p^k is rebuilt on demand (launch_finish).
 #include <algorithm>
 #include <cfloat>
+#include <type_traits>
 #include <cmath>
 
 #include "engine.h"
@@ -521,6 +522,27 @@ template <> __device__ __forceinline__ void put_rec<double>(void* rec, uint32_t 
       make_double4_32a(ox, oy, oz, __longlong_as_double((long long)bits));
 }
 
+// Offset of a position from the centre of its cell, formed in float64 (the
+// records store it in float32 on the mixed path: |o| <= cs/2 keeps its
+// rounding small).
+__device__ __forceinline__ void cell_offsets(const SysDev& S, uint32_t cell, double x, double y, double z,
+                                             double o[3]) {
+  int c[3];
+  cell_decode(S, cell, c[0], c[1], c[2]);
+  const double xv[3] = {x, y, z};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {  // offset from the cell centre: |o| <= cs/2 keeps float32 rounding small
+    // c + 1/2 is exact in float32 (c < 2^22), so the centre is the same float64 value either way
+    o[k] = xv[k] - fma(f2d((float)c[k] + 0.5f), S.cs[k], S.grid_lo[k]);
+    // the image the binning chose. With three or more cells on the axis, o lies within cs/2 <= L/6 of a
+    // multiple of the box length L, far from an odd multiple of L/2, so o / L and o * (1 / L) round to
+    // the same integer and the reciprocal form (no float64 divide) picks the same image.
+    if (S.periodic[k])
+      o[k] = S.nc[k] >= 3 ? fma(-S.box_len[k], rint(o[k] * S.inv_box_len[k]), o[k])
+                          : wrap_min_image(o[k], S.box_len[k]);
+  }
+}
+
 // One thread per slot: a particle's place inside its bucket is the number of
 // bucket members with a smaller id, which gives every bucket one canonical
 // order (so every force sum has one fixed order and runs repeat bit for bit).
@@ -540,21 +562,8 @@ __global__ void k_bucket_build(DevArrays A) {
   const uint32_t d = s0 + rank;
   const uint32_t m = A.meta[tag];
   const SysDev& S = A.sys[meta_sys(m)];
-  int c[3];
-  cell_decode(S, cell, c[0], c[1], c[2]);
-  const double xv[3] = {A.x[tag], A.x[n + tag], A.x[2 * n + tag]};
   double o[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {  // offset from the cell centre: |o| <= cs/2 keeps float32 rounding small
-    // c + 1/2 is exact in float32 (c < 2^22), so the centre is the same float64 value either way
-    o[k] = xv[k] - fma(f2d((float)c[k] + 0.5f), S.cs[k], S.grid_lo[k]);
-    // the image the binning chose. With three or more cells on the axis, o lies within cs/2 <= L/6 of a
-    // multiple of the box length L, far from an odd multiple of L/2, so o / L and o * (1 / L) round to
-    // the same integer and the reciprocal form (no float64 divide) picks the same image.
-    if (S.periodic[k])
-      o[k] = S.nc[k] >= 3 ? fma(-S.box_len[k], rint(o[k] * S.inv_box_len[k]), o[k])
-                          : wrap_min_image(o[k], S.box_len[k]);
-  }
+  cell_offsets(S, cell, A.x[tag], A.x[n + tag], A.x[2 * n + tag], o);
   const uint32_t mol = A.mol ? (uint32_t)A.mol[tag] : 0u;
   A.stag[d] = tag;
   A.scell[d] = cell;
@@ -783,24 +792,35 @@ __device__ __forceinline__ void bonded_terms(const DevArrays& A, const SysDev& S
 // particles, a cell whose box lies farther than the tangent slab from the
 // particle's tangent plane cannot hold a neighbour and is skipped. The bucket
 // ranges of one stencil row are loaded together before its candidates.
-template <typename R, bool BONDS, bool WALLS, bool EXCL>
-__global__ void __launch_bounds__(256) k_pair_row(DevArrays A) {
-  __shared__ PairTab<R> tab;
-  load_tab<R>(tab, A.types);
-  __syncthreads();
-  const uint32_t t_id = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t_id >= (uint32_t)A.n) return;
-  // with a visiting order, neighbouring threads take spatially neighbouring
-  // particles, whose stencils share cache lines; the particle's own slot
-  // follows from the slot map (the arithmetic per particle is unchanged)
-  const uint32_t s = A.order ? A.slot_of[A.order[t_id]] : t_id;
+// The cell list as the pair code reads it: slot -> particle, cell and record,
+// bucket -> first slot, cell -> bucket. GlobalCells is the handle's list in
+// global memory; the resident engine keeps one system's list in shared memory.
+template <typename R> struct GlobalCells {
   using Rec = typename RecT<R>::T;
-  const Rec* __restrict__ rec = reinterpret_cast<const Rec*>(A.rec);
-  const uint32_t* __restrict__ scell = A.scell;
-  const uint32_t* __restrict__ start = A.start;
-  const uint32_t tag = A.stag[s];
-  const uint32_t cell = scell[s];
-  const Rec ri = rec[s];
+  const Rec* __restrict__ rec_;
+  const uint32_t* __restrict__ scell_;
+  const uint32_t* __restrict__ start_;
+  const uint32_t* __restrict__ stag_;
+  int hashed, log_t;
+  __device__ __forceinline__ explicit GlobalCells(const DevArrays& A)
+      : rec_(reinterpret_cast<const Rec*>(A.rec)), scell_(A.scell), start_(A.start), stag_(A.stag),
+        hashed(A.hashed), log_t(A.log_t) {}
+  __device__ __forceinline__ uint32_t tag(uint32_t s) const { return stag_[s]; }
+  __device__ __forceinline__ uint32_t scell(uint32_t t) const { return scell_[t]; }
+  __device__ __forceinline__ Rec rec(uint32_t t) const { return rec_[t]; }
+  __device__ __forceinline__ uint32_t start(uint32_t b) const { return start_[b]; }
+  __device__ __forceinline__ uint32_t bucket(uint32_t cell) const { return bucket_of(cell, hashed, log_t); }
+};
+
+// Force and energy on the particle in slot s from the 27 neighbour cells (and
+// its bonds and walls); returns the particle's id.
+template <typename R, bool BONDS, bool WALLS, bool EXCL, class Cells>
+__device__ __forceinline__ uint32_t pair_slot(const DevArrays& A, const Cells& C, const PairTab<R>& tab, uint32_t s,
+                                              R& fx, R& fy, R& fz, R& u) {
+  using Rec = typename RecT<R>::T;
+  const uint32_t tag = C.tag(s);
+  const uint32_t cell = C.scell(s);
+  const Rec ri = C.rec(s);
   const uint32_t bi = RecT<R>::bits(ri);
   const uint32_t ti = bi & 7u, moli = bi >> 3;
   const uint32_t m = A.meta[tag];
@@ -831,7 +851,7 @@ __global__ void __launch_bounds__(256) k_pair_row(DevArrays A) {
       prune = false;
     }
   }
-  R fx = 0, fy = 0, fz = 0, u = 0;
+  fx = 0; fy = 0; fz = 0; u = 0;
   for (int dz = -1; dz <= 1; ++dz) {
     int z = c[2] + dz;
     if (z < 0 || z >= S.nc[2]) {
@@ -862,16 +882,16 @@ __global__ void __launch_bounds__(256) k_pair_row(DevArrays A) {
           if (fabsf(dist) > reach) continue;
         }
         nb[q] = cell_id(S, x, y, z);
-        const uint32_t b = bucket_of(nb[q], A.hashed, A.log_t);
-        t0[q] = start[b];
-        t1[q] = start[b + 1];
+        const uint32_t b = C.bucket(nb[q]);
+        t0[q] = C.start(b);
+        t1[q] = C.start(b + 1);
       }
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const R shx = (R)(q - 1) * csx, shy = (R)dy * csy, shz = (R)dz * csz;
         for (uint32_t t = t0[q]; t < t1[q]; ++t) {
-          const uint32_t cj = scell[t];
-          const Rec rj = rec[t];  // issued together with the cell id
+          const uint32_t cj = C.scell(t);
+          const Rec rj = C.rec(t);  // issued together with the cell id
           if (cj != nb[q] || t == s) continue;
           const uint32_t bj = RecT<R>::bits(rj);
           if (EXCL && (bj >> 3) == moli) continue;
@@ -892,6 +912,22 @@ __global__ void __launch_bounds__(256) k_pair_row(DevArrays A) {
     }
   }
   if (BONDS || WALLS) bonded_terms<R>(A, S, tag, m, BONDS, WALLS, fx, fy, fz, u);
+  return tag;
+}
+
+template <typename R, bool BONDS, bool WALLS, bool EXCL>
+__global__ void __launch_bounds__(256) k_pair_row(DevArrays A) {
+  __shared__ PairTab<R> tab;
+  load_tab<R>(tab, A.types);
+  __syncthreads();
+  const uint32_t t_id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t_id >= (uint32_t)A.n) return;
+  // with a visiting order, neighbouring threads take spatially neighbouring
+  // particles, whose stencils share cache lines; the particle's own slot
+  // follows from the slot map (the arithmetic per particle is unchanged)
+  const uint32_t s = A.order ? A.slot_of[A.order[t_id]] : t_id;
+  R fx, fy, fz, u;
+  const uint32_t tag = pair_slot<R, BONDS, WALLS, EXCL>(A, GlobalCells<R>(A), tab, s, fx, fy, fz, u);
   store_f<R>(A.f, tag, fx, fy, fz, u);
 }
 
@@ -1182,6 +1218,29 @@ __device__ __forceinline__ bool finite_bits(double v) {
   return (__double2hiint(v) & 0x7ff00000) != 0x7ff00000;
 }
 
+// Where the integrator puts the cell of x^{k+1}: nowhere (no pair forces),
+// the handle's global bucket counters, or (resident engine) one system's
+// counters in shared memory. put() records the cell and the particle's rank
+// in its bucket (the order of the atomic; the bucket build makes it canonical).
+struct NoBin {
+  static constexpr bool kOn = false;
+  __device__ __forceinline__ explicit NoBin(const DevArrays&) {}
+  __device__ __forceinline__ void put(int64_t, uint32_t) const {}
+};
+struct GlobalBin {
+  static constexpr bool kOn = true;
+  uint32_t* cell;
+  uint32_t* rank;
+  uint32_t* count;
+  int hashed, log_t;
+  __device__ __forceinline__ explicit GlobalBin(const DevArrays& A)
+      : cell(A.cell), rank(A.rank), count(A.count), hashed(A.hashed), log_t(A.log_t) {}
+  __device__ __forceinline__ void put(int64_t i, uint32_t c) const {
+    cell[i] = c;
+    rank[i] = atomicAdd(&count[bucket_of(c, hashed, log_t)], 1u);
+  }
+};
+
 // Float64 path: combine + momentum half of step k + position half of step
 // k+1, then the cell of x^{k+1} and its rank in the bucket counter.
 //
@@ -1192,11 +1251,10 @@ __device__ __forceinline__ bool finite_bits(double v) {
 // (n1 = n0 for the frozen-normal variant). Stop when |g| < eta |n|, with
 // |n| = |n0| (the two differ by |x - x^k| times the curvature), or when the
 // update falls under 4 ulp of the position (round-off floor).
-template <bool BIN>
-__device__ __forceinline__ void integrate_particle_fp64(const DevArrays& A, int64_t i, Force3<double> fr_in) {
+template <class Bin>
+__device__ __forceinline__ void integrate_particle_fp64(const DevArrays& A, int64_t i, Force3<double> fr_in,
+                                                        unsigned long long k, int mode, const Bin& bin) {
   const int64_t n = A.n;
-  const unsigned long long k = *A.step;
-  const int mode = *A.mode;
   const uint32_t m = A.meta[i];
   const SysDev& S = A.sys[meta_sys(m)];
   const TypeTable* T = A.types;
@@ -1261,12 +1319,11 @@ __device__ __forceinline__ void integrate_particle_fp64(const DevArrays& A, int6
     flag(A.status, kFlagNonfinite);
   A.x[i] = xn; A.x[n + i] = yn; A.x[2 * n + i] = zn;
   A.ph[i] = qx; A.ph[n + i] = qy; A.ph[2 * n + i] = qz;
-  if (BIN) {
+  if (Bin::kOn) {
     bool out = false;
     const uint32_t cell = cell_of_d(S, xn, yn, zn, out);
     if (out) flag(A.status, kFlagOutOfGrid);
-    A.cell[i] = cell;
-    A.rank[i] = atomicAdd(&A.count[bucket_of(cell, A.hashed, A.log_t)], 1u);
+    bin.put(i, cell);
   }
 }
 
@@ -1371,11 +1428,10 @@ __device__ __forceinline__ bool newton_line(L& line, int max_newton, bool frozen
   return false;
 }
 
-template <bool BIN>
-__device__ __forceinline__ void integrate_particle_mixed(const DevArrays& A, int64_t i, Force3<float> fr_in) {
+template <class Bin>
+__device__ __forceinline__ void integrate_particle_mixed(const DevArrays& A, int64_t i, Force3<float> fr_in,
+                                                         unsigned long long k, int mode, const Bin& bin) {
   const int64_t n = A.n;
-  const unsigned long long k = *A.step;
-  const int mode = *A.mode;
   const uint32_t m = A.meta[i];
   const SysDev& S = A.sys[meta_sys(m)];
   const uint32_t ty = meta_type(m);
@@ -1475,12 +1531,11 @@ __device__ __forceinline__ void integrate_particle_mixed(const DevArrays& A, int
     flag(A.status, kFlagNonfinite);
   A.x[i] = xn; A.x[n + i] = yn; A.x[2 * n + i] = zn;
   A.ph[i] = qx; A.ph[n + i] = qy; A.ph[2 * n + i] = qz;
-  if (BIN) {
+  if (Bin::kOn) {
     bool out = false;
     const uint32_t cell = cell_of_f(S, xn, yn, zn, out);
     if (out) flag(A.status, kFlagOutOfGrid);
-    A.cell[i] = cell;
-    A.rank[i] = atomicAdd(&A.count[bucket_of(cell, A.hashed, A.log_t)], 1u);
+    bin.put(i, cell);
   }
 }
 
@@ -1488,8 +1543,265 @@ template <typename R, bool BIN>
 __global__ void __launch_bounds__(256, 4) k_integrate(DevArrays A) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
-  if constexpr (sizeof(R) == 4) integrate_particle_mixed<BIN>(A, i, load_f3<float>(A.f, i));
-  else integrate_particle_fp64<BIN>(A, i, load_f3<double>(A.f, i));
+  const unsigned long long k = *A.step;
+  const int mode = *A.mode;
+  using Bin = typename std::conditional<BIN, GlobalBin, NoBin>::type;
+  const Bin bin(A);
+  if constexpr (sizeof(R) == 4) integrate_particle_mixed(A, i, load_f3<float>(A.f, i), k, mode, bin);
+  else integrate_particle_fp64(A, i, load_f3<double>(A.f, i), k, mode, bin);
+}
+
+// ---------------------------------------------------------------------------
+// Resident engine. One CTA takes one whole system from the work list and
+// advances it J.nsteps time steps with the system's cell list (bucket starts,
+// sorted ids, cells and records) and its forces in shared memory; positions
+// and momenta stay in global memory, read and written once per step. The
+// per-particle code is the global kernels' own (pair_slot, the integrators,
+// cell_offsets), the stencil visits the cells in the same order and each cell
+// lists its particles by id as in the global buckets, so every force sum and
+// every update is the same: the two engines give the same bits. Buckets are
+// per system (res_t of them, dense or hashed on local cell ids).
+// ---------------------------------------------------------------------------
+template <typename R> struct SharedCells {
+  using Rec = typename RecT<R>::T;
+  const Rec* rec_;
+  const uint32_t* scell_;
+  const uint32_t* start_;
+  const uint16_t* stag_;
+  uint32_t first, base;
+  int hashed, log_t;
+  __device__ __forceinline__ uint32_t tag(uint32_t s) const { return first + stag_[s]; }
+  __device__ __forceinline__ uint32_t scell(uint32_t t) const { return scell_[t]; }
+  __device__ __forceinline__ Rec rec(uint32_t t) const { return rec_[t]; }
+  __device__ __forceinline__ uint32_t start(uint32_t b) const { return start_[b]; }
+  __device__ __forceinline__ uint32_t bucket(uint32_t cell) const { return bucket_of(cell - base, hashed, log_t); }
+};
+
+struct SharedBin {
+  static constexpr bool kOn = true;
+  uint32_t* cell;
+  uint16_t* rank;
+  uint32_t* count;
+  int64_t first;
+  uint32_t base;
+  int hashed, log_t;
+  __device__ __forceinline__ void put(int64_t i, uint32_t c) const {
+    const uint32_t li = (uint32_t)(i - first);
+    cell[li] = c;
+    rank[li] = (uint16_t)atomicAdd(&count[bucket_of(c - base, hashed, log_t)], 1u);
+  }
+};
+
+// Bucket counters (s_start[0..T)) -> bucket starts, scatter, canonical order
+// and records, for the n particles of the system starting at `first`.
+template <typename R>
+__device__ __forceinline__ void resident_cells(const DevArrays& A, const SysDev& S, int64_t first, uint32_t n,
+                                               uint32_t T, uint32_t* s_start, const uint32_t* s_cell,
+                                               const uint16_t* s_rank, uint16_t* s_tmp, uint16_t* s_stag,
+                                               uint32_t* s_scell, void* s_rec, uint32_t* warp_tot) {
+  const uint32_t tid = threadIdx.x, bd = blockDim.x;
+  {
+    const uint32_t per = (T + bd - 1) / bd;
+    const uint32_t lo = min(tid * per, T), hi = min(lo + per, T);
+    uint32_t sum = 0;
+    for (uint32_t e = lo; e < hi; ++e) sum += s_start[e];
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(sum, warp_tot, total);
+    for (uint32_t e = lo; e < hi; ++e) {
+      const uint32_t c = s_start[e];
+      s_start[e] = run;
+      run += c;
+    }
+    if (tid == 0) s_start[T] = n;
+  }
+  __syncthreads();
+  for (uint32_t li = tid; li < n; li += bd)
+    s_tmp[s_start[bucket_of(s_cell[li] - S.cell_base, S.res_hashed, S.res_log_t)] + s_rank[li]] = (uint16_t)li;
+  __syncthreads();
+  const int64_t nn = A.n;
+  for (uint32_t d = tid; d < n; d += bd) {
+    const uint32_t li = s_tmp[d];
+    const uint32_t c = s_cell[li];
+    const uint32_t b = bucket_of(c - S.cell_base, S.res_hashed, S.res_log_t);
+    const uint32_t s0 = s_start[b], s1 = s_start[b + 1];
+    uint32_t r = 0;
+    for (uint32_t t = s0; t < s1; ++t) r += (s_tmp[t] < li) ? 1u : 0u;
+    const uint32_t dd = s0 + r;
+    const int64_t i = first + li;
+    const uint32_t m = A.meta[i];
+    double o[3];
+    cell_offsets(S, c, A.x[i], A.x[nn + i], A.x[2 * nn + i], o);
+    const uint32_t mol = A.mol ? (uint32_t)A.mol[i] : 0u;
+    s_stag[dd] = (uint16_t)li;
+    s_scell[dd] = c;
+    put_rec<R>(s_rec, dd, o[0], o[1], o[2], meta_type(m) | (mol << 3));
+  }
+  __syncthreads();
+}
+
+template <typename R, bool BONDS, bool WALLS, bool EXCL>
+__global__ void __launch_bounds__(512) k_resident(DevArrays A, ResidentJob J) {
+  using Rec = typename RecT<R>::T;
+  using V = typename V4<R>::T;
+  __shared__ PairTab<R> tab;
+  __shared__ uint32_t warp_tot[33];
+  __shared__ int s_job;
+  extern __shared__ __align__(32) unsigned char smem[];
+  // 32-byte alignment for the float64 path's double4 records and forces (the
+  // size carries 32 bytes of slack for this)
+  const uint32_t mis = (uint32_t)__cvta_generic_to_shared(smem) & 31u;
+  V* s_f = reinterpret_cast<V*>(smem + (mis ? 32u - mis : 0u));
+  Rec* s_rec = reinterpret_cast<Rec*>(s_f + J.nmax);
+  uint32_t* s_scell = reinterpret_cast<uint32_t*>(s_rec + J.nmax);
+  uint32_t* s_cell = s_scell + J.nmax;
+  uint32_t* s_start = s_cell + J.nmax;  // bucket counters, then (after the scan) bucket starts
+  uint16_t* s_stag = reinterpret_cast<uint16_t*>(s_start + J.tmax + 1);
+  uint16_t* s_tmp = s_stag + J.nmax;
+  uint16_t* s_rank = s_tmp + J.nmax;
+  load_tab<R>(tab, A.types);
+  const unsigned long long k0 = *A.step;
+  const int mode0 = *A.mode;
+  const uint32_t tid = threadIdx.x, bd = blockDim.x;
+  const int64_t nn = A.n;
+  for (;;) {
+    __syncthreads();  // the previous system is finished by every thread
+    if (tid == 0) s_job = (int)atomicAdd(J.next, 1u);
+    __syncthreads();
+    const int job = s_job;
+    if (job >= J.nsys) break;
+    const SysDev& S = A.sys[J.order[job]];
+    const int64_t first = S.first;
+    const uint32_t n = (uint32_t)S.n;
+    const uint32_t T = S.res_t;
+    const SharedBin bin{s_cell, s_rank, s_start, first, S.cell_base, S.res_hashed, S.res_log_t};
+    const SharedCells<R> C{s_rec, s_scell, s_start, s_stag, (uint32_t)first, S.cell_base, S.res_hashed,
+                           S.res_log_t};
+    // cell list of the positions the launch starts from
+    for (uint32_t e = tid; e <= T; e += bd) s_start[e] = 0u;
+    __syncthreads();
+    for (uint32_t li = tid; li < n; li += bd) {
+      const int64_t i = first + li;
+      bool out = false;
+      const uint32_t cell = cell_of<R>(S, A.x[i], A.x[nn + i], A.x[2 * nn + i], out);
+      if (out) flag(A.status, kFlagOutOfGrid);
+      bin.put(i, cell);
+    }
+    __syncthreads();
+    resident_cells<R>(A, S, first, n, T, s_start, s_cell, s_rank, s_tmp, s_stag, s_scell, s_rec, warp_tot);
+    for (int j = 0; j < J.nsteps; ++j) {
+      for (uint32_t s = tid; s < n; s += bd) {
+        R fx, fy, fz, u;
+        const uint32_t tag = pair_slot<R, BONDS, WALLS, EXCL>(A, C, tab, s, fx, fy, fz, u);
+        store_f<R>(s_f, tag - (uint32_t)first, fx, fy, fz, u);
+      }
+      __syncthreads();
+      for (uint32_t e = tid; e <= T; e += bd) s_start[e] = 0u;  // the starts are not read again this step
+      __syncthreads();
+      const unsigned long long k = k0 + (unsigned long long)j;
+      const int mode = j == 0 ? mode0 : 1;
+      for (uint32_t li = tid; li < n; li += bd) {
+        if constexpr (sizeof(R) == 4) integrate_particle_mixed(A, first + li, load_f3<float>(s_f, li), k, mode, bin);
+        else integrate_particle_fp64(A, first + li, load_f3<double>(s_f, li), k, mode, bin);
+      }
+      __syncthreads();
+      // the last step's list would only be rebuilt by the next launch
+      if (j + 1 < J.nsteps)
+        resident_cells<R>(A, S, first, n, T, s_start, s_cell, s_rank, s_tmp, s_stag, s_scell, s_rec, warp_tot);
+    }
+  }
+}
+
+__global__ void k_advance_n(unsigned long long* step, int32_t* mode, int32_t nsteps) {
+  *step += (unsigned long long)nsteps;
+  *mode = 1;
+}
+
+size_t resident_smem_bytes(int precision, uint32_t nmax, uint32_t tmax) {
+  const size_t v = precision == 0 ? sizeof(double4_32a) : sizeof(float4);
+  return (size_t)nmax * (2 * v + 2 * sizeof(uint32_t) + 3 * sizeof(uint16_t)) + sizeof(uint32_t) * ((size_t)tmax + 1) +
+         32;
+}
+
+template <typename R, bool BONDS, bool WALLS, bool EXCL>
+cudaError_t resident_one(const DevArrays& A, const ResidentJob& J, int threads, int grid_cap, cudaStream_t st) {
+  const size_t smem = resident_smem_bytes(sizeof(R) == 4 ? 1 : 0, J.nmax, J.tmax);
+  auto kern = k_resident<R, BONDS, WALLS, EXCL>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int grid = std::min(J.nsys, per_sm * sms);
+  if (grid_cap > 0) grid = std::min(grid, grid_cap);
+  kern<<<grid, threads, smem, st>>>(A, J);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_advance_n<<<1, 1, 0, st>>>(A.step, A.mode, J.nsteps);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t resident_dispatch(const DevArrays& A, const ResidentJob& J, int bonds, int walls, int excl, int threads,
+                              int grid_cap, cudaStream_t st) {
+  const int key = (bonds ? 4 : 0) | (walls ? 2 : 0) | (excl ? 1 : 0);
+  switch (key) {
+    case 0: return resident_one<R, false, false, false>(A, J, threads, grid_cap, st);
+    case 1: return resident_one<R, false, false, true>(A, J, threads, grid_cap, st);
+    case 2: return resident_one<R, false, true, false>(A, J, threads, grid_cap, st);
+    case 3: return resident_one<R, false, true, true>(A, J, threads, grid_cap, st);
+    case 4: return resident_one<R, true, false, false>(A, J, threads, grid_cap, st);
+    case 5: return resident_one<R, true, false, true>(A, J, threads, grid_cap, st);
+    case 6: return resident_one<R, true, true, false>(A, J, threads, grid_cap, st);
+    default: return resident_one<R, true, true, true>(A, J, threads, grid_cap, st);
+  }
+}
+
+cudaError_t launch_resident(const DevArrays& A, int precision, const ResidentJob& J, int bonds, int walls, int excl,
+                            int threads, int grid_cap, cudaStream_t st) {
+  if (J.nsys <= 0 || J.nsteps <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(J.next, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  return precision == 0 ? resident_dispatch<double>(A, J, bonds, walls, excl, threads, grid_cap, st)
+                        : resident_dispatch<float>(A, J, bonds, walls, excl, threads, grid_cap, st);
+}
+
+int resident_blocks_per_sm(int precision, int bonds, int walls, int excl, uint32_t nmax, uint32_t tmax, int threads) {
+  const size_t smem = resident_smem_bytes(precision, nmax, tmax);
+  int per_sm = 0;
+  cudaError_t e;
+  const int key = (bonds ? 4 : 0) | (walls ? 2 : 0) | (excl ? 1 : 0);
+  auto q = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  };
+  if (precision == 0) {
+    switch (key) {
+      case 0: e = q(k_resident<double, false, false, false>); break;
+      case 1: e = q(k_resident<double, false, false, true>); break;
+      case 2: e = q(k_resident<double, false, true, false>); break;
+      case 3: e = q(k_resident<double, false, true, true>); break;
+      case 4: e = q(k_resident<double, true, false, false>); break;
+      case 5: e = q(k_resident<double, true, false, true>); break;
+      case 6: e = q(k_resident<double, true, true, false>); break;
+      default: e = q(k_resident<double, true, true, true>); break;
+    }
+  } else {
+    switch (key) {
+      case 0: e = q(k_resident<float, false, false, false>); break;
+      case 1: e = q(k_resident<float, false, false, true>); break;
+      case 2: e = q(k_resident<float, false, true, false>); break;
+      case 3: e = q(k_resident<float, false, true, true>); break;
+      case 4: e = q(k_resident<float, true, false, false>); break;
+      case 5: e = q(k_resident<float, true, false, true>); break;
+      case 6: e = q(k_resident<float, true, true, false>); break;
+      default: e = q(k_resident<float, true, true, true>); break;
+    }
+  }
+  return e == cudaSuccess ? per_sm : 0;
 }
 
 __global__ void k_advance(unsigned long long* step, int32_t* mode) {

@@ -59,6 +59,10 @@ struct SysDev {
   float slab;                // tangent-slab half thickness for stencil pruning (0: off)
   int32_t nc[3];
   uint32_t cell_base;
+  // resident engine: this system's buckets in shared memory (res_t of them,
+  // res_t = 2^res_log_t; hashed when the grid has more cells than that)
+  uint32_t res_t;
+  int32_t res_log_t, res_hashed;
   // bonds, exclusions, walls
   int32_t bpm;
   int32_t excl;
@@ -90,6 +94,16 @@ template <> struct V4<float> { using T = float4; };
 template <> struct V4<double> { using T = double4_32a; };
 
 // Control words of the one-pass scan (zero at creation).
+// Work list of the resident engine: systems in the order CTAs take them
+// (largest first), a queue counter (zero before the launch), steps per launch
+// and the shared-memory capacity of one CTA.
+struct ResidentJob {
+  const int32_t* order;
+  uint32_t* next;
+  int32_t nsys, nsteps;
+  uint32_t nmax, tmax;
+};
+
 struct ScanCtl {
   uint32_t tile;   // next tile index
   uint32_t done;   // tiles finished in this launch

@@ -1,11 +1,19 @@
 """Autotuner of the step's launch options.
 
-For a handle with a state, times one step (every kernel, CUDA events, L2
-flushed between trials when a flush buffer is given) under each combination
-of the tunable options -- the visiting order of the pair kernel and the lanes
-per particle -- applies the fastest and returns the measurements. The choice
-can be cached in a JSON file keyed by a caller-given GPU name and the workload's
-shape (particles, systems), so later runs skip the trials.
+For a handle with a state, times the step under each candidate setting and
+applies the fastest:
+
+* the global engine (one graph of five kernels per step) with every
+  combination of the pair kernel's visiting order and lanes per particle,
+  one step per trial after an L2 flush (as the benchmark times it);
+* the resident engine (one persistent launch, one CTA per system), if the
+  systems fit it, for several CTA sizes, a run of `resident_steps` steps per
+  trial (its cost per step, with its one cell-list rebuild per call spread
+  over the run).
+
+No setting changes a bit of the results. The choice can be cached in a JSON
+file keyed by a caller-given GPU name and the workload's shape (particles,
+systems), so later runs skip the trials.
 """
 from __future__ import annotations
 
@@ -15,11 +23,10 @@ import os
 
 from . import md
 
-OPTIONS = {
-    md.MD_OPT_PAIR_ORDER: (1, 0),
-    md.MD_OPT_PAIR_LANES: (1, 2, 4),
-}
-NAMES = {md.MD_OPT_PAIR_ORDER: "pair_order", md.MD_OPT_PAIR_LANES: "pair_lanes"}
+GLOBAL_OPTIONS = {md.MD_OPT_PAIR_ORDER: (1, 0), md.MD_OPT_PAIR_LANES: (1, 2, 4)}
+RESIDENT_THREADS = (128, 256, 512)
+NAMES = {md.MD_OPT_PAIR_ORDER: "pair_order", md.MD_OPT_PAIR_LANES: "pair_lanes", md.MD_OPT_ENGINE: "engine",
+         md.MD_OPT_RESIDENT_THREADS: "resident_threads"}
 
 
 def _key(h, gpu_name: str) -> str:
@@ -27,33 +34,63 @@ def _key(h, gpu_name: str) -> str:
     return f"{gpu_name}|n={info['n']}|nsys={info['nsys']}"
 
 
-def autotune(h, trials: int = 3, flush=None, cache: str | None = None, gpu_name: str = "gpu"):
-    """Try every option combination on handle h; apply and return the best."""
+def candidates(h):
+    """Option settings to try: the global engine's combinations, then the
+    resident engine's CTA sizes if the handle's systems fit it."""
+    out = []
+    opts = list(GLOBAL_OPTIONS)
+    for combo in itertools.product(*(GLOBAL_OPTIONS[o] for o in opts)):
+        out.append({md.MD_OPT_ENGINE: 0, **dict(zip(opts, combo))})
+    md.md_set_option(h, md.MD_OPT_ENGINE, 0)
+    for thr in RESIDENT_THREADS:
+        try:
+            md.md_set_option(h, md.MD_OPT_RESIDENT_THREADS, thr)
+            md.md_set_option(h, md.MD_OPT_ENGINE, 1)
+        except md.MdError:
+            continue
+        finally:
+            md.md_set_option(h, md.MD_OPT_ENGINE, 0)
+        out.append({md.MD_OPT_ENGINE: 1, md.MD_OPT_RESIDENT_THREADS: thr})
+    return out
+
+
+def apply(h, setting: dict) -> None:
+    md.md_set_option(h, md.MD_OPT_ENGINE, 0)
+    for opt, val in setting.items():
+        if opt != md.MD_OPT_ENGINE:
+            md.md_set_option(h, opt, val)
+    md.md_set_option(h, md.MD_OPT_ENGINE, setting.get(md.MD_OPT_ENGINE, 0))
+
+
+def time_setting(h, setting: dict, trials: int, flush, resident_steps: int) -> float:
+    """Mean milliseconds per step of one setting."""
+    apply(h, setting)
+    steps = resident_steps if setting.get(md.MD_OPT_ENGINE, 0) == 1 else 1
+    md.md_profile_step(h, steps)  # warm this configuration
+    total = 0.0
+    for _ in range(trials):
+        if flush is not None:
+            flush()
+        total += sum(md.md_profile_step(h, steps).values())
+    return total / trials
+
+
+def autotune(h, trials: int = 3, flush=None, cache: str | None = None, gpu_name: str = "gpu",
+             resident_steps: int = 32):
+    """Try every candidate setting on handle h; apply and return the best.
+    The trial steps advance the handle's state."""
     key = _key(h, gpu_name)
     if cache and os.path.exists(cache):
         with open(cache) as fh:
             known = json.load(fh)
         if key in known:
             best = {int(k): v for k, v in known[key]["options"].items()}
-            for opt, val in best.items():
-                md.md_set_option(h, opt, val)
+            apply(h, best)
             return {"cached": True, "options": {NAMES[k]: v for k, v in best.items()}}
-    results = []
-    opts = list(OPTIONS)
-    for combo in itertools.product(*(OPTIONS[o] for o in opts)):
-        for opt, val in zip(opts, combo):
-            md.md_set_option(h, opt, val)
-        md.md_profile_step(h, 1)  # warm this configuration
-        total = 0.0
-        for _ in range(trials):
-            if flush is not None:
-                flush()
-            total += sum(md.md_profile_step(h, 1).values())
-        results.append((total / trials, dict(zip(opts, combo))))
+    results = [(time_setting(h, c, trials, flush, resident_steps), c) for c in candidates(h)]
     results.sort(key=lambda r: r[0])
     best_ms, best = results[0]
-    for opt, val in best.items():
-        md.md_set_option(h, opt, val)
+    apply(h, best)
     if cache:
         known = {}
         if os.path.exists(cache):

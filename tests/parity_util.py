@@ -8,7 +8,7 @@ import numpy as np
 import oracle
 from paper_1411_3019_gb300 import md
 
-# Tolerances (derived in the design doc): float64 path and mixed path.
+# Tolerances of the float64 path and of the mixed path.
 # Forces: fp64 is checked as |df| / max(|f|, 1); mixed (float32 pair
 # arithmetic) as |df| / max(S, 1) with S the particle's force scale, the sum
 # of the magnitudes of its pair/bond/wall terms (the net force can cancel).

@@ -86,9 +86,16 @@ def test_autotuner_applies_a_valid_choice_and_keeps_parity(tmp_path):
     sim.set_state()
     cache = str(tmp_path / "tune.json")
     out = tune.autotune(sim.h, trials=1, cache=cache)
-    assert out["options"]["pair_order"] in (0, 1) and out["options"]["pair_lanes"] in (1, 2, 4)
-    assert len(out["trials"]) == 6 and out["trials"][0]["ms"] == out["best_ms"]
-    assert md.md_get_option(sim.h, md.MD_OPT_PAIR_ORDER) == out["options"]["pair_order"]
+    # six global settings (visiting order x lanes) and three resident CTA sizes
+    assert len(out["trials"]) == 9 and out["trials"][0]["ms"] == out["best_ms"]
+    assert sorted(t["engine"] for t in out["trials"]) == [0] * 6 + [1] * 3
+    opts = out["options"]
+    assert md.md_get_option(sim.h, md.MD_OPT_ENGINE) == opts["engine"]
+    if opts["engine"] == 0:
+        assert opts["pair_order"] in (0, 1) and opts["pair_lanes"] in (1, 2, 4)
+        assert md.md_get_option(sim.h, md.MD_OPT_PAIR_ORDER) == opts["pair_order"]
+    else:
+        assert md.md_get_option(sim.h, md.MD_OPT_RESIDENT_THREADS) == opts["resident_threads"]
     again = tune.autotune(sim.h, cache=cache)
     assert again["cached"] and again["options"] == out["options"]
     # the trial steps advanced the state: restart from the inputs and compare
