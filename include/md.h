@@ -233,8 +233,11 @@ int md_step(md_handle* h, int64_t nsteps);
  * of the final positions once, and md_profile_step reports two entries:
  * "resident" (the launches, per step) and "rebuild" (per step of the call). */
 #define MD_OPT_ENGINE 3
-/* MD_OPT_RESIDENT_THREADS: threads per CTA of the resident engine, a
- * multiple of 32 in 64..512 (default 256). */
+/* MD_OPT_RESIDENT_THREADS: threads per CTA of the resident engine: 0
+ * (default) chooses per size class of the batch (systems grouped by the
+ * CTAs their shared memory lets one SM hold; each class its own launch and
+ * the CTA size that keeps the most warps resident), or a multiple of 32 in
+ * 64..512 for every class. */
 #define MD_OPT_RESIDENT_THREADS 4
 /* MD_OPT_RESIDENT_STEPS: most steps one resident launch runs (1..100000,
  * default 256); longer md_step calls are split into several launches. */

@@ -50,11 +50,19 @@ struct md_handle {
   int kernels_per_step = 0;
   // resident engine (MD_OPT_ENGINE = 1): systems largest first, a work counter
   int engine = 0;
-  int res_threads = 256;
+  int res_threads = 0;  // 0: chosen per size class
   int64_t res_steps_per_launch = 256;
   uint32_t res_nmax = 0, res_tmax = 0;
   int32_t* d_res_order = nullptr;
   uint32_t* d_res_next = nullptr;
+  std::vector<int64_t> res_n_sorted;  // system sizes in work-list order (largest first)
+  std::vector<uint32_t> res_t_sorted;  // their bucket counts
+  struct ResClass {
+    int32_t offset, count;
+    uint32_t nmax, tmax;
+    int threads;
+  };
+  std::vector<ResClass> res_classes;  // launches of one resident chunk
   std::vector<void*> allocs;
   std::string err;
 
@@ -368,34 +376,92 @@ int build_graph(md_handle* h) {
   return MD_OK;
 }
 
-// Why the resident engine cannot run this handle ("" when it can).
-std::string resident_unfit(md_handle* h, int threads) {
+// The largest bucket count a system of n particles can have on the resident
+// engine (2^k >= 2n, at least 64).
+uint32_t res_t_bound(int64_t n) {
+  uint32_t t = 64;
+  while ((int64_t)t < 2 * n && t < (1u << 16)) t <<= 1;
+  return t;
+}
+
+// Size classes of the resident engine: consecutive runs of the work list
+// (largest systems first). A class's shared memory is sized for its largest
+// system; its CTA size maximises the warps resident per SM (registers and
+// shared memory both limit the CTAs), or is the fixed size `threads` (> 0).
+// A class ends where a smaller system would fit more CTAs of that size.
+// Returns "" or why the engine cannot run this handle.
+std::string plan_resident(md_handle* h, int threads) {
+  h->res_classes.clear();
   if (!h->has_pairs) return "the resident engine needs pair interactions";
   if (h->res_nmax > 65535) return "the resident engine holds at most 65535 particles per system";
   if (h->res_nmax == 0) return "the batch has no particles";
-  const int per_sm = resident_blocks_per_sm(h->precision, h->bonds, h->walls, h->excl, h->res_nmax, h->res_tmax,
-                                            threads);
-  if (per_sm < 1)
-    return "the largest system (" + std::to_string(h->res_nmax) + " particles, " +
-           std::to_string(resident_smem_bytes(h->precision, h->res_nmax, h->res_tmax)) +
-           " bytes of shared memory) does not fit one CTA of " + std::to_string(threads) + " threads";
+  const int cands_auto[] = {512, 384, 256, 128};
+  std::vector<int> cands;
+  if (threads > 0) cands.push_back(threads);
+  else cands.assign(std::begin(cands_auto), std::end(cands_auto));
+  auto ctas = [&](int64_t n, uint32_t t_b, int thr) {
+    return resident_blocks_per_sm(h->precision, h->bonds, h->walls, h->excl, (uint32_t)n, t_b, thr);
+  };
+  const int nsys = (int)h->res_n_sorted.size();
+  for (int i = 0; i < nsys;) {
+    const int64_t nmax = h->res_n_sorted[(size_t)i];
+    int best_t = 0, best_k = 0, best_w = 0;
+    for (int thr : cands) {
+      const int k = ctas(nmax, res_t_bound(nmax), thr);
+      const int w = k * thr / 32;
+      if (w > best_w || (w == best_w && w > 0 && thr > best_t)) {
+        best_t = thr;
+        best_k = k;
+        best_w = w;
+      }
+    }
+    if (best_w == 0)
+      return "the largest system (" + std::to_string(nmax) + " particles, " +
+             std::to_string(resident_smem_bytes(h->precision, (uint32_t)nmax, res_t_bound(nmax))) +
+             " bytes of shared memory) does not fit one CTA" +
+             (threads > 0 ? " of " + std::to_string(threads) + " threads" : std::string());
+    uint32_t tmax = h->res_t_sorted[(size_t)i];
+    int j = i + 1;
+    while (j < nsys) {
+      const int64_t nj = h->res_n_sorted[(size_t)j];
+      if (nj > 0 && ctas(nj, res_t_bound(nj), best_t) > best_k) break;
+      tmax = std::max(tmax, h->res_t_sorted[(size_t)j]);
+      ++j;
+    }
+    h->res_classes.push_back({i, j - i, (uint32_t)std::max<int64_t>(nmax, 1), tmax, best_t});
+    i = j;
+  }
   return "";
 }
 
 constexpr int64_t kRebuildLaunches = 7;  // bin, scan, scatter, bucket build, visiting order (3)
 
-// nsteps steps of every system by the resident engine, in launches of at most
-// res_steps_per_launch steps, then the global cell list of the new positions
-// (read by md_forces, md_get_state, the global engine and the observables).
-int resident_steps(md_handle* h, int64_t nsteps) {
-  int64_t launches = 0;
+// Enqueue nsteps steps of every system on the resident engine: chunks of at
+// most res_steps_per_launch steps, one launch per size class per chunk, the
+// step counter advanced after each chunk. Returns the launches.
+cudaError_t enqueue_resident(md_handle* h, int64_t nsteps, cudaStream_t st, int64_t* launches) {
   for (int64_t done = 0; done < nsteps;) {
     const int64_t chunk = std::min(nsteps - done, h->res_steps_per_launch);
-    ResidentJob J{h->d_res_order, h->d_res_next, h->nsys, (int32_t)chunk, h->res_nmax, h->res_tmax};
-    CK(h, launch_resident(h->A, h->precision, J, h->bonds, h->walls, h->excl, h->res_threads, 0, h->stream()));
+    for (const auto& c : h->res_classes) {
+      ResidentJob J{h->d_res_order + c.offset, h->d_res_next, c.count, (int32_t)chunk, c.nmax, c.tmax};
+      cudaError_t e = launch_resident(h->A, h->precision, J, h->bonds, h->walls, h->excl, c.threads, 0, st);
+      if (e != cudaSuccess) return e;
+      ++*launches;
+    }
+    cudaError_t e = launch_advance_n(h->A, (int32_t)chunk, st);
+    if (e != cudaSuccess) return e;
+    ++*launches;
     done += chunk;
-    launches += 2;
   }
+  return cudaSuccess;
+}
+
+// nsteps steps by the resident engine, then the global cell list of the new
+// positions (read by md_forces, md_get_state, the global engine and the
+// observables).
+int resident_steps(md_handle* h, int64_t nsteps) {
+  int64_t launches = 0;
+  CK(h, enqueue_resident(h, nsteps, h->stream(), &launches));
   int rc = rebuild_cells(h);
   if (rc) return rc;
   h->last_launches = launches + kRebuildLaunches;
@@ -731,6 +797,10 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
     for (int q = 0; q < nsys; ++q) ord[(size_t)q] = q;
     std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return n_per_sys[a] > n_per_sys[b]; });
     e = cudaMemcpy(h->d_res_order, ord.data(), sizeof(int32_t) * (size_t)nsys, cudaMemcpyHostToDevice);
+    for (int32_t q : ord) {
+      h->res_n_sorted.push_back(n_per_sys[q]);
+      h->res_t_sorted.push_back(h->sys[(size_t)q].res_t);
+    }
   }
   if (e != cudaSuccess) {
     std::string m = std::string("allocation / upload failed: ") + cudaGetErrorString(e);
@@ -847,13 +917,7 @@ int md_profile_step(md_handle* h, int64_t nsteps, double* kernel_ms, int32_t max
     int status = MD_OK;
     int64_t launches = 0;
     cudaError_t e = cudaEventRecord(ev[0], st);
-    for (int64_t done = 0; done < nsteps && e == cudaSuccess;) {
-      const int64_t chunk = std::min(nsteps - done, h->res_steps_per_launch);
-      ResidentJob J{h->d_res_order, h->d_res_next, h->nsys, (int32_t)chunk, h->res_nmax, h->res_tmax};
-      e = launch_resident(h->A, h->precision, J, h->bonds, h->walls, h->excl, h->res_threads, 0, st);
-      done += chunk;
-      launches += 2;
-    }
+    if (e == cudaSuccess) e = enqueue_resident(h, nsteps, st, &launches);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
     if (e != cudaSuccess) status = cuda_fail(h, e, "resident");
     if (status == MD_OK) status = rebuild_cells(h);
@@ -941,18 +1005,21 @@ int md_set_option(md_handle* h, int32_t key, int64_t value) {
     case MD_OPT_ENGINE: {
       if (value != 0 && value != 1) return fail(h, MD_ERR_INVALID_ARG, "engine must be 0 or 1");
       if (value == 1) {
-        const std::string why = resident_unfit(h, h->res_threads);
+        const std::string why = plan_resident(h, h->res_threads);
         if (!why.empty()) return fail(h, MD_ERR_INVALID_ARG, why);
       }
       h->engine = (int)value;
       break;
     }
     case MD_OPT_RESIDENT_THREADS: {
-      if (value < 64 || value > 512 || value % 32 != 0)
-        return fail(h, MD_ERR_INVALID_ARG, "resident threads must be a multiple of 32 in 64..512");
+      if (value != 0 && (value < 64 || value > kResidentMaxThreads || value % 32 != 0))
+        return fail(h, MD_ERR_INVALID_ARG, "resident threads must be 0 (automatic) or a multiple of 32 in 64..512");
       if (h->engine == 1) {
-        const std::string why = resident_unfit(h, (int)value);
-        if (!why.empty()) return fail(h, MD_ERR_INVALID_ARG, why);
+        const std::string why = plan_resident(h, (int)value);
+        if (!why.empty()) {
+          plan_resident(h, h->res_threads);  // keep the previous plan
+          return fail(h, MD_ERR_INVALID_ARG, why);
+        }
       }
       h->res_threads = (int)value;
       break;

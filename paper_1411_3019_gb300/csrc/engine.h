@@ -62,11 +62,13 @@ cudaError_t launch_get_forces(const DevArrays& A, int precision, double* d_f_aos
 
 // Resident engine: every system of J advances J.nsteps steps inside one
 // launch (one CTA per system at a time, cell list and forces in shared
-// memory), then the step counter advances by J.nsteps. threads: CTA size
-// (a multiple of 32, <= 512); grid_cap > 0 limits the CTAs.
+// memory); the step counter is advanced afterwards by launch_advance_n.
+// threads: CTA size (a multiple of 32, <= kResidentMaxThreads); grid_cap > 0
+// limits the CTAs.
 size_t resident_smem_bytes(int precision, uint32_t nmax, uint32_t tmax);
 cudaError_t launch_resident(const DevArrays& A, int precision, const ResidentJob& J, int bonds, int walls, int excl,
                             int threads, int grid_cap, cudaStream_t st);
+cudaError_t launch_advance_n(const DevArrays& A, int32_t nsteps, cudaStream_t st);
 // CTAs of the resident kernel that fit on one SM (0: none).
 int resident_blocks_per_sm(int precision, int bonds, int walls, int excl, uint32_t nmax, uint32_t tmax, int threads);
 

@@ -1577,9 +1577,13 @@ template <typename R> struct SharedCells {
   __device__ __forceinline__ uint32_t bucket(uint32_t cell) const { return bucket_of(cell - base, hashed, log_t); }
 };
 
+// The cell of particle li is kept in word li * stride of the x-force array
+// (stride = sizeof(R) / 4), the slot where the same thread has just read the
+// particle's force: the two are never live at the same time.
 struct SharedBin {
   static constexpr bool kOn = true;
   uint32_t* cell;
+  uint32_t stride;
   uint16_t* rank;
   uint32_t* count;
   int64_t first;
@@ -1587,7 +1591,7 @@ struct SharedBin {
   int hashed, log_t;
   __device__ __forceinline__ void put(int64_t i, uint32_t c) const {
     const uint32_t li = (uint32_t)(i - first);
-    cell[li] = c;
+    cell[li * stride] = c;
     rank[li] = (uint16_t)atomicAdd(&count[bucket_of(c - base, hashed, log_t)], 1u);
   }
 };
@@ -1597,8 +1601,9 @@ struct SharedBin {
 template <typename R>
 __device__ __forceinline__ void resident_cells(const DevArrays& A, const SysDev& S, int64_t first, uint32_t n,
                                                uint32_t T, uint32_t* s_start, const uint32_t* s_cell,
-                                               const uint16_t* s_rank, uint16_t* s_tmp, uint16_t* s_stag,
-                                               uint32_t* s_scell, void* s_rec, uint32_t* warp_tot) {
+                                               uint32_t cstride, const uint16_t* s_rank, uint16_t* s_tmp,
+                                               uint16_t* s_stag, uint32_t* s_scell, void* s_rec,
+                                               uint32_t* warp_tot) {
   const uint32_t tid = threadIdx.x, bd = blockDim.x;
   {
     const uint32_t per = (T + bd - 1) / bd;
@@ -1616,12 +1621,13 @@ __device__ __forceinline__ void resident_cells(const DevArrays& A, const SysDev&
   }
   __syncthreads();
   for (uint32_t li = tid; li < n; li += bd)
-    s_tmp[s_start[bucket_of(s_cell[li] - S.cell_base, S.res_hashed, S.res_log_t)] + s_rank[li]] = (uint16_t)li;
+    s_tmp[s_start[bucket_of(s_cell[li * cstride] - S.cell_base, S.res_hashed, S.res_log_t)] + s_rank[li]] =
+        (uint16_t)li;
   __syncthreads();
   const int64_t nn = A.n;
   for (uint32_t d = tid; d < n; d += bd) {
     const uint32_t li = s_tmp[d];
-    const uint32_t c = s_cell[li];
+    const uint32_t c = s_cell[li * cstride];
     const uint32_t b = bucket_of(c - S.cell_base, S.res_hashed, S.res_log_t);
     const uint32_t s0 = s_start[b], s1 = s_start[b + 1];
     uint32_t r = 0;
@@ -1640,24 +1646,30 @@ __device__ __forceinline__ void resident_cells(const DevArrays& A, const SysDev&
 }
 
 template <typename R, bool BONDS, bool WALLS, bool EXCL>
-__global__ void __launch_bounds__(512) k_resident(DevArrays A, ResidentJob J) {
+__global__ void __launch_bounds__(kResidentMaxThreads, 2) k_resident(DevArrays A, ResidentJob J) {
   using Rec = typename RecT<R>::T;
-  using V = typename V4<R>::T;
   __shared__ PairTab<R> tab;
   __shared__ uint32_t warp_tot[33];
   __shared__ int s_job;
   extern __shared__ __align__(32) unsigned char smem[];
-  // 32-byte alignment for the float64 path's double4 records and forces (the
-  // size carries 32 bytes of slack for this)
+  // Layout (nmax particles, tmax buckets): records, then the force components
+  // (each nmax R; the x-forces double as the particles' cells and the
+  // y-forces as the scatter's slot list, which are live only while the
+  // forces are not), sorted cells, bucket counters / starts, sorted ids,
+  // ranks. 32-byte alignment for the float64 path's double4 records (the
+  // size carries 32 bytes of slack for this).
   const uint32_t mis = (uint32_t)__cvta_generic_to_shared(smem) & 31u;
-  V* s_f = reinterpret_cast<V*>(smem + (mis ? 32u - mis : 0u));
-  Rec* s_rec = reinterpret_cast<Rec*>(s_f + J.nmax);
-  uint32_t* s_scell = reinterpret_cast<uint32_t*>(s_rec + J.nmax);
-  uint32_t* s_cell = s_scell + J.nmax;
-  uint32_t* s_start = s_cell + J.nmax;  // bucket counters, then (after the scan) bucket starts
+  Rec* s_rec = reinterpret_cast<Rec*>(smem + (mis ? 32u - mis : 0u));
+  R* s_fx = reinterpret_cast<R*>(s_rec + J.nmax);
+  R* s_fy = s_fx + J.nmax;
+  R* s_fz = s_fy + J.nmax;
+  uint32_t* s_cell = reinterpret_cast<uint32_t*>(s_fx);
+  constexpr uint32_t cstride = sizeof(R) / 4;
+  uint16_t* s_tmp = reinterpret_cast<uint16_t*>(s_fy);
+  uint32_t* s_scell = reinterpret_cast<uint32_t*>(s_fz + J.nmax);
+  uint32_t* s_start = s_scell + J.nmax;  // bucket counters, then (after the scan) bucket starts
   uint16_t* s_stag = reinterpret_cast<uint16_t*>(s_start + J.tmax + 1);
-  uint16_t* s_tmp = s_stag + J.nmax;
-  uint16_t* s_rank = s_tmp + J.nmax;
+  uint16_t* s_rank = s_stag + J.nmax;
   load_tab<R>(tab, A.types);
   const unsigned long long k0 = *A.step;
   const int mode0 = *A.mode;
@@ -1673,7 +1685,7 @@ __global__ void __launch_bounds__(512) k_resident(DevArrays A, ResidentJob J) {
     const int64_t first = S.first;
     const uint32_t n = (uint32_t)S.n;
     const uint32_t T = S.res_t;
-    const SharedBin bin{s_cell, s_rank, s_start, first, S.cell_base, S.res_hashed, S.res_log_t};
+    const SharedBin bin{s_cell, cstride, s_rank, s_start, first, S.cell_base, S.res_hashed, S.res_log_t};
     const SharedCells<R> C{s_rec, s_scell, s_start, s_stag, (uint32_t)first, S.cell_base, S.res_hashed,
                            S.res_log_t};
     // cell list of the positions the launch starts from
@@ -1687,12 +1699,15 @@ __global__ void __launch_bounds__(512) k_resident(DevArrays A, ResidentJob J) {
       bin.put(i, cell);
     }
     __syncthreads();
-    resident_cells<R>(A, S, first, n, T, s_start, s_cell, s_rank, s_tmp, s_stag, s_scell, s_rec, warp_tot);
+    resident_cells<R>(A, S, first, n, T, s_start, s_cell, cstride, s_rank, s_tmp, s_stag, s_scell, s_rec,
+                      warp_tot);
     for (int j = 0; j < J.nsteps; ++j) {
       for (uint32_t s = tid; s < n; s += bd) {
         R fx, fy, fz, u;
-        const uint32_t tag = pair_slot<R, BONDS, WALLS, EXCL>(A, C, tab, s, fx, fy, fz, u);
-        store_f<R>(s_f, tag - (uint32_t)first, fx, fy, fz, u);
+        const uint32_t li = pair_slot<R, BONDS, WALLS, EXCL>(A, C, tab, s, fx, fy, fz, u) - (uint32_t)first;
+        s_fx[li] = fx;
+        s_fy[li] = fy;
+        s_fz[li] = fz;
       }
       __syncthreads();
       for (uint32_t e = tid; e <= T; e += bd) s_start[e] = 0u;  // the starts are not read again this step
@@ -1700,13 +1715,15 @@ __global__ void __launch_bounds__(512) k_resident(DevArrays A, ResidentJob J) {
       const unsigned long long k = k0 + (unsigned long long)j;
       const int mode = j == 0 ? mode0 : 1;
       for (uint32_t li = tid; li < n; li += bd) {
-        if constexpr (sizeof(R) == 4) integrate_particle_mixed(A, first + li, load_f3<float>(s_f, li), k, mode, bin);
-        else integrate_particle_fp64(A, first + li, load_f3<double>(s_f, li), k, mode, bin);
+        const Force3<R> f{s_fx[li], s_fy[li], s_fz[li]};
+        if constexpr (sizeof(R) == 4) integrate_particle_mixed(A, first + li, f, k, mode, bin);
+        else integrate_particle_fp64(A, first + li, f, k, mode, bin);
       }
       __syncthreads();
       // the last step's list would only be rebuilt by the next launch
       if (j + 1 < J.nsteps)
-        resident_cells<R>(A, S, first, n, T, s_start, s_cell, s_rank, s_tmp, s_stag, s_scell, s_rec, warp_tot);
+        resident_cells<R>(A, S, first, n, T, s_start, s_cell, cstride, s_rank, s_tmp, s_stag, s_scell, s_rec,
+                          warp_tot);
     }
   }
 }
@@ -1717,9 +1734,10 @@ __global__ void k_advance_n(unsigned long long* step, int32_t* mode, int32_t nst
 }
 
 size_t resident_smem_bytes(int precision, uint32_t nmax, uint32_t tmax) {
-  const size_t v = precision == 0 ? sizeof(double4_32a) : sizeof(float4);
-  return (size_t)nmax * (2 * v + 2 * sizeof(uint32_t) + 3 * sizeof(uint16_t)) + sizeof(uint32_t) * ((size_t)tmax + 1) +
-         32;
+  const size_t rec = precision == 0 ? sizeof(double4_32a) : sizeof(float4);
+  const size_t r = precision == 0 ? sizeof(double) : sizeof(float);
+  return (size_t)nmax * (rec + 3 * r + sizeof(uint32_t) + 2 * sizeof(uint16_t)) +
+         sizeof(uint32_t) * ((size_t)tmax + 1) + 32;
 }
 
 template <typename R, bool BONDS, bool WALLS, bool EXCL>
@@ -1738,9 +1756,11 @@ cudaError_t resident_one(const DevArrays& A, const ResidentJob& J, int threads, 
   int grid = std::min(J.nsys, per_sm * sms);
   if (grid_cap > 0) grid = std::min(grid, grid_cap);
   kern<<<grid, threads, smem, st>>>(A, J);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_advance_n<<<1, 1, 0, st>>>(A.step, A.mode, J.nsteps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance_n(const DevArrays& A, int32_t nsteps, cudaStream_t st) {
+  k_advance_n<<<1, 1, 0, st>>>(A.step, A.mode, nsteps);
   return cudaGetLastError();
 }
 

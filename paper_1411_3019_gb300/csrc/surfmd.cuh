@@ -94,6 +94,8 @@ template <> struct V4<float> { using T = float4; };
 template <> struct V4<double> { using T = double4_32a; };
 
 // Control words of the one-pass scan (zero at creation).
+constexpr int kResidentMaxThreads = 512;  // CTA size limit of the resident kernel (64 registers at 2 CTAs)
+
 // Work list of the resident engine: systems in the order CTAs take them
 // (largest first), a queue counter (zero before the launch), steps per launch
 // and the shared-memory capacity of one CTA.

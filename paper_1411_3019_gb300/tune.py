@@ -24,7 +24,7 @@ import os
 from . import md
 
 GLOBAL_OPTIONS = {md.MD_OPT_PAIR_ORDER: (1, 0), md.MD_OPT_PAIR_LANES: (1, 2, 4)}
-RESIDENT_THREADS = (128, 256, 512)
+RESIDENT_THREADS = (0, 256, 128)  # 0: chosen per size class
 NAMES = {md.MD_OPT_PAIR_ORDER: "pair_order", md.MD_OPT_PAIR_LANES: "pair_lanes", md.MD_OPT_ENGINE: "engine",
          md.MD_OPT_RESIDENT_THREADS: "resident_threads"}
 

@@ -70,6 +70,17 @@ def test_every_cta_size_gives_the_same_bits(threads):
     _same_bits(_run(systems, 20, 0), _run(systems, 20, 1, threads=threads))
 
 
+def test_size_classes_of_a_wide_batch_give_the_same_bits():
+    # sizes 96..1191: with 128-thread CTAs the registers allow six per SM and
+    # shared memory three to eight, so the batch splits into several size
+    # classes (one launch each per chunk); automatic CTA sizes as well
+    systems = I.c4_replicas(nrep=24, seed=9, nmin=30, nmax=1500, rmin=4.0, rmax=16.0, precision="mixed",
+                            dt=0.002, tol=1e-10)
+    g = _run(systems, 12, 0)
+    _same_bits(g, _run(systems, 12, 1, threads=128, per_launch=5))
+    _same_bits(g, _run(systems, 12, 1, per_launch=5))
+
+
 def test_resident_engine_matches_the_oracle():
     systems = _replicas("mixed", nrep=4)
     st, f, _, _ = _run(systems, 40, 1)
@@ -118,7 +129,7 @@ def test_systems_the_resident_engine_cannot_hold_are_refused():
         md.md_set_option(sim.h, md.MD_OPT_ENGINE, 1)
     sim.close()
     sim = md.Simulation(_replicas("mixed", nrep=2))
-    for key, val in ((md.MD_OPT_ENGINE, 2), (md.MD_OPT_RESIDENT_THREADS, 100), (md.MD_OPT_RESIDENT_THREADS, 1024),
+    for key, val in ((md.MD_OPT_ENGINE, 2), (md.MD_OPT_RESIDENT_THREADS, 100), (md.MD_OPT_RESIDENT_THREADS, 544),
                      (md.MD_OPT_RESIDENT_STEPS, 0)):
         with pytest.raises(md.MdError):
             md.md_set_option(sim.h, key, val)
