@@ -67,7 +67,7 @@ class Params(C.Structure):
                 ("wall_lo_z", C.c_double), ("wall_hi_z", C.c_double),
                 ("wall_eps", C.c_double), ("wall_sigma", C.c_double),
                 ("seed", C.c_uint64), ("replica", C.c_uint32),
-                ("force_mode", C.c_int32)]
+                ("force_mode", C.c_int32), ("pair_form", C.c_int32)]
 
 
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -178,6 +178,7 @@ def make_params(prm: dict, force_mode: int = 0) -> Params:
     P.seed = prm.get("seed", 1) & 0xFFFFFFFFFFFFFFFF
     P.replica = prm.get("replica", 0) & 0xFFFFFFFF
     P.force_mode = force_mode
+    P.pair_form = int(prm.get("pair_form", 0))
     return P
 
 

@@ -36,6 +36,11 @@
  *   R5  The bond potential carries no factor 1/2: V = k (r - r0)^2.
  *   R6  The wall V_w acts on unconstrained particles with r - R_w replaced by
  *       the distance to each of two planes z = wall_lo_z, z = wall_hi_z.
+ *   R7  The linearly smoothed Lennard-Jones potential is printed with
+ *       "+ (r - r_c) phi'(r_c)", whose force does not vanish at r_c (it
+ *       doubles the jump); the text states that energy and force are both
+ *       continuous at r_c, which holds for "- (r - r_c) phi'(r_c)", the form
+ *       used here.
  */
 #include <math.h>
 #include <stdint.h>
@@ -71,6 +76,8 @@ typedef struct {
   uint32_t replica;
   int32_t force_mode; /* 0: brute force up to 4000 particles, else cells;
                          1: brute force; 2: cell list */
+  int32_t pair_form;  /* 0: truncated and shifted (Eq. S1); 1: linearly
+                         smoothed (V*_LJ of the energy-conservation study) */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -355,8 +362,12 @@ int orc_momentum_half(const orc_surface* S, const orc_params* P, const double x_
 /* ------------------------------------------------------------------------ */
 /* Forces: f = -grad V                                                       */
 /* ------------------------------------------------------------------------ */
-/* Truncated-shifted Lennard-Jones of Eq. (S1) for one pair at displacement
- * d = x_i - x_j. Adds the force on i to fi and returns V (0 beyond r_c). */
+/* Lennard-Jones pair term at displacement d = x_i - x_j, with
+ * phi(r) = 4 eps [(s/r)^12 - (s/r)^6]:
+ *   pair_form 0, truncated and shifted (Eq. S1):  V = phi(r) - phi(r_c);
+ *   pair_form 1, linearly smoothed (energy-conservation study of the SI):
+ *                V = phi(r) - phi(r_c) - (r - r_c) phi'(r_c)   (reading R7),
+ * both 0 for r >= r_c. Adds the force -dV/dr d/r on i to fi and returns V. */
 static double lj_pair(const orc_params* P, int ti, int tj, const double d[3],
                       double fi[3]) {
   double rc = P->rcut[ti][tj];
@@ -372,8 +383,16 @@ static double lj_pair(const orc_params* P, int ti, int tj, const double d[3],
   double phic = 4.0 * eps * (src6 * src6 - src6);
   /* -dphi/dr = 24 eps (2 (s/r)^12 - (s/r)^6) / r; along d/r */
   double fr_over_r = 24.0 * eps * (2.0 * sr12 - sr6) / r2;
+  double v = phi - phic;
+  if (P->pair_form == 1) {
+    /* phi'(r_c) = -24 eps (2 (s/r_c)^12 - (s/r_c)^6) / r_c; the linear term
+       adds +phi'(r_c) to -dV/dr, so the force vanishes at r_c */
+    double dphic = -24.0 * eps * (2.0 * src6 * src6 - src6) / rc;
+    v -= (r - rc) * dphic;
+    fr_over_r += dphic / r;
+  }
   for (int k = 0; k < 3; ++k) fi[k] += fr_over_r * d[k];
-  return phi - phic;
+  return v;
 }
 
 static int same_molecule(const orc_params* P, const int32_t* mol, int64_t i, int64_t j) {

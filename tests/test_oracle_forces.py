@@ -171,3 +171,59 @@ def test_periodic_forces_equal_explicit_image_sum(orc):
     centre = slice(4 * n, 5 * n)
     np.testing.assert_allclose(f_per, f_big[centre], rtol=1e-12, atol=1e-10)
     np.testing.assert_allclose(u_per, u_big[centre], rtol=1e-12, atol=1e-12)
+
+
+def _lj25(form, eps=2.0):
+    prm = I.wca_params(ntypes=1, pair_form=form)
+    prm["eps"][0, 0] = eps
+    prm["rcut"][0, 0] = 2.5
+    return prm
+
+
+def test_linearly_smoothed_lj_is_continuous_at_the_cutoff(orc):
+    """The smoothed potential of the energy-conservation study: energy and force
+    both vanish continuously at r_c (the energy quadratically in r_c - r), where
+    the truncated-shifted force jumps by phi'(r_c) = -24 eps (2 (s/r_c)^12 -
+    (s/r_c)^6) / r_c and its energy vanishes only linearly."""
+    jump = abs(24 * 2.0 * (2 * 2.5 ** -12 - 2.5 ** -6) / 2.5)  # |phi'(r_c)| at eps = 2
+    for delta in (1e-5, 1e-7):
+        f_s, u_s = _two(orc, 2.5 - delta, _lj25(1))
+        f_t, u_t = _two(orc, 2.5 - delta, _lj25(0))
+        assert abs(u_t.sum()) == pytest.approx(jump * delta, rel=1e-3)
+        assert abs(u_s.sum()) < 1e-3 * jump * delta
+        assert abs(f_s[0, 0]) < 1e-3 * jump
+        assert abs(f_t[0, 0]) == pytest.approx(jump, rel=1e-3)
+    f, u = _two(orc, 2.5 + 1e-12, _lj25(1))
+    assert np.abs(f).max() == 0.0 and np.abs(u).max() == 0.0
+
+
+def test_smoothing_shifts_the_force_by_a_constant_and_vanishes_for_wca(orc):
+    """V* - V = -(r - r_c) phi'(r_c): the force differs by the constant
+    phi'(r_c) along the pair axis at every r; with the WCA cutoff phi'(r_c) = 0."""
+    dphic = -24 * 2.0 * (2 * 2.5 ** -12 - 2.5 ** -6) / 2.5
+    for r in (0.95, 1.1, 1.5, 2.0, 2.4):
+        f_s, u_s = _two(orc, r, _lj25(1))
+        f_t, u_t = _two(orc, r, _lj25(0))
+        assert u_s.sum() - u_t.sum() == pytest.approx(-(r - 2.5) * dphic, rel=1e-12, abs=1e-15)
+        # force on particle 1 (at +r along x) is +(-dV/dr)
+        assert f_s[1, 0] - f_t[1, 0] == pytest.approx(dphic, rel=1e-12)
+    for r in (0.9, 1.0, 1.1):
+        f_s, u_s = _two(orc, r, I.wca_params(pair_form=1))
+        f_t, u_t = _two(orc, r, I.wca_params(pair_form=0))
+        np.testing.assert_allclose(f_s, f_t, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(u_s, u_t, rtol=1e-12, atol=1e-12)
+
+
+def test_smoothed_forces_are_minus_energy_gradient(orc):
+    g = np.random.default_rng(21)
+    prm = _lj25(1, eps=1.0)
+    x = I.rsa(lambda k, m: g.uniform(-3.0, 3.0, (m, 3)), [60], 0.95, g)[0]
+    f, _ = orc.pair_forces(prm, x)
+    h = 1e-6
+    for i in range(0, 60, 7):
+        for k in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[i, k] += h
+            xm[i, k] -= h
+            fd = -(orc.pair_forces(prm, xp)[1].sum() - orc.pair_forces(prm, xm)[1].sum()) / (2 * h)
+            assert f[i, k] == pytest.approx(fd, rel=1e-6, abs=1e-6)
