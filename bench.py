@@ -39,7 +39,7 @@ METRIC = ("particle-steps/sec on 1 GB300 (FP32-force/FP64-RATTLE vs plain FP64) 
           "≤1e-10")
 UNIT = "particle-steps/s"
 L2_FLUSH_BYTES = 256 << 20  # larger than the 129 MB L2
-WORKLOADS = ("ellipsoid_torus", "plain_sphere", "replicas", "bead_molecules", "bump_crowders")
+WORKLOADS = ("ellipsoid_torus", "plain_sphere", "replicas", "bead_molecules", "bump_crowders", "nve_surfaces")
 # float64 pipe of one GB300: 152 SMs x 2 float64 operations per SM per clock
 FP64_OPS_PER_SM_CLK = 2
 SMS = 152
@@ -60,6 +60,8 @@ def parse(argv=None):
     ap.add_argument("--engine", default="auto", choices=["auto", "global", "resident"],
                     help="auto: the autotuner picks the engine and its options")
     ap.add_argument("--nrep", type=int, default=4096, help="systems of the replicas workload")
+    ap.add_argument("--pair-form", type=int, default=1, choices=[0, 1],
+                    help="nve_surfaces: 0 truncated-shifted, 1 linearly smoothed Lennard-Jones")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args(argv)
@@ -72,7 +74,7 @@ def rank_seed(rank: int) -> int:
     return 1 + rank
 
 
-def workload(name: str, rank: int, precision: str, nrep: int = 4096):
+def workload(name: str, rank: int, precision: str, nrep: int = 4096, pair_form: int = 1):
     """The systems rank `rank` advances: an independently seeded copy of the
     named workload (weak scaling)."""
     from paper_1411_3019_gb300 import inputs
@@ -89,6 +91,9 @@ def workload(name: str, rank: int, precision: str, nrep: int = 4096):
         return inputs.c5_bead_molecules(seed=seed, precision=precision)
     if name == "bump_crowders":
         return inputs.c3_bump_crowders(seed=seed, precision=precision)
+    if name == "nve_surfaces":
+        return inputs.nve_systems(pair_form, seed=seed, precision=precision,
+                                  tol=1e-12 if precision == "fp64" else 1e-10)
     raise ValueError(name)
 
 
@@ -99,6 +104,10 @@ def workload_config(name, systems, precision):
         desc = (f"ellipsoid+torus: {systems[0]['n']} WCA on ellipsoid semi-axes "
                 f"({ell[0]:.1f},{ell[1]:.1f},{ell[2]:.1f}) at phi=0.4 + {systems[1]['n']} on torus "
                 f"R={tor[0]:g} r={tor[1]:g} (separate system); kT=gamma=1, dt=0.002, tol=1e-10")
+    elif name == "nve_surfaces":
+        desc = (f"nve_surfaces: {len(systems)} x {systems[0]['n']} LJ (rc=2.5) on "
+                f"{'/'.join(s['name'] for s in systems)} at phi=0.3, gamma=0, dt=0.0005, "
+                f"pair_form={systems[0]['params'].get('pair_form', 0)}")
     else:
         desc = f"{name}: {n} particles in {len(systems)} system(s)"
     return {"workload": f"{desc}, {precision}", "particles": n, "systems": len(systems),
@@ -279,7 +288,7 @@ def main(argv=None):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    precision = args.precision or ("fp64" if args.workload == "plain_sphere" else "mixed")
+    precision = args.precision or ("fp64" if args.workload in ("plain_sphere", "nve_surfaces") else "mixed")
     if args.impl == "reference":
         return reference_arm(args, rank, world, precision)
 
@@ -330,7 +339,7 @@ def main(argv=None):
         stream.synchronize()
         return [a.elapsed_time(b) / k] * k, md.md_last_launch_count(sim.h)
 
-    systems = workload(args.workload, rank, precision, args.nrep)
+    systems = workload(args.workload, rank, precision, args.nrep, args.pair_form)
     n_local = int(sum(s["n"] for s in systems))
     sim = md.Simulation(systems, stream=stream)
     sim.set_state()
@@ -432,7 +441,7 @@ def main(argv=None):
 
     plain = None
     if not args.no_plain and precision == "mixed":
-        systems64 = workload(args.workload, rank, "fp64", args.nrep)
+        systems64 = workload(args.workload, rank, "fp64", args.nrep, args.pair_form)
         sim64 = md.Simulation(systems64, stream=stream)
         sim64.set_state()
         sim64.step(args.warmup)
@@ -509,7 +518,7 @@ def reference_arm(args, rank: int, world: int, precision: str):
     time steps of the same workload (at most 60 timed steps)."""
     if rank != 0:
         return
-    systems = workload(args.workload, 0, precision, args.nrep)
+    systems = workload(args.workload, 0, precision, args.nrep, args.pair_form)
     sims = _oracle_systems(systems)
     n = sum(s["n"] for s in systems)
     for _ in range(args.warmup):

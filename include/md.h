@@ -108,6 +108,17 @@ typedef struct md_surface {
 #define MD_PREC_MIXED 1  /* float32 pair forces and noise; float64 state,
                             Newton solve, projection and position update      */
 
+/* Pair potential forms, phi(r) = 4 eps [(sigma/r)^12 - (sigma/r)^6], both 0
+ * for r >= rcut:
+ *   MD_PAIR_TRUNC_SHIFT    V = phi(r) - phi(rcut)                  (Eq. S1)
+ *   MD_PAIR_LINEAR_SMOOTH  V = phi(r) - phi(rcut) - (r - rcut) phi'(rcut),
+ *     the linearly smoothed potential of the SI energy-conservation study,
+ *     whose energy and force are both continuous at rcut (the SI prints the
+ *     linear term with a plus sign, under which the force would not vanish
+ *     at rcut; the sign here is the one that gives the stated continuity). */
+#define MD_PAIR_TRUNC_SHIFT 0
+#define MD_PAIR_LINEAR_SMOOTH 1
+
 typedef struct md_params {
   double dt;            /* time step                                          */
   double kT;            /* thermal energy                                     */
@@ -133,7 +144,7 @@ typedef struct md_params {
   double wall_lo_z, wall_hi_z, wall_eps, wall_sigma;
   uint64_t seed;        /* Philox key word 0 = low 32 bits of seed            */
   uint32_t replica;     /* Philox key word 1                                  */
-  int32_t reserved;     /* must be 0                                          */
+  int32_t pair_form;    /* MD_PAIR_TRUNC_SHIFT or MD_PAIR_LINEAR_SMOOTH        */
   double cell_size;     /* 0: largest rcut (plus a 2^-12 relative margin)     */
 } md_params;
 
@@ -168,8 +179,8 @@ int md_create(const md_surface* surf, const md_params* prm, int64_t n,
 
 /* Create nsys independent systems advanced together (ensembles of replicas).
  * surfs[s], prms[s], n_per_sys[s] describe system s. All systems must share
- * precision, ntypes, mass, eps, sigma, rcut and cell_size; the other fields
- * may differ. Systems never interact. */
+ * precision, ntypes, mass, eps, sigma, rcut, pair_form and cell_size; the
+ * other fields may differ. Systems never interact. */
 int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms,
                     const int64_t* n_per_sys, md_handle** out);
 

@@ -129,7 +129,8 @@ int check_system(const md_surface& s, const md_params& p, SysDev& S, std::string
     for (int b = 0; b < p.ntypes; ++b)
       if (p.rcut[a][b] > 0.0 && !(p.sigma[a][b] > 0.0)) return bad("sigma must be > 0 where rcut > 0");
   if (s.kind < MD_SURF_NONE || s.kind > MD_SURF_CYLINDER) return bad("unknown surface kind");
-  if (s.reserved != 0 || p.reserved != 0) return bad("reserved fields must be 0");
+  if (s.reserved != 0) return bad("reserved fields must be 0");
+  if (p.pair_form != MD_PAIR_TRUNC_SHIFT && p.pair_form != MD_PAIR_LINEAR_SMOOTH) return bad("unknown pair_form");
   for (int d = 0; d < 3; ++d)
     if (p.periodic[d] && !(p.box_hi[d] > p.box_lo[d])) return bad("a periodic axis needs box_hi > box_lo");
   if (p.beads_per_mol > 1 && !(p.bond_k >= 0.0 && p.bond_r0 >= 0.0)) return bad("bond_k, bond_r0 >= 0");
@@ -268,16 +269,28 @@ void fill_types(const md_params& p, TypeTable& T) {
         shift = 4.0 * ep * (s6 * s6 - s6);
       }
       T.shift[a][b] = shift;
+      // linear smoothing: phi'(r_c) (0 for the truncated-shifted form)
+      double lin = 0.0;
+      if (rc > 0.0 && p.pair_form == MD_PAIR_LINEAR_SMOOTH) {
+        const double s6 = std::pow(sg / rc, 6.0);
+        lin = -24.0 * ep * (2.0 * s6 * s6 - s6) / rc;
+      }
+      T.lin[a][b] = lin;
+      T.rc[a][b] = rc;
       T.eps_f[a][b] = (float)ep;
       T.sig2_f[a][b] = (float)(sg * sg);
       T.rc2_f[a][b] = (float)(rc * rc);
       T.shift_f[a][b] = (float)shift;
+      T.lin_f[a][b] = (float)lin;
+      T.rc_f[a][b] = (float)rc;
     }
   }
 }
 
 bool same_interactions(const md_params& a, const md_params& b) {
-  if (a.precision != b.precision || a.ntypes != b.ntypes || a.cell_size != b.cell_size) return false;
+  if (a.precision != b.precision || a.ntypes != b.ntypes || a.cell_size != b.cell_size ||
+      a.pair_form != b.pair_form)
+    return false;
   for (int i = 0; i < a.ntypes; ++i) {
     if (a.mass[i] != b.mass[i]) return false;
     for (int j = 0; j < a.ntypes; ++j)
@@ -521,7 +534,7 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
     if (!same_interactions(prms[0], prms[s])) {
       delete h;
       return fail(nullptr, MD_ERR_INVALID_ARG,
-                  "systems of a batch must share precision, ntypes, mass, eps, sigma, rcut, cell_size");
+                  "systems of a batch must share precision, ntypes, mass, eps, sigma, rcut, pair_form, cell_size");
     }
     h->first[s] = total;
     h->sys[s].first = total;

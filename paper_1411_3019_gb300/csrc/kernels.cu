@@ -690,7 +690,7 @@ template <> struct RecT<double> {
 
 template <typename R> struct PairTab {
   R eps[kMaxTypes * kMaxTypes], sig2[kMaxTypes * kMaxTypes], rc2[kMaxTypes * kMaxTypes],
-      shift[kMaxTypes * kMaxTypes];
+      shift[kMaxTypes * kMaxTypes], lin[kMaxTypes * kMaxTypes], rc[kMaxTypes * kMaxTypes];
 };
 
 template <typename R> __device__ __forceinline__ void load_tab(PairTab<R>& t, const TypeTable* T);
@@ -701,6 +701,8 @@ template <> __device__ __forceinline__ void load_tab<float>(PairTab<float>& t, c
     t.sig2[q] = T->sig2_f[a][b];
     t.rc2[q] = T->rc2_f[a][b];
     t.shift[q] = T->shift_f[a][b];
+    t.lin[q] = T->lin_f[a][b];
+    t.rc[q] = T->rc_f[a][b];
   }
 }
 template <> __device__ __forceinline__ void load_tab<double>(PairTab<double>& t, const TypeTable* T) {
@@ -710,12 +712,43 @@ template <> __device__ __forceinline__ void load_tab<double>(PairTab<double>& t,
     t.sig2[q] = T->sig2[a][b];
     t.rc2[q] = T->rc2[a][b];
     t.shift[q] = T->shift[a][b];
+    t.lin[q] = T->lin[a][b];
+    t.rc[q] = T->rc[a][b];
   }
 }
 
 template <typename R> __device__ __forceinline__ R rcp(R v);
 template <> __device__ __forceinline__ float rcp<float>(float v) { return __frcp_rn(v); }
 template <> __device__ __forceinline__ double rcp<double>(double v) { return 1.0 / v; }
+
+template <typename R> __device__ __forceinline__ R rsq(R v);
+template <> __device__ __forceinline__ float rsq<float>(float v) { return rsqrtf(v); }
+template <> __device__ __forceinline__ double rsq<double>(double v) { return nr_rsqrt(v); }
+
+// Lennard-Jones pair term inside the cutoff (r2 < r_c^2), phi(r) = 4 eps
+// [(s/r)^12 - (s/r)^6]: the truncated-shifted V = phi(r) - phi(r_c) of Eq. S1
+// and, where the table holds phi'(r_c) != 0, the linearly smoothed form of the
+// energy-conservation study, V = phi(r) - phi(r_c) - (r - r_c) phi'(r_c), whose
+// force -phi'(r) + phi'(r_c) vanishes at r_c. Adds the force on i (along the
+// displacement d = x_i - x_j) and half the pair energy.
+template <typename R>
+__device__ __forceinline__ void lj_term(const PairTab<R>& tab, uint32_t qt, R r2, R ddx, R ddy, R ddz, R& fx,
+                                        R& fy, R& fz, R& u) {
+  const R inv_r2 = rcp<R>(r2);
+  const R s2 = tab.sig2[qt] * inv_r2;
+  const R s6 = s2 * s2 * s2;
+  const R e = tab.eps[qt];
+  R fr = (R)24 * e * s6 * ((R)2 * s6 - (R)1) * inv_r2;
+  R v = (R)4 * e * s6 * (s6 - (R)1) - tab.shift[qt];
+  const R lin = tab.lin[qt];
+  if (lin != (R)0) {
+    const R inv_r = rsq<R>(r2);
+    fr += lin * inv_r;
+    v -= (r2 * inv_r - tab.rc[qt]) * lin;
+  }
+  fx += fr * ddx; fy += fr * ddy; fz += fr * ddz;
+  u += (R)0.5 * v;
+}
 
 template <typename R> __device__ __forceinline__ void store_f(void* f, uint32_t i, R fx, R fy, R fz, R u);
 template <> __device__ __forceinline__ void store_f<float>(void* f, uint32_t i, float fx, float fy, float fz,
@@ -898,15 +931,7 @@ __device__ __forceinline__ uint32_t pair_slot(const DevArrays& A, const Cells& C
           const uint32_t qt = ti * kMaxTypes + (bj & 7u);
           const R ddx = ri.x - rj.x - shx, ddy = ri.y - rj.y - shy, ddz = ri.z - rj.z - shz;
           const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-          if (r2 < tab.rc2[qt]) {
-            const R inv_r2 = rcp<R>(r2);
-            const R s2 = tab.sig2[qt] * inv_r2;
-            const R s6 = s2 * s2 * s2;
-            const R e = tab.eps[qt];
-            const R fr = (R)24 * e * s6 * ((R)2 * s6 - (R)1) * inv_r2;
-            fx += fr * ddx; fy += fr * ddy; fz += fr * ddz;
-            u += (R)0.5 * ((R)4 * e * s6 * (s6 - (R)1) - tab.shift[qt]);
-          }
+          if (r2 < tab.rc2[qt]) lj_term<R>(tab, qt, r2, ddx, ddy, ddz, fx, fy, fz, u);
         }
       }
     }
@@ -1017,15 +1042,7 @@ __global__ void __launch_bounds__(256) k_pair_lanes(DevArrays A) {
         const uint32_t qt = ti * kMaxTypes + (bj & 7u);
         const R ddx = ri.x - rj.x - shx, ddy = ri.y - rj.y - shy, ddz = ri.z - rj.z - shz;
         const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-        if (r2 < tab.rc2[qt]) {
-          const R inv_r2 = rcp<R>(r2);
-          const R s2 = tab.sig2[qt] * inv_r2;
-          const R s6 = s2 * s2 * s2;
-          const R e = tab.eps[qt];
-          const R fr = (R)24 * e * s6 * ((R)2 * s6 - (R)1) * inv_r2;
-          fx += fr * ddx; fy += fr * ddy; fz += fr * ddz;
-          u += (R)0.5 * ((R)4 * e * s6 * (s6 - (R)1) - tab.shift[qt]);
-        }
+        if (r2 < tab.rc2[qt]) lj_term<R>(tab, qt, r2, ddx, ddy, ddz, fx, fy, fz, u);
       }
     }
   }
@@ -2001,6 +2018,22 @@ __global__ void k_observables(DevArrays A, double* obs) {
 // ---------------------------------------------------------------------------
 static inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
+// Threads per block of the per-particle step kernels: 256, or fewer (a
+// multiple of 32) for small systems, so that the blocks spread over the SMs.
+// An SM's float64 pipe retires two operations per clock, and a system of a
+// thousand particles in 256-thread blocks would occupy four of them.
+static int block_for(int64_t units) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    sms = v > 0 ? v : 1;
+  }
+  const int64_t per = (units + sms - 1) / sms;
+  return (int)std::max<int64_t>(32, std::min<int64_t>(256, (per + 31) / 32 * 32));
+}
+
 cudaError_t launch_build_meta(const DevArrays& A, const int64_t* d_first, int nsys, const int32_t* d_type,
                               const uint8_t* d_con, const int32_t* d_mol, int, cudaStream_t st) {
   if (A.n == 0) return cudaSuccess;
@@ -2022,8 +2055,9 @@ cudaError_t launch_restore(const DevArrays& A, const double* d_x, const double* 
 
 cudaError_t launch_bin(const DevArrays& A, int precision, cudaStream_t st) {
   if (A.n == 0) return cudaSuccess;
-  if (precision == 0) k_bin<double><<<grid_for(A.n, 256), 256, 0, st>>>(A);
-  else k_bin<float><<<grid_for(A.n, 256), 256, 0, st>>>(A);
+  const int b = block_for(A.n);
+  if (precision == 0) k_bin<double><<<grid_for(A.n, b), b, 0, st>>>(A);
+  else k_bin<float><<<grid_for(A.n, b), b, 0, st>>>(A);
   return cudaGetLastError();
 }
 
@@ -2038,7 +2072,7 @@ cudaError_t launch_scan(const DevArrays& A, int advance, cudaStream_t st) {
 
 cudaError_t launch_scatter(const DevArrays& A, cudaStream_t st) {
   if (A.n == 0) return cudaSuccess;
-  k_scatter<<<grid_for(A.n, 256), 256, 0, st>>>(A);
+  k_scatter<<<grid_for(A.n, block_for(A.n)), block_for(A.n), 0, st>>>(A);
   return cudaGetLastError();
 }
 
@@ -2062,40 +2096,43 @@ cudaError_t launch_cells_after_bin(const DevArrays& A, int advance, cudaStream_t
 
 cudaError_t launch_bucket_build(const DevArrays& A, int precision, cudaStream_t st) {
   if (A.n == 0) return cudaSuccess;
-  if (precision == 0) k_bucket_build<double><<<grid_for(A.n, 256), 256, 0, st>>>(A);
-  else k_bucket_build<float><<<grid_for(A.n, 256), 256, 0, st>>>(A);
+  const int b = block_for(A.n);
+  if (precision == 0) k_bucket_build<double><<<grid_for(A.n, b), b, 0, st>>>(A);
+  else k_bucket_build<float><<<grid_for(A.n, b), b, 0, st>>>(A);
   return cudaGetLastError();
 }
 
 template <typename R>
 static void pair_dispatch_row(const DevArrays& A, int bonds, int walls, int excl, cudaStream_t st) {
-  const unsigned g = grid_for(A.n, 256);
+  const int b = block_for(A.n);
+  const unsigned g = grid_for(A.n, b);
   const int key = (bonds ? 4 : 0) | (walls ? 2 : 0) | (excl ? 1 : 0);
   switch (key) {
-    case 0: k_pair_row<R, false, false, false><<<g, 256, 0, st>>>(A); break;
-    case 1: k_pair_row<R, false, false, true><<<g, 256, 0, st>>>(A); break;
-    case 2: k_pair_row<R, false, true, false><<<g, 256, 0, st>>>(A); break;
-    case 3: k_pair_row<R, false, true, true><<<g, 256, 0, st>>>(A); break;
-    case 4: k_pair_row<R, true, false, false><<<g, 256, 0, st>>>(A); break;
-    case 5: k_pair_row<R, true, false, true><<<g, 256, 0, st>>>(A); break;
-    case 6: k_pair_row<R, true, true, false><<<g, 256, 0, st>>>(A); break;
-    default: k_pair_row<R, true, true, true><<<g, 256, 0, st>>>(A); break;
+    case 0: k_pair_row<R, false, false, false><<<g, b, 0, st>>>(A); break;
+    case 1: k_pair_row<R, false, false, true><<<g, b, 0, st>>>(A); break;
+    case 2: k_pair_row<R, false, true, false><<<g, b, 0, st>>>(A); break;
+    case 3: k_pair_row<R, false, true, true><<<g, b, 0, st>>>(A); break;
+    case 4: k_pair_row<R, true, false, false><<<g, b, 0, st>>>(A); break;
+    case 5: k_pair_row<R, true, false, true><<<g, b, 0, st>>>(A); break;
+    case 6: k_pair_row<R, true, true, false><<<g, b, 0, st>>>(A); break;
+    default: k_pair_row<R, true, true, true><<<g, b, 0, st>>>(A); break;
   }
 }
 
 template <typename R, int L>
 static void pair_dispatch_l(const DevArrays& A, int bonds, int walls, int excl, cudaStream_t st) {
-  const unsigned g = (unsigned)(((uint64_t)A.n * L + 255) / 256);
+  const int b = block_for((int64_t)A.n * L);
+  const unsigned g = grid_for((int64_t)A.n * L, b);
   const int key = (bonds ? 4 : 0) | (walls ? 2 : 0) | (excl ? 1 : 0);
   switch (key) {
-    case 0: k_pair_lanes<R, false, false, false, L><<<g, 256, 0, st>>>(A); break;
-    case 1: k_pair_lanes<R, false, false, true, L><<<g, 256, 0, st>>>(A); break;
-    case 2: k_pair_lanes<R, false, true, false, L><<<g, 256, 0, st>>>(A); break;
-    case 3: k_pair_lanes<R, false, true, true, L><<<g, 256, 0, st>>>(A); break;
-    case 4: k_pair_lanes<R, true, false, false, L><<<g, 256, 0, st>>>(A); break;
-    case 5: k_pair_lanes<R, true, false, true, L><<<g, 256, 0, st>>>(A); break;
-    case 6: k_pair_lanes<R, true, true, false, L><<<g, 256, 0, st>>>(A); break;
-    default: k_pair_lanes<R, true, true, true, L><<<g, 256, 0, st>>>(A); break;
+    case 0: k_pair_lanes<R, false, false, false, L><<<g, b, 0, st>>>(A); break;
+    case 1: k_pair_lanes<R, false, false, true, L><<<g, b, 0, st>>>(A); break;
+    case 2: k_pair_lanes<R, false, true, false, L><<<g, b, 0, st>>>(A); break;
+    case 3: k_pair_lanes<R, false, true, true, L><<<g, b, 0, st>>>(A); break;
+    case 4: k_pair_lanes<R, true, false, false, L><<<g, b, 0, st>>>(A); break;
+    case 5: k_pair_lanes<R, true, false, true, L><<<g, b, 0, st>>>(A); break;
+    case 6: k_pair_lanes<R, true, true, false, L><<<g, b, 0, st>>>(A); break;
+    default: k_pair_lanes<R, true, true, true, L><<<g, b, 0, st>>>(A); break;
   }
 }
 
@@ -2113,8 +2150,9 @@ cudaError_t launch_pair(const DevArrays& A, int precision, int has_pairs, int bo
                         cudaStream_t st) {
   if (A.n == 0) return cudaSuccess;
   if (!has_pairs) {
-    if (precision == 0) k_nopair<double><<<grid_for(A.n, 256), 256, 0, st>>>(A, bonds, walls);
-    else k_nopair<float><<<grid_for(A.n, 256), 256, 0, st>>>(A, bonds, walls);
+    const int b = block_for(A.n);
+    if (precision == 0) k_nopair<double><<<grid_for(A.n, b), b, 0, st>>>(A, bonds, walls);
+    else k_nopair<float><<<grid_for(A.n, b), b, 0, st>>>(A, bonds, walls);
   } else if (precision == 0) {
     pair_dispatch<double>(A, bonds, walls, excl, A.pair_lanes, st);
   } else {
@@ -2125,13 +2163,14 @@ cudaError_t launch_pair(const DevArrays& A, int precision, int has_pairs, int bo
 
 cudaError_t launch_integrate(const DevArrays& A, int precision, int has_pairs, cudaStream_t st) {
   if (A.n == 0) return cudaSuccess;
-  const unsigned g = grid_for(A.n, 256);
+  const int b = block_for(A.n);
+  const unsigned g = grid_for(A.n, b);
   if (precision == 0) {
-    if (has_pairs) k_integrate<double, true><<<g, 256, 0, st>>>(A);
-    else k_integrate<double, false><<<g, 256, 0, st>>>(A);
+    if (has_pairs) k_integrate<double, true><<<g, b, 0, st>>>(A);
+    else k_integrate<double, false><<<g, b, 0, st>>>(A);
   } else {
-    if (has_pairs) k_integrate<float, true><<<g, 256, 0, st>>>(A);
-    else k_integrate<float, false><<<g, 256, 0, st>>>(A);
+    if (has_pairs) k_integrate<float, true><<<g, b, 0, st>>>(A);
+    else k_integrate<float, false><<<g, b, 0, st>>>(A);
   }
   return cudaGetLastError();
 }
@@ -2143,8 +2182,9 @@ cudaError_t launch_advance(const DevArrays& A, cudaStream_t st) {
 
 cudaError_t launch_finish(const DevArrays& A, int precision, cudaStream_t st) {
   if (A.n == 0) return cudaSuccess;
-  if (precision == 0) k_finish<double><<<grid_for(A.n, 256), 256, 0, st>>>(A);
-  else k_finish<float><<<grid_for(A.n, 256), 256, 0, st>>>(A);
+  const int b = block_for(A.n);
+  if (precision == 0) k_finish<double><<<grid_for(A.n, b), b, 0, st>>>(A);
+  else k_finish<float><<<grid_for(A.n, b), b, 0, st>>>(A);
   return cudaGetLastError();
 }
 

@@ -81,10 +81,14 @@ struct TypeTable {
   double sig2[kMaxTypes][kMaxTypes];
   double rc2[kMaxTypes][kMaxTypes];
   double shift[kMaxTypes][kMaxTypes];  // phi(r_c)
+  double lin[kMaxTypes][kMaxTypes];    // phi'(r_c) for the linearly smoothed form, else 0
+  double rc[kMaxTypes][kMaxTypes];
   float eps_f[kMaxTypes][kMaxTypes];
   float sig2_f[kMaxTypes][kMaxTypes];
   float rc2_f[kMaxTypes][kMaxTypes];
   float shift_f[kMaxTypes][kMaxTypes];
+  float lin_f[kMaxTypes][kMaxTypes];
+  float rc_f[kMaxTypes][kMaxTypes];
   double mass[kMaxTypes], inv_mass[kMaxTypes], sqrt_mass[kMaxTypes];
   float sqrt_mass_f[kMaxTypes];
 };

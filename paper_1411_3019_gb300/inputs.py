@@ -461,3 +461,39 @@ def c5_bead_molecules(nmol=20_000, beads=5, R=60.0, seed=1, dmin=1.0, precision=
     con = (type_ == 0).astype(np.uint8)
     return [_system("bead_molecules", surf, prm, x, maxwell(x.shape[0], 1.0, 1.0, g),
                     type_=type_, constrained=con)]
+
+
+def nve_systems(pair_form: int, n: int = 500, phi: float = 0.3, seed: int = 1, precision: str = "fp64",
+                dt: float = 0.0005, tol: float = 1e-12, rc: float = 2.5, dmin: float = 1.0):
+    """Energy-conservation workload of the SI: n Lennard-Jones particles
+    (eps = sigma = m = 1, cutoff rc, truncated-shifted (pair_form 0) or
+    linearly smoothed (1)) held on a sphere, a cylinder (periodic along its
+    axis), a torus and a plane (periodic in x and y), each at area fraction
+    phi, gamma = 0 (constant energy), Maxwell velocities at kT = 1. Returns
+    the four systems (one batch)."""
+    area = n * A_P / phi
+    out = []
+    specs = []
+    R_s = math.sqrt(area / (4 * math.pi))
+    specs.append(("sphere", {"kind": "sphere", "center": (0.0, 0.0, 0.0), "p": (R_s, 0, 0, 0)}, {}))
+    R_c = 6.0
+    L_c = area / (2 * math.pi * R_c)
+    specs.append(("cylinder", {"kind": "cylinder", "center": (0.0, 0.0, 0.0), "p": (R_c, 2.0, 0, 0)},
+                  dict(box_lo=(-R_c - 3, -R_c - 3, -L_c / 2), box_hi=(R_c + 3, R_c + 3, L_c / 2),
+                       periodic=(0, 0, 1))))
+    r_t = 3.0
+    R_t = area / (4 * math.pi ** 2 * r_t)
+    specs.append(("torus", {"kind": "torus", "center": (0.0, 0.0, 0.0), "p": (R_t, r_t, 0, 0)}, {}))
+    L_p = math.sqrt(area)
+    specs.append(("plane", {"kind": "plane", "center": (0.0, 0.0, 0.0), "p": (0.0, 0.0, 1.0, 0)},
+                  dict(box_lo=(-L_p / 2, -L_p / 2, -3.0), box_hi=(L_p / 2, L_p / 2, 3.0), periodic=(1, 1, 0))))
+    for k, (name, surf, extra) in enumerate(specs):
+        prm = wca_params(precision=precision, dt=dt, rattle_tol=tol, gamma=0.0, seed=seed, replica=k,
+                         pair_form=pair_form, **extra)
+        prm["rcut"][0, 0] = rc
+        g = rng(seed, 100 + k)
+        box = (prm["box_lo"], prm["box_hi"]) if extra else None
+        x = rsa(lambda kk, m: sample_surface(surf, m, g, box=box), [n], dmin, g, periodic=prm["periodic"],
+                box=box)[0]
+        out.append(_system(name, surf, prm, x, maxwell(n, 1.0, 1.0, g)))
+    return out

@@ -27,6 +27,7 @@ MD_OK, MD_ERR_INVALID_ARG, MD_ERR_CUDA, MD_ERR_RATTLE_DIVERGED = 0, 1, 2, 3
 MD_ERR_NONFINITE, MD_ERR_OUT_OF_GRID, MD_ERR_TIMEOUT, MD_ERR_NO_DEVICE = 4, 5, 6, 7
 MD_FLAG_RATTLE_DIVERGED, MD_FLAG_NONFINITE, MD_FLAG_OUT_OF_GRID, MD_FLAG_TIMEOUT = 1, 2, 4, 8
 MD_OPT_PAIR_LANES = 1
+MD_PAIR_TRUNC_SHIFT, MD_PAIR_LINEAR_SMOOTH = 0, 1
 MD_OPT_PAIR_ORDER = 2
 MD_OPT_ENGINE = 3
 MD_OPT_RESIDENT_THREADS = 4
@@ -60,7 +61,7 @@ class md_params(C.Structure):
                 ("exclude_intramol", C.c_int32), ("wall_enable", C.c_int32),
                 ("wall_lo_z", C.c_double), ("wall_hi_z", C.c_double), ("wall_eps", C.c_double),
                 ("wall_sigma", C.c_double), ("seed", C.c_uint64), ("replica", C.c_uint32),
-                ("reserved", C.c_int32), ("cell_size", C.c_double)]
+                ("pair_form", C.c_int32), ("cell_size", C.c_double)]
 
 
 class md_obs(C.Structure):
@@ -185,7 +186,7 @@ def make_params(prm: dict) -> md_params:
     P.wall_sigma = prm.get("wall_sigma", 1.0)
     P.seed = prm.get("seed", 1) & 0xFFFFFFFFFFFFFFFF
     P.replica = prm.get("replica", 0) & 0xFFFFFFFF
-    P.reserved = 0
+    P.pair_form = int(prm.get("pair_form", 0))
     P.cell_size = prm.get("cell_size", 0.0)
     return P
 

@@ -70,7 +70,7 @@ def _valid():
     ("params", "dt", 0.0), ("params", "dt", -1.0), ("params", "rattle_tol", 0.0),
     ("params", "precision", 7), ("params", "ntypes", 0), ("params", "ntypes", 9),
     ("params", "gamma", -1.0), ("params", "max_newton", -1),
-    ("surface", "p", (-1.0, 0, 0, 0)), ("surface", "kind", 42),
+    ("surface", "p", (-1.0, 0, 0, 0)), ("surface", "kind", 42), ("params", "pair_form", 2),
 ])
 def test_bad_arguments_are_rejected_on_the_host(md, change):
     s = _valid()

@@ -135,3 +135,25 @@ def test_frozen_normal_reaches_the_same_root(frozen):
     st = gpu_run(systems, 30)[0]
     ref = oracle_run(systems, 30)[0]
     assert np.abs(st["x"] - ref["x"]).max() <= POS_100["fp64"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("form", [0, 1])
+def test_lj_cutoff_25_in_both_pair_forms_matches_oracle(precision, form):
+    """Truncated-shifted (Eq. S1) and linearly smoothed LJ at r_c = 2.5 sigma,
+    where the two forms differ: forces at the start and after 50 steps."""
+    prm = I.wca_params(precision=precision, dt=0.002, rattle_tol=1e-12 if precision == "fp64" else 1e-10,
+                       seed=6, pair_form=form)
+    prm["rcut"][0, 0] = 2.5
+    surf = {"kind": "sphere", "center": (0.0, 0.0, 0.0), "p": (9.0, 0, 0, 0)}
+    g = I.rng(6, 11)
+    x = I.rsa(lambda k, m: I.sample_surface(surf, m, g), [500], 0.95, g)[0]
+    systems = [I._system("lj25", surf, prm, x, I.maxwell(500, 1.0, 1.0, g))]
+    st0, f0, u0, _, _ = gpu_run(systems, 0)
+    assert_forces(systems, st0["x"], f0, precision)
+    _, _, u_ref, _, _ = oracle_run(systems, 0)
+    np.testing.assert_allclose(u0.sum(), u_ref.sum(), rtol=1e-10 if precision == "fp64" else 1e-5)
+    st, f, u, res, _ = gpu_run(systems, 50)
+    ref = oracle_run(systems, 50)[0]
+    assert np.abs(st["x"] - ref["x"]).max() <= POS_100[precision]
+    assert_forces(systems, st["x"], f, precision)

@@ -64,6 +64,13 @@ def test_free_crowders_walls_and_periodic_box_bit_identical():
     _same_bits(_run(systems, 25, 0), _run(systems, 25, 1, per_launch=10))
 
 
+def test_linearly_smoothed_pairs_bit_identical():
+    systems = _replicas("mixed", nrep=4)
+    for sy in systems:
+        sy["params"] = dict(sy["params"], pair_form=1, rcut=sy["params"]["rcut"] * 0 + 2.5)
+    _same_bits(_run(systems, 20, 0), _run(systems, 20, 1))
+
+
 @pytest.mark.parametrize("threads", [64, 128, 512])
 def test_every_cta_size_gives_the_same_bits(threads):
     systems = _replicas("mixed", nrep=5)
