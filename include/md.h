@@ -119,6 +119,9 @@ typedef struct md_surface {
 #define MD_PAIR_TRUNC_SHIFT 0
 #define MD_PAIR_LINEAR_SMOOTH 1
 
+#define MD_WALL_PLANES 0
+#define MD_WALL_SPHERE 1
+
 typedef struct md_params {
   double dt;            /* time step                                          */
   double kT;            /* thermal energy                                     */
@@ -140,12 +143,27 @@ typedef struct md_params {
   double bond_k;        /* V = bond_k (r - bond_r0)^2                         */
   double bond_r0;
   int32_t exclude_intramol; /* 1: no pair term between beads of one molecule  */
-  int32_t wall_enable;  /* 1: V_w on unconstrained particles at two z faces   */
+  int32_t wall_enable;  /* 1: V_w on the unconstrained particles (wall_kind)  */
   double wall_lo_z, wall_hi_z, wall_eps, wall_sigma;
   uint64_t seed;        /* Philox key word 0 = low 32 bits of seed            */
   uint32_t replica;     /* Philox key word 1                                  */
   int32_t pair_form;    /* MD_PAIR_TRUNC_SHIFT or MD_PAIR_LINEAR_SMOOTH        */
   double cell_size;     /* 0: largest rcut (plus a 2^-12 relative margin)     */
+  /* Capsid-model terms (SI Section S3.2); all zero: none.                  */
+  double angle_k;       /* V_bend = angle_k (theta - angle_theta0)^2 on every
+                           three consecutive beads i, j, k of a chain, theta
+                           the angle at j between x_i - x_j and x_k - x_j
+                           (pi for a straight chain); needs beads_per_mol >= 3 */
+  double angle_theta0;
+  int32_t bond_r0_mix;  /* 1: bond rest length 2^{1/6} sigma[t_i][t_j] / 2 from
+                           the bonded beads' types (with sigma_ij = (sigma_i +
+                           sigma_j)/2 this is the SI's 2^{1/6}(sigma_i +
+                           sigma_j)/4); 0: bond_r0 for every bond            */
+  int32_t wall_kind;    /* MD_WALL_PLANES: V_w at z = wall_lo_z and wall_hi_z;
+                           MD_WALL_SPHERE: V_w(r - wall_radius) with r the
+                           distance from wall_center, pushing outwards      */
+  double wall_radius;
+  double wall_center[3];
 } md_params;
 
 /* Per-system observables (Section 3.1: kT = 2K/N_dof with 2 degrees of

@@ -67,7 +67,10 @@ class Params(C.Structure):
                 ("wall_lo_z", C.c_double), ("wall_hi_z", C.c_double),
                 ("wall_eps", C.c_double), ("wall_sigma", C.c_double),
                 ("seed", C.c_uint64), ("replica", C.c_uint32),
-                ("force_mode", C.c_int32), ("pair_form", C.c_int32)]
+                ("force_mode", C.c_int32), ("pair_form", C.c_int32),
+                ("angle_k", C.c_double), ("angle_theta0", C.c_double),
+                ("bond_r0_mix", C.c_int32), ("wall_kind", C.c_int32),
+                ("wall_radius", C.c_double), ("wall_center", C.c_double * 3)]
 
 
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -99,7 +102,8 @@ def lib():
             L.orc_pair_forces_cells.restype = C.c_int
             L.orc_pair_forces_cells.argtypes = [C.POINTER(Params), C.c_int64, _dp, _ip, _ip, _dp, _dp]
             L.orc_bond_wall_forces.restype = C.c_int
-            L.orc_bond_wall_forces.argtypes = [C.POINTER(Params), C.c_int64, _dp, C.c_void_p, _dp, _dp]
+            L.orc_bond_wall_forces.argtypes = [C.POINTER(Params), C.c_int64, _dp, C.c_void_p, C.c_void_p, _dp,
+                                               _dp]
             L.orc_create.restype = C.c_void_p
             L.orc_create.argtypes = [C.POINTER(Surface), C.POINTER(Params), C.c_int64]
             L.orc_destroy.argtypes = [C.c_void_p]
@@ -179,6 +183,13 @@ def make_params(prm: dict, force_mode: int = 0) -> Params:
     P.replica = prm.get("replica", 0) & 0xFFFFFFFF
     P.force_mode = force_mode
     P.pair_form = int(prm.get("pair_form", 0))
+    P.angle_k = float(prm.get("angle_k", 0.0))
+    P.angle_theta0 = float(prm.get("angle_theta0", 0.0))
+    P.bond_r0_mix = int(prm.get("bond_r0_mix", 0))
+    P.wall_kind = int(prm.get("wall_kind", 0))
+    P.wall_radius = float(prm.get("wall_radius", 0.0))
+    for k in range(3):
+        P.wall_center[k] = float(prm.get("wall_center", (0.0, 0.0, 0.0))[k])
     return P
 
 
@@ -247,13 +258,16 @@ def pair_forces(prm, x, type_=None, mol=None, mode="brute"):
     return f, u
 
 
-def bond_wall_forces(prm, x, constrained=None):
+def bond_wall_forces(prm, x, constrained=None, type_=None):
+    """Bonded (bonds, bend angles) and wall forces and per-particle energies
+    (SI S3.2); returns (f, u, behind_a_wall)."""
     x = _f64(x, (-1, 3))
     n = x.shape[0]
     f, u = np.zeros((n, 3)), np.zeros(n)
     con = None if constrained is None else np.ascontiguousarray(constrained, np.uint8)
+    t = None if type_ is None else np.ascontiguousarray(type_, np.int32)
     P = make_params(prm)
-    bad = lib().orc_bond_wall_forces(C.byref(P), n, x,
+    bad = lib().orc_bond_wall_forces(C.byref(P), n, x, None if t is None else t.ctypes.data,
                                      None if con is None else con.ctypes.data, f, u)
     return f, u, bad
 

@@ -36,6 +36,12 @@
  *   R5  The bond potential carries no factor 1/2: V = k (r - r0)^2.
  *   R6  The wall V_w acts on unconstrained particles with r - R_w replaced by
  *       the distance to each of two planes z = wall_lo_z, z = wall_hi_z.
+ *   R8  The bend angle theta of V_bend (SI S3.2) is the angle at the middle
+ *       bead between x_i - x_j and x_k - x_j (pi for a straight chain, the
+ *       rest angle theta0 = pi of the capsid model); the SI's arccos of
+ *       (x_i - x_j).(x_j - x_k) / (...) would be 0 for a straight chain. It
+ *       is evaluated as atan2(|u x w|, u.w), equal to the arccos and well
+ *       conditioned near 0 and pi.
  *   R7  The linearly smoothed Lennard-Jones potential is printed with
  *       "+ (r - r_c) phi'(r_c)", whose force does not vanish at r_c (it
  *       doubles the jump); the text states that energy and force are both
@@ -78,6 +84,12 @@ typedef struct {
                          1: brute force; 2: cell list */
   int32_t pair_form;  /* 0: truncated and shifted (Eq. S1); 1: linearly
                          smoothed (V*_LJ of the energy-conservation study) */
+  /* capsid-model terms (SI S3.2) */
+  double angle_k, angle_theta0;
+  int32_t bond_r0_mix; /* 1: bond rest length 2^(1/6) sigma[ti][tj] / 2 */
+  int32_t wall_kind;   /* 0: planes z = wall_lo_z, wall_hi_z; 1: sphere */
+  double wall_radius;
+  double wall_center[3];
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -552,52 +564,131 @@ int orc_pair_forces_cells(const orc_params* P, int64_t n, const double* x,
 /* Harmonic bonds along each molecule's chain (reading R5) and the wall of
  * reading R6; both add to f and u. Returns 1 if a free particle sits on or
  * behind a wall plane. */
-int orc_bond_wall_forces(const orc_params* P, int64_t n, const double* x,
-                         const uint8_t* constrained, double* f, double* u) {
-  int bad = 0;
-  if (P->beads_per_mol > 1) {
-    int64_t B = P->beads_per_mol;
-    for (int64_t i = 0; i + 1 < n; ++i) {
-      if ((i % B) == B - 1) continue;
-      int64_t j = i + 1;
-      double d[3] = {x[3 * i] - x[3 * j], x[3 * i + 1] - x[3 * j + 1],
-                     x[3 * i + 2] - x[3 * j + 2]};
+/* Bend angle of three beads (SI S3.2, reading R8): u = x_a - x_m,
+ * w = x_b - x_m, theta = atan2(|u x w|, u.w), V = k (theta - theta0)^2.
+ * With c = cos(theta), s = sin(theta), dV = dV/dtheta = 2 k (theta - theta0):
+ *   F_a = (dV / s) (w / (|u| |w|) - c u / |u|^2),
+ *   F_b = (dV / s) (u / (|u| |w|) - c w / |w|^2),   F_m = -(F_a + F_b)
+ * (F = -dV/dx with dtheta/dc = -1/s). At s = 0 the bracket is zero. */
+static double angle_term(const orc_params* P, const double xa[3], const double xm[3], const double xb[3],
+                         double fa[3], double fm[3], double fb[3]) {
+  double u[3] = {xa[0] - xm[0], xa[1] - xm[1], xa[2] - xm[2]};
+  double w[3] = {xb[0] - xm[0], xb[1] - xm[1], xb[2] - xm[2]};
+  min_image(P, u);
+  min_image(P, w);
+  double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  double ww = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  double uw = u[0] * w[0] + u[1] * w[1] + u[2] * w[2];
+  double cr[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+  double sn = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+  double theta = atan2(sn, uw);
+  double norm = sqrt(uu * ww);
+  double c = uw / norm, sth = sn / norm;
+  double dV = 2.0 * P->angle_k * (theta - P->angle_theta0);
+  double ratio = sth > 0.0 ? dV / sth : 0.0;
+  for (int k = 0; k < 3; ++k) {
+    fa[k] = ratio * (w[k] / norm - c * u[k] / uu);
+    fb[k] = ratio * (u[k] / norm - c * w[k] / ww);
+    fm[k] = -(fa[k] + fb[k]);
+  }
+  return P->angle_k * (theta - P->angle_theta0) * (theta - P->angle_theta0);
+}
+
+static double bond_r0_of(const orc_params* P, const int32_t* type, int64_t i, int64_t j) {
+  if (!P->bond_r0_mix) return P->bond_r0;
+  int ti = type ? type[i] : 0, tj = type ? type[j] : 0;
+  return pow(2.0, 1.0 / 6.0) * P->sigma[ti][tj] / 2.0;
+}
+
+/* Wall V_w of SI S3.2 on one unconstrained particle: planes z = wall_lo_z and
+ * z = wall_hi_z (reading R6), or the sphere of radius wall_radius about
+ * wall_center (r - R_w with r the distance from the centre, pushing outward).
+ * Adds the force to f and returns the energy; sets *bad behind a wall. */
+static double wall_term(const orc_params* P, const double xi[3], double f[3], double* scale, int* bad) {
+  double sw = P->wall_sigma, ew = P->wall_eps, v = 0.0;
+  double rcw = pow(2.0, 1.0 / 6.0) * sw;
+  if (P->wall_kind == 1) {
+    double d[3] = {xi[0] - P->wall_center[0], xi[1] - P->wall_center[1], xi[2] - P->wall_center[2]};
+    double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double h = r - P->wall_radius;
+    if (h <= 0.0) {
+      if (bad) *bad = 1;
+      return 0.0;
+    }
+    if (h >= rcw) return 0.0;
+    double s6 = pow(sw / h, 6.0);
+    double fr = 24.0 * ew * (2.0 * s6 * s6 - s6) / h;
+    for (int k = 0; k < 3; ++k) f[k] += fr * d[k] / r;
+    if (scale) *scale += fabs(fr);
+    return 4.0 * ew * (s6 * s6 - s6 + 0.25);
+  }
+  double dist[2] = {xi[2] - P->wall_lo_z, P->wall_hi_z - xi[2]};
+  double sign[2] = {+1.0, -1.0};
+  for (int w = 0; w < 2; ++w) {
+    double r = dist[w];
+    if (r <= 0.0) {
+      if (bad) *bad = 1;
+      continue;
+    }
+    if (r >= rcw) continue;
+    double s6 = pow(sw / r, 6.0);
+    double fr = 24.0 * ew * (2.0 * s6 * s6 - s6) / r;
+    f[2] += sign[w] * fr;
+    if (scale) *scale += fabs(fr);
+    v += 4.0 * ew * (s6 * s6 - s6 + 0.25);
+  }
+  return v;
+}
+
+/* Bonded and wall terms acting on particle i (SI S3.2): the bonds to its
+ * chain neighbours, every bend angle of three consecutive beads containing
+ * i, and the wall (unconstrained particles). Adds the force on i to f and
+ * returns i's share of the energy (half of each bond, a third of each angle,
+ * all of its wall term); adds each term's force magnitude on i to *scale. */
+static double bonded_on(const orc_params* P, int64_t n, const double* x, const int32_t* type,
+                        const uint8_t* con, int64_t i, double f[3], double* scale, int* bad) {
+  double ui = 0.0;
+  int64_t B = P->beads_per_mol;
+  if (B > 1) {
+    for (int side = 0; side < 2; ++side) {
+      int64_t j = side == 0 ? i - 1 : i + 1;
+      if (side == 0 && (i % B) == 0) continue;
+      if (side == 1 && ((i % B) == B - 1 || j >= n)) continue;
+      double d[3] = {x[3 * i] - x[3 * j], x[3 * i + 1] - x[3 * j + 1], x[3 * i + 2] - x[3 * j + 2]};
       min_image(P, d);
       double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-      double dr = r - P->bond_r0;
-      double v = P->bond_k * dr * dr;
-      double fmag_over_r = -2.0 * P->bond_k * dr / r;
-      for (int k = 0; k < 3; ++k) {
-        f[3 * i + k] += fmag_over_r * d[k];
-        f[3 * j + k] -= fmag_over_r * d[k];
-      }
-      if (u) {
-        u[i] += 0.5 * v;
-        u[j] += 0.5 * v;
-      }
+      double dr = r - bond_r0_of(P, type, i, j);
+      for (int k = 0; k < 3; ++k) f[k] += -2.0 * P->bond_k * dr / r * d[k];
+      if (scale) *scale += fabs(2.0 * P->bond_k * dr);
+      ui += 0.5 * P->bond_k * dr * dr;
     }
   }
-  if (P->wall_enable) {
-    double sw = P->wall_sigma, ew = P->wall_eps;
-    double rcw = pow(2.0, 1.0 / 6.0) * sw;
-    for (int64_t i = 0; i < n; ++i) {
-      if (constrained && constrained[i]) continue;
-      double dist[2] = {x[3 * i + 2] - P->wall_lo_z, P->wall_hi_z - x[3 * i + 2]};
-      double sign[2] = {+1.0, -1.0};
-      for (int w = 0; w < 2; ++w) {
-        double r = dist[w];
-        if (r <= 0.0) {
-          bad = 1;
-          continue;
-        }
-        if (r >= rcw) continue;
-        double s6 = pow(sw / r, 6.0);
-        double v = 4.0 * ew * (s6 * s6 - s6 + 0.25);
-        double fr = 24.0 * ew * (2.0 * s6 * s6 - s6) / r;
-        f[3 * i + 2] += sign[w] * fr;
-        if (u) u[i] += v;
-      }
+  if (B > 2 && P->angle_k != 0.0) {
+    for (int64_t m = i - 1; m <= i + 1; ++m) { /* middle bead of each angle containing i */
+      if (m < 1 || m + 1 >= n) continue;
+      if ((m % B) == 0 || (m % B) == B - 1) continue; /* m needs both chain neighbours */
+      double fa[3], fm[3], fb[3];
+      double v = angle_term(P, &x[3 * (m - 1)], &x[3 * m], &x[3 * (m + 1)], fa, fm, fb);
+      const double* fi = (i == m - 1) ? fa : (i == m ? fm : fb);
+      for (int k = 0; k < 3; ++k) f[k] += fi[k];
+      if (scale) *scale += sqrt(fi[0] * fi[0] + fi[1] * fi[1] + fi[2] * fi[2]);
+      ui += v / 3.0;
     }
+  }
+  if (P->wall_enable && !(con && con[i])) ui += wall_term(P, &x[3 * i], f, scale, bad);
+  return ui;
+}
+
+/* Bonded and wall forces and energies of all particles (f and u are added
+ * to). Returns 1 if a particle is behind a wall. */
+int orc_bond_wall_forces(const orc_params* P, int64_t n, const double* x, const int32_t* type,
+                         const uint8_t* constrained, double* f, double* u) {
+  int bad = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    double fi[3] = {0.0, 0.0, 0.0};
+    double ui = bonded_on(P, n, x, type, constrained, i, fi, NULL, &bad);
+    for (int k = 0; k < 3; ++k) f[3 * i + k] += fi[k];
+    if (u) u[i] += ui;
   }
   return bad;
 }
@@ -665,7 +756,7 @@ int orc_sys_forces(orc_sys* s) {
     orc_pair_forces_brute(&s->P, s->n, s->x, s->type, s->mol, s->fc, s->u);
   else if (orc_pair_forces_cells(&s->P, s->n, s->x, s->type, s->mol, s->fc, s->u))
     return -1;
-  if (orc_bond_wall_forces(&s->P, s->n, s->x, s->con, s->fc, s->u)) s->wall_bad = 1;
+  if (orc_bond_wall_forces(&s->P, s->n, s->x, s->type, s->con, s->fc, s->u)) s->wall_bad = 1;
   return 0;
 }
 
@@ -878,33 +969,7 @@ void orc_force_on(const orc_params* P, int64_t n, const double* x, const int32_t
     min_image(P, d);
     ui += 0.5 * lj_pair(P, type[i], type[j], d, f);
   }
-  if (P->beads_per_mol > 1) {
-    int64_t B = P->beads_per_mol;
-    for (int side = 0; side < 2; ++side) {
-      int64_t j = side == 0 ? i - 1 : i + 1;
-      if (side == 0 && (i % B) == 0) continue;
-      if (side == 1 && ((i % B) == B - 1 || j >= n)) continue;
-      double d[3] = {x[3 * i] - x[3 * j], x[3 * i + 1] - x[3 * j + 1], x[3 * i + 2] - x[3 * j + 2]};
-      min_image(P, d);
-      double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-      double dr = r - P->bond_r0;
-      for (int k = 0; k < 3; ++k) f[k] += -2.0 * P->bond_k * dr / r * d[k];
-      ui += 0.5 * P->bond_k * dr * dr;
-    }
-  }
-  if (P->wall_enable && !(con && con[i])) {
-    double sw = P->wall_sigma, ew = P->wall_eps;
-    double rcw = pow(2.0, 1.0 / 6.0) * sw;
-    double dist[2] = {x[3 * i + 2] - P->wall_lo_z, P->wall_hi_z - x[3 * i + 2]};
-    double sign[2] = {+1.0, -1.0};
-    for (int w = 0; w < 2; ++w) {
-      double r = dist[w];
-      if (r <= 0.0 || r >= rcw) continue;
-      double s6 = pow(sw / r, 6.0);
-      ui += 4.0 * ew * (s6 * s6 - s6 + 0.25);
-      f[2] += sign[w] * 24.0 * ew * (2.0 * s6 * s6 - s6) / r;
-    }
-  }
+  ui += bonded_on(P, n, x, type, con, i, f, NULL, NULL);
   if (u) *u = ui;
 }
 
@@ -965,33 +1030,9 @@ void orc_force_scale(const orc_params* P, int64_t n, const double* x, const int3
       scale[i] += sqrt(fi[0] * fi[0] + fi[1] * fi[1] + fi[2] * fi[2]);
     }
   }
-  /* bonds and walls: add |f| of each term */
-  if (P->beads_per_mol > 1 || P->wall_enable) {
-    for (int64_t i = 0; i < n; ++i) {
-      if (P->beads_per_mol > 1) {
-        int64_t B = P->beads_per_mol;
-        for (int side = 0; side < 2; ++side) {
-          int64_t j = side == 0 ? i - 1 : i + 1;
-          if (side == 0 && (i % B) == 0) continue;
-          if (side == 1 && ((i % B) == B - 1 || j >= n)) continue;
-          double d[3] = {x[3 * i] - x[3 * j], x[3 * i + 1] - x[3 * j + 1], x[3 * i + 2] - x[3 * j + 2]};
-          min_image(P, d);
-          double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-          scale[i] += fabs(2.0 * P->bond_k * (r - P->bond_r0));
-        }
-      }
-    }
-    if (P->wall_enable) {
-      for (int64_t i = 0; i < n; ++i) {
-        if (con && con[i]) continue;
-        double fw[3] = {0.0, 0.0, 0.0};
-        double xi[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
-        orc_params Q = *P;
-        Q.beads_per_mol = 0;
-        double dummy;
-        orc_force_on(&Q, 1, xi, &type[i], &mol[i], NULL, 0, fw, &dummy);
-        scale[i] += fabs(fw[2]);
-      }
-    }
+  /* bonds, angles and walls: add |f| of each term */
+  for (int64_t i = 0; i < n; ++i) {
+    double fi[3] = {0.0, 0.0, 0.0};
+    bonded_on(P, n, x, type, con, i, fi, &scale[i], NULL);
   }
 }

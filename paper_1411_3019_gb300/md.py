@@ -28,6 +28,7 @@ MD_ERR_NONFINITE, MD_ERR_OUT_OF_GRID, MD_ERR_TIMEOUT, MD_ERR_NO_DEVICE = 4, 5, 6
 MD_FLAG_RATTLE_DIVERGED, MD_FLAG_NONFINITE, MD_FLAG_OUT_OF_GRID, MD_FLAG_TIMEOUT = 1, 2, 4, 8
 MD_OPT_PAIR_LANES = 1
 MD_PAIR_TRUNC_SHIFT, MD_PAIR_LINEAR_SMOOTH = 0, 1
+MD_WALL_PLANES, MD_WALL_SPHERE = 0, 1
 MD_OPT_PAIR_ORDER = 2
 MD_OPT_ENGINE = 3
 MD_OPT_RESIDENT_THREADS = 4
@@ -61,7 +62,9 @@ class md_params(C.Structure):
                 ("exclude_intramol", C.c_int32), ("wall_enable", C.c_int32),
                 ("wall_lo_z", C.c_double), ("wall_hi_z", C.c_double), ("wall_eps", C.c_double),
                 ("wall_sigma", C.c_double), ("seed", C.c_uint64), ("replica", C.c_uint32),
-                ("pair_form", C.c_int32), ("cell_size", C.c_double)]
+                ("pair_form", C.c_int32), ("cell_size", C.c_double),
+                ("angle_k", C.c_double), ("angle_theta0", C.c_double), ("bond_r0_mix", C.c_int32),
+                ("wall_kind", C.c_int32), ("wall_radius", C.c_double), ("wall_center", C.c_double * 3)]
 
 
 class md_obs(C.Structure):
@@ -188,6 +191,13 @@ def make_params(prm: dict) -> md_params:
     P.replica = prm.get("replica", 0) & 0xFFFFFFFF
     P.pair_form = int(prm.get("pair_form", 0))
     P.cell_size = prm.get("cell_size", 0.0)
+    P.angle_k = float(prm.get("angle_k", 0.0))
+    P.angle_theta0 = float(prm.get("angle_theta0", 0.0))
+    P.bond_r0_mix = int(prm.get("bond_r0_mix", 0))
+    P.wall_kind = int(prm.get("wall_kind", 0))
+    P.wall_radius = float(prm.get("wall_radius", 0.0))
+    for k in range(3):
+        P.wall_center[k] = float(prm.get("wall_center", (0.0, 0.0, 0.0))[k])
     return P
 
 
