@@ -39,7 +39,8 @@ METRIC = ("particle-steps/sec on 1 GB300 (FP32-force/FP64-RATTLE vs plain FP64) 
           "≤1e-10")
 UNIT = "particle-steps/s"
 L2_FLUSH_BYTES = 256 << 20  # larger than the 129 MB L2
-WORKLOADS = ("ellipsoid_torus", "plain_sphere", "replicas", "bead_molecules", "bump_crowders", "nve_surfaces")
+WORKLOADS = ("ellipsoid_torus", "plain_sphere", "replicas", "bead_molecules", "bump_crowders", "nve_surfaces",
+             "capsids")
 # float64 pipe of one GB300: 152 SMs x 2 float64 operations per SM per clock
 FP64_OPS_PER_SM_CLK = 2
 SMS = 152
@@ -91,6 +92,8 @@ def workload(name: str, rank: int, precision: str, nrep: int = 4096, pair_form: 
         return inputs.c5_bead_molecules(seed=seed, precision=precision)
     if name == "bump_crowders":
         return inputs.c3_bump_crowders(seed=seed, precision=precision)
+    if name == "capsids":
+        return inputs.capsid_systems(nsys=max(1, nrep // 4), ncone=60, seed=seed, precision=precision)
     if name == "nve_surfaces":
         return inputs.nve_systems(pair_form, seed=seed, precision=precision,
                                   tol=1e-12 if precision == "fp64" else 1e-10)

@@ -26,7 +26,7 @@ struct md_handle {
   int precision = 1;
   int64_t n = 0;
   int nsys = 0;
-  int has_pairs = 0, bonds = 0, walls = 0, excl = 0;
+  int has_pairs = 0, bonds = 0, walls = 0, excl = 0, bends = 0;
   bool state_set = false;
   std::vector<SysDev> sys;
   std::vector<int64_t> first;
@@ -134,8 +134,18 @@ int check_system(const md_surface& s, const md_params& p, SysDev& S, std::string
   for (int d = 0; d < 3; ++d)
     if (p.periodic[d] && !(p.box_hi[d] > p.box_lo[d])) return bad("a periodic axis needs box_hi > box_lo");
   if (p.beads_per_mol > 1 && !(p.bond_k >= 0.0 && p.bond_r0 >= 0.0)) return bad("bond_k, bond_r0 >= 0");
-  if (p.wall_enable && !(p.wall_hi_z > p.wall_lo_z && p.wall_sigma > 0.0 && p.wall_eps >= 0.0))
+  if (p.wall_kind != MD_WALL_PLANES && p.wall_kind != MD_WALL_SPHERE) return bad("unknown wall_kind");
+  if (p.wall_enable && p.wall_kind == MD_WALL_PLANES &&
+      !(p.wall_hi_z > p.wall_lo_z && p.wall_sigma > 0.0 && p.wall_eps >= 0.0))
     return bad("wall needs wall_hi_z > wall_lo_z and wall_sigma > 0");
+  if (p.wall_enable && p.wall_kind == MD_WALL_SPHERE &&
+      !(p.wall_radius >= 0.0 && p.wall_sigma > 0.0 && p.wall_eps >= 0.0 && std::isfinite(p.wall_center[0]) &&
+        std::isfinite(p.wall_center[1]) && std::isfinite(p.wall_center[2])))
+    return bad("a spherical wall needs wall_radius >= 0, wall_sigma > 0 and a finite wall_center");
+  if (!(p.angle_k >= 0.0 && std::isfinite(p.angle_k) && std::isfinite(p.angle_theta0)))
+    return bad("angle_k must be >= 0 and finite");
+  if (p.angle_k > 0.0 && p.beads_per_mol < 3) return bad("bend angles need beads_per_mol >= 3");
+  if (p.bond_r0_mix != 0 && p.bond_r0_mix != 1) return bad("bond_r0_mix must be 0 or 1");
   std::memset(&S, 0, sizeof(S));
   S.kind = s.kind;
   for (int d = 0; d < 3; ++d) S.c[d] = s.center[d];
@@ -210,6 +220,12 @@ int check_system(const md_surface& s, const md_params& p, SysDev& S, std::string
   S.wall_lo = p.wall_lo_z;
   S.wall_hi = p.wall_hi_z;
   S.wall_eps = p.wall_eps;
+  S.angle_k = p.angle_k;
+  S.angle_theta0 = p.angle_theta0;
+  S.bond_mix = p.bond_r0_mix;
+  S.wall_kind = p.wall_kind;
+  S.wall_radius = p.wall_radius;
+  for (int d = 0; d < 3; ++d) S.wall_center[d] = p.wall_center[d];
   S.wall_sigma = p.wall_sigma;
   S.wall_rc = std::pow(2.0, 1.0 / 6.0) * p.wall_sigma;
   S.seed_lo = (uint32_t)(p.seed & 0xffffffffu);
@@ -277,6 +293,7 @@ void fill_types(const md_params& p, TypeTable& T) {
       }
       T.lin[a][b] = lin;
       T.rc[a][b] = rc;
+      T.bond_r0_mix[a][b] = std::pow(2.0, 1.0 / 6.0) * sg / 2.0;
       T.eps_f[a][b] = (float)ep;
       T.sig2_f[a][b] = (float)(sg * sg);
       T.rc2_f[a][b] = (float)(rc * rc);
@@ -337,6 +354,7 @@ struct StepKernel {
 cudaError_t k_pair_step(md_handle* h, cudaStream_t st) {
   return launch_pair(h->A, h->precision, h->has_pairs, h->bonds, h->walls, h->excl, st);
 }
+cudaError_t k_bend_step(md_handle* h, cudaStream_t st) { return launch_bend(h->A, h->precision, st); }
 cudaError_t k_integrate_step(md_handle* h, cudaStream_t st) {
   return launch_integrate(h->A, h->precision, h->has_pairs, st);
 }
@@ -352,16 +370,24 @@ const StepKernel kStepWithCells[] = {{"pair", k_pair_step},
                                      {"scan", k_scan_step},
                                      {"scatter", k_scatter_step},
                                      {"bucket_build", k_bucket_step}};
+const StepKernel kStepWithCellsBends[] = {{"pair", k_pair_step},
+                                          {"bend", k_bend_step},
+                                          {"integrate", k_integrate_step},
+                                          {"scan", k_scan_step},
+                                          {"scatter", k_scatter_step},
+                                          {"bucket_build", k_bucket_step}};
 const StepKernel kStepNoCells[] = {{"pair", k_pair_step}, {"integrate", k_integrate_step},
                                    {"advance", k_advance_step}};
+const StepKernel kStepNoCellsBends[] = {{"pair", k_pair_step}, {"bend", k_bend_step},
+                                        {"integrate", k_integrate_step}, {"advance", k_advance_step}};
 
 int step_kernels(const md_handle* h, const StepKernel** list) {
   if (h->has_pairs) {
-    *list = kStepWithCells;
-    return 5;
+    *list = h->bends ? kStepWithCellsBends : kStepWithCells;
+    return h->bends ? 6 : 5;
   }
-  *list = kStepNoCells;
-  return 3;
+  *list = h->bends ? kStepNoCellsBends : kStepNoCells;
+  return h->bends ? 4 : 3;
 }
 
 // One time step, enqueued on stream st.
@@ -483,6 +509,7 @@ int resident_steps(md_handle* h, int64_t nsteps) {
 
 int forces_now(md_handle* h) {
   CK(h, launch_pair(h->A, h->precision, h->has_pairs, h->bonds, h->walls, h->excl, h->stream()));
+  if (h->bends) CK(h, launch_bend(h->A, h->precision, h->stream()));
   return MD_OK;
 }
 
@@ -558,6 +585,7 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
     if (prms[s].beads_per_mol > 1) h->bonds = 1;
     if (prms[s].wall_enable) h->walls = 1;
     if (prms[s].exclude_intramol) h->excl = 1;
+    if (prms[s].beads_per_mol > 2 && prms[s].angle_k != 0.0) h->bends = 1;
   }
   // cell grids
   // cell edge: the largest cutoff plus a 2^-12 margin, rounded up to a float
@@ -820,7 +848,7 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
     md_destroy(h);
     return fail(nullptr, MD_ERR_CUDA, m);
   }
-  h->kernels_per_step = h->has_pairs ? 5 : 3;
+  h->kernels_per_step = (h->has_pairs ? 5 : 3) + (h->bends ? 1 : 0);
   *out = h;
   return MD_OK;
 }
@@ -1474,6 +1502,7 @@ extern "C" int md_forces_noalloc(const md_surface* surf, const md_params* prm, i
     if (e == cudaSuccess) e = launch_bucket_build(A, prm->precision, st);
   }
   if (e == cudaSuccess) e = launch_pair(A, prm->precision, has_pairs, bonds, walls, excl, st);
+  if (e == cudaSuccess && prm->beads_per_mol > 2 && prm->angle_k != 0.0) e = launch_bend(A, prm->precision, st);
   if (e == cudaSuccess) e = launch_get_forces(A, prm->precision, d_f, d_u, st);
   uint32_t status = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&status, A.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);

@@ -44,6 +44,8 @@ cudaError_t launch_pair(const DevArrays& A, int precision, int has_pairs, int bo
                         int excl, cudaStream_t st);
 
 // Combine + momentum half + position half (+ binning when has_pairs).
+// Bend-angle forces added to the pair kernel's output (systems with angles).
+cudaError_t launch_bend(const DevArrays& A, int precision, cudaStream_t st);
 cudaError_t launch_integrate(const DevArrays& A, int precision, int has_pairs, cudaStream_t st);
 
 // Step counter on by one, mode = 1 (used when there is no cell list).

@@ -760,14 +760,82 @@ template <> __device__ __forceinline__ void store_f<double>(void* f, uint32_t i,
   reinterpret_cast<double4_32a*>(f)[i] = make_double4_32a(fx, fy, fz, u);
 }
 
-// Bond (V = k (r - r0)^2, no factor 1/2) and wall (V_w) terms of particle
-// `tag`, in float64 on both paths: the bond stretch r - r0 cancels (r is
-// close to r0) and its stiffness 2k would amplify float32 rounding of r.
+// Minimum-image difference a - b of two positions of one system.
+__device__ __forceinline__ void min_image_diff(const SysDev& S, const double* a, const double* b, double d[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    d[k] = a[k] - b[k];
+    if (S.periodic[k]) d[k] = wrap_min_image(d[k], S.box_len[k]);
+  }
+}
+
+// Bend angle of three beads (SI S3.2): u = x_a - x_m, w = x_b - x_m,
+// theta = atan2(|u x w|, u.w) (the angle at the middle bead, pi for a
+// straight chain), V = k (theta - theta0)^2. With c = cos theta, s = sin
+// theta and dV = 2k (theta - theta0), the force on a is (dV/s)(w/(|u||w|) -
+// c u/|u|^2), on b the same with u and w exchanged, on m minus their sum
+// (zero bracket at s = 0). `which` selects the bead (0 a, 1 m, 2 b); returns V.
+__device__ __forceinline__ double bend_term(const SysDev& S, const double* xa, const double* xm, const double* xb,
+                                            int which, double f[3]) {
+  double u[3], w[3];
+  min_image_diff(S, xa, xm, u);
+  min_image_diff(S, xb, xm, w);
+  const double uu = fma(u[0], u[0], fma(u[1], u[1], u[2] * u[2]));
+  const double ww = fma(w[0], w[0], fma(w[1], w[1], w[2] * w[2]));
+  const double uw = fma(u[0], w[0], fma(u[1], w[1], u[2] * w[2]));
+  const double c0 = u[1] * w[2] - u[2] * w[1], c1 = u[2] * w[0] - u[0] * w[2], c2 = u[0] * w[1] - u[1] * w[0];
+  const double sn = sqrt(fma(c0, c0, fma(c1, c1, c2 * c2)));
+  const double theta = atan2(sn, uw);
+  const double norm = sqrt(uu * ww);
+  const double c = uw / norm, sth = sn / norm;
+  const double dth = theta - S.angle_theta0;
+  const double ratio = sth > 0.0 ? 2.0 * S.angle_k * dth / sth : 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double fa = ratio * (w[k] / norm - c * u[k] / uu);
+    const double fb = ratio * (u[k] / norm - c * w[k] / ww);
+    f[k] = which == 0 ? fa : (which == 2 ? fb : -(fa + fb));
+  }
+  return S.angle_k * dth * dth;
+}
+
+// Bend angles of particle `tag` (float64): the force on it from every angle
+// of three consecutive beads of its chain that contains it, and its energy
+// share (a third of each angle). Kept out of the pair kernels (its registers
+// would lower their occupancy): k_bend and a phase of the resident engine add
+// it to the particle's force after the pair kernel.
+__device__ __forceinline__ void bend_on(const DevArrays& A, const SysDev& S, int64_t tag, double f[3], double& v) {
+  const int64_t n = A.n;
+  const int64_t pid = tag - S.first;
+  const int64_t B = S.bpm;
+  f[0] = f[1] = f[2] = 0.0;
+  v = 0.0;
+  for (int64_t mid = pid - 1; mid <= pid + 1; ++mid) {  // middle bead of each angle containing the particle
+    if (mid < 1 || mid + 1 >= S.n || mid % B == 0 || mid % B == B - 1) continue;
+    const int64_t gm = S.first + mid;
+    const double xa[3] = {A.x[gm - 1], A.x[n + gm - 1], A.x[2 * n + gm - 1]};
+    const double xm[3] = {A.x[gm], A.x[n + gm], A.x[2 * n + gm]};
+    const double xb[3] = {A.x[gm + 1], A.x[n + gm + 1], A.x[2 * n + gm + 1]};
+    double fa[3];
+    v += bend_term(S, xa, xm, xb, (int)(pid - mid + 1), fa) / 3.0;
+    f[0] += fa[0]; f[1] += fa[1]; f[2] += fa[2];
+  }
+}
+
+__device__ __forceinline__ bool has_bends(const SysDev& S) { return S.bpm > 2 && S.angle_k != 0.0; }
+
+// Bonded and wall terms of particle `tag`, in float64 on both paths (the bond
+// stretch r - r0 cancels, r being close to r0, and the stiffness would
+// amplify float32 rounding): bonds V = k (r - r0)^2 (no factor 1/2) to the
+// chain neighbours, r0 from the bead types when bond_mix is set, and the wall
+// V_w (two z planes, or a sphere about wall_center) on unconstrained
+// particles. The particle's energy share is half of each bond and all of its
+// wall term.
 template <typename R>
 __device__ __forceinline__ void bonded_terms(const DevArrays& A, const SysDev& S, uint32_t tag, uint32_t m,
                                              bool bonds, bool walls, R& fx, R& fy, R& fz, R& u) {
   const int64_t n = A.n;
-  const double xi = A.x[tag], yi = A.x[n + tag], zi = A.x[2 * n + tag];
+  const double xi[3] = {A.x[tag], A.x[n + tag], A.x[2 * n + tag]};
   double bx = 0.0, by = 0.0, bz = 0.0, bu = 0.0;
   if (bonds && S.bpm > 1) {
     const int64_t pid = (int64_t)tag - S.first;
@@ -782,49 +850,55 @@ __device__ __forceinline__ void bonded_terms(const DevArrays& A, const SysDev& S
         if (pid % B == B - 1 || pid + 1 >= S.n) continue;
         j = (int64_t)tag + 1;
       }
-      double dx = xi - A.x[j], dy = yi - A.x[n + j], dz = zi - A.x[2 * n + j];
-      if (S.periodic[0]) dx = wrap_min_image(dx, S.box_len[0]);
-      if (S.periodic[1]) dy = wrap_min_image(dy, S.box_len[1]);
-      if (S.periodic[2]) dz = wrap_min_image(dz, S.box_len[2]);
-      const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+      const double xj[3] = {A.x[j], A.x[n + j], A.x[2 * n + j]};
+      double d[3];
+      min_image_diff(S, xi, xj, d);
+      const double r2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]));
       const double ir = nr_rsqrt(r2);
-      const double dr = fma(r2, ir, -S.bond_r0);  // r - r0
+      const double r0 = S.bond_mix ? A.types->bond_r0_mix[meta_type(m)][meta_type(A.meta[j])] : S.bond_r0;
+      const double dr = fma(r2, ir, -r0);  // r - r0
       const double fo = -2.0 * S.bond_k * dr * ir;
-      bx = fma(fo, dx, bx); by = fma(fo, dy, by); bz = fma(fo, dz, bz);
+      bx = fma(fo, d[0], bx); by = fma(fo, d[1], by); bz = fma(fo, d[2], bz);
       bu = fma(0.5 * S.bond_k * dr, dr, bu);
     }
   }
   if (walls && S.wall && !meta_con(m)) {
-    const double dist[2] = {zi - S.wall_lo, S.wall_hi - zi};
-#pragma unroll
-    for (int w = 0; w < 2; ++w) {
-      const double r = dist[w];
-      if (!(r > 0.0)) {
+    if (S.wall_kind == 1) {
+      const double d0 = xi[0] - S.wall_center[0], d1 = xi[1] - S.wall_center[1], d2 = xi[2] - S.wall_center[2];
+      const double r = sqrt(fma(d0, d0, fma(d1, d1, d2 * d2)));
+      const double h = r - S.wall_radius;
+      if (!(h > 0.0)) {
         flag(A.status, kFlagOutOfGrid);
-        continue;
+      } else if (h < S.wall_rc) {
+        const double ih = nr_rcp(h);
+        const double s2 = S.wall_sigma * S.wall_sigma * ih * ih;
+        const double s6 = s2 * s2 * s2;
+        const double fr = 24.0 * S.wall_eps * (2.0 * s6 * s6 - s6) * ih / r;
+        bx = fma(fr, d0, bx); by = fma(fr, d1, by); bz = fma(fr, d2, bz);
+        bu += 4.0 * S.wall_eps * (s6 * s6 - s6 + 0.25);
       }
-      if (r >= S.wall_rc) continue;
-      const double ir = nr_rcp(r);
-      const double s2 = S.wall_sigma * S.wall_sigma * ir * ir;
-      const double s6 = s2 * s2 * s2;
-      const double fr = 24.0 * S.wall_eps * (2.0 * s6 * s6 - s6) * ir;
-      bz += (w == 0) ? fr : -fr;
-      bu += 4.0 * S.wall_eps * (s6 * s6 - s6 + 0.25);
+    } else {
+      const double dist[2] = {xi[2] - S.wall_lo, S.wall_hi - xi[2]};
+#pragma unroll
+      for (int w = 0; w < 2; ++w) {
+        const double r = dist[w];
+        if (!(r > 0.0)) {
+          flag(A.status, kFlagOutOfGrid);
+          continue;
+        }
+        if (r >= S.wall_rc) continue;
+        const double ir = nr_rcp(r);
+        const double s2 = S.wall_sigma * S.wall_sigma * ir * ir;
+        const double s6 = s2 * s2 * s2;
+        const double fr = 24.0 * S.wall_eps * (2.0 * s6 * s6 - s6) * ir;
+        bz += (w == 0) ? fr : -fr;
+        bu += 4.0 * S.wall_eps * (s6 * s6 - s6 + 0.25);
+      }
     }
   }
   fx += (R)bx; fy += (R)by; fz += (R)bz; u += (R)bu;
 }
 
-// One thread per sorted slot: the forces on its particle from the 27
-// neighbour cells. For a particle held on a surface in a system without free
-// particles, a cell whose box lies farther than the tangent slab from the
-// particle's tangent plane cannot hold a neighbour and is skipped. The bucket
-// ranges of one stencil row are loaded together before its candidates.
-// One thread per sorted slot: the forces on its particle from the 27
-// neighbour cells. For a particle held on a surface in a system without free
-// particles, a cell whose box lies farther than the tangent slab from the
-// particle's tangent plane cannot hold a neighbour and is skipped. The bucket
-// ranges of one stencil row are loaded together before its candidates.
 // The cell list as the pair code reads it: slot -> particle, cell and record,
 // bucket -> first slot, cell -> bucket. GlobalCells is the handle's list in
 // global memory; the resident engine keeps one system's list in shared memory.
@@ -845,8 +919,6 @@ template <typename R> struct GlobalCells {
   __device__ __forceinline__ uint32_t bucket(uint32_t cell) const { return bucket_of(cell, hashed, log_t); }
 };
 
-// Force and energy on the particle in slot s from the 27 neighbour cells (and
-// its bonds and walls); returns the particle's id.
 template <typename R, bool BONDS, bool WALLS, bool EXCL, class Cells>
 __device__ __forceinline__ uint32_t pair_slot(const DevArrays& A, const Cells& C, const PairTab<R>& tab, uint32_t s,
                                               R& fx, R& fy, R& fz, R& u) {
@@ -954,6 +1026,22 @@ __global__ void __launch_bounds__(256) k_pair_row(DevArrays A) {
   R fx, fy, fz, u;
   const uint32_t tag = pair_slot<R, BONDS, WALLS, EXCL>(A, GlobalCells<R>(A), tab, s, fx, fy, fz, u);
   store_f<R>(A.f, tag, fx, fy, fz, u);
+}
+
+// Bend-angle forces (and energy shares) added to the pair kernel's output.
+template <typename R>
+__global__ void k_bend(DevArrays A) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  const SysDev& S = A.sys[meta_sys(A.meta[i])];
+  if (!has_bends(S)) return;
+  double f[3], v;
+  bend_on(A, S, i, f, v);
+  using V = typename V4<R>::T;
+  V* fv = reinterpret_cast<V*>(A.f);
+  V q = fv[i];
+  q.x += (R)f[0]; q.y += (R)f[1]; q.z += (R)f[2]; q.w += (R)v;
+  fv[i] = q;
 }
 
 // L lanes of one warp share one particle: lane q walks the stencil cells
@@ -1728,6 +1816,15 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 2) k_resident(DevArrays A
       }
       __syncthreads();
       for (uint32_t e = tid; e <= T; e += bd) s_start[e] = 0u;  // the starts are not read again this step
+      if (has_bends(S)) {
+        for (uint32_t li = tid; li < n; li += bd) {
+          double f[3], v;
+          bend_on(A, S, first + li, f, v);
+          s_fx[li] += (R)f[0];
+          s_fy[li] += (R)f[1];
+          s_fz[li] += (R)f[2];
+        }
+      }
       __syncthreads();
       const unsigned long long k = k0 + (unsigned long long)j;
       const int mode = j == 0 ? mode0 : 1;
@@ -2158,6 +2255,14 @@ cudaError_t launch_pair(const DevArrays& A, int precision, int has_pairs, int bo
   } else {
     pair_dispatch<float>(A, bonds, walls, excl, A.pair_lanes, st);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bend(const DevArrays& A, int precision, cudaStream_t st) {
+  if (A.n == 0) return cudaSuccess;
+  const int b = block_for(A.n);
+  if (precision == 0) k_bend<double><<<grid_for(A.n, b), b, 0, st>>>(A);
+  else k_bend<float><<<grid_for(A.n, b), b, 0, st>>>(A);
   return cudaGetLastError();
 }
 

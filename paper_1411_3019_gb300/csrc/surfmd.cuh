@@ -70,6 +70,10 @@ struct SysDev {
   int32_t wall;
   int32_t pad1;
   double wall_lo, wall_hi, wall_eps, wall_sigma, wall_rc;
+  // capsid-model terms: bend angles, type-dependent bond lengths, spherical wall
+  double angle_k, angle_theta0;
+  int32_t bond_mix, wall_kind;
+  double wall_radius, wall_center[3];
   // noise key, particle range
   uint32_t seed_lo, replica;
   int64_t first, n;
@@ -89,6 +93,7 @@ struct TypeTable {
   float shift_f[kMaxTypes][kMaxTypes];
   float lin_f[kMaxTypes][kMaxTypes];
   float rc_f[kMaxTypes][kMaxTypes];
+  double bond_r0_mix[kMaxTypes][kMaxTypes];  // 2^(1/6) sigma_ij / 2
   double mass[kMaxTypes], inv_mass[kMaxTypes], sqrt_mass[kMaxTypes];
   float sqrt_mass_f[kMaxTypes];
 };

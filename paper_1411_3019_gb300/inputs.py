@@ -497,3 +497,50 @@ def nve_systems(pair_form: int, n: int = 500, phi: float = 0.3, seed: int = 1, p
                 box=box)[0]
         out.append(_system(name, surf, prm, x, maxwell(n, 1.0, 1.0, g)))
     return out
+
+
+def capsid_systems(nsys: int = 1, ncone: int = 60, sigma3: float = 1.75, seed: int = 1, precision: str = "mixed",
+                   dt: float = 0.002, tol: float = 1e-10, dmin: float = 1.8, phi_base: float = 0.45):
+    """Capsomere (cone) self-assembly on a spherical template, the capsid model
+    of SI S3.2: ncone cones of four beads (types 0..3 with sizes sigma_i =
+    1, 1.35, sigma3, 1), additive mixing sigma_ij = (sigma_i + sigma_j)/2,
+    well depth 4 kT, cutoff 4 sigma_0 between like beads of types 1 and 2
+    (the SI's types 2 and 3) and 2^(1/6) sigma_ij (purely repulsive) for
+    every other pair, Lennard-Jones only between different cones; masses
+    proportional to the bead volume; bonds k = 50 kT/sigma_0^2 with rest
+    lengths 2^(1/6)(sigma_i + sigma_j)/4; bend angles k_a = 250 kT/rad^2,
+    theta0 = pi; the first bead of each cone held on the sphere, the others
+    free; a repulsive spherical wall (eps_w = sigma_w = 1) at R - 1 keeps
+    free beads out of the sphere. The sphere radius follows from the base
+    beads' area fraction phi_base; cones start straight and radial with
+    their bases placed by random sequential addition at distance >= dmin.
+    Returns nsys independently seeded systems (one batch)."""
+    sig = np.array([1.0, 1.35, sigma3, 1.0])
+    nt = 4
+    sij = 0.5 * (sig[:, None] + sig[None, :])
+    eps = np.full((nt, nt), 4.0)
+    rc = 2 ** (1 / 6) * sij
+    rc[1, 1] = 4.0
+    rc[2, 2] = 4.0
+    r0 = 2 ** (1 / 6) * sij / 2
+    R = math.sqrt(ncone * math.pi * (dmin / 2) ** 2 / phi_base / (4 * math.pi))
+    ext = R + r0[0, 1] + r0[1, 2] + r0[2, 3] + 6.0
+    out = []
+    for s in range(nsys):
+        prm = wca_params(ntypes=nt, precision=precision, dt=dt, rattle_tol=tol, seed=seed, replica=s,
+                         mass=list(sig ** 3), beads_per_mol=4, bond_k=50.0, bond_r0=0.0, bond_r0_mix=1,
+                         angle_k=250.0, angle_theta0=math.pi, exclude_intramol=1, wall_enable=1, wall_kind=1,
+                         wall_radius=R - 1.0, wall_center=(0.0, 0.0, 0.0), wall_eps=1.0, wall_sigma=1.0,
+                         box_lo=(-ext, -ext, -ext), box_hi=(ext, ext, ext))
+        prm["sigma"], prm["eps"], prm["rcut"] = sij.copy(), eps.copy(), rc.copy()
+        g = rng(seed, 1000 + s)
+        surf = {"kind": "sphere", "center": (0.0, 0.0, 0.0), "p": (R, 0.0, 0.0, 0.0)}
+        base = rsa(lambda k, m: sample_surface(surf, m, g), [ncone], dmin, g)[0]
+        u = base / np.linalg.norm(base, axis=1, keepdims=True)
+        radii = R + np.concatenate([[0.0], np.cumsum([r0[0, 1], r0[1, 2], r0[2, 3]])])
+        x = (u[:, None, :] * radii[None, :, None]).reshape(-1, 3)
+        type_ = np.tile(np.arange(4, dtype=np.int32), ncone)
+        con = (type_ == 0).astype(np.uint8)
+        out.append(_system("capsid", surf, prm, x, maxwell(x.shape[0], 1.0, np.asarray(prm["mass"])[type_], g),
+                           type_=type_, constrained=con))
+    return out

@@ -93,7 +93,7 @@ def oracle_forces_at(systems, x):
             bpm = s["params"].get("beads_per_mol", 0)
             mol = (np.arange(s["n"]) // bpm if bpm > 1 else np.arange(s["n"])).astype(np.int32)
         f, _ = oracle.pair_forces(s["params"], xs, s["type"], mol)
-        fb, _, _ = oracle.bond_wall_forces(s["params"], xs, s["constrained"])
+        fb, _, _ = oracle.bond_wall_forces(s["params"], xs, s["constrained"], s["type"])
         out.append(f + fb)
         off += s["n"]
     return np.concatenate(out) if out else np.zeros((0, 3))
