@@ -31,7 +31,7 @@ _lib = None
 
 MAXT = 8
 SURF_KINDS = {"none": 0, "plane": 1, "sphere": 2, "ellipsoid": 3, "torus": 4,
-              "gaussian_bump": 5, "cylinder": 6}
+              "gaussian_bump": 5, "cylinder": 6, "xy2d": 7}
 
 
 def build(force: bool = False) -> str:
@@ -283,7 +283,7 @@ def _arrays(x, type_, mol, constrained, surf, prm):
         mo = np.ascontiguousarray(mol, np.int32)
     if constrained is None:
         kind = (surf or {}).get("kind", "none")
-        con = np.full(n, 0 if kind == "none" else 1, np.uint8)
+        con = np.full(n, 0 if kind in ("none", "xy2d") else 1, np.uint8)
     else:
         con = np.ascontiguousarray(constrained, np.uint8)
     return x, t, mo, con

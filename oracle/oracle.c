@@ -60,7 +60,9 @@
 /* ------------------------------------------------------------------------ */
 typedef struct {
   int32_t kind; /* 0 none, 1 plane, 2 sphere, 3 ellipsoid, 4 torus,
-                   5 gaussian bump, 6 cylinder */
+                   5 gaussian bump, 6 cylinder, 7 unconstrained 2D plane
+                   z = c[2] (no z updates; the baseline of Section 3.1's
+                   performance comparison) */
   int32_t pad;
   double c[3];
   double p[4];
@@ -782,11 +784,16 @@ int orc_set_state(orc_sys* s, const double* x, const double* v, const int32_t* t
     if (mol) s->mol[i] = mol[i];
     else s->mol[i] = (int32_t)(s->P.beads_per_mol > 1 ? i / s->P.beads_per_mol : i);
     s->con[i] = con ? con[i] : (uint8_t)(s->S.kind != 0);
+    if (s->S.kind == 7) s->con[i] = 0; /* 2D: no constraint, no z motion */
   }
   for (int64_t i = 0; i < n; ++i) {
     double m = mass_of(s, i);
     double vi[3] = {v ? v[3 * i] : 0.0, v ? v[3 * i + 1] : 0.0, v ? v[3 * i + 2] : 0.0};
     for (int k = 0; k < 3; ++k) s->x[3 * i + k] = x[3 * i + k];
+    if (s->S.kind == 7) {
+      if (!(fabs(x[3 * i + 2] - s->S.c[2]) < 1e-6)) return 1;
+      vi[2] = 0.0;
+    }
     if (s->con[i]) {
       double nn[3];
       double g = orc_surface_g(&s->S, &s->P, &x[3 * i], nn);
@@ -840,7 +847,9 @@ int64_t orc_step(orc_sys* s, int64_t nsteps) {
           s->ph[3 * i + k] = phn[k];
         }
       } else {
-        for (int k = 0; k < 3; ++k) {
+        /* free particle; in the 2D plane the z updates are not evaluated */
+        int dims = s->S.kind == 7 ? 2 : 3;
+        for (int k = 0; k < dims; ++k) {
           s->ph[3 * i + k] = pi[k] + 0.5 * dt * Fi[k];
           xi[k] += dt / m * s->ph[3 * i + k];
         }
@@ -871,7 +880,8 @@ int64_t orc_step(orc_sys* s, int64_t nsteps) {
         }
         for (int k = 0; k < 3; ++k) s->p[3 * i + k] = pn[k];
       } else {
-        for (int k = 0; k < 3; ++k) s->p[3 * i + k] = s->ph[3 * i + k] + 0.5 * dt * s->F[3 * i + k];
+        int dims = s->S.kind == 7 ? 2 : 3;
+        for (int k = 0; k < dims; ++k) s->p[3 * i + k] = s->ph[3 * i + k] + 0.5 * dt * s->F[3 * i + k];
       }
     }
   }
@@ -934,7 +944,7 @@ void orc_observables(const orc_sys* s, double out[6]) {
     U += s->u[i];
     msd += d2;
     rr += dot;
-    ndof += s->con[i] ? 2 : 3;
+    ndof += (s->con[i] || s->S.kind == 7) ? 2 : 3;
   }
   out[0] = K;
   out[1] = U;

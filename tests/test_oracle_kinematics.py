@@ -93,3 +93,28 @@ def test_noise_counter_convention(orc):
     assert st["step"] == k0 + 1
     np.testing.assert_allclose(st["x"][0], dt / m * ph, rtol=1e-14, atol=1e-16)
     np.testing.assert_allclose(st["v"][0] * m, ph + 0.5 * dt * F1, rtol=1e-14, atol=1e-15)
+
+
+def test_unconstrained_2d_plane_is_the_xy_projection_of_free_motion(orc):
+    """The 2D baseline of the performance comparison (Section 3.1: particles in
+    a plane with the z updates not evaluated): for non-interacting particles
+    under Langevin noise, x and y follow exactly the x and y of free 3D
+    motion with the same noise, z never moves and p_z stays 0."""
+    g = np.random.default_rng(17)
+    n = 40
+    prm = I.noninteracting(I.wca_params(dt=0.002, gamma=1.0, kT=1.0, seed=9))
+    x = np.column_stack([g.uniform(-5, 5, (n, 2)), np.full(n, 0.7)])
+    v = g.normal(0, 1, (n, 3))
+    flat = orc.System({"kind": "xy2d", "center": (0.0, 0.0, 0.7), "p": (0, 0, 0, 0)}, prm, n)
+    flat.set_state(x, v)
+    free = orc.System(None, prm, n)
+    free.set_state(x, v)
+    flat.step(40)
+    free.step(40)
+    a, b = flat.state(), free.state()
+    assert np.array_equal(a["x"][:, :2], b["x"][:, :2])
+    assert np.array_equal(a["p_half"][:, :2], b["p_half"][:, :2])
+    assert np.all(a["x"][:, 2] == 0.7)
+    assert np.all(a["v"][:, 2] == 0.0) and np.all(a["p_half"][:, 2] == 0.0)
+    assert not np.all(b["x"][:, 2] == 0.7)
+    assert flat.observables()["ndof"] == 2 * n
