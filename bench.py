@@ -40,7 +40,7 @@ METRIC = ("particle-steps/sec on 1 GB300 (FP32-force/FP64-RATTLE vs plain FP64) 
 UNIT = "particle-steps/s"
 L2_FLUSH_BYTES = 256 << 20  # larger than the 129 MB L2
 WORKLOADS = ("ellipsoid_torus", "plain_sphere", "replicas", "bead_molecules", "bump_crowders", "nve_surfaces",
-             "capsids")
+             "capsids", "sphere_vs_2d")
 # float64 pipe of one GB300: 152 SMs x 2 float64 operations per SM per clock
 FP64_OPS_PER_SM_CLK = 2
 SMS = 152
@@ -92,6 +92,8 @@ def workload(name: str, rank: int, precision: str, nrep: int = 4096, pair_form: 
         return inputs.c5_bead_molecules(seed=seed, precision=precision)
     if name == "bump_crowders":
         return inputs.c3_bump_crowders(seed=seed, precision=precision)
+    if name == "sphere_vs_2d":
+        return inputs.sphere_and_plane2d(n=250_000, seed=seed, precision=precision)[0]
     if name == "capsids":
         return inputs.capsid_systems(nsys=max(1, nrep // 4), ncone=60, seed=seed, precision=precision)
     if name == "nve_surfaces":
@@ -107,6 +109,9 @@ def workload_config(name, systems, precision):
         desc = (f"ellipsoid+torus: {systems[0]['n']} WCA on ellipsoid semi-axes "
                 f"({ell[0]:.1f},{ell[1]:.1f},{ell[2]:.1f}) at phi=0.4 + {systems[1]['n']} on torus "
                 f"R={tor[0]:g} r={tor[1]:g} (separate system); kT=gamma=1, dt=0.002, tol=1e-10")
+    elif name == "sphere_vs_2d":
+        desc = (f"sphere_vs_2d: {n} WCA on a sphere R={systems[0]['surface']['p'][0]:.1f} at phi=0.4 (RATTLE), "
+                f"against the same n in a periodic 2D plane at the same density (unconstrained_2d)")
     elif name == "nve_surfaces":
         desc = (f"nve_surfaces: {len(systems)} x {systems[0]['n']} LJ (rc=2.5) on "
                 f"{'/'.join(s['name'] for s in systems)} at phi=0.3, gamma=0, dt=0.0005, "
@@ -460,6 +465,28 @@ def main(argv=None):
                  "mixed_speedup": ms64 / ms}
         sim64.close()
 
+    # the performance comparison of Section 3.1: the same number of particles
+    # at the same density in a periodic 2D plane with no constraint
+    flat = None
+    if args.workload == "sphere_vs_2d":
+        from paper_1411_3019_gb300 import inputs
+
+        plane = inputs.sphere_and_plane2d(n=250_000, seed=rank_seed(rank), precision=precision)[1]
+        simp = md.Simulation(plane, stream=stream)
+        simp.set_state()
+        simp.step(args.warmup)
+        simp.sync()
+        if args.engine == "auto" and not args.no_tune:
+            with torch.cuda.stream(stream):
+                tune.autotune(simp.h, trials=3, flush=lambda: flush.add_(1.0))
+        barrier()
+        dp, _ = timed_steps(simp, args.steps)
+        simp.close()
+        msp, _ = reduce_over_ranks(dist, sum(dp) / len(dp), 0.0, "cuda")
+        flat = {"value": total_particles / (msp / 1e3), "unit": UNIT, "ms_per_step": msp,
+                "workload": "250000 WCA in a periodic 2D plane (z updates not evaluated) at the sphere's "
+                            "area fraction 0.4", "rattle_over_2d": ms / msp}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(systems, args.cpu_seconds)
@@ -478,7 +505,7 @@ def main(argv=None):
             "l2_resident": {"value": total_particles / (ms_resident / 1e3), "ms_per_step": ms_resident},
             "wall_s_timed_region": t_wall,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": launches, "plain_fp64": plain,
+            "gpu_launches": launches, "plain_fp64": plain, "unconstrained_2d": flat,
             "tuned": {"options": tuned["options"], "trials": tuned.get("trials")},
         }
         print(json.dumps(line), flush=True)

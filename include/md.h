@@ -84,6 +84,10 @@ extern "C" {
  *              taken with the minimum image in periodic x, y
  *   CYLINDER   g = sum_{d != axis} (x_d-c_d)^2 - R^2, p = (R, axis 0|1|2)
  *              (SI S3.1 with the axis coefficient 0 and the others 1)
+ *   XY2D       no constraint: particles move in the plane z = c_z with the
+ *              z components of force, noise and momentum dropped (the
+ *              unconstrained 2D baseline of Section 3.1's performance
+ *              comparison); needs periodic x and y; 2 degrees of freedom
  * The Newton stopping test works on |g| / |grad g|, a length, so one
  * tolerance means the same thing on every surface. */
 typedef enum {
@@ -93,7 +97,8 @@ typedef enum {
   MD_SURF_ELLIPSOID = 3,
   MD_SURF_TORUS = 4,
   MD_SURF_GAUSSIAN_BUMP = 5,
-  MD_SURF_CYLINDER = 6
+  MD_SURF_CYLINDER = 6,
+  MD_SURF_XY2D = 7
 } md_surface_kind;
 
 typedef struct md_surface {

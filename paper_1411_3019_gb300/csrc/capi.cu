@@ -128,7 +128,7 @@ int check_system(const md_surface& s, const md_params& p, SysDev& S, std::string
   for (int a = 0; a < p.ntypes; ++a)
     for (int b = 0; b < p.ntypes; ++b)
       if (p.rcut[a][b] > 0.0 && !(p.sigma[a][b] > 0.0)) return bad("sigma must be > 0 where rcut > 0");
-  if (s.kind < MD_SURF_NONE || s.kind > MD_SURF_CYLINDER) return bad("unknown surface kind");
+  if (s.kind < MD_SURF_NONE || s.kind > MD_SURF_XY2D) return bad("unknown surface kind");
   if (s.reserved != 0) return bad("reserved fields must be 0");
   if (p.pair_form != MD_PAIR_TRUNC_SHIFT && p.pair_form != MD_PAIR_LINEAR_SMOOTH) return bad("unknown pair_form");
   for (int d = 0; d < 3; ++d)
@@ -169,6 +169,10 @@ int check_system(const md_surface& s, const md_params& p, SysDev& S, std::string
     case MD_SURF_GAUSSIAN_BUMP:
       if (!(s.p[1] > 0.0)) return bad("bump width must be > 0");
       if (!p.periodic[0] || !p.periodic[1]) return bad("the bump needs periodic x and y");
+      break;
+    case MD_SURF_XY2D:
+      if (!p.periodic[0] || !p.periodic[1] || p.periodic[2])
+        return bad("the 2D plane needs periodic x and y and an open z axis");
       break;
     case MD_SURF_CYLINDER:
       if (!(s.p[0] > 0.0)) return bad("cylinder radius must be > 0");
@@ -244,6 +248,10 @@ bool surface_extent(const md_surface& s, int d, double& lo, double& hi) {
       lo = c - e; hi = c + e;
       return true;
     }
+    case MD_SURF_XY2D:
+      if (d < 2) return false;
+      lo = c; hi = c;
+      return true;
     case MD_SURF_CYLINDER:
       if (d == (int)s.p[1]) return false;
       lo = c - s.p[0]; hi = c + s.p[0];
@@ -601,6 +609,10 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
         S.nc[d] = 1;
         S.cs[d] = 1.0;
         S.grid_lo[d] = 0.0;
+      } else if (surfs[s].kind == MD_SURF_XY2D && d == 2) {  // one layer of cells about z = c_z
+        S.nc[d] = 1;
+        S.cs[d] = rc_eff;
+        S.grid_lo[d] = surfs[s].center[2] - 0.5 * rc_eff;
       } else if (p.periodic[d]) {
         const double L = p.box_hi[d] - p.box_lo[d];
         const int nc = (int)std::floor(L / rc_eff);

@@ -284,7 +284,8 @@ __global__ void k_build_meta(DevArrays A, const int64_t* __restrict__ first, int
     flag(A.status, kFlagOffSurface);
     t = 0;
   }
-  const uint32_t c = con ? (con[i] ? 1u : 0u) : (S.kind != kNone ? 1u : 0u);
+  // the unconstrained 2D plane holds no particle by a constraint
+  const uint32_t c = S.kind == kXY2D ? 0u : (con ? (con[i] ? 1u : 0u) : (S.kind != kNone ? 1u : 0u));
   A.meta[i] = meta_pack((uint32_t)t, (S.kind != kNone) ? c : 0u, (uint32_t)lo);
   if (S.kind != kNone && !c) atomicAdd(&A.sys_free[lo], 1);
   if (A.mol) {
@@ -302,6 +303,10 @@ __global__ void k_set_state(DevArrays A, const double* __restrict__ xa, const do
   const double x = xa[3 * i], y = xa[3 * i + 1], z = xa[3 * i + 2];
   double vx = va ? va[3 * i] : 0.0, vy = va ? va[3 * i + 1] : 0.0, vz = va ? va[3 * i + 2] : 0.0;
   if (!finite3(x, y, z) || !finite3(vx, vy, vz)) flag(A.status, kFlagOffSurface);
+  if (S.kind == kXY2D) {  // in the plane z = c_z, no motion along z
+    if (!(fabs(z - S.c[2]) < 1e-6)) flag(A.status, kFlagOffSurface);
+    vz = 0.0;
+  }
   if (meta_con(m)) {
     double nx, ny, nz;
     const double g = surf_eval(S, x, y, z, nx, ny, nz);
@@ -1367,7 +1372,7 @@ __device__ __forceinline__ void integrate_particle_fp64(const DevArrays& A, int6
   const double x = A.x[i], y = A.x[n + i], z = A.x[2 * n + i];
   double px = A.ph[i], py = A.ph[n + i], pz = A.ph[2 * n + i];
   const Force3<double> Fr = combine<double>(S, T, ty, (uint32_t)(i - S.first), k, mode, fr_in, px, py, pz);
-  const double Fx = Fr.x, Fy = Fr.y, Fz = Fr.z;
+  const double Fx = Fr.x, Fy = Fr.y, Fz = S.kind == kXY2D ? 0.0 : Fr.z;  // 2D plane: no z update
   const double h = S.half_dt;
   const bool con = meta_con(m);
   double n0x = 0.0, n0y = 0.0, n0z = 0.0, nn = 1.0, inv_nn = 0.0;
@@ -1543,7 +1548,8 @@ __device__ __forceinline__ void integrate_particle_mixed(const DevArrays& A, int
   const double x = A.x[i], y = A.x[n + i], z = A.x[2 * n + i];
   const double px = A.ph[i], py = A.ph[n + i], pz = A.ph[2 * n + i];
   const float pxf = d2f_rn(px), pyf = d2f_rn(py), pzf = d2f_rn(pz);
-  const Force3<float> F = combine<float>(S, A.types, ty, (uint32_t)(i - S.first), k, mode, fr_in, pxf, pyf, pzf);
+  Force3<float> F = combine<float>(S, A.types, ty, (uint32_t)(i - S.first), k, mode, fr_in, pxf, pyf, pzf);
+  if (S.kind == kXY2D) F.z = 0.f;  // 2D plane: no z update
   const double kick = mode ? S.dt : S.half_dt;
   double qx = fma(kick, f2d(F.x), px), qy = fma(kick, f2d(F.y), py), qz = fma(kick, f2d(F.z), pz);
   const double dtm = S.dtm[ty];
@@ -1961,8 +1967,9 @@ __global__ void k_finish(DevArrays A) {
   const uint32_t ty = meta_type(m);
   const double x = A.x[i], y = A.x[n + i], z = A.x[2 * n + i];
   double px = A.ph[i], py = A.ph[n + i], pz = A.ph[2 * n + i];
-  const Force3<R> Fr = combine<R>(S, A.types, ty, (uint32_t)(i - S.first), k, 1, load_f3<R>(A.f, i), (R)px, (R)py,
-                                  (R)pz);
+  Force3<R> Fr = combine<R>(S, A.types, ty, (uint32_t)(i - S.first), k, 1, load_f3<R>(A.f, i), (R)px, (R)py,
+                            (R)pz);
+  if (S.kind == kXY2D) Fr.z = (R)0;
   const bool con = meta_con(m);
   double nx = 0.0, ny = 0.0, nz = 0.0, inv_nn = 0.0;
   if (con) {
@@ -2082,7 +2089,7 @@ __global__ void k_observables(DevArrays A, double* obs) {
               (A.xref[2 * n + i] - S.c[2]) * (z - S.c[2])) / R2;
     }
     const bool con = meta_con(m);
-    v[4] = con ? 2.0 : 3.0;
+    v[4] = (con || S.kind == kXY2D) ? 2.0 : 3.0;
     if (con) {
       double nx, ny, nz;
       const double g = surf_eval(S, x, y, z, nx, ny, nz);

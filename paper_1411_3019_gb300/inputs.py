@@ -137,6 +137,10 @@ def sample_surface(surf: dict, n: int, g: np.random.Generator, box=None) -> np.n
             z = c[2] + e[keep]
             out = np.vstack([out, np.column_stack([xy[keep], z])])
         return out[:n]
+    if kind == "xy2d":
+        lo, hi = np.asarray(box[0], float), np.asarray(box[1], float)
+        xy = lo[:2] + g.random((n, 2)) * (hi - lo)[:2]
+        return np.column_stack([xy, np.full(n, c[2])])
     if kind == "plane":
         lo, hi = np.asarray(box[0], float), np.asarray(box[1], float)
         nrm = np.asarray(p[:3], float)
@@ -544,3 +548,29 @@ def capsid_systems(nsys: int = 1, ncone: int = 60, sigma3: float = 1.75, seed: i
         out.append(_system("capsid", surf, prm, x, maxwell(x.shape[0], 1.0, np.asarray(prm["mass"])[type_], g),
                            type_=type_, constrained=con))
     return out
+
+
+def sphere_and_plane2d(n: int = 1_000_000, phi: float = 0.4, seed: int = 1, precision: str = "mixed",
+                       dt: float = 0.002, tol: float = 1e-10, dmin: float = 1.0):
+    """The performance comparison of Section 3.1 at equal density: n WCA
+    particles held on a sphere by RATTLE, and n WCA particles in a periodic
+    2D plane of the same area with no constraint (surface kind xy2d: the z
+    updates are not evaluated), both at area fraction phi, kT = gamma = 1.
+    Returns (sphere systems, plane systems), one system each."""
+    area = n * A_P / phi
+    R = math.sqrt(area / (4 * math.pi))
+    g = rng(seed, 300)
+    prm = wca_params(precision=precision, dt=dt, rattle_tol=tol, seed=seed)
+    surf = {"kind": "sphere", "center": (0.0, 0.0, 0.0), "p": (R, 0, 0, 0)}
+    x = rsa(lambda k, m: sample_surface(surf, m, g), [n], dmin, g)[0]
+    sphere = [_system("sphere", surf, prm, x, maxwell(n, 1.0, 1.0, g))]
+    L = math.sqrt(area)
+    prm2 = wca_params(precision=precision, dt=dt, rattle_tol=tol, seed=seed, box_lo=(-L / 2, -L / 2, -1.0),
+                      box_hi=(L / 2, L / 2, 1.0), periodic=(1, 1, 0))
+    flat = {"kind": "xy2d", "center": (0.0, 0.0, 0.0), "p": (0, 0, 0, 0)}
+    box = (prm2["box_lo"], prm2["box_hi"])
+    x2 = rsa(lambda k, m: sample_surface(flat, m, g, box=box), [n], dmin, g, periodic=prm2["periodic"], box=box)[0]
+    v2 = maxwell(n, 1.0, 1.0, g)
+    v2[:, 2] = 0.0
+    plane = [_system("plane2d", flat, prm2, x2, v2, constrained=np.zeros(n, np.uint8))]
+    return sphere, plane
