@@ -1,0 +1,75 @@
+"""Diffusion laws of SI Section S1.3 on the GPU with many non-interacting
+particles (Langevin, gamma = kT = m = 1, so D = 1 and tau = 1), inertial
+forms of the closed expressions:
+
+* cylinder of radius R: MSD = s2 + 2R^2 (1 - exp(-s2 / 2R^2)) with
+  s2(t) = 2D[t - tau(1 - e^{-t/tau})] (the SI's 2Dt + 2R^2(1 - e^{-Dt/R^2})
+  for t >> tau);
+* sphere of radius R: <r(0).r(t)>/R^2 = exp(-2 D t'/R^2),
+  t' = t - tau(1 - e^{-t/tau}), and the diffusion coefficient fitted from it
+  within 2 % of kT/(m gamma);
+* plane: MSD = 4D[t - tau(1 - e^{-t/tau})].
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1411_3019_gb300 import inputs as I
+from paper_1411_3019_gb300 import md
+
+pytestmark = pytest.mark.gpu
+
+D, TAU = 1.0, 1.0
+
+
+def _free(surf, n, box=None, dt=0.002, seed=3, precision="mixed"):
+    prm = I.noninteracting(I.wca_params(dt=dt, seed=seed, precision=precision, rattle_tol=1e-10))
+    g = np.random.default_rng(seed)
+    x = I.sample_surface(surf, n, g, box=box)
+    return [I._system("free", surf, prm, x, I.maxwell(n, 1.0, 1.0, g))]
+
+
+def _sweep(systems, times, dt):
+    sim = md.Simulation(systems)
+    sim.set_state()
+    out, t = [], 0.0
+    for tc in times:
+        k = int(round((tc - t) / dt))
+        sim.step(k)
+        t += k * dt
+        out.append((t, sim.observables()[0]))
+    sim.close()
+    return out
+
+
+def test_cylinder_msd_closed_form():
+    R = 3.0
+    surf = {"kind": "cylinder", "center": (0.0, 0.0, 0.0), "p": (R, 2.0, 0.0, 0.0)}
+    for t, o in _sweep(_free(surf, 40_000, box=((-4, -4, -100), (4, 4, 100))), (2.0, 8.0, 20.0, 40.0), 0.002):
+        s2 = 2 * D * (t - TAU * (1 - math.exp(-t / TAU)))
+        theory = s2 + 2 * R ** 2 * (1 - math.exp(-s2 / (2 * R ** 2)))
+        assert abs(o["msd"] / theory - 1) < 0.03, (t, o["msd"], theory)
+
+
+def test_sphere_correlation_and_fitted_diffusion_coefficient():
+    R = 10.0
+    surf = {"kind": "sphere", "center": (0.0, 0.0, 0.0), "p": (R, 0.0, 0.0, 0.0)}
+    ts, cs = [], []
+    for t, o in _sweep(_free(surf, 40_000), (10.0, 25.0, 50.0, 80.0), 0.002):
+        tp = t - TAU * (1 - math.exp(-t / TAU))
+        assert abs(o["r0_dot_rt"] - math.exp(-2 * D * tp / R ** 2)) < 0.01, (t, o["r0_dot_rt"])
+        ts.append(tp)
+        cs.append(o["r0_dot_rt"])
+    # least squares of ln c = -2 D t' / R^2 through the origin
+    ts, lc = np.array(ts), np.log(np.array(cs))
+    d_fit = -(ts @ lc) / (ts @ ts) * R ** 2 / 2
+    assert abs(d_fit / D - 1) < 0.02, d_fit
+
+
+def test_plane_msd():
+    surf = {"kind": "plane", "center": (0.0, 0.0, 0.0), "p": (0.0, 0.0, 1.0, 0.0)}
+    systems = _free(surf, 40_000, box=((-100, -100, 0), (100, 100, 0)))
+    for t, o in _sweep(systems, (1.0, 5.0, 20.0), 0.002):
+        theory = 4 * D * (t - TAU * (1 - math.exp(-t / TAU)))
+        assert abs(o["msd"] / theory - 1) < 0.03, (t, o["msd"], theory)

@@ -14,6 +14,11 @@ the mathematics fix:
   D = kT tau / m;
 * on a sphere <r0.rt>/R^2 = exp(-2 D t' / R^2) (SI Section S1.3), with the
   same inertial shift t' = t - tau(1 - e^{-t/tau});
+* on a cylinder of radius R the MSD is 2Dt + 2R^2 (1 - e^{-Dt/R^2}) (SI
+  Section S1.3); with inertia the arc-length displacement is Gaussian with
+  variance s2(t) = 2D[t - tau(1 - e^{-t/tau})] (the tangential velocity is an
+  Ornstein-Uhlenbeck process), so MSD = s2 + 2R^2 (1 - e^{-s2/(2R^2)}),
+  which reduces to the SI's form for t >> tau;
 * the temperature 2K/N_dof with 2 degrees of freedom per constrained
   particle equals the set kT (Section 3.1).
 """
@@ -150,6 +155,32 @@ def test_sphere_correlation_decays_as_exp_minus_2Dt_over_R2(orc):
         assert abs(c - theory) < 0.04, (t, c, theory)
         msd = s.observables()["msd"]
         assert abs(msd - 2 * R ** 2 * (1 - c)) < 1e-8 * R ** 2
+
+
+def cylinder_msd(t, D, tau, R):
+    s2 = 2 * D * (t - tau * (1 - math.exp(-t / tau)))
+    return s2 + 2 * R ** 2 * (1 - math.exp(-s2 / (2 * R ** 2)))
+
+
+def test_cylinder_msd_follows_the_closed_form(orc):
+    m, kT, gamma, dt = 1.0, 1.0, 1.0, 0.01
+    D, tau, R = kT / (m * gamma), 1.0 / gamma, 2.0
+    surf = {"kind": "cylinder", "center": (0.0, 0.0, 0.0), "p": (R, 2.0, 0.0, 0.0)}
+    n = 4000
+    s, _ = _free_system(orc, n, m, kT, gamma, dt, surface=surf, box=((-3, -3, -50), (3, 3, 50)))
+    t = 0.0
+    for t_check in (1.0, 4.0, 10.0):
+        k = int(round((t_check - t) / dt))
+        s.step(k)
+        t += k * dt
+        msd = s.observables()["msd"]
+        theory = cylinder_msd(t, D, tau, R)
+        assert abs(msd / theory - 1) < 0.06, (t, msd, theory)
+    # the circumferential part saturates at 2R^2: the late slope is that of the axis alone, 2D
+    m2 = s.observables()["msd"]
+    s.step(int(round(10.0 / dt)))
+    slope = (s.observables()["msd"] - m2) / 10.0
+    assert abs(slope / (2 * D) - 1) < 0.25, slope
 
 
 def test_temperature_with_two_dof_per_constrained_particle(orc):
