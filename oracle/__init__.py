@@ -31,7 +31,7 @@ _lib = None
 
 MAXT = 8
 SURF_KINDS = {"none": 0, "plane": 1, "sphere": 2, "ellipsoid": 3, "torus": 4,
-              "gaussian_bump": 5, "cylinder": 6, "xy2d": 7}
+              "gaussian_bump": 5, "cylinder": 6, "xy2d": 7, "thylakoid": 8}
 
 
 def build(force: bool = False) -> str:

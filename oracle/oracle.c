@@ -42,6 +42,23 @@
  *       (x_i - x_j).(x_j - x_k) / (...) would be 0 for a straight chain. It
  *       is evaluated as atan2(|u x w|, u.w), equal to the arccos and well
  *       conditioned near 0 and pi.
+ *   R9  The thylakoid surface of SI S3.1 is assembled from its pieces as
+ *       follows (p = (R_b, L_x, R_c, L_b), centre c, z periodic): a bridge
+ *       cylinder of radius R_b along x through (c_y, c_z) for
+ *       |x - c_x| <= L_b/2; at each end a connector (SI form, tube radius
+ *       R = R_c) joining it tangentially to the face plane of a block at
+ *       x = c_x -/+ (L_b/2 + R_c); each block a tube along z whose cross
+ *       section is a square of side L_x + 2 R_c with its corners rounded by
+ *       quarter cylinders of radius R_c (four planes L_x x L_z and four
+ *       quarter cylinders, as the SI's area sum counts). The piece of a
+ *       particle is chosen from the position where its half step starts:
+ *       between the block faces and within R_b + R_c of the bridge axis the
+ *       bridge or the nearer connector (by x against the bridge ends);
+ *       otherwise the block's rounded square: a corner cylinder where the
+ *       point lies beyond the inner square in both x and y, else the plane
+ *       of the side it lies beyond (the nearest side when inside), except
+ *       that the face plane's hole (within R_b + R_c of the axis) belongs to
+ *       the connector. The pieces meet with continuous tangent planes.
  *   R7  The linearly smoothed Lennard-Jones potential is printed with
  *       "+ (r - r_c) phi'(r_c)", whose force does not vanish at r_c (it
  *       doubles the jump); the text states that energy and force are both
@@ -62,7 +79,8 @@ typedef struct {
   int32_t kind; /* 0 none, 1 plane, 2 sphere, 3 ellipsoid, 4 torus,
                    5 gaussian bump, 6 cylinder, 7 unconstrained 2D plane
                    z = c[2] (no z updates; the baseline of Section 3.1's
-                   performance comparison) */
+                   performance comparison), 8 thylakoid composite (SI S3.1,
+                   reading R9) */
   int32_t pad;
   double c[3];
   double p[4];
@@ -169,6 +187,89 @@ static double ulp_of(double v) {
 /* g(x) and its unnormalised gradient n = dg/dx for each surface kind
  * (Eq. 1 text for the sphere, SI S3.1 for plane / cylinder / connector,
  * reading R4 for torus, ellipsoid and bump). */
+/* Thylakoid pieces (reading R9). type: 0 plane normal to x, 1 plane normal
+ * to y (g = s (x_d - c)), 2 cylinder along z about (c0, c1) with radius rad,
+ * 3 the bridge (cylinder along x), 4 a connector whose circle centre sits at
+ * x = c0. */
+typedef struct {
+  int type;
+  double s, c0, c1, rad;
+} thyl_piece;
+
+static double thyl_dz(const orc_surface* S, const orc_params* P, double z) {
+  double d[3] = {0.0, 0.0, z - S->c[2]};
+  min_image(P, d);
+  return d[2];
+}
+
+static thyl_piece thyl_select(const orc_surface* S, const orc_params* P, const double x[3]) {
+  double Rb = S->p[0], Lx = S->p[1], Rc = S->p[2], Lb = S->p[3];
+  double xc = S->c[0], yc = S->c[1];
+  double x0L = xc - 0.5 * Lb, x0R = xc + 0.5 * Lb, xfL = x0L - Rc, xfR = x0R + Rc;
+  double dy = x[1] - yc, dz = thyl_dz(S, P, x[2]);
+  double r = sqrt(dy * dy + dz * dz), Rout = Rb + Rc;
+  thyl_piece q = {0, 1.0, 0.0, 0.0, 0.0};
+  if (x[0] > xfL && x[0] < xfR && r < Rout) {
+    if (x[0] < x0L) { q.type = 4; q.c0 = x0L; }
+    else if (x[0] > x0R) { q.type = 4; q.c0 = x0R; }
+    else { q.type = 3; q.rad = Rb; }
+    return q;
+  }
+  int left = x[0] <= xc;
+  /* inner square of the block (centres of its corner cylinders) */
+  double ixl = left ? xfL - Rc - Lx : xfR + Rc, ixh = ixl + Lx;
+  double iyl = yc - 0.5 * Lx, iyh = yc + 0.5 * Lx;
+  double ex = x[0] < ixl ? x[0] - ixl : (x[0] > ixh ? x[0] - ixh : 0.0);
+  double ey = x[1] < iyl ? x[1] - iyl : (x[1] > iyh ? x[1] - iyh : 0.0);
+  if (ex != 0.0 && ey != 0.0) {
+    q.type = 2; q.c0 = ex < 0.0 ? ixl : ixh; q.c1 = ey < 0.0 ? iyl : iyh; q.rad = Rc;
+    return q;
+  }
+  if (ex == 0.0 && ey == 0.0) { /* inside: the nearest side */
+    double dxl = x[0] - (ixl - Rc), dxh = (ixh + Rc) - x[0], dyl = x[1] - (iyl - Rc), dyh = (iyh + Rc) - x[1];
+    double mx = dxl < dxh ? dxl : dxh, my = dyl < dyh ? dyl : dyh;
+    if (mx <= my) ex = dxl < dxh ? -1.0 : 1.0;
+    else ey = dyl < dyh ? -1.0 : 1.0;
+  }
+  if (ex != 0.0) {
+    int face = left ? ex > 0.0 : ex < 0.0; /* the side that faces the bridge */
+    if (face && r < Rout) { q.type = 4; q.c0 = left ? x0L : x0R; return q; }
+    q.type = 0; q.s = ex < 0.0 ? -1.0 : 1.0; q.c0 = ex < 0.0 ? ixl - Rc : ixh + Rc;
+    return q;
+  }
+  q.type = 1; q.s = ey < 0.0 ? -1.0 : 1.0; q.c0 = ey < 0.0 ? iyl - Rc : iyh + Rc;
+  return q;
+}
+
+static double thyl_eval(const orc_surface* S, const orc_params* P, const thyl_piece* q, const double x[3],
+                        double n[3]) {
+  double Rc = S->p[2], Rout = S->p[0] + Rc;
+  double dy = x[1] - S->c[1], dz = thyl_dz(S, P, x[2]);
+  switch (q->type) {
+    case 0: n[0] = q->s; n[1] = 0.0; n[2] = 0.0; return q->s * (x[0] - q->c0);
+    case 1: n[0] = 0.0; n[1] = q->s; n[2] = 0.0; return q->s * (x[1] - q->c0);
+    case 2: {
+      double a = x[0] - q->c0, b = x[1] - q->c1;
+      n[0] = 2.0 * a; n[1] = 2.0 * b; n[2] = 0.0;
+      return a * a + b * b - q->rad * q->rad;
+    }
+    case 3:
+      n[0] = 0.0; n[1] = 2.0 * dy; n[2] = 2.0 * dz;
+      return dy * dy + dz * dz - q->rad * q->rad;
+    default: {
+      double r = sqrt(dy * dy + dz * dz), a = x[0] - q->c0, t = r - Rout;
+      double w = 2.0 * (1.0 - Rout / r);
+      n[0] = 2.0 * a; n[1] = w * dy; n[2] = w * dz;
+      return a * a + t * t - Rc * Rc;
+    }
+  }
+}
+
+/* g at x_eval on the piece selected at x_sel (the thylakoid; any other
+ * surface is evaluated at x_eval). */
+static double surface_g_from(const orc_surface* S, const orc_params* P, const double x_sel[3],
+                             const double x_eval[3], double n[3]);
+
 double orc_surface_g(const orc_surface* S, const orc_params* P, const double x[3],
                      double n[3]) {
   double d[3] = {x[0] - S->c[0], x[1] - S->c[1], x[2] - S->c[2]};
@@ -211,6 +312,10 @@ double orc_surface_g(const orc_surface* S, const orc_params* P, const double x[3
       n[2] = 1.0;
       return d[2] - e;
     }
+    case 8: { /* thylakoid composite (reading R9): the piece at x */
+      thyl_piece q = thyl_select(S, P, x);
+      return thyl_eval(S, P, &q, x, n);
+    }
     case 6: { /* cylinder, axis p[1] */
       double R = S->p[0];
       int ax = (int)S->p[1];
@@ -229,6 +334,13 @@ double orc_surface_g(const orc_surface* S, const orc_params* P, const double x[3
       n[0] = n[1] = n[2] = 0.0;
       return 0.0;
   }
+}
+
+static double surface_g_from(const orc_surface* S, const orc_params* P, const double x_sel[3],
+                             const double x_eval[3], double n[3]) {
+  if (S->kind != 8) return orc_surface_g(S, P, x_eval, n);
+  thyl_piece q = thyl_select(S, P, x_sel);
+  return thyl_eval(S, P, &q, x_eval, n);
 }
 
 /* Solve the 4x4 system J d = r by Gaussian elimination with partial
@@ -288,7 +400,7 @@ int orc_position_half(const orc_surface* S, const orc_params* P, const double x[
     double ph[3], rx[3], n1[3];
     for (int k = 0; k < 3; ++k) ph[k] = p[k] + 0.5 * dt * (f[k] - lam * nm[k]);
     for (int k = 0; k < 3; ++k) rx[k] = x[k] - xn[k] + dt / m * ph[k];
-    double rg = orc_surface_g(S, P, xn, n1);
+    double rg = surface_g_from(S, P, x, xn, n1); /* the piece of x^m (R9) */
     double gn = sqrt(n1[0] * n1[0] + n1[1] * n1[1] + n1[2] * n1[2]);
     if (fabs(rg) / gn < eta && maxabs3(rx) < eta) {
       status = 0;

@@ -574,3 +574,91 @@ def sphere_and_plane2d(n: int = 1_000_000, phi: float = 0.4, seed: int = 1, prec
     v2[:, 2] = 0.0
     plane = [_system("plane2d", flat, prm2, x2, v2, constrained=np.zeros(n, np.uint8))]
     return sphere, plane
+
+
+THYLAKOID_SI = dict(Lx=15.0, Lz=30.0, Rc=3.0, Lb=10.0)  # the SI's surface parameters (R = R_c = 3)
+
+
+def thylakoid_surface(Rb: float = 1.5, Lx: float = 15.0, Rc: float = 3.0, Lb: float = 10.0,
+                      center=(0.0, 0.0, 0.0)) -> dict:
+    """The thylakoid composite of SI S3.1 (two rounded-square blocks joined by
+    a bridge of radius Rb through toroidal connectors; z is periodic)."""
+    return {"kind": "thylakoid", "center": tuple(center), "p": (Rb, Lx, Rc, Lb)}
+
+
+def thylakoid_area_parts(Rb, Lx, Rc, Lb, Lz):
+    """Areas of the pieces: the planes of both blocks (the two face planes
+    without their connector holes), the corner cylinders, the bridge and the
+    two connectors (SI S3.1: A_conn = pi R^2 (pi - 2) + pi^2 R R_b with R = R_c)."""
+    a_planes = 8 * Lx * Lz - 2 * math.pi * (Rb + Rc) ** 2
+    a_corners = 2 * 2 * math.pi * Rc * Lz
+    a_bridge = 2 * math.pi * Rb * Lb
+    a_conn = math.pi * Rc ** 2 * (math.pi - 2) + math.pi ** 2 * Rc * Rb
+    return dict(planes=a_planes, corners=a_corners, bridge=a_bridge, connectors=2 * a_conn)
+
+
+def sample_thylakoid(surf: dict, n: int, g: np.random.Generator, Lz: float) -> np.ndarray:
+    """n points uniform in area on the thylakoid composite (z in [c_z - Lz/2,
+    c_z + Lz/2))."""
+    Rb, Lx, Rc, Lb = surf["p"]
+    xc, yc, zc = surf["center"]
+    x0L, x0R = xc - Lb / 2, xc + Lb / 2
+    xfL, xfR = x0L - Rc, x0R + Rc
+    parts = thylakoid_area_parts(Rb, Lx, Rc, Lb, Lz)
+    names = list(parts)
+    w = np.array([parts[k] for k in names])
+    which = g.choice(len(names), size=n, p=w / w.sum())
+    out = np.empty((n, 3))
+    for kk, name in enumerate(names):
+        idx = np.flatnonzero(which == kk)
+        m = idx.size
+        if m == 0:
+            continue
+        z = zc - Lz / 2 + g.random(m) * Lz
+        if name == "bridge":
+            ph = g.random(m) * 2 * math.pi
+            out[idx] = np.column_stack([x0L + g.random(m) * Lb, yc + Rb * np.cos(ph), zc + Rb * np.sin(ph)])
+        elif name == "connectors":
+            pts = []
+            while len(pts) < m:
+                k = 2 * (m - len(pts)) + 16
+                al = g.random(k) * math.pi / 2
+                r = Rb + Rc - Rc * np.cos(al)
+                keep = g.random(k) < r / (Rb + Rc)
+                al, r = al[keep], r[keep]
+                side = g.random(al.size) < 0.5
+                xx = np.where(side, x0L - Rc * np.sin(al), x0R + Rc * np.sin(al))
+                ph = g.random(al.size) * 2 * math.pi
+                pts.extend(np.column_stack([xx, yc + r * np.cos(ph), zc + r * np.sin(ph)]))
+            out[idx] = np.array(pts[:m])
+        elif name == "corners":
+            blk = g.random(m) < 0.5
+            cor = g.integers(0, 4, m)
+            ixl = np.where(blk, xfL - Rc - Lx, xfR + Rc)
+            cx = ixl + np.where(cor % 2 == 1, Lx, 0.0)
+            cy = yc + np.where(cor // 2 == 1, Lx / 2, -Lx / 2)
+            base = np.where(cor % 2 == 1, 0.0, math.pi)  # quarter facing outward in x
+            sgn = np.where(cor // 2 == 1, 1.0, -1.0)
+            a = g.random(m) * math.pi / 2
+            # the quarter between the outward x direction and the outward y direction
+            ang = np.where(cor % 2 == 1, sgn * a, math.pi - sgn * a)
+            del base
+            out[idx] = np.column_stack([cx + Rc * np.cos(ang), cy + Rc * np.sin(ang), z])
+        else:  # planes: 4 per block; the face planes lose the connector holes
+            pts = []
+            while len(pts) < m:
+                k = 2 * (m - len(pts)) + 16
+                blk = g.random(k) < 0.5
+                side = g.integers(0, 4, k)
+                t = g.random(k) * Lx - Lx / 2
+                zz = zc - Lz / 2 + g.random(k) * Lz
+                ixl = np.where(blk, xfL - Rc - Lx, xfR + Rc)
+                ixh = ixl + Lx
+                xs = np.where(side == 0, ixl - Rc, np.where(side == 1, ixh + Rc, (ixl + ixh) / 2 + t))
+                ys = np.where(side < 2, yc + t, np.where(side == 2, yc - Lx / 2 - Rc, yc + Lx / 2 + Rc))
+                dz = zz - zc
+                hole = (np.abs(xs - np.where(blk, xfL, xfR)) < 1e-12) & (np.hypot(ys - yc, dz) < Rb + Rc)
+                ok = ~hole
+                pts.extend(np.column_stack([xs[ok], ys[ok], zz[ok]]))
+            out[idx] = np.array(pts[:m])
+    return out
