@@ -84,6 +84,14 @@ extern "C" {
  *              taken with the minimum image in periodic x, y
  *   CYLINDER   g = sum_{d != axis} (x_d-c_d)^2 - R^2, p = (R, axis 0|1|2)
  *              (SI S3.1 with the axis coefficient 0 and the others 1)
+ *   THYLAKOID  the composite of SI S3.1, p = (R_b, L_x, R_c, L_b): a bridge
+ *              cylinder (radius R_b, length L_b) along x through (c_y, c_z),
+ *              toroidal connectors (tube radius R_c) joining it to the face
+ *              planes of two blocks at x = c_x -/+ (L_b/2 + R_c), each block
+ *              a tube along z with a square section of side L_x + 2 R_c and
+ *              corners rounded by quarter cylinders of radius R_c; needs
+ *              periodic z and open x, y. A particle's piece is chosen where
+ *              its half step starts and held for that solve.
  *   XY2D       no constraint: particles move in the plane z = c_z with the
  *              z components of force, noise and momentum dropped (the
  *              unconstrained 2D baseline of Section 3.1's performance
@@ -98,7 +106,8 @@ typedef enum {
   MD_SURF_TORUS = 4,
   MD_SURF_GAUSSIAN_BUMP = 5,
   MD_SURF_CYLINDER = 6,
-  MD_SURF_XY2D = 7
+  MD_SURF_XY2D = 7,
+  MD_SURF_THYLAKOID = 8
 } md_surface_kind;
 
 typedef struct md_surface {

@@ -128,7 +128,7 @@ int check_system(const md_surface& s, const md_params& p, SysDev& S, std::string
   for (int a = 0; a < p.ntypes; ++a)
     for (int b = 0; b < p.ntypes; ++b)
       if (p.rcut[a][b] > 0.0 && !(p.sigma[a][b] > 0.0)) return bad("sigma must be > 0 where rcut > 0");
-  if (s.kind < MD_SURF_NONE || s.kind > MD_SURF_XY2D) return bad("unknown surface kind");
+  if (s.kind < MD_SURF_NONE || s.kind > MD_SURF_THYLAKOID) return bad("unknown surface kind");
   if (s.reserved != 0) return bad("reserved fields must be 0");
   if (p.pair_form != MD_PAIR_TRUNC_SHIFT && p.pair_form != MD_PAIR_LINEAR_SMOOTH) return bad("unknown pair_form");
   for (int d = 0; d < 3; ++d)
@@ -173,6 +173,11 @@ int check_system(const md_surface& s, const md_params& p, SysDev& S, std::string
     case MD_SURF_XY2D:
       if (!p.periodic[0] || !p.periodic[1] || p.periodic[2])
         return bad("the 2D plane needs periodic x and y and an open z axis");
+      break;
+    case MD_SURF_THYLAKOID:
+      if (!(s.p[0] > 0.0 && s.p[1] > 0.0 && s.p[2] > 0.0 && s.p[3] > 0.0))
+        return bad("the thylakoid needs R_b, L_x, R_c, L_b > 0");
+      if (p.periodic[0] || p.periodic[1] || !p.periodic[2]) return bad("the thylakoid needs periodic z and open x, y");
       break;
     case MD_SURF_CYLINDER:
       if (!(s.p[0] > 0.0)) return bad("cylinder radius must be > 0");
@@ -252,6 +257,13 @@ bool surface_extent(const md_surface& s, int d, double& lo, double& hi) {
       if (d < 2) return false;
       lo = c; hi = c;
       return true;
+    case MD_SURF_THYLAKOID: {
+      if (d == 2) return false;
+      const double w = s.p[1] + 2.0 * s.p[2];  // block width
+      const double e = d == 0 ? 0.5 * s.p[3] + s.p[2] + w : 0.5 * w;
+      lo = c - e; hi = c + e;
+      return true;
+    }
     case MD_SURF_CYLINDER:
       if (d == (int)s.p[1]) return false;
       lo = c - s.p[0]; hi = c + s.p[0];
@@ -671,6 +683,7 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
         }
         case MD_SURF_TORUS: kappa = 1.0 / sf.p[1] + 1.0 / (sf.p[0] - sf.p[1]); break;
         case MD_SURF_GAUSSIAN_BUMP: kappa = 2.0 * std::fabs(sf.p[0]) / (sf.p[1] * sf.p[1]); break;
+        case MD_SURF_THYLAKOID: kappa = std::max(1.0 / sf.p[0], 1.0 / sf.p[2]); break;
         default: break;
       }
       S.slab = (h->has_pairs && kappa >= 0.0 && rcmax * kappa < 0.5) ? (float)(rcmax * rcmax * kappa + 1e-3) : 0.0f;

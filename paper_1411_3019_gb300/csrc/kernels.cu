@@ -122,6 +122,91 @@ __device__ __forceinline__ double f2d(float v) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double wrap_min_image(double d, double L) { return d - L * rint(d / L); }
 
+// Thylakoid composite (SI S3.1), p = (R_b, L_x, R_c, L_b), centre c, z
+// periodic: a bridge cylinder of radius R_b along x through (c_y, c_z) for
+// |x - c_x| <= L_b/2; at each end a connector (tube radius R_c) meeting it
+// and the face plane of a block at x = c_x -/+ (L_b/2 + R_c) with continuous
+// tangent planes; each block a tube along z with a square cross section of
+// side L_x + 2 R_c whose corners are quarter cylinders of radius R_c. A
+// particle's piece is chosen from the position where its half step starts
+// and held for that solve: between the block faces and within R_b + R_c of
+// the bridge axis the bridge or the nearer connector, otherwise the block's
+// rounded square (a corner cylinder beyond the inner square in x and y, else
+// the plane of the side it lies beyond, the nearest side when inside), the
+// face plane's hole belonging to the connector.
+struct Piece {
+  int type;  // 0 plane normal to x, 1 plane normal to y, 2 cylinder along z, 3 bridge, 4 connector
+  double s, c0, c1, rad;
+};
+
+__device__ __forceinline__ double thyl_dz(const SysDev& S, double z) {
+  const double d = z - S.c[2];
+  return S.periodic[2] ? wrap_min_image(d, S.box_len[2]) : d;
+}
+
+__device__ __forceinline__ Piece thyl_select(const SysDev& S, double x, double y, double z) {
+  const double Rb = S.p[0], Lx = S.p[1], Rc = S.p[2], Lb = S.p[3];
+  const double xc = S.c[0], yc = S.c[1];
+  const double x0L = xc - 0.5 * Lb, x0R = xc + 0.5 * Lb, xfL = x0L - Rc, xfR = x0R + Rc;
+  const double dy = y - yc, dz = thyl_dz(S, z);
+  const double r = sqrt(dy * dy + dz * dz), Rout = Rb + Rc;
+  Piece q{0, 1.0, 0.0, 0.0, 0.0};
+  if (x > xfL && x < xfR && r < Rout) {
+    if (x < x0L) { q.type = 4; q.c0 = x0L; }
+    else if (x > x0R) { q.type = 4; q.c0 = x0R; }
+    else { q.type = 3; q.rad = Rb; }
+    return q;
+  }
+  const bool left = x <= xc;
+  const double ixl = left ? xfL - Rc - Lx : xfR + Rc, ixh = ixl + Lx;
+  const double iyl = yc - 0.5 * Lx, iyh = yc + 0.5 * Lx;
+  double ex = x < ixl ? x - ixl : (x > ixh ? x - ixh : 0.0);
+  double ey = y < iyl ? y - iyl : (y > iyh ? y - iyh : 0.0);
+  if (ex != 0.0 && ey != 0.0) {
+    q.type = 2; q.c0 = ex < 0.0 ? ixl : ixh; q.c1 = ey < 0.0 ? iyl : iyh; q.rad = Rc;
+    return q;
+  }
+  if (ex == 0.0 && ey == 0.0) {  // inside: the nearest side
+    const double dxl = x - (ixl - Rc), dxh = (ixh + Rc) - x, dyl = y - (iyl - Rc), dyh = (iyh + Rc) - y;
+    const double mx = dxl < dxh ? dxl : dxh, my = dyl < dyh ? dyl : dyh;
+    if (mx <= my) ex = dxl < dxh ? -1.0 : 1.0;
+    else ey = dyl < dyh ? -1.0 : 1.0;
+  }
+  if (ex != 0.0) {
+    const bool face = left ? ex > 0.0 : ex < 0.0;  // the side that faces the bridge
+    if (face && r < Rout) { q.type = 4; q.c0 = left ? x0L : x0R; return q; }
+    q.type = 0; q.s = ex < 0.0 ? -1.0 : 1.0; q.c0 = ex < 0.0 ? ixl - Rc : ixh + Rc;
+    return q;
+  }
+  q.type = 1; q.s = ey < 0.0 ? -1.0 : 1.0; q.c0 = ey < 0.0 ? iyl - Rc : iyh + Rc;
+  return q;
+}
+
+// g and grad g of one piece at (x, y, z).
+__device__ __forceinline__ double thyl_eval(const SysDev& S, const Piece& q, double x, double y, double z,
+                                            double& nx, double& ny, double& nz) {
+  const double Rc = S.p[2], Rout = S.p[0] + Rc;
+  const double dy = y - S.c[1], dz = thyl_dz(S, z);
+  switch (q.type) {
+    case 0: nx = q.s; ny = 0.0; nz = 0.0; return q.s * (x - q.c0);
+    case 1: nx = 0.0; ny = q.s; nz = 0.0; return q.s * (y - q.c0);
+    case 2: {
+      const double a = x - q.c0, b = y - q.c1;
+      nx = 2.0 * a; ny = 2.0 * b; nz = 0.0;
+      return a * a + b * b - q.rad * q.rad;
+    }
+    case 3:
+      nx = 0.0; ny = 2.0 * dy; nz = 2.0 * dz;
+      return dy * dy + dz * dz - q.rad * q.rad;
+    default: {
+      const double r = sqrt(dy * dy + dz * dz), a = x - q.c0, t = r - Rout;
+      const double w = 2.0 * (1.0 - Rout / r);
+      nx = 2.0 * a; ny = w * dy; nz = w * dz;
+      return a * a + t * t - Rc * Rc;
+    }
+  }
+}
+
 __device__ __forceinline__ double surf_eval(const SysDev& S, double x, double y, double z,
                                             double& nx, double& ny, double& nz) {
   double dx = x - S.c[0], dy = y - S.c[1], dz = z - S.c[2];
@@ -159,6 +244,10 @@ __device__ __forceinline__ double surf_eval(const SysDev& S, double x, double y,
       else dz = 0.0;
       nx = 2.0 * dx; ny = 2.0 * dy; nz = 2.0 * dz;
       return fma(dx, dx, fma(dy, dy, fma(dz, dz, -S.p[0] * S.p[0])));
+    }
+    case kThylakoid: {  // the piece at the point itself
+      const Piece q = thyl_select(S, x, y, z);
+      return thyl_eval(S, q, x, y, z, nx, ny, nz);
     }
     default:
       nx = ny = nz = 0.0;
@@ -1219,8 +1308,17 @@ __device__ __forceinline__ GEval surf_g(const SysDev& S, double x, double y, dou
   return e;
 }
 
+// g at (x, y, z) on a held thylakoid piece; the gradient is kept in (ux, uy, uz).
+__device__ __forceinline__ GEval thyl_geval(const SysDev& S, const Piece& q, double x, double y, double z) {
+  GEval e;
+  e.q = 0.0;
+  e.g = thyl_eval(S, q, x, y, z, e.ux, e.uy, e.uz);
+  return e;
+}
+
 __device__ __forceinline__ void surf_n(const SysDev& S, const GEval& e, double& nx, double& ny, double& nz) {
   switch (S.kind) {
+    case kThylakoid: nx = e.ux; ny = e.uy; nz = e.uz; break;
     case kPlane: nx = S.p[0]; ny = S.p[1]; nz = S.p[2]; break;
     case kTorus: nx = e.q * e.ux; ny = e.q * e.uy; nz = 2.0 * e.uz; break;
     case kBump: nx = e.q * e.ux; ny = e.q * e.uy; nz = 1.0; break;
@@ -1234,6 +1332,7 @@ __device__ __forceinline__ void surf_n(const SysDev& S, const GEval& e, double& 
 // Float32 gradient from the pieces surf_g kept (offsets in float64).
 __device__ __forceinline__ void surf_n_f(const SysDev& S, const GEval& e, float& nx, float& ny, float& nz) {
   switch (S.kind) {
+    case kThylakoid: nx = d2f_rn(e.ux); ny = d2f_rn(e.uy); nz = d2f_rn(e.uz); break;
     case kPlane: nx = S.p_f[0]; ny = S.p_f[1]; nz = S.p_f[2]; break;
     case kTorus: {
       const float q = d2f_rn(e.q);
@@ -1376,8 +1475,11 @@ __device__ __forceinline__ void integrate_particle_fp64(const DevArrays& A, int6
   const double h = S.half_dt;
   const bool con = meta_con(m);
   double n0x = 0.0, n0y = 0.0, n0z = 0.0, nn = 1.0, inv_nn = 0.0;
+  Piece q0{};
+  const bool held = S.kind == kThylakoid;  // composite surface: the piece at x^k for the whole solve
   if (con) {
-    surf_n(S, surf_g(S, x, y, z), n0x, n0y, n0z);
+    if (held) q0 = thyl_select(S, x, y, z);
+    surf_n(S, held ? thyl_geval(S, q0, x, y, z) : surf_g(S, x, y, z), n0x, n0y, n0z);
     nn = fma(n0x, n0x, fma(n0y, n0y, n0z * n0z));
     inv_nn = nr_rcp(nn);
   }
@@ -1395,7 +1497,7 @@ __device__ __forceinline__ void integrate_particle_fp64(const DevArrays& A, int6
     double lam = 0.0;
     bool ok = false;
     for (int it = 0; it <= S.max_newton; ++it) {
-      const GEval e = surf_g(S, xn, yn, zn);
+      const GEval e = held ? thyl_geval(S, q0, xn, yn, zn) : surf_g(S, xn, yn, zn);
       if (e.g * e.g < tol2nn) {
         ok = true;
         break;
@@ -1506,9 +1608,11 @@ struct LineGeneric {
   const SysDev* S;
   double yx, yy, yz, n0x, n0y, n0z;
   float n0xf, n0yf, n0zf;
+  Piece q;  // the held piece of a composite surface
   GEval e;
   __device__ __forceinline__ double g(double mu) {
-    e = surf_g(*S, fma(-mu, n0x, yx), fma(-mu, n0y, yy), fma(-mu, n0z, yz));
+    const double px = fma(-mu, n0x, yx), py = fma(-mu, n0y, yy), pz = fma(-mu, n0z, yz);
+    e = S->kind == kThylakoid ? thyl_geval(*S, q, px, py, pz) : surf_g(*S, px, py, pz);
     return e.g;
   }
   __device__ __forceinline__ float n1n0(float) const {
@@ -1558,7 +1662,15 @@ __device__ __forceinline__ void integrate_particle_mixed(const DevArrays& A, int
   if (meta_con(m)) {
     const float xf = d2f_rn(x), yf = d2f_rn(y), zf = d2f_rn(z);
     float n0xf, n0yf, n0zf;
-    surf_grad_f(S, xf - S.c_f[0], yf - S.c_f[1], zf - S.c_f[2], n0xf, n0yf, n0zf);
+    Piece q0{};
+    if (S.kind == kThylakoid) {  // composite surface: the piece at x^k, held for the solve
+      q0 = thyl_select(S, x, y, z);
+      double gx, gy, gz;
+      thyl_eval(S, q0, x, y, z, gx, gy, gz);
+      n0xf = d2f_rn(gx); n0yf = d2f_rn(gy); n0zf = d2f_rn(gz);
+    } else {
+      surf_grad_f(S, xf - S.c_f[0], yf - S.c_f[1], zf - S.c_f[2], n0xf, n0yf, n0zf);
+    }
     const float nnf = fmaf(n0xf, n0xf, fmaf(n0yf, n0yf, n0zf * n0zf));
     float mu0f = 0.f;
     if (mode) {  // mu_0 = (dt/m) n0.(p + h F) / |n0|^2
@@ -1629,6 +1741,7 @@ __device__ __forceinline__ void integrate_particle_mixed(const DevArrays& A, int
         L.yx = yx; L.yy = yy; L.yz = yz;
         L.n0x = n0x; L.n0y = n0y; L.n0z = n0z;
         L.n0xf = n0xf; L.n0yf = n0yf; L.n0zf = n0zf;
+        L.q = q0;
         ok = newton_line(L, S.max_newton, S.frozen, nnf, tol_n, floor_mu, mu0f, mu);
       }
     }
@@ -1975,7 +2088,13 @@ __global__ void k_finish(DevArrays A) {
   if (con) {
     if (sizeof(R) == 4) {
       float fx, fy, fz;
-      surf_grad_f(S, (float)x - S.c_f[0], (float)y - S.c_f[1], (float)z - S.c_f[2], fx, fy, fz);
+      if (S.kind == kThylakoid) {
+        double gx, gy, gz;
+        surf_eval(S, x, y, z, gx, gy, gz);
+        fx = d2f_rn(gx); fy = d2f_rn(gy); fz = d2f_rn(gz);
+      } else {
+        surf_grad_f(S, (float)x - S.c_f[0], (float)y - S.c_f[1], (float)z - S.c_f[2], fx, fy, fz);
+      }
       nx = fx; ny = fy; nz = fz;
       inv_nn = (double)(1.0f / fmaf(fx, fx, fmaf(fy, fy, fz * fz)));
     } else {

@@ -17,7 +17,7 @@ constexpr uint32_t kFlagTimeout = 0x8u;
 constexpr uint32_t kFlagOffSurface = 0x100u;  // set-state validation only
 
 enum SurfKind : int32_t {
-  kNone = 0, kPlane = 1, kSphere = 2, kEllipsoid = 3, kTorus = 4, kBump = 5, kCylinder = 6, kXY2D = 7
+  kNone = 0, kPlane = 1, kSphere = 2, kEllipsoid = 3, kTorus = 4, kBump = 5, kCylinder = 6, kXY2D = 7, kThylakoid = 8
 };
 
 // Per-particle meta word: type (bits 0-2), constrained (bit 3), system (bits 4-31).

@@ -662,3 +662,28 @@ def sample_thylakoid(surf: dict, n: int, g: np.random.Generator, Lz: float) -> n
                 pts.extend(np.column_stack([xs[ok], ys[ok], zz[ok]]))
             out[idx] = np.array(pts[:m])
     return out
+
+
+def thylakoid_system(n: int = 3000, Rb: float = 1.5, phi: float = None, seed: int = 1, precision: str = "mixed",
+                     dt: float = 0.002, tol: float = 1e-10, dmin: float = 1.0, interacting: bool = True):
+    """Crowded diffusion on the thylakoid composite of SI S3.1 with its surface
+    parameters (L_x = 15, L_z = 30, R_c = R = 3, L_b = 10, bridge radius Rb):
+    n WCA particles (the SI uses 2000-4000) placed by random sequential
+    addition, periodic z of length L_z, kT = gamma = 1. (phi is ignored; the
+    area fraction follows from n.)"""
+    surf = thylakoid_surface(Rb, THYLAKOID_SI["Lx"], THYLAKOID_SI["Rc"], THYLAKOID_SI["Lb"])
+    Lz = THYLAKOID_SI["Lz"]
+    w = THYLAKOID_SI["Lx"] + 2 * THYLAKOID_SI["Rc"]
+    ext_x = THYLAKOID_SI["Lb"] / 2 + THYLAKOID_SI["Rc"] + w + 3.0
+    prm = wca_params(precision=precision, dt=dt, rattle_tol=tol, seed=seed,
+                     box_lo=(-ext_x, -w / 2 - 3.0, -Lz / 2), box_hi=(ext_x, w / 2 + 3.0, Lz / 2),
+                     periodic=(0, 0, 1))
+    if not interacting:
+        prm = noninteracting(prm)
+    g = rng(seed, 400)
+    box = (prm["box_lo"], prm["box_hi"])
+    if interacting:
+        x = rsa(lambda k, m: sample_thylakoid(surf, m, g, Lz), [n], dmin, g, periodic=prm["periodic"], box=box)[0]
+    else:  # free particles may overlap
+        x = sample_thylakoid(surf, n, g, Lz)
+    return [_system("thylakoid", surf, prm, x, maxwell(n, 1.0, 1.0, g))]

@@ -21,7 +21,7 @@ from . import _build
 
 MAX_TYPES = 8
 SURF_KINDS = {"none": 0, "plane": 1, "sphere": 2, "ellipsoid": 3, "torus": 4, "gaussian_bump": 5,
-              "cylinder": 6, "xy2d": 7}
+              "cylinder": 6, "xy2d": 7, "thylakoid": 8}
 PRECISION = {"fp64": 0, "mixed": 1}
 MD_OK, MD_ERR_INVALID_ARG, MD_ERR_CUDA, MD_ERR_RATTLE_DIVERGED = 0, 1, 2, 3
 MD_ERR_NONFINITE, MD_ERR_OUT_OF_GRID, MD_ERR_TIMEOUT, MD_ERR_NO_DEVICE = 4, 5, 6, 7
