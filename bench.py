@@ -40,7 +40,7 @@ METRIC = ("particle-steps/sec on 1 GB300 (FP32-force/FP64-RATTLE vs plain FP64) 
 UNIT = "particle-steps/s"
 L2_FLUSH_BYTES = 256 << 20  # larger than the 129 MB L2
 WORKLOADS = ("ellipsoid_torus", "plain_sphere", "replicas", "bead_molecules", "bump_crowders", "nve_surfaces",
-             "capsids", "sphere_vs_2d")
+             "capsids", "sphere_vs_2d", "thylakoids")
 # float64 pipe of one GB300: 152 SMs x 2 float64 operations per SM per clock
 FP64_OPS_PER_SM_CLK = 2
 SMS = 152
@@ -94,6 +94,14 @@ def workload(name: str, rank: int, precision: str, nrep: int = 4096, pair_form: 
         return inputs.c3_bump_crowders(seed=seed, precision=precision)
     if name == "sphere_vs_2d":
         return inputs.sphere_and_plane2d(n=250_000, seed=seed, precision=precision)[0]
+    if name == "thylakoids":  # 128 crowded thylakoids of the SI (2500 crowders, bridge radius 1.5)
+        out = []
+        for k in range(max(1, nrep // 32)):
+            sy = inputs.thylakoid_system(n=2500, Rb=1.5, seed=seed * 100_003 + k, precision=precision,
+                                         dmin=0.9)[0]
+            sy["params"] = dict(sy["params"], replica=k)
+            out.append(sy)
+        return out
     if name == "capsids":
         return inputs.capsid_systems(nsys=max(1, nrep // 4), ncone=60, seed=seed, precision=precision)
     if name == "nve_surfaces":
