@@ -740,6 +740,7 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
   }
   if (!h->has_pairs) A.nbucket = 1;
   A.pair_lanes = 1;
+  A.rec_cell = (!h->excl && cell_total < (uint64_t(1) << 29)) ? 1 : 0;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
     delete h;

@@ -662,7 +662,7 @@ __global__ void k_bucket_build(DevArrays A) {
   A.stag[d] = tag;
   A.scell[d] = cell;
   if (A.slot_of) A.slot_of[tag] = d;
-  put_rec<R>(A.rec, d, o[0], o[1], o[2], meta_type(m) | (mol << 3));
+  put_rec<R>(A.rec, d, o[0], o[1], o[2], meta_type(m) | ((A.rec_cell ? cell : mol) << 3));
 }
 
 // float64 reciprocal and inverse square root without the long divide/sqrt
@@ -1089,8 +1089,8 @@ __device__ __forceinline__ uint32_t pair_slot(const DevArrays& A, const Cells& C
       for (int q = 0; q < 3; ++q) {
         const R shx = (R)(q - 1) * csx, shy = (R)dy * csy, shz = (R)dz * csz;
         for (uint32_t t = t0[q]; t < t1[q]; ++t) {
-          const uint32_t cj = C.scell(t);
-          const Rec rj = C.rec(t);  // issued together with the cell id
+          const Rec rj = C.rec(t);
+          const uint32_t cj = A.rec_cell ? RecT<R>::bits(rj) >> 3 : C.scell(t);
           if (cj != nb[q] || t == s) continue;
           const uint32_t bj = RecT<R>::bits(rj);
           if (EXCL && (bj >> 3) == moli) continue;
@@ -1216,8 +1216,8 @@ __global__ void __launch_bounds__(256) k_pair_lanes(DevArrays A) {
       const uint32_t t1 = start[b + 1];
       const R shx = (R)dx * csx, shy = (R)dy * csy, shz = (R)dz * csz;
       for (uint32_t t = start[b]; t < t1; ++t) {
-        const uint32_t cj = scell[t];
-        const Rec rj = rec[t];  // issued together with the cell id
+        const Rec rj = rec[t];
+        const uint32_t cj = A.rec_cell ? RecT<R>::bits(rj) >> 3 : scell[t];
         if (cj != nb || t == s) continue;
         const uint32_t bj = RecT<R>::bits(rj);
         if (EXCL && (bj >> 3) == moli) continue;
@@ -1864,7 +1864,7 @@ __device__ __forceinline__ void resident_cells(const DevArrays& A, const SysDev&
     const uint32_t mol = A.mol ? (uint32_t)A.mol[i] : 0u;
     s_stag[dd] = (uint16_t)li;
     s_scell[dd] = c;
-    put_rec<R>(s_rec, dd, o[0], o[1], o[2], meta_type(m) | (mol << 3));
+    put_rec<R>(s_rec, dd, o[0], o[1], o[2], meta_type(m) | ((A.rec_cell ? c : mol) << 3));
   }
   __syncthreads();
 }

@@ -130,6 +130,9 @@ struct DevArrays {
   int32_t hashed;       // 0: bucket = cell id; 1: hashed buckets
   int32_t log_t;
   int32_t pair_lanes;   // lanes per particle in the pair kernel (1, 2, 4 or 8)
+  int32_t rec_cell;     // 1: a record's w word holds type | cell << 3 (no exclusions,
+                        // cells < 2^29), so the pair kernel needs no sorted-cell load;
+                        // 0: type | molecule << 3
   double* x;            // [3][n] positions (unwrapped), SoA
   double* ph;           // [3][n] p^{k-1/2} (or p^k before the first step)
   double* pk;           // [3][n] p^k scratch
