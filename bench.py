@@ -572,11 +572,7 @@ def reference_arm(args, rank: int, world: int, precision: str):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
             "warmup": args.warmup, "ms_per_step": el / steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(workload_config(args.workload, systems, precision),
-                           **({"l2": f"one md_step({args.steps}) call (persistent resident launches), L2 flushed "
-                                     f"before it; the state x, p ({48 * n_local / 1e6:.0f} MB) is larger than "
-                                     f"the 129 MB L2"} if resident else {}),
-                           engine="resident" if resident else "global"), "impl": "reference",
+            "config": workload_config(args.workload, systems, precision), "impl": "reference",
             "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
                              "sample": f"{steps} whole time steps of the {n}-particle workload"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -32,3 +32,21 @@ def test_no_sample_in_the_window_gives_none():
     assert bench.ClockSampler.parse(_row(t, 2070), t + datetime.timedelta(seconds=1),
                                     t + datetime.timedelta(seconds=2)) is None
     assert bench.ClockSampler.parse("garbage line\n", None, None) is None
+
+
+def test_reference_arm_prints_one_json_line():
+    """bench.py --impl reference runs the oracle on the host and prints the
+    line the driver reads (small workload: the 1,000-particle sphere)."""
+    import json
+    import subprocess
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload",
+                        "plain_sphere", "--steps", "2", "--warmup", "1"], capture_output=True, text=True,
+                       timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 2
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["config"]["workload"].startswith("plain_sphere")
