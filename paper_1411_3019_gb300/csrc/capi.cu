@@ -1095,6 +1095,12 @@ int md_set_option(md_handle* h, int32_t key, int64_t value) {
       if (value < 1 || value > 100000) return fail(h, MD_ERR_INVALID_ARG, "steps per launch must be in 1..100000");
       h->res_steps_per_launch = value;
       break;
+    case MD_OPT_PAIR_TILE:
+      if (value != 0 && value != 1) return fail(h, MD_ERR_INVALID_ARG, "pair tile must be 0 or 1");
+      if (value == 1 && h->has_pairs && h->A.hashed)
+        return fail(h, MD_ERR_INVALID_ARG, "the cell-tiled pair kernel needs a grid of at most max(2^20, 4N) cells");
+      h->A.pair_tile = (int32_t)value;
+      break;
     default:
       return fail(h, MD_ERR_INVALID_ARG, "unknown option");
   }
@@ -1113,6 +1119,7 @@ int md_get_option(md_handle* h, int32_t key, int64_t* value) {
     case MD_OPT_ENGINE: *value = h->engine; return MD_OK;
     case MD_OPT_RESIDENT_THREADS: *value = h->res_threads; return MD_OK;
     case MD_OPT_RESIDENT_STEPS: *value = h->res_steps_per_launch; return MD_OK;
+    case MD_OPT_PAIR_TILE: *value = h->A.pair_tile; return MD_OK;
     default: return fail(h, MD_ERR_INVALID_ARG, "unknown option");
   }
 }

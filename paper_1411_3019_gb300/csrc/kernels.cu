@@ -1240,6 +1240,233 @@ __global__ void __launch_bounds__(256) k_pair_lanes(DevArrays A) {
   store_f<R>(A.f, tag, fx, fy, fz, u);
 }
 
+// ---------------------------------------------------------------------------
+// Cell-tiled pair kernel (bucket = cell id, no hashing). Warp w evaluates
+// the particles of its run of kTileSlots sorted slots, one cell at a time:
+// the run splits at cell boundaries into pieces of p <= kTileSlots particles
+// of one home cell. For each piece the warp stages the records of the home
+// cell's 27-cell stencil in shared memory, each shifted into the frame of the
+// home cell, and the piece's particles share the lanes: P = p rounded up to a
+// power of two groups of 32/P lanes, lane j of a group walking the staged
+// candidates j, j + 32/P, ...; a fixed xor-shuffle tree adds each group's
+// partial sums. A candidate's record is read from global memory once per
+// piece instead of once per particle, the stencil's bucket bounds once per
+// piece, and the lanes walk one shared list in step; every warp has the same
+// number of particles whatever the cells' occupancy. The pieces leave their
+// pair forces in shared memory; then every lane adds the bonded terms of its
+// own slot and stores the force, so the float64 bond arithmetic runs on all
+// 32 lanes at once (the float64 pipe costs the same per warp instruction
+// whatever the number of active lanes).
+// Each lane tests a segment of 32 of its candidates against the home
+// particle's largest cutoff first, one bit per hit in a register mask, then
+// evaluates the pair terms over the set bits (self and same-molecule pairs
+// are dropped there): the lanes of a warp run the Lennard-Jones arithmetic
+// together instead of once per candidate that any lane finds in range.
+// ---------------------------------------------------------------------------
+constexpr int kTileWarps = 4;   // warps per CTA
+constexpr int kTileSlots = 32;  // sorted slots (particles) per warp: one per lane
+// staged candidates per warp and window (256 float4 or 128 double4 records,
+// 4 KB a warp)
+template <typename R> constexpr int tile_cap() { return sizeof(R) == 4 ? 256 : 128; }
+
+// Copy the staged candidates [w0, w0 + len) of one cell into the warp's
+// stage. Lane k < 27 holds stencil cell k's first slot t0 and its staged
+// offset pre (exclusive prefix of the counts). Four loads per lane are in
+// flight before their stores. All 32 lanes call this.
+template <typename R>
+__device__ __forceinline__ void tile_stage(const typename RecT<R>::T* __restrict__ rec, typename RecT<R>::T* stage,
+                                           uint32_t t0, uint32_t pre, R csx, R csy, R csz, uint32_t w0,
+                                           uint32_t len, int lane) {
+  using Rec = typename RecT<R>::T;
+  constexpr int U = 4;
+  for (uint32_t e0 = 0; e0 < len; e0 += 32u * U) {
+    Rec r[U];
+    int kk[U];
+#pragma unroll
+    for (int v = 0; v < U; ++v) {
+      const uint32_t e = e0 + 32u * v + (uint32_t)lane, g = w0 + e;
+      // stencil cell of candidate g: the last k < 27 with pre_k <= g
+      int k = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t pk = __shfl_sync(0xffffffffu, pre, k + step);
+        if (k + step < 27 && pk <= g) k += step;
+      }
+      kk[v] = k;
+      const uint32_t tk = __shfl_sync(0xffffffffu, t0, k), pk = __shfl_sync(0xffffffffu, pre, k);
+      if (e < len) r[v] = rec[tk + (g - pk)];
+    }
+#pragma unroll
+    for (int v = 0; v < U; ++v) {
+      const uint32_t e = e0 + 32u * v + (uint32_t)lane;
+      if (e < len) {
+        const int k = kk[v];
+        Rec q = r[v];
+        q.x += (R)(k % 3 - 1) * csx;
+        q.y += (R)((k / 3) % 3 - 1) * csy;
+        q.z += (R)(k / 9 - 1) * csz;
+        stage[e] = q;
+      }
+    }
+  }
+}
+
+// One piece: the particles in sorted slots [lo, hi) of home cell `home`;
+// their pair forces (and energy shares) go to fw[0 .. hi - lo).
+template <typename R, bool EXCL>
+__device__ __forceinline__ void tile_piece(const DevArrays& A, const PairTab<R>& tab,
+                                           const typename RecT<R>::T* __restrict__ rec, typename RecT<R>::T* stage,
+                                           typename V4<R>::T* fw, uint32_t home, uint32_t lo,
+                                           uint32_t hi, int lane) {
+  using Rec = typename RecT<R>::T;
+  const uint32_t* __restrict__ start = A.start;
+  const SysDev& S = A.nsys == 1 ? A.sys[0] : A.sys[meta_sys(A.meta[A.stag[lo]])];
+  int cx, cy, cz;
+  cell_decode(S, home, cx, cy, cz);
+  // lane k < 27: stencil cell (dx, dy, dz) = (k % 3, k / 3 % 3, k / 9) - 1
+  uint32_t t0 = 0, cnt = 0;
+  if (lane < 27) {
+    int x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
+    bool ok = true;
+    if (x < 0 || x >= S.nc[0]) {
+      ok = ok && S.periodic[0];
+      x = (x + S.nc[0]) % S.nc[0];
+    }
+    if (y < 0 || y >= S.nc[1]) {
+      ok = ok && S.periodic[1];
+      y = (y + S.nc[1]) % S.nc[1];
+    }
+    if (z < 0 || z >= S.nc[2]) {
+      ok = ok && S.periodic[2];
+      z = (z + S.nc[2]) % S.nc[2];
+    }
+    if (ok) {
+      const uint32_t nb = cell_id(S, x, y, z);
+      t0 = start[nb];
+      cnt = start[nb + 1] - t0;
+    }
+  }
+  const R csx = sizeof(R) == 4 ? (R)S.cs_f[0] : (R)S.cs[0];
+  const R csy = sizeof(R) == 4 ? (R)S.cs_f[1] : (R)S.cs[1];
+  const R csz = sizeof(R) == 4 ? (R)S.cs_f[2] : (R)S.cs[2];
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const uint32_t pre = incl - cnt;
+  const uint32_t M = __shfl_sync(0xffffffffu, incl, 31);
+  // the home cell is stencil cell 13 (periodic axes have at least 3 cells,
+  // so no other stencil cell is the home cell); its first slot is t0 there
+  const uint32_t self0 = __shfl_sync(0xffffffffu, pre, 13) + lo - __shfl_sync(0xffffffffu, t0, 13);
+  const uint32_t p = hi - lo;  // 1..kTileSlots
+  const uint32_t P = p <= 1u ? 1u : 1u << (32 - __clz(p - 1u));
+  const uint32_t L = 32u / P;
+  const uint32_t g = (uint32_t)lane / L, lj = (uint32_t)lane % L;
+  const bool act = g < p;
+  const uint32_t s = lo + (act ? g : 0u);
+  const Rec ri = rec[s];
+  const uint32_t bi = RecT<R>::bits(ri);
+  const uint32_t ti = bi & 7u, moli = bi >> 3;
+  const uint32_t self = self0 + g;
+  R rcm = 0;  // largest squared cutoff of the particle's type
+#pragma unroll
+  for (int b = 0; b < kMaxTypes; ++b) rcm = max(rcm, tab.rc2[ti * kMaxTypes + b]);
+  R fx = 0, fy = 0, fz = 0, u = 0;
+  for (uint32_t w0 = 0; w0 < M; w0 += (uint32_t)tile_cap<R>()) {
+    const uint32_t len = min(M - w0, (uint32_t)tile_cap<R>());
+    __syncwarp();
+    tile_stage<R>(rec, stage, t0, pre, csx, csy, csz, w0, len, lane);
+    __syncwarp();
+    if (act) {
+      // the lane's candidates are e = lj + i L, i < ne
+      const uint32_t ne = len > lj ? (len - lj + L - 1u) / L : 0u;
+      for (uint32_t i0 = 0; i0 < ne; i0 += 32u) {
+        const uint32_t nseg = min(ne - i0, 32u);
+        uint32_t mask = 0;
+#pragma unroll 4
+        for (uint32_t i = 0; i < nseg; ++i) {
+          const Rec rj = stage[lj + (i0 + i) * L];
+          const R ddx = ri.x - rj.x, ddy = ri.y - rj.y, ddz = ri.z - rj.z;
+          const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+          if (r2 < rcm) mask |= 1u << i;
+        }
+        while (mask) {
+          const uint32_t e = lj + (i0 + (uint32_t)(__ffs(mask) - 1)) * L;
+          mask &= mask - 1u;
+          if (w0 + e == self) continue;
+          const Rec rj = stage[e];
+          const uint32_t bj = RecT<R>::bits(rj);
+          if (EXCL && (bj >> 3) == moli) continue;
+          const uint32_t qt = ti * kMaxTypes + (bj & 7u);
+          const R ddx = ri.x - rj.x, ddy = ri.y - rj.y, ddz = ri.z - rj.z;
+          const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+          if (r2 < tab.rc2[qt]) lj_term<R>(tab, qt, r2, ddx, ddy, ddz, fx, fy, fz, u);
+        }
+      }
+    }
+  }
+  for (uint32_t o = L >> 1; o > 0; o >>= 1) {
+    fx += __shfl_xor_sync(0xffffffffu, fx, o);
+    fy += __shfl_xor_sync(0xffffffffu, fy, o);
+    fz += __shfl_xor_sync(0xffffffffu, fz, o);
+    u += __shfl_xor_sync(0xffffffffu, u, o);
+  }
+  if (act && lj == 0) {
+    typename V4<R>::T q;
+    q.x = fx;
+    q.y = fy;
+    q.z = fz;
+    q.w = u;
+    fw[g] = q;
+  }
+  __syncwarp();  // the stage is rewritten for the next piece
+}
+
+template <typename R, bool BONDS, bool WALLS, bool EXCL>
+__global__ void __launch_bounds__(kTileWarps * 32, sizeof(R) == 4 ? 6 : 4) k_pair_cell(DevArrays A) {
+  using Rec = typename RecT<R>::T;
+  __shared__ PairTab<R> tab;
+  __shared__ Rec stage_all[kTileWarps][tile_cap<R>()];
+  __shared__ typename V4<R>::T f_all[kTileWarps][kTileSlots];
+  load_tab<R>(tab, A.types);
+  __syncthreads();
+  const int lane = (int)(threadIdx.x & 31u);
+  const uint32_t wib = threadIdx.x >> 5;
+  const Rec* __restrict__ rec = reinterpret_cast<const Rec*>(A.rec);
+  const uint64_t n = (uint64_t)A.n;
+  const uint64_t r0 = ((uint64_t)blockIdx.x * kTileWarps + wib) * kTileSlots;
+  if (r0 >= n) return;  // warp-uniform
+  const uint32_t r1 = (uint32_t)min(r0 + (uint64_t)kTileSlots, n);
+  const uint64_t s = r0 + (uint64_t)lane;
+  uint32_t c = 0;
+  bool first = false;
+  if (s < n) {
+    c = A.scell[s];
+    first = lane == 0 || A.scell[s - 1] != c;
+  }
+  uint32_t cut = __ballot_sync(0xffffffffu, first);  // piece starts: bit 0 is always set
+  while (cut) {
+    const int a = __ffs(cut) - 1;
+    cut &= cut - 1u;
+    const uint32_t lo = (uint32_t)r0 + (uint32_t)a;
+    const uint32_t hi = cut ? (uint32_t)r0 + (uint32_t)(__ffs(cut) - 1) : r1;
+    const uint32_t home = __shfl_sync(0xffffffffu, c, a);
+    tile_piece<R, EXCL>(A, tab, rec, stage_all[wib], f_all[wib] + (lo - (uint32_t)r0), home, lo, hi, lane);
+  }
+  if (s < n) {  // the pieces' leaders wrote f_all before the last __syncwarp
+    const typename V4<R>::T q = f_all[wib][lane];
+    R fx = q.x, fy = q.y, fz = q.z, u = q.w;
+    const uint32_t tag = A.stag[s];
+    if (BONDS || WALLS) {
+      const uint32_t m = A.meta[tag];
+      bonded_terms<R>(A, A.sys[meta_sys(m)], tag, m, BONDS, WALLS, fx, fy, fz, u);
+    }
+    store_f<R>(A.f, tag, fx, fy, fz, u);
+  }
+}
+
 // No pair term anywhere: only bonds and walls, in particle order.
 template <typename R>
 __global__ void k_nopair(DevArrays A, int bonds, int walls) {
@@ -2360,7 +2587,29 @@ static void pair_dispatch_l(const DevArrays& A, int bonds, int walls, int excl, 
 }
 
 template <typename R>
+static void pair_dispatch_cell(const DevArrays& A, int bonds, int walls, int excl, cudaStream_t st) {
+  const uint64_t per_cta = (uint64_t)kTileWarps * kTileSlots;
+  const unsigned g = (unsigned)std::max<uint64_t>(1, ((uint64_t)A.n + per_cta - 1) / per_cta);
+  const int b = kTileWarps * 32;
+  const int key = (bonds ? 4 : 0) | (walls ? 2 : 0) | (excl ? 1 : 0);
+  switch (key) {
+    case 0: k_pair_cell<R, false, false, false><<<g, b, 0, st>>>(A); break;
+    case 1: k_pair_cell<R, false, false, true><<<g, b, 0, st>>>(A); break;
+    case 2: k_pair_cell<R, false, true, false><<<g, b, 0, st>>>(A); break;
+    case 3: k_pair_cell<R, false, true, true><<<g, b, 0, st>>>(A); break;
+    case 4: k_pair_cell<R, true, false, false><<<g, b, 0, st>>>(A); break;
+    case 5: k_pair_cell<R, true, false, true><<<g, b, 0, st>>>(A); break;
+    case 6: k_pair_cell<R, true, true, false><<<g, b, 0, st>>>(A); break;
+    default: k_pair_cell<R, true, true, true><<<g, b, 0, st>>>(A); break;
+  }
+}
+
+template <typename R>
 static void pair_dispatch(const DevArrays& A, int bonds, int walls, int excl, int lanes, cudaStream_t st) {
+  if (A.pair_tile && !A.hashed) {
+    pair_dispatch_cell<R>(A, bonds, walls, excl, st);
+    return;
+  }
   switch (lanes) {
     case 2: pair_dispatch_l<R, 2>(A, bonds, walls, excl, st); break;
     case 4: pair_dispatch_l<R, 4>(A, bonds, walls, excl, st); break;

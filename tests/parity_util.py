@@ -22,8 +22,11 @@ def force_err(f_gpu, f_ref):
     return float(np.max(np.linalg.norm(f_gpu - f_ref, axis=1) / scale)) if len(f_ref) else 0.0
 
 
-def gpu_run(systems, nsteps, step0=0, chunks=None):
+def gpu_run(systems, nsteps, step0=0, chunks=None, opts=None):
     sim = md.Simulation(systems)
+    for key, val in (opts or {}).items():
+        md.md_set_option(sim.h, key, val)
+        assert md.md_get_option(sim.h, key) == val
     sim.set_state(step0)
     for k in (chunks or [nsteps]):
         if k:
