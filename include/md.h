@@ -286,14 +286,16 @@ int md_step(md_handle* h, int64_t nsteps);
  * default 256); longer md_step calls are split into several launches. */
 #define MD_OPT_RESIDENT_STEPS 5
 /* MD_OPT_PAIR_TILE: 0 (default) = the pair kernel runs one particle per
- * thread (or MD_OPT_PAIR_LANES lanes per particle); 1 = cell-tiled: one warp
- * per occupied cell copies the records of the cell's 27-cell stencil into
- * shared memory once and the cell's particles share the warp's lanes over
- * that list (MD_OPT_PAIR_LANES and MD_OPT_PAIR_ORDER are then unused). Pays
- * where cells hold several particles (long cutoffs, dense 3D systems). Only
- * for handles whose buckets are the cell ids (grids of at most max(2^20, 4N)
- * cells; else MD_ERR_INVALID_ARG). Forces agree with the other settings to
- * float rounding (summation order differs). */
+ * thread (or MD_OPT_PAIR_LANES lanes per particle); 8, 16 or 32 = cell-tiled:
+ * each warp takes that many consecutive sorted particles, split at cell
+ * boundaries; for each piece it copies the records of the home cell's
+ * 27-cell stencil into shared memory once and the piece's particles share
+ * the warp's lanes over that list (MD_OPT_PAIR_LANES and MD_OPT_PAIR_ORDER
+ * are then unused). Pays where cells hold several particles (long cutoffs,
+ * dense 3D systems); fewer particles per warp give more warps to small
+ * systems. Only for handles whose buckets are the cell ids (grids of at most
+ * max(2^20, 4N) cells; else MD_ERR_INVALID_ARG). Forces agree with the other
+ * settings to float rounding (summation order differs). */
 #define MD_OPT_PAIR_TILE 6
 int md_set_option(md_handle* h, int32_t key, int64_t value);
 int md_get_option(md_handle* h, int32_t key, int64_t* value);

@@ -1096,8 +1096,9 @@ int md_set_option(md_handle* h, int32_t key, int64_t value) {
       h->res_steps_per_launch = value;
       break;
     case MD_OPT_PAIR_TILE:
-      if (value != 0 && value != 1) return fail(h, MD_ERR_INVALID_ARG, "pair tile must be 0 or 1");
-      if (value == 1 && h->has_pairs && h->A.hashed)
+      if (value != 0 && value != 8 && value != 16 && value != 32)
+        return fail(h, MD_ERR_INVALID_ARG, "pair tile must be 0, 8, 16 or 32");
+      if (value != 0 && h->has_pairs && h->A.hashed)
         return fail(h, MD_ERR_INVALID_ARG, "the cell-tiled pair kernel needs a grid of at most max(2^20, 4N) cells");
       h->A.pair_tile = (int32_t)value;
       break;

@@ -918,16 +918,100 @@ __device__ __forceinline__ void bend_on(const DevArrays& A, const SysDev& S, int
 
 __device__ __forceinline__ bool has_bends(const SysDev& S) { return S.bpm > 2 && S.angle_k != 0.0; }
 
-// Bonded and wall terms of particle `tag`, in float64 on both paths (the bond
-// stretch r - r0 cancels, r being close to r0, and the stiffness would
-// amplify float32 rounding): bonds V = k (r - r0)^2 (no factor 1/2) to the
-// chain neighbours, r0 from the bead types when bond_mix is set, and the wall
-// V_w (two z planes, or a sphere about wall_center) on unconstrained
-// particles. The particle's energy share is half of each bond and all of its
-// wall term.
+// Bonded and wall terms of particle `tag`: bonds V = k (r - r0)^2 (no factor
+// 1/2) to the chain neighbours, r0 from the bead types when bond_mix is set,
+// and the wall V_w (two z planes, or a sphere about wall_center) on
+// unconstrained particles. The particle's energy share is half of each bond
+// and all of its wall term. The float64 path works in float64 throughout.
+// The mixed path forms in float64 only what cancels: the displacement, r^2
+// and r^2 - r0^2 (the stretch r - r0 is small against r), the wall distance,
+// or r^2 - R_w^2 for the spherical wall; then r - r0 = (r^2 - r0^2) / (r + r0)
+// and the rest in float32, where the rounding of r enters denominators only.
+__device__ __forceinline__ void bonded_terms_f(const DevArrays& A, const SysDev& S, uint32_t tag, uint32_t m,
+                                               bool bonds, bool walls, float& fx, float& fy, float& fz,
+                                               float& u) {
+  const int64_t n = A.n;
+  const double xi[3] = {A.x[tag], A.x[n + tag], A.x[2 * n + tag]};
+  float bx = 0.f, by = 0.f, bz = 0.f, bu = 0.f;
+  if (bonds && S.bpm > 1) {
+    const int64_t pid = (int64_t)tag - S.first;
+    const int64_t B = S.bpm;
+    const float k = (float)S.bond_k;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      int64_t j;
+      if (side == 0) {
+        if (pid % B == 0) continue;
+        j = (int64_t)tag - 1;
+      } else {
+        if (pid % B == B - 1 || pid + 1 >= S.n) continue;
+        j = (int64_t)tag + 1;
+      }
+      const double xj[3] = {A.x[j], A.x[n + j], A.x[2 * n + j]};
+      double d[3];
+      min_image_diff(S, xi, xj, d);
+      const double r2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]));
+      const double r0 = S.bond_mix ? A.types->bond_r0_mix[meta_type(m)][meta_type(A.meta[j])] : S.bond_r0;
+      const float q = d2f_rn(fma(-r0, r0, r2));  // r^2 - r0^2
+      const float r2f = d2f_rn(r2);
+      const float ir = rsqrtf(r2f);
+      const float dr = __fdividef(q, fmaf(r2f, ir, (float)r0));  // r - r0
+      const float fo = -2.f * k * dr * ir;
+      bx = fmaf(fo, d2f_rn(d[0]), bx);
+      by = fmaf(fo, d2f_rn(d[1]), by);
+      bz = fmaf(fo, d2f_rn(d[2]), bz);
+      bu = fmaf(0.5f * k * dr, dr, bu);
+    }
+  }
+  if (walls && S.wall && !meta_con(m)) {
+    const float eps = (float)S.wall_eps, sig2 = (float)(S.wall_sigma * S.wall_sigma);
+    if (S.wall_kind == 1) {
+      const double d0 = xi[0] - S.wall_center[0], d1 = xi[1] - S.wall_center[1], d2 = xi[2] - S.wall_center[2];
+      const double r2 = fma(d0, d0, fma(d1, d1, d2 * d2));
+      const float q = d2f_rn(fma(-S.wall_radius, S.wall_radius, r2));  // r^2 - R_w^2
+      const float r2f = d2f_rn(r2);
+      const float ir = rsqrtf(r2f);
+      const float h = __fdividef(q, fmaf(r2f, ir, (float)S.wall_radius));  // r - R_w
+      if (!(h > 0.f)) {
+        flag(A.status, kFlagOutOfGrid);
+      } else if (h < (float)S.wall_rc) {
+        const float ih = __fdividef(1.f, h);
+        const float s2 = sig2 * ih * ih;
+        const float s6 = s2 * s2 * s2;
+        const float fr = 24.f * eps * (2.f * s6 * s6 - s6) * ih * ir;
+        bx = fmaf(fr, d2f_rn(d0), bx);
+        by = fmaf(fr, d2f_rn(d1), by);
+        bz = fmaf(fr, d2f_rn(d2), bz);
+        bu += 4.f * eps * (s6 * s6 - s6 + 0.25f);
+      }
+    } else {
+      const double dist[2] = {xi[2] - S.wall_lo, S.wall_hi - xi[2]};
+#pragma unroll
+      for (int w = 0; w < 2; ++w) {
+        if (!(dist[w] > 0.0)) {
+          flag(A.status, kFlagOutOfGrid);
+          continue;
+        }
+        if (dist[w] >= S.wall_rc) continue;
+        const float ir = __fdividef(1.f, d2f_rn(dist[w]));
+        const float s2 = sig2 * ir * ir;
+        const float s6 = s2 * s2 * s2;
+        const float fr = 24.f * eps * (2.f * s6 * s6 - s6) * ir;
+        bz += (w == 0) ? fr : -fr;
+        bu += 4.f * eps * (s6 * s6 - s6 + 0.25f);
+      }
+    }
+  }
+  fx += bx; fy += by; fz += bz; u += bu;
+}
+
 template <typename R>
 __device__ __forceinline__ void bonded_terms(const DevArrays& A, const SysDev& S, uint32_t tag, uint32_t m,
                                              bool bonds, bool walls, R& fx, R& fy, R& fz, R& u) {
+  if constexpr (sizeof(R) == 4) {
+    bonded_terms_f(A, S, tag, m, bonds, walls, fx, fy, fz, u);
+    return;
+  }
   const int64_t n = A.n;
   const double xi[3] = {A.x[tag], A.x[n + tag], A.x[2 * n + tag]};
   double bx = 0.0, by = 0.0, bz = 0.0, bu = 0.0;
@@ -1242,21 +1326,21 @@ __global__ void __launch_bounds__(256) k_pair_lanes(DevArrays A) {
 
 // ---------------------------------------------------------------------------
 // Cell-tiled pair kernel (bucket = cell id, no hashing). Warp w evaluates
-// the particles of its run of kTileSlots sorted slots, one cell at a time:
-// the run splits at cell boundaries into pieces of p <= kTileSlots particles
+// the particles of its run of A.pair_tile (8, 16 or 32) sorted slots, one
+// cell at a time: the run splits at cell boundaries into pieces of p particles
 // of one home cell. For each piece the warp stages the records of the home
 // cell's 27-cell stencil in shared memory, each shifted into the frame of the
-// home cell, and the piece's particles share the lanes: P = p rounded up to a
-// power of two groups of 32/P lanes, lane j of a group walking the staged
-// candidates j, j + 32/P, ...; a fixed xor-shuffle tree adds each group's
-// partial sums. A candidate's record is read from global memory once per
+// home cell, and the piece's particles share the lanes: p groups of
+// L = floor(32/p) lanes, lane j of a group walking the staged candidates j,
+// j + L, ...; a fixed segmented shuffle tree adds each group's partial
+// sums. A candidate's record is read from global memory once per
 // piece instead of once per particle, the stencil's bucket bounds once per
 // piece, and the lanes walk one shared list in step; every warp has the same
 // number of particles whatever the cells' occupancy. The pieces leave their
 // pair forces in shared memory; then every lane adds the bonded terms of its
 // own slot and stores the force, so the float64 bond arithmetic runs on all
-// 32 lanes at once (the float64 pipe costs the same per warp instruction
-// whatever the number of active lanes).
+// the run's lanes at once (the float64 pipe costs the same per warp
+// instruction whatever the number of active lanes).
 // Each lane tests a segment of 32 of its candidates against the home
 // particle's largest cutoff first, one bit per hit in a register mask, then
 // evaluates the pair terms over the set bits (self and same-molecule pairs
@@ -1264,7 +1348,7 @@ __global__ void __launch_bounds__(256) k_pair_lanes(DevArrays A) {
 // together instead of once per candidate that any lane finds in range.
 // ---------------------------------------------------------------------------
 constexpr int kTileWarps = 4;   // warps per CTA
-constexpr int kTileSlots = 32;  // sorted slots (particles) per warp: one per lane
+constexpr int kTileSlots = 32;  // most sorted slots (particles) per warp: one per lane
 // staged candidates per warp and window (256 float4 or 128 double4 records,
 // 4 KB a warp)
 template <typename R> constexpr int tile_cap() { return sizeof(R) == 4 ? 256 : 128; }
@@ -1361,9 +1445,8 @@ __device__ __forceinline__ void tile_piece(const DevArrays& A, const PairTab<R>&
   // so no other stencil cell is the home cell); its first slot is t0 there
   const uint32_t self0 = __shfl_sync(0xffffffffu, pre, 13) + lo - __shfl_sync(0xffffffffu, t0, 13);
   const uint32_t p = hi - lo;  // 1..kTileSlots
-  const uint32_t P = p <= 1u ? 1u : 1u << (32 - __clz(p - 1u));
-  const uint32_t L = 32u / P;
-  const uint32_t g = (uint32_t)lane / L, lj = (uint32_t)lane % L;
+  const uint32_t L = 32u / p;  // lanes per particle: p L of the 32 lanes work
+  const uint32_t g = (uint32_t)lane / L, lj = (uint32_t)lane - g * L;
   const bool act = g < p;
   const uint32_t s = lo + (act ? g : 0u);
   const Rec ri = rec[s];
@@ -1407,11 +1490,17 @@ __device__ __forceinline__ void tile_piece(const DevArrays& A, const PairTab<R>&
       }
     }
   }
-  for (uint32_t o = L >> 1; o > 0; o >>= 1) {
-    fx += __shfl_xor_sync(0xffffffffu, fx, o);
-    fy += __shfl_xor_sync(0xffffffffu, fy, o);
-    fz += __shfl_xor_sync(0xffffffffu, fz, o);
-    u += __shfl_xor_sync(0xffffffffu, u, o);
+  // segmented tree: after offset o, lane j of a group holds the sum of its
+  // group's lanes j .. min(j + 2o, L) - 1; lane 0 ends with the group's sum
+  for (uint32_t o = 1; o < L; o <<= 1) {
+    const R ox = __shfl_down_sync(0xffffffffu, fx, o), oy = __shfl_down_sync(0xffffffffu, fy, o);
+    const R oz = __shfl_down_sync(0xffffffffu, fz, o), ou = __shfl_down_sync(0xffffffffu, u, o);
+    if (lj + o < L) {
+      fx += ox;
+      fy += oy;
+      fz += oz;
+      u += ou;
+    }
   }
   if (act && lj == 0) {
     typename V4<R>::T q;
@@ -1436,13 +1525,15 @@ __global__ void __launch_bounds__(kTileWarps * 32, sizeof(R) == 4 ? 6 : 4) k_pai
   const uint32_t wib = threadIdx.x >> 5;
   const Rec* __restrict__ rec = reinterpret_cast<const Rec*>(A.rec);
   const uint64_t n = (uint64_t)A.n;
-  const uint64_t r0 = ((uint64_t)blockIdx.x * kTileWarps + wib) * kTileSlots;
+  const uint32_t slots = (uint32_t)A.pair_tile;  // 8, 16 or 32 particles per warp
+  const uint64_t r0 = ((uint64_t)blockIdx.x * kTileWarps + wib) * slots;
   if (r0 >= n) return;  // warp-uniform
-  const uint32_t r1 = (uint32_t)min(r0 + (uint64_t)kTileSlots, n);
+  const uint32_t r1 = (uint32_t)min(r0 + (uint64_t)slots, n);
   const uint64_t s = r0 + (uint64_t)lane;
+  const bool mine = (uint32_t)lane < slots && s < n;
   uint32_t c = 0;
   bool first = false;
-  if (s < n) {
+  if (mine) {
     c = A.scell[s];
     first = lane == 0 || A.scell[s - 1] != c;
   }
@@ -1455,7 +1546,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, sizeof(R) == 4 ? 6 : 4) k_pai
     const uint32_t home = __shfl_sync(0xffffffffu, c, a);
     tile_piece<R, EXCL>(A, tab, rec, stage_all[wib], f_all[wib] + (lo - (uint32_t)r0), home, lo, hi, lane);
   }
-  if (s < n) {  // the pieces' leaders wrote f_all before the last __syncwarp
+  if (mine) {  // the pieces' leaders wrote f_all before the last __syncwarp
     const typename V4<R>::T q = f_all[wib][lane];
     R fx = q.x, fy = q.y, fz = q.z, u = q.w;
     const uint32_t tag = A.stag[s];
@@ -2588,7 +2679,7 @@ static void pair_dispatch_l(const DevArrays& A, int bonds, int walls, int excl, 
 
 template <typename R>
 static void pair_dispatch_cell(const DevArrays& A, int bonds, int walls, int excl, cudaStream_t st) {
-  const uint64_t per_cta = (uint64_t)kTileWarps * kTileSlots;
+  const uint64_t per_cta = (uint64_t)kTileWarps * (uint64_t)A.pair_tile;
   const unsigned g = (unsigned)std::max<uint64_t>(1, ((uint64_t)A.n + per_cta - 1) / per_cta);
   const int b = kTileWarps * 32;
   const int key = (bonds ? 4 : 0) | (walls ? 2 : 0) | (excl ? 1 : 0);

@@ -130,7 +130,7 @@ struct DevArrays {
   int32_t hashed;       // 0: bucket = cell id; 1: hashed buckets
   int32_t log_t;
   int32_t pair_lanes;   // lanes per particle in the pair kernel (1, 2, 4 or 8)
-  int32_t pair_tile;    // 1: cell-tiled pair kernel, one warp per occupied cell (needs hashed == 0)
+  int32_t pair_tile;    // 0, or particles per warp (8, 16, 32) of the cell-tiled pair kernel (needs hashed == 0)
   int32_t rec_cell;     // 1: a record's w word holds type | cell << 3 (no exclusions,
                         // cells < 2^29), so the pair kernel needs no sorted-cell load;
                         // 0: type | molecule << 3

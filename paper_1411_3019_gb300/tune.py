@@ -5,7 +5,8 @@ applies the fastest:
 
 * the global engine (one graph of five kernels per step) with every
   combination of the pair kernel's visiting order and lanes per particle,
-  and with the cell-tiled pair kernel where the grid allows it, one step per
+  and with the cell-tiled pair kernel at 32, 16 and 8 particles per warp
+  where the grid allows it, one step per
   trial after an L2 flush (as the benchmark times it);
 * the resident engine (one persistent launch, one CTA per system), if the
   systems fit it, for several CTA sizes, a run of `resident_steps` steps per
@@ -29,6 +30,7 @@ from . import md
 
 GLOBAL_OPTIONS = {md.MD_OPT_PAIR_ORDER: (1, 0), md.MD_OPT_PAIR_LANES: (1, 2, 4)}
 RESIDENT_THREADS = (0, 256, 128)  # 0: chosen per size class
+TILE_SLOTS = (32, 16, 8)  # particles per warp of the cell-tiled pair kernel
 NAMES = {md.MD_OPT_PAIR_ORDER: "pair_order", md.MD_OPT_PAIR_LANES: "pair_lanes", md.MD_OPT_ENGINE: "engine",
          md.MD_OPT_RESIDENT_THREADS: "resident_threads", md.MD_OPT_PAIR_TILE: "pair_tile"}
 
@@ -47,8 +49,8 @@ def candidates(h):
         out.append({md.MD_OPT_ENGINE: 0, md.MD_OPT_PAIR_TILE: 0, **dict(zip(opts, combo))})
     md.md_set_option(h, md.MD_OPT_ENGINE, 0)
     try:
-        md.md_set_option(h, md.MD_OPT_PAIR_TILE, 1)
-        out.append({md.MD_OPT_ENGINE: 0, md.MD_OPT_PAIR_TILE: 1})
+        md.md_set_option(h, md.MD_OPT_PAIR_TILE, TILE_SLOTS[0])
+        out.extend({md.MD_OPT_ENGINE: 0, md.MD_OPT_PAIR_TILE: t} for t in TILE_SLOTS)
     except md.MdError:
         pass  # buckets are hashed: no cell-tiled kernel
     finally:

@@ -74,7 +74,7 @@ def test_switching_options_mid_run_keeps_the_trajectory():
 
 def test_bad_option_values_are_rejected():
     sim = md.Simulation(_systems("mixed"))
-    for key, val in ((md.MD_OPT_PAIR_LANES, 3), (md.MD_OPT_PAIR_ORDER, 2), (md.MD_OPT_PAIR_TILE, 2), (99, 1)):
+    for key, val in ((md.MD_OPT_PAIR_LANES, 3), (md.MD_OPT_PAIR_ORDER, 2), (md.MD_OPT_PAIR_TILE, 1), (md.MD_OPT_PAIR_TILE, 2), (99, 1)):
         with pytest.raises(md.MdError):
             md.md_set_option(sim.h, key, val)
     sim.close()
@@ -87,14 +87,15 @@ def test_autotuner_applies_a_valid_choice_and_keeps_parity(tmp_path):
     cache = str(tmp_path / "tune.json")
     out = tune.autotune(sim.h, trials=1, cache=cache)
     # six global settings (visiting order x lanes), the cell-tiled pair kernel
-    # (these small grids have cell-id buckets) and three resident CTA sizes
-    assert len(out["trials"]) == 10 and out["trials"][0]["ms"] == out["best_ms"]
-    assert sorted(t["engine"] for t in out["trials"]) == [0] * 7 + [1] * 3
-    assert sum(t.get("pair_tile", 0) for t in out["trials"]) == 1
+    # at three run lengths (these small grids have cell-id buckets) and three
+    # resident CTA sizes
+    assert len(out["trials"]) == 12 and out["trials"][0]["ms"] == out["best_ms"]
+    assert sorted(t["engine"] for t in out["trials"]) == [0] * 9 + [1] * 3
+    assert sorted(t.get("pair_tile", 0) for t in out["trials"] if t.get("pair_tile")) == [8, 16, 32]
     opts = out["options"]
     assert md.md_get_option(sim.h, md.MD_OPT_ENGINE) == opts["engine"]
-    if opts["engine"] == 0 and opts["pair_tile"] == 1:
-        assert md.md_get_option(sim.h, md.MD_OPT_PAIR_TILE) == 1
+    if opts["engine"] == 0 and opts["pair_tile"]:
+        assert md.md_get_option(sim.h, md.MD_OPT_PAIR_TILE) == opts["pair_tile"]
     elif opts["engine"] == 0:
         assert opts["pair_order"] in (0, 1) and opts["pair_lanes"] in (1, 2, 4)
         assert md.md_get_option(sim.h, md.MD_OPT_PAIR_ORDER) == opts["pair_order"]

@@ -6,7 +6,8 @@ hold one to several dozen particles: bead molecules on a spherical template
 (bonds, exclusions, Lennard-Jones r_c = 2.5; runs spanning several cells), a
 Gaussian bump with free crowders between walls (periodic x, y), and a dense
 periodic Lennard-Jones lattice with r_c = 4 (64 particles per cell, shared
-by eight warps; stencils of 1,728 candidates, seven shared-memory windows).
+by several warps; stencils of 1,728 candidates, seven shared-memory windows),
+at 8, 16 and 32 particles per warp.
 Forces at the start and after a trajectory, the trajectory itself, and the
 option's refusal where buckets are hashed."""
 import numpy as np
@@ -19,7 +20,7 @@ from parity_util import POS_100, assert_forces, gpu_run, oracle_run
 
 pytestmark = pytest.mark.gpu
 
-TILE = {md.MD_OPT_PAIR_TILE: 1}
+TILE = {md.MD_OPT_PAIR_TILE: 32}
 
 
 def _tol(precision):
@@ -41,22 +42,24 @@ def _lattice(precision, k=12, a=1.0833, rc=4.0, seed=3):
     return [I._system("lj_lattice", surf, prm, x, I.maxwell(x.shape[0], 1.0, 1.0, g))]
 
 
-def _check(systems, precision, nsteps):
-    st0, f0, u0, _, _ = gpu_run(systems, 0, opts=TILE)
+def _check(systems, precision, nsteps, slots=32):
+    opts = {md.MD_OPT_PAIR_TILE: slots}
+    st0, f0, u0, _, _ = gpu_run(systems, 0, opts=opts)
     assert_forces(systems, st0["x"], f0, precision)
     _, _, u_ref, _, _ = oracle_run(systems, 0)
     np.testing.assert_allclose(u0.sum(), u_ref.sum(), rtol=1e-10 if precision == "fp64" else 1e-5)
-    st, f, _, res, _ = gpu_run(systems, nsteps, opts=TILE)
+    st, f, _, res, _ = gpu_run(systems, nsteps, opts=opts)
     ref = oracle_run(systems, nsteps)[0]
     assert np.abs(st["x"] - ref["x"]).max() <= POS_100[precision]
     assert_forces(systems, st["x"], f, precision)
     return st, res
 
 
+@pytest.mark.parametrize("slots", [8, 16, 32])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_bead_molecules(precision):
+def test_bead_molecules(precision, slots):
     systems = I.c5_bead_molecules(nmol=300, beads=5, R=10.0, seed=4, precision=precision, tol=_tol(precision))
-    _check(systems, precision, 60)
+    _check(systems, precision, 60, slots)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -66,9 +69,10 @@ def test_bump_with_crowders_and_walls(precision):
     assert res["max_g_over_gradg"] < 10 * _tol(precision)
 
 
+@pytest.mark.parametrize("slots", [8, 32])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_dense_lattice_with_several_windows_and_batches(precision):
-    _check(_lattice(precision), precision, 30)
+def test_dense_lattice_with_several_windows(precision, slots):
+    _check(_lattice(precision), precision, 30, slots)
 
 
 def test_batch_of_systems_and_default_agree():
@@ -95,6 +99,6 @@ def test_hashed_grid_refuses_the_tiled_kernel():
     x = I.rsa(lambda k, m: I.sample_surface(surf, m, g), [200], 1.0, g)[0]
     sim = md.Simulation([I._system("sphere_big_box", surf, prm, x, I.maxwell(200, 1.0, 1.0, g))])
     with pytest.raises(md.MdError):
-        md.md_set_option(sim.h, md.MD_OPT_PAIR_TILE, 1)
+        md.md_set_option(sim.h, md.MD_OPT_PAIR_TILE, 32)
     assert md.md_get_option(sim.h, md.MD_OPT_PAIR_TILE) == 0
     sim.close()
