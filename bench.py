@@ -40,7 +40,7 @@ METRIC = ("particle-steps/sec on 1 GB300 (FP32-force/FP64-RATTLE vs plain FP64) 
 UNIT = "particle-steps/s"
 L2_FLUSH_BYTES = 256 << 20  # larger than the 129 MB L2
 WORKLOADS = ("ellipsoid_torus", "plain_sphere", "replicas", "bead_molecules", "bump_crowders", "nve_surfaces",
-             "capsids", "sphere_vs_2d", "thylakoids")
+             "capsids", "sphere_vs_2d", "thylakoids", "lj_lattice")
 # float64 pipe of one GB300: 152 SMs x 2 float64 operations per SM per clock
 FP64_OPS_PER_SM_CLK = 2
 SMS = 152
@@ -60,6 +60,9 @@ def parse(argv=None):
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch options")
     ap.add_argument("--engine", default="auto", choices=["auto", "global", "resident"],
                     help="auto: the autotuner picks the engine and its options")
+    ap.add_argument("--pair-tile", type=int, default=None, choices=[0, 8, 16, 32],
+                    help="global engine with this cell-tiled pair kernel setting (0: per-particle rows) "
+                         "instead of the autotuner's choice")
     ap.add_argument("--nrep", type=int, default=4096, help="systems of the replicas workload")
     ap.add_argument("--pair-form", type=int, default=1, choices=[0, 1],
                     help="nve_surfaces: 0 truncated-shifted, 1 linearly smoothed Lennard-Jones")
@@ -107,6 +110,9 @@ def workload(name: str, rank: int, precision: str, nrep: int = 4096, pair_form: 
     if name == "nve_surfaces":
         return inputs.nve_systems(pair_form, seed=seed, precision=precision,
                                   tol=1e-12 if precision == "fp64" else 1e-10)
+    if name == "lj_lattice":  # dense free LJ liquid, 97,336 particles, rc = 2.5 (pair-kernel stress case)
+        return inputs.lj_lattice(46, seed=seed + 2, precision=precision,
+                                 tol=1e-12 if precision == "fp64" else 1e-10)
     raise ValueError(name)
 
 
@@ -368,6 +374,9 @@ def main(argv=None):
     if args.engine == "resident":
         md.md_set_option(sim.h, md.MD_OPT_ENGINE, 1)
         tuned = {"options": {"engine": 1, "resident_threads": md.md_get_option(sim.h, md.MD_OPT_RESIDENT_THREADS)}}
+    elif args.pair_tile is not None:
+        md.md_set_option(sim.h, md.MD_OPT_PAIR_TILE, args.pair_tile)
+        tuned = {"options": {**tuned["options"], "pair_tile": args.pair_tile}}
     elif args.engine == "auto" and not args.no_tune:
         with torch.cuda.stream(stream):  # launch options chosen by the autotuner during warm-up
             tuned = tune.autotune(sim.h, trials=3, flush=lambda: flush.add_(1.0))

@@ -231,6 +231,8 @@ int check_system(const md_surface& s, const md_params& p, SysDev& S, std::string
   S.wall_eps = p.wall_eps;
   S.angle_k = p.angle_k;
   S.angle_theta0 = p.angle_theta0;
+  S.angle_sin0 = std::sin(p.angle_theta0);
+  S.angle_cos0 = std::cos(p.angle_theta0);
   S.bond_mix = p.bond_r0_mix;
   S.wall_kind = p.wall_kind;
   S.wall_radius = p.wall_radius;

@@ -893,25 +893,65 @@ __device__ __forceinline__ double bend_term(const SysDev& S, const double* xa, c
   return S.angle_k * dth * dth;
 }
 
-// Bend angles of particle `tag` (float64): the force on it from every angle
+// The bend term on the mixed path. Float64 forms what cancels: u, w, the
+// cross product C = u x w, u.w, |C| and the two arguments of
+// dth = atan2(sin(theta - theta0), cos(theta - theta0)) (both scaled by
+// |u||w|), so dth keeps float32's relative precision even near theta0 and near
+// a straight chain. Float32 does the rest, with the brackets written without
+// cancellation: w - (u.w / |u|^2) u = (C x u) / |u|^2 and
+// u - (u.w / |w|^2) w = (w x C) / |w|^2.
+__device__ __forceinline__ float bend_term_f(const SysDev& S, const double* xa, const double* xm, const double* xb,
+                                             int which, float f[3]) {
+  double u[3], w[3];
+  min_image_diff(S, xa, xm, u);
+  min_image_diff(S, xb, xm, w);
+  const double C[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+  const double uw = fma(u[0], w[0], fma(u[1], w[1], u[2] * w[2]));
+  const double CC = fma(C[0], C[0], fma(C[1], C[1], C[2] * C[2]));
+  const double sn = CC > 0.0 ? CC * nr_rsqrt(CC) : 0.0;  // |u||w| sin(theta)
+  const float dth = atan2f(d2f_rn(fma(sn, S.angle_cos0, -uw * S.angle_sin0)),
+                           d2f_rn(fma(uw, S.angle_cos0, sn * S.angle_sin0)));  // theta - theta0
+  const float uf[3] = {d2f_rn(u[0]), d2f_rn(u[1]), d2f_rn(u[2])};
+  const float wf[3] = {d2f_rn(w[0]), d2f_rn(w[1]), d2f_rn(w[2])};
+  const float Cf[3] = {d2f_rn(C[0]), d2f_rn(C[1]), d2f_rn(C[2])};
+  const float uu = fmaf(uf[0], uf[0], fmaf(uf[1], uf[1], uf[2] * uf[2]));
+  const float ww = fmaf(wf[0], wf[0], fmaf(wf[1], wf[1], wf[2] * wf[2]));
+  const float inv_norm = rsqrtf(uu * ww);
+  const float sth = d2f_rn(sn) * inv_norm;
+  const float k = (float)S.angle_k;
+  const float ratio = sth > 0.f ? __fdividef(2.f * k * dth, sth) : 0.f;
+  const float ga = __fdividef(ratio * inv_norm, uu), gb = __fdividef(ratio * inv_norm, ww);
+  const float fa[3] = {ga * (Cf[1] * uf[2] - Cf[2] * uf[1]), ga * (Cf[2] * uf[0] - Cf[0] * uf[2]),
+                       ga * (Cf[0] * uf[1] - Cf[1] * uf[0])};
+  const float fb[3] = {gb * (wf[1] * Cf[2] - wf[2] * Cf[1]), gb * (wf[2] * Cf[0] - wf[0] * Cf[2]),
+                       gb * (wf[0] * Cf[1] - wf[1] * Cf[0])};
+#pragma unroll
+  for (int q = 0; q < 3; ++q) f[q] = which == 0 ? fa[q] : (which == 2 ? fb[q] : -(fa[q] + fb[q]));
+  return k * dth * dth;
+}
+
+// Bend angles of particle `tag` (float64 on the float64 path, float32 after
+// float64 bond vectors on the mixed path): the force on it from every angle
 // of three consecutive beads of its chain that contains it, and its energy
 // share (a third of each angle). Kept out of the pair kernels (its registers
 // would lower their occupancy): k_bend and a phase of the resident engine add
 // it to the particle's force after the pair kernel.
-__device__ __forceinline__ void bend_on(const DevArrays& A, const SysDev& S, int64_t tag, double f[3], double& v) {
+template <typename R>
+__device__ __forceinline__ void bend_on(const DevArrays& A, const SysDev& S, int64_t tag, R f[3], R& v) {
   const int64_t n = A.n;
   const int64_t pid = tag - S.first;
   const int64_t B = S.bpm;
-  f[0] = f[1] = f[2] = 0.0;
-  v = 0.0;
+  f[0] = f[1] = f[2] = (R)0;
+  v = (R)0;
   for (int64_t mid = pid - 1; mid <= pid + 1; ++mid) {  // middle bead of each angle containing the particle
     if (mid < 1 || mid + 1 >= S.n || mid % B == 0 || mid % B == B - 1) continue;
     const int64_t gm = S.first + mid;
     const double xa[3] = {A.x[gm - 1], A.x[n + gm - 1], A.x[2 * n + gm - 1]};
     const double xm[3] = {A.x[gm], A.x[n + gm], A.x[2 * n + gm]};
     const double xb[3] = {A.x[gm + 1], A.x[n + gm + 1], A.x[2 * n + gm + 1]};
-    double fa[3];
-    v += bend_term(S, xa, xm, xb, (int)(pid - mid + 1), fa) / 3.0;
+    R fa[3];
+    if constexpr (sizeof(R) == 4) v += bend_term_f(S, xa, xm, xb, (int)(pid - mid + 1), fa) * (1.f / 3.f);
+    else v += bend_term(S, xa, xm, xb, (int)(pid - mid + 1), fa) / 3.0;
     f[0] += fa[0]; f[1] += fa[1]; f[2] += fa[2];
   }
 }
@@ -1213,12 +1253,12 @@ __global__ void k_bend(DevArrays A) {
   if (i >= A.n) return;
   const SysDev& S = A.sys[meta_sys(A.meta[i])];
   if (!has_bends(S)) return;
-  double f[3], v;
-  bend_on(A, S, i, f, v);
+  R f[3], v;
+  bend_on<R>(A, S, i, f, v);
   using V = typename V4<R>::T;
   V* fv = reinterpret_cast<V*>(A.f);
   V q = fv[i];
-  q.x += (R)f[0]; q.y += (R)f[1]; q.z += (R)f[2]; q.w += (R)v;
+  q.x += f[0]; q.y += f[1]; q.z += f[2]; q.w += v;
   fv[i] = q;
 }
 
@@ -2255,11 +2295,11 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 2) k_resident(DevArrays A
       for (uint32_t e = tid; e <= T; e += bd) s_start[e] = 0u;  // the starts are not read again this step
       if (has_bends(S)) {
         for (uint32_t li = tid; li < n; li += bd) {
-          double f[3], v;
-          bend_on(A, S, first + li, f, v);
-          s_fx[li] += (R)f[0];
-          s_fy[li] += (R)f[1];
-          s_fz[li] += (R)f[2];
+          R f[3], v;
+          bend_on<R>(A, S, first + li, f, v);
+          s_fx[li] += f[0];
+          s_fy[li] += f[1];
+          s_fz[li] += f[2];
         }
       }
       __syncthreads();

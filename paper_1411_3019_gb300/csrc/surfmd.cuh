@@ -72,6 +72,7 @@ struct SysDev {
   double wall_lo, wall_hi, wall_eps, wall_sigma, wall_rc;
   // capsid-model terms: bend angles, type-dependent bond lengths, spherical wall
   double angle_k, angle_theta0;
+  double angle_sin0, angle_cos0;  // sin and cos of theta0
   int32_t bond_mix, wall_kind;
   double wall_radius, wall_center[3];
   // noise key, particle range

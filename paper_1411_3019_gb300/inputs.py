@@ -503,6 +503,23 @@ def nve_systems(pair_form: int, n: int = 500, phi: float = 0.3, seed: int = 1, p
     return out
 
 
+def lj_lattice(k: int = 46, a: float = 1.0833, rc: float = 2.5, seed: int = 3, precision: str = "mixed",
+               dt: float = 0.001, tol: float = 1e-10, jitter: float = 0.06) -> list:
+    """Dense free Lennard-Jones liquid (a stress case of the pair kernel, not
+    a workload of the paper): k^3 particles on a simple cubic lattice of
+    spacing a (density 1/a^3, 0.79 at a = 1.0833) moved by uniform jitter of
+    +-jitter, in a periodic cube of edge k a, cutoff rc, no surface."""
+    L = k * a
+    g = rng(seed, 21)
+    idx = np.stack(np.meshgrid(*[np.arange(k)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    x = (idx + 0.5) * a + g.uniform(-jitter, jitter, idx.shape) - L / 2
+    prm = wca_params(precision=precision, dt=dt, rattle_tol=tol, seed=seed,
+                     box_lo=(-L / 2,) * 3, box_hi=(L / 2,) * 3, periodic=(1, 1, 1))
+    prm["rcut"][0, 0] = rc
+    surf = {"kind": "none", "center": (0.0, 0.0, 0.0), "p": (0.0, 0.0, 0.0, 0.0)}
+    return [_system("lj_lattice", surf, prm, x, maxwell(x.shape[0], 1.0, 1.0, g))]
+
+
 def capsid_systems(nsys: int = 1, ncone: int = 60, sigma3: float = 1.75, seed: int = 1, precision: str = "mixed",
                    dt: float = 0.002, tol: float = 1e-10, dmin: float = 1.8, phi_base: float = 0.45):
     """Capsomere (cone) self-assembly on a spherical template, the capsid model

@@ -27,19 +27,10 @@ def _tol(precision):
     return 1e-12 if precision == "fp64" else 1e-10
 
 
-def _lattice(precision, k=12, a=1.0833, rc=4.0, seed=3):
-    """k^3 Lennard-Jones particles on a jittered simple cubic lattice of
-    spacing a (density 1/a^3 ~ 0.79) in a periodic box, cutoff rc: the box is
-    three cells of 4.33 along each axis, 64 particles per cell."""
-    L = k * a
-    g = I.rng(seed, 21)
-    idx = np.stack(np.meshgrid(*[np.arange(k)] * 3, indexing="ij"), -1).reshape(-1, 3)
-    x = (idx + 0.5) * a + g.uniform(-0.06, 0.06, idx.shape) - L / 2
-    prm = I.wca_params(precision=precision, dt=0.001, rattle_tol=_tol(precision), seed=seed,
-                       box_lo=(-L / 2,) * 3, box_hi=(L / 2,) * 3, periodic=(1, 1, 1))
-    prm["rcut"][0, 0] = rc
-    surf = {"kind": "none", "center": (0.0, 0.0, 0.0), "p": (0.0, 0.0, 0.0, 0.0)}
-    return [I._system("lj_lattice", surf, prm, x, I.maxwell(x.shape[0], 1.0, 1.0, g))]
+def _lattice(precision, k=12, rc=4.0, seed=3):
+    """k^3 = 1,728 Lennard-Jones particles at density 0.79 in a periodic box
+    of three cells of 4.33 along each axis at rc = 4: 64 particles per cell."""
+    return I.lj_lattice(k, rc=rc, seed=seed, precision=precision, tol=_tol(precision))
 
 
 def _check(systems, precision, nsteps, slots=32):
