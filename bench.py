@@ -63,6 +63,10 @@ def parse(argv=None):
     ap.add_argument("--pair-tile", type=int, default=None, choices=[0, 8, 16, 32],
                     help="global engine with this cell-tiled pair kernel setting (0: per-particle rows) "
                          "instead of the autotuner's choice")
+    ap.add_argument("--skin", type=float, default=-1.0,
+                    help="> 0: Verlet neighbour list with this skin (cell edge r_c + skin), rebuilt when a "
+                         "particle has moved skin / 2; 0: cell list every step; < 0: the workload's default")
+    ap.add_argument("--max-neighbors", type=int, default=64)
     ap.add_argument("--nrep", type=int, default=4096, help="systems of the replicas workload")
     ap.add_argument("--pair-form", type=int, default=1, choices=[0, 1],
                     help="nve_surfaces: 0 truncated-shifted, 1 linearly smoothed Lennard-Jones")
@@ -114,6 +118,23 @@ def workload(name: str, rank: int, precision: str, nrep: int = 4096, pair_form: 
         return inputs.lj_lattice(46, seed=seed + 2, precision=precision,
                                  tol=1e-12 if precision == "fp64" else 1e-10)
     raise ValueError(name)
+
+
+# Verlet-list skin per workload when --skin is not given (0: cell list every
+# step): the list where systems are large and the global engine runs them.
+DEFAULT_SKIN = {}
+
+
+def workload_skin(args) -> float:
+    return DEFAULT_SKIN.get(args.workload, 0.0) if args.skin < 0 else args.skin
+
+
+def cells_for_skin(systems, skin: float):
+    """With a neighbour list the cell edge must be at least r_c + skin."""
+    if skin > 0:
+        for sy in systems:
+            sy["params"] = dict(sy["params"], cell_size=float(max(map(max, sy["params"]["rcut"]))) + skin)
+    return systems
 
 
 def workload_config(name, systems, precision):
@@ -361,9 +382,12 @@ def main(argv=None):
         stream.synchronize()
         return [a.elapsed_time(b) / k] * k, md.md_last_launch_count(sim.h)
 
-    systems = workload(args.workload, rank, precision, args.nrep, args.pair_form)
+    skin = workload_skin(args)
+    systems = cells_for_skin(workload(args.workload, rank, precision, args.nrep, args.pair_form), skin)
     n_local = int(sum(s["n"] for s in systems))
     sim = md.Simulation(systems, stream=stream)
+    if skin > 0:
+        md.md_set_neighbor_list(sim.h, skin, args.max_neighbors)
     sim.set_state()
     sim.step(args.warmup)
     sim.sync()
@@ -374,6 +398,8 @@ def main(argv=None):
     if args.engine == "resident":
         md.md_set_option(sim.h, md.MD_OPT_ENGINE, 1)
         tuned = {"options": {"engine": 1, "resident_threads": md.md_get_option(sim.h, md.MD_OPT_RESIDENT_THREADS)}}
+    elif skin > 0:
+        tuned = {"options": {"neighbor_list_skin": skin, "max_neighbors": args.max_neighbors}}
     elif args.pair_tile is not None:
         md.md_set_option(sim.h, md.MD_OPT_PAIR_TILE, args.pair_tile)
         tuned = {"options": {**tuned["options"], "pair_tile": args.pair_tile}}
@@ -466,8 +492,10 @@ def main(argv=None):
 
     plain = None
     if not args.no_plain and precision == "mixed":
-        systems64 = workload(args.workload, rank, "fp64", args.nrep, args.pair_form)
+        systems64 = cells_for_skin(workload(args.workload, rank, "fp64", args.nrep, args.pair_form), skin)
         sim64 = md.Simulation(systems64, stream=stream)
+        if skin > 0:
+            md.md_set_neighbor_list(sim64.h, skin, args.max_neighbors)
         sim64.set_state()
         sim64.step(args.warmup)
         sim64.sync()
@@ -488,12 +516,15 @@ def main(argv=None):
     if args.workload == "sphere_vs_2d":
         from paper_1411_3019_gb300 import inputs
 
-        plane = inputs.sphere_and_plane2d(n=250_000, seed=rank_seed(rank), precision=precision)[1]
+        plane = cells_for_skin(inputs.sphere_and_plane2d(n=250_000, seed=rank_seed(rank), precision=precision)[1],
+                               skin)
         simp = md.Simulation(plane, stream=stream)
+        if skin > 0:
+            md.md_set_neighbor_list(simp.h, skin, args.max_neighbors)
         simp.set_state()
         simp.step(args.warmup)
         simp.sync()
-        if args.engine == "auto" and not args.no_tune:
+        if args.engine == "auto" and not args.no_tune and skin <= 0:
             with torch.cuda.stream(stream):
                 tune.autotune(simp.h, trials=3, flush=lambda: flush.add_(1.0))
         barrier()

@@ -63,6 +63,8 @@ extern "C" {
 #define MD_ERR_OUT_OF_GRID     5  /* a particle left the cell grid of its system   */
 #define MD_ERR_TIMEOUT         6  /* a bounded device-side wait ran out            */
 #define MD_ERR_NO_DEVICE       7  /* no CUDA device is visible                     */
+#define MD_ERR_NLIST_FULL      8  /* a particle had more neighbours than the Verlet
+                                     list holds (md_set_neighbor_list)              */
 
 /* Bits of the device status word (md_status); a set bit maps to the code
  * given beside it, lowest code first. */
@@ -297,6 +299,24 @@ int md_step(md_handle* h, int64_t nsteps);
  * max(2^20, 4N) cells; else MD_ERR_INVALID_ARG). Forces agree with the other
  * settings to float rounding (summation order differs). */
 #define MD_OPT_PAIR_TILE 6
+/* Verlet neighbour list (the LAMMPS-style list the paper's simulations
+ * ran with; the cell list is how it is built). With skin > 0 every pair
+ * within r_c + skin is listed from the cell list, and the pair kernel walks
+ * the list. Between builds each particle keeps its cell and its record
+ * moves with it. When any particle has moved more than skin / 2 since the
+ * last build, the same step rebuilds the cell list and the list, so every
+ * pair within r_c is always listed and forces equal the cell-list path's to
+ * float rounding (summation order). max_neighbors bounds the entries per
+ * particle (4 bytes each); a build that needs more latches MD_ERR_NLIST_FULL
+ * (reported by the next synchronising call; those forces miss pairs).
+ * The handle's cell edge must be >= the largest cutoff + skin on every axis
+ * with more than one cell (md_params.cell_size), else MD_ERR_INVALID_ARG.
+ * skin <= 0 switches the list off. Used by the global engine (md_step,
+ * md_forces); the resident engine keeps its own per-step cell lists.
+ * Cost: one pair pass over about (r_c + skin)^d / r_c^d times the partners
+ * in range, and the cell-list kernels return at once on steps without a
+ * rebuild. */
+int md_set_neighbor_list(md_handle* h, double skin, int32_t max_neighbors);
 int md_set_option(md_handle* h, int32_t key, int64_t value);
 int md_get_option(md_handle* h, int32_t key, int64_t* value);
 

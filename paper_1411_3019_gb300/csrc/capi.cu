@@ -48,6 +48,9 @@ struct md_handle {
   int64_t steps_since_order = 0;
   int64_t last_launches = 0;
   int kernels_per_step = 0;
+  // Verlet neighbour list (md_set_neighbor_list); A.nl_dirty != null when on
+  uint32_t* d_nl_dirty = nullptr;
+  int32_t nl_capacity = 0;  // entries per particle the allocated list holds
   // resident engine (MD_OPT_ENGINE = 1): systems largest first, a work counter
   int engine = 0;
   int res_threads = 0;  // 0: chosen per size class
@@ -350,6 +353,8 @@ int check_device_status(md_handle* h) {
   if (st & kFlagNonfinite) return fail(h, MD_ERR_NONFINITE, "non-finite position or momentum");
   if (st & kFlagOutOfGrid) return fail(h, MD_ERR_OUT_OF_GRID, "a particle left its cell grid or crossed a wall");
   if (st & kFlagTimeout) return fail(h, MD_ERR_TIMEOUT, "a bounded device wait ran out");
+  if (st & kFlagNlistFull)
+    return fail(h, MD_ERR_NLIST_FULL, "a particle has more neighbours than the neighbour list holds");
   if (st & kFlagOffSurface)
     return fail(h, MD_ERR_INVALID_ARG, "a constrained particle is off its surface, or bad input values");
   return MD_OK;
@@ -358,9 +363,14 @@ int check_device_status(md_handle* h) {
 // Cell list of the current positions (no step advance).
 int rebuild_cells(md_handle* h) {
   if (!h->has_pairs) return MD_OK;
+  if (h->A.nl_dirty) {  // neighbour-list mode: raise the flag so every rebuild kernel runs
+    const uint32_t one = 1u;
+    CK(h, cudaMemcpyAsync(h->A.nl_dirty, &one, sizeof(one), cudaMemcpyHostToDevice, h->stream()));
+  }
   CK(h, launch_bin(h->A, h->precision, h->stream()));
   CK(h, launch_cells_after_bin(h->A, 0, h->stream()));
   CK(h, launch_bucket_build(h->A, h->precision, h->stream()));
+  if (h->A.nl_dirty) CK(h, launch_nl_build(h->A, h->precision, h->excl, h->stream()));
   CK(h, launch_order(h->A, h->O, h->order_coord_shift, h->order_morton_drop, h->order_sys_shift, h->d_order,
                      h->stream()));
   h->steps_since_order = 0;
@@ -386,6 +396,10 @@ cudaError_t k_bucket_step(md_handle* h, cudaStream_t st) {
   return launch_bucket_build(h->A, h->precision, st);
 }
 cudaError_t k_advance_step(md_handle* h, cudaStream_t st) { return launch_advance(h->A, st); }
+cudaError_t k_bin_step(md_handle* h, cudaStream_t st) { return launch_bin(h->A, h->precision, st); }
+cudaError_t k_nl_build_step(md_handle* h, cudaStream_t st) {
+  return launch_nl_build(h->A, h->precision, h->excl, st);
+}
 
 const StepKernel kStepWithCells[] = {{"pair", k_pair_step},
                                      {"integrate", k_integrate_step},
@@ -403,7 +417,23 @@ const StepKernel kStepNoCells[] = {{"pair", k_pair_step}, {"integrate", k_integr
 const StepKernel kStepNoCellsBends[] = {{"pair", k_pair_step}, {"bend", k_bend_step},
                                         {"integrate", k_integrate_step}, {"advance", k_advance_step}};
 
+// Neighbour-list mode: the cell-list kernels and the list build return at
+// once unless the integrator raised the rebuild flag (the scan still
+// advances the step counter).
+const StepKernel kStepNl[] = {{"pair", k_pair_step},       {"integrate", k_integrate_step},
+                              {"bin", k_bin_step},         {"scan", k_scan_step},
+                              {"scatter", k_scatter_step}, {"bucket_build", k_bucket_step},
+                              {"nl_build", k_nl_build_step}};
+const StepKernel kStepNlBends[] = {{"pair", k_pair_step},       {"bend", k_bend_step},
+                                   {"integrate", k_integrate_step}, {"bin", k_bin_step},
+                                   {"scan", k_scan_step},       {"scatter", k_scatter_step},
+                                   {"bucket_build", k_bucket_step}, {"nl_build", k_nl_build_step}};
+
 int step_kernels(const md_handle* h, const StepKernel** list) {
+  if (h->has_pairs && h->A.nl_dirty) {
+    *list = h->bends ? kStepNlBends : kStepNl;
+    return h->bends ? 8 : 7;
+  }
   if (h->has_pairs) {
     *list = h->bends ? kStepWithCellsBends : kStepWithCells;
     return h->bends ? 6 : 5;
@@ -962,7 +992,7 @@ int md_step(md_handle* h, int64_t nsteps) {
   int64_t extra = 0;
   for (int64_t s = 0; s < nsteps; ++s) {
     CK(h, cudaGraphLaunch(h->graph, h->stream()));
-    if (h->has_pairs && h->A.order && ++h->steps_since_order >= kOrderEvery) {
+    if (h->has_pairs && h->A.order && !h->A.nl_dirty && ++h->steps_since_order >= kOrderEvery) {
       // any permutation is a valid visiting order; a fresh one keeps it spatial
       CK(h, launch_order(h->A, h->O, h->order_coord_shift, h->order_morton_drop, h->order_sys_shift, h->d_order,
                      h->stream()));
@@ -970,7 +1000,8 @@ int md_step(md_handle* h, int64_t nsteps) {
       extra += 3;
     }
   }
-  h->last_launches = nsteps * h->kernels_per_step + extra;
+  const StepKernel* ks;
+  h->last_launches = nsteps * step_kernels(h, &ks) + extra;
   return MD_OK;
 }
 
@@ -1052,6 +1083,60 @@ const char* md_profile_kernel_name(md_handle* h, int32_t i) {
   const StepKernel* ks;
   const int nk = step_kernels(h, &ks);
   return (i >= 0 && i < nk) ? ks[i].name : "";
+}
+
+int md_set_neighbor_list(md_handle* h, double skin, int32_t max_neighbors) {
+  if (!h) return MD_ERR_INVALID_ARG;
+  if (!(skin > 0.0)) {  // off: back to the per-step cell list
+    if (h->A.nl_dirty) {
+      h->A.nl_dirty = nullptr;
+      if (h->state_set) {
+        int rc = rebuild_cells(h);
+        if (rc) return rc;
+      }
+    }
+  } else {
+    if (!h->has_pairs) return fail(h, MD_ERR_INVALID_ARG, "the neighbour list needs pair interactions");
+    if (!std::isfinite(skin) || max_neighbors < 1 || max_neighbors > 4096)
+      return fail(h, MD_ERR_INVALID_ARG, "skin must be finite and max_neighbors in 1..4096");
+    if (h->n >= (int64_t(1) << 27)) return fail(h, MD_ERR_INVALID_ARG, "the neighbour list holds at most 2^27 particles");
+    double rcmax = 0.0;
+    for (int a = 0; a < MD_MAX_TYPES; ++a)
+      for (int b = 0; b < MD_MAX_TYPES; ++b) rcmax = std::max(rcmax, std::sqrt(h->types.rc2[a][b]));
+    for (const SysDev& S : h->sys)
+      for (int d = 0; d < 3; ++d)
+        if ((S.nc[d] > 1 || S.periodic[d]) && S.cs[d] < rcmax + skin)
+          return fail(h, MD_ERR_INVALID_ARG,
+                      "cell edge " + std::to_string(S.cs[d]) + " is below r_c + skin = " +
+                          std::to_string(rcmax + skin) + ": create the handle with cell_size >= r_c + skin");
+    DevArrays& A = h->A;
+    if (max_neighbors > h->nl_capacity) {  // the arrays of a smaller list stay allocated until md_destroy
+      const size_t n = (size_t)h->n;
+      cudaError_t e = cudaSuccess;
+      if (!h->d_nl_dirty) e = dalloc(h, &h->d_nl_dirty, 1);
+      if (e == cudaSuccess) e = dalloc(h, &A.nl, (size_t)max_neighbors * n);
+      if (e == cudaSuccess) e = dalloc(h, &A.nl_cnt, n);
+      if (e == cudaSuccess) e = dalloc(h, &A.xb, 3 * n);
+      if (e == cudaSuccess)
+        e = h->precision == MD_PREC_FP64 ? dalloc(h, reinterpret_cast<double4_32a**>(&A.rec0), n)
+                                         : dalloc(h, reinterpret_cast<float4**>(&A.rec0), n);
+      if (e != cudaSuccess) return cuda_fail(h, e, "neighbour list allocation");
+      h->nl_capacity = max_neighbors;
+    }
+    A.nl_max = max_neighbors;
+    A.nl_skin = skin;
+    A.nl_half_skin2 = (float)(0.25 * skin * skin);
+    A.nl_dirty = h->d_nl_dirty;
+    if (h->state_set) {
+      int rc = rebuild_cells(h);
+      if (rc) return rc;
+    }
+  }
+  if (h->graph) {  // the captured step used the old mode
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return check_device_status(h);
 }
 
 int md_set_option(md_handle* h, int32_t key, int64_t value) {

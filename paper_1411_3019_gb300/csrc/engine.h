@@ -40,6 +40,8 @@ cudaError_t launch_order(const DevArrays& A, const DevArrays& O, uint32_t coord_
 cudaError_t launch_scatter(const DevArrays& A, cudaStream_t st);
 
 // Conservative forces at the current positions into A.f.
+// Neighbour-list build (only when *A.nl_dirty; every pair within r_c + skin).
+cudaError_t launch_nl_build(const DevArrays& A, int precision, int excl, cudaStream_t st);
 cudaError_t launch_pair(const DevArrays& A, int precision, int has_pairs, int bonds, int walls,
                         int excl, cudaStream_t st);
 

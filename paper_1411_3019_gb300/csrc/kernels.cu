@@ -427,6 +427,7 @@ __global__ void k_restore(DevArrays A, const double* __restrict__ xa, const doub
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void k_bin(DevArrays A) {
+  if (A.nl_dirty && *A.nl_dirty == 0u) return;  // neighbour-list mode, no rebuild this step
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = A.n;
   if (i >= n) return;
@@ -493,6 +494,16 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_onepass(DevArrays A, int 
   const uint32_t T = A.nbucket;
   ScanCtl* ctl = A.scan;
   const uint32_t epoch = ctl->epoch;
+  if (A.nl_dirty && *A.nl_dirty == 0u) {  // neighbour-list mode, no rebuild: only the step advance
+    if (threadIdx.x == 0 && atomicAdd(&ctl->done, 1u) == gridDim.x - 1) {
+      ctl->done = 0u;
+      if (advance) {
+        *A.step += 1ull;
+        *A.mode = 1;
+      }
+    }
+    return;
+  }
   if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->tile, 1u);
   __syncthreads();
   const uint32_t tile = s_tile;
@@ -598,6 +609,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_onepass(DevArrays A, int 
 }
 
 __global__ void k_scatter(DevArrays A) {
+  if (A.nl_dirty && *A.nl_dirty == 0u) return;  // neighbour-list mode, no rebuild this step
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
   const uint32_t b = bucket_of(A.cell[i], A.hashed, A.log_t);
@@ -644,6 +656,7 @@ __device__ __forceinline__ void cell_offsets(const SysDev& S, uint32_t cell, dou
 // cell centre (formed in float64, stored in R).
 template <typename R>
 __global__ void k_bucket_build(DevArrays A) {
+  if (A.nl_dirty && *A.nl_dirty == 0u) return;  // neighbour-list mode, no rebuild this step
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = A.n;
   if (s >= n) return;
@@ -1246,6 +1259,128 @@ __global__ void __launch_bounds__(256) k_pair_row(DevArrays A) {
   store_f<R>(A.f, tag, fx, fy, fz, u);
 }
 
+// ---------------------------------------------------------------------------
+// Verlet neighbour list. k_nl_build (one thread per sorted slot, only when
+// the rebuild flag is up) lists every pair within r_c + skin of the fresh
+// cell list: entry = neighbour slot << 5 | stencil cell k (k = 9(dz+1) +
+// 3(dy+1) + dx+1, the shift of the neighbour's cell), in stencil order, no
+// self pair, no same-molecule pair; it also keeps the records and the
+// positions of the build. k_pair_nl walks the list with the records the
+// integrator moved in place, with the row kernel's arithmetic (the cell
+// edge is at least r_c + skin, so a particle within skin / 2 of its build
+// position is still within r_c + skin of any partner it had).
+// ---------------------------------------------------------------------------
+template <typename R, bool EXCL>
+__global__ void __launch_bounds__(256) k_nl_build(DevArrays A) {
+  __shared__ PairTab<R> tab;
+  if (*A.nl_dirty == 0u) return;  // uniform: nothing moved far enough
+  load_tab<R>(tab, A.types);
+  __syncthreads();
+  using Rec = typename RecT<R>::T;
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= (uint32_t)A.n) return;
+  const GlobalCells<R> C(A);
+  const int64_t n = A.n;
+  const uint32_t tag = C.tag(s);
+  const uint32_t cell = C.scell(s);
+  const Rec ri = C.rec(s);
+  const uint32_t bi = RecT<R>::bits(ri);
+  const uint32_t ti = bi & 7u, moli = bi >> 3;
+  const SysDev& S = A.sys[meta_sys(A.meta[tag])];
+  int c[3];
+  cell_decode(S, cell, c[0], c[1], c[2]);
+  const R csx = sizeof(R) == 4 ? (R)S.cs_f[0] : (R)S.cs[0];
+  const R csy = sizeof(R) == 4 ? (R)S.cs_f[1] : (R)S.cs[1];
+  const R csz = sizeof(R) == 4 ? (R)S.cs_f[2] : (R)S.cs[2];
+  const R skin = (R)A.nl_skin;
+  const uint32_t cap = (uint32_t)A.nl_max;
+  uint32_t cnt = 0;
+  for (int dz = -1; dz <= 1; ++dz) {
+    int z = c[2] + dz;
+    if (z < 0 || z >= S.nc[2]) {
+      if (!S.periodic[2]) continue;
+      z = (z + S.nc[2]) % S.nc[2];
+    }
+    for (int dy = -1; dy <= 1; ++dy) {
+      int y = c[1] + dy;
+      if (y < 0 || y >= S.nc[1]) {
+        if (!S.periodic[1]) continue;
+        y = (y + S.nc[1]) % S.nc[1];
+      }
+      for (int dx = -1; dx <= 1; ++dx) {
+        int x = c[0] + dx;
+        if (x < 0 || x >= S.nc[0]) {
+          if (!S.periodic[0]) continue;
+          x = (x + S.nc[0]) % S.nc[0];
+        }
+        const uint32_t nb = cell_id(S, x, y, z);
+        const uint32_t b = C.bucket(nb);
+        const uint32_t t1 = C.start(b + 1);
+        const uint32_t code = (uint32_t)(9 * (dz + 1) + 3 * (dy + 1) + dx + 1);
+        const R shx = (R)dx * csx, shy = (R)dy * csy, shz = (R)dz * csz;
+        for (uint32_t t = C.start(b); t < t1; ++t) {
+          const Rec rj = C.rec(t);
+          const uint32_t cj = A.rec_cell ? RecT<R>::bits(rj) >> 3 : C.scell(t);
+          if (cj != nb || t == s) continue;
+          const uint32_t bj = RecT<R>::bits(rj);
+          if (EXCL && (bj >> 3) == moli) continue;
+          const uint32_t qt = ti * kMaxTypes + (bj & 7u);
+          if (!(tab.rc2[qt] > (R)0)) continue;
+          const R ddx = ri.x - rj.x - shx, ddy = ri.y - rj.y - shy, ddz = ri.z - rj.z - shz;
+          const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+          const R rs = tab.rc[qt] + skin;
+          if (r2 < rs * rs) {
+            if (cnt < cap) A.nl[(int64_t)cnt * n + s] = t << 5 | code;
+            ++cnt;
+          }
+        }
+      }
+    }
+  }
+  if (cnt > cap) flag(A.status, kFlagNlistFull);
+  A.nl_cnt[s] = min(cnt, cap);
+  reinterpret_cast<Rec*>(A.rec0)[s] = ri;
+  A.xb[tag] = A.x[tag];
+  A.xb[n + tag] = A.x[n + tag];
+  A.xb[2 * n + tag] = A.x[2 * n + tag];
+}
+
+template <typename R, bool BONDS, bool WALLS>
+__global__ void __launch_bounds__(256) k_pair_nl(DevArrays A) {
+  __shared__ PairTab<R> tab;
+  load_tab<R>(tab, A.types);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *A.nl_dirty = 0u;  // the previous step's rebuild is done
+  __syncthreads();
+  using Rec = typename RecT<R>::T;
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= (uint32_t)A.n) return;
+  const int64_t n = A.n;
+  const Rec* __restrict__ rec = reinterpret_cast<const Rec*>(A.rec);
+  const uint32_t tag = A.stag[s];
+  const uint32_t m = A.meta[tag];
+  const SysDev& S = A.sys[meta_sys(m)];
+  const Rec ri = rec[s];
+  const uint32_t ti = RecT<R>::bits(ri) & 7u;
+  const R csx = sizeof(R) == 4 ? (R)S.cs_f[0] : (R)S.cs[0];
+  const R csy = sizeof(R) == 4 ? (R)S.cs_f[1] : (R)S.cs[1];
+  const R csz = sizeof(R) == 4 ? (R)S.cs_f[2] : (R)S.cs[2];
+  const uint32_t cnt = A.nl_cnt[s];
+  const uint32_t* __restrict__ nl = A.nl + s;
+  R fx = 0, fy = 0, fz = 0, u = 0;
+  for (uint32_t k = 0; k < cnt; ++k) {
+    const uint32_t e = nl[(int64_t)k * n];
+    const uint32_t code = e & 31u;
+    const Rec rj = rec[e >> 5];
+    const int dz = (int)(code / 9u) - 1, dy = (int)(code / 3u % 3u) - 1, dx = (int)(code % 3u) - 1;
+    const uint32_t qt = ti * kMaxTypes + (RecT<R>::bits(rj) & 7u);
+    const R ddx = ri.x - rj.x - (R)dx * csx, ddy = ri.y - rj.y - (R)dy * csy, ddz = ri.z - rj.z - (R)dz * csz;
+    const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+    if (r2 < tab.rc2[qt]) lj_term<R>(tab, qt, r2, ddx, ddy, ddz, fx, fy, fz, u);
+  }
+  if (BONDS || WALLS) bonded_terms<R>(A, S, tag, m, BONDS, WALLS, fx, fy, fz, u);
+  store_f<R>(A.f, tag, fx, fy, fz, u);
+}
+
 // Bend-angle forces (and energy shares) added to the pair kernel's output.
 template <typename R>
 __global__ void k_bend(DevArrays A) {
@@ -1790,12 +1925,14 @@ __device__ __forceinline__ bool finite_bits(double v) {
 // counters in shared memory. put() records the cell and the particle's rank
 // in its bucket (the order of the atomic; the bucket build makes it canonical).
 struct NoBin {
-  static constexpr bool kOn = false;
+  static constexpr bool kOn = false, kPos = false;
   __device__ __forceinline__ explicit NoBin(const DevArrays&) {}
   __device__ __forceinline__ void put(int64_t, uint32_t) const {}
+  __device__ __forceinline__ void pos(int64_t, double, double, double) const {}
 };
 struct GlobalBin {
-  static constexpr bool kOn = true;
+  static constexpr bool kOn = true, kPos = false;
+  __device__ __forceinline__ void pos(int64_t, double, double, double) const {}
   uint32_t* cell;
   uint32_t* rank;
   uint32_t* count;
@@ -1805,6 +1942,42 @@ struct GlobalBin {
   __device__ __forceinline__ void put(int64_t i, uint32_t c) const {
     cell[i] = c;
     rank[i] = atomicAdd(&count[bucket_of(c, hashed, log_t)], 1u);
+  }
+};
+
+// Neighbour-list mode: the particle keeps its cell until the next rebuild;
+// its record moves with it (record at the build + the float64 displacement
+// since the build, rounded once), and a displacement beyond skin / 2 raises
+// the rebuild flag for this step's cell-list kernels.
+template <typename R> struct NlSink {
+  static constexpr bool kOn = false, kPos = true;
+  using Rec = typename RecT<R>::T;
+  const uint32_t* slot_of;
+  const double* xb;
+  const Rec* rec0;
+  Rec* rec;
+  uint32_t* dirty;
+  float half_skin2;
+  int64_t n;
+  __device__ __forceinline__ explicit NlSink(const DevArrays& A)
+      : slot_of(A.slot_of), xb(A.xb), rec0(reinterpret_cast<const Rec*>(A.rec0)),
+        rec(reinterpret_cast<Rec*>(A.rec)), dirty(A.nl_dirty), half_skin2(A.nl_half_skin2), n(A.n) {}
+  __device__ __forceinline__ void put(int64_t, uint32_t) const {}
+  __device__ __forceinline__ void pos(int64_t i, double xn, double yn, double zn) const {
+    const uint32_t s = slot_of[i];
+    const double dx = xn - xb[i], dy = yn - xb[n + i], dz = zn - xb[2 * n + i];
+    Rec r = rec0[s];
+    float d2;
+    if constexpr (sizeof(R) == 4) {
+      const float fx = d2f_rn(dx), fy = d2f_rn(dy), fz = d2f_rn(dz);
+      r.x += fx; r.y += fy; r.z += fz;
+      d2 = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+    } else {
+      r.x += dx; r.y += dy; r.z += dz;
+      d2 = d2f_rn(fma(dx, dx, fma(dy, dy, dz * dz)));
+    }
+    rec[s] = r;
+    if (!(d2 <= half_skin2)) atomicOr(dirty, 1u);
   }
 };
 
@@ -1889,6 +2062,7 @@ __device__ __forceinline__ void integrate_particle_fp64(const DevArrays& A, int6
     flag(A.status, kFlagNonfinite);
   A.x[i] = xn; A.x[n + i] = yn; A.x[2 * n + i] = zn;
   A.ph[i] = qx; A.ph[n + i] = qy; A.ph[2 * n + i] = qz;
+  if constexpr (Bin::kPos) bin.pos(i, xn, yn, zn);
   if (Bin::kOn) {
     bool out = false;
     const uint32_t cell = cell_of_d(S, xn, yn, zn, out);
@@ -2113,12 +2287,24 @@ __device__ __forceinline__ void integrate_particle_mixed(const DevArrays& A, int
     flag(A.status, kFlagNonfinite);
   A.x[i] = xn; A.x[n + i] = yn; A.x[2 * n + i] = zn;
   A.ph[i] = qx; A.ph[n + i] = qy; A.ph[2 * n + i] = qz;
+  if constexpr (Bin::kPos) bin.pos(i, xn, yn, zn);
   if (Bin::kOn) {
     bool out = false;
     const uint32_t cell = cell_of_f(S, xn, yn, zn, out);
     if (out) flag(A.status, kFlagOutOfGrid);
     bin.put(i, cell);
   }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256, 4) k_integrate_nl(DevArrays A) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  const unsigned long long k = *A.step;
+  const int mode = *A.mode;
+  const NlSink<R> bin(A);
+  if constexpr (sizeof(R) == 4) integrate_particle_mixed(A, i, load_f3<float>(A.f, i), k, mode, bin);
+  else integrate_particle_fp64(A, i, load_f3<double>(A.f, i), k, mode, bin);
 }
 
 template <typename R, bool BIN>
@@ -2163,7 +2349,8 @@ template <typename R> struct SharedCells {
 // (stride = sizeof(R) / 4), the slot where the same thread has just read the
 // particle's force: the two are never live at the same time.
 struct SharedBin {
-  static constexpr bool kOn = true;
+  static constexpr bool kOn = true, kPos = false;
+  __device__ __forceinline__ void pos(int64_t, double, double, double) const {}
   uint32_t* cell;
   uint32_t stride;
   uint16_t* rank;
@@ -2749,9 +2936,38 @@ static void pair_dispatch(const DevArrays& A, int bonds, int walls, int excl, in
   }
 }
 
+template <typename R>
+static void pair_dispatch_nl(const DevArrays& A, int bonds, int walls, cudaStream_t st) {
+  const unsigned g = grid_for(A.n, 256);
+  switch ((bonds ? 2 : 0) | (walls ? 1 : 0)) {
+    case 0: k_pair_nl<R, false, false><<<g, 256, 0, st>>>(A); break;
+    case 1: k_pair_nl<R, false, true><<<g, 256, 0, st>>>(A); break;
+    case 2: k_pair_nl<R, true, false><<<g, 256, 0, st>>>(A); break;
+    default: k_pair_nl<R, true, true><<<g, 256, 0, st>>>(A); break;
+  }
+}
+
+cudaError_t launch_nl_build(const DevArrays& A, int precision, int excl, cudaStream_t st) {
+  if (A.n == 0) return cudaSuccess;
+  const unsigned g = grid_for(A.n, 256);
+  if (precision == 0) {
+    if (excl) k_nl_build<double, true><<<g, 256, 0, st>>>(A);
+    else k_nl_build<double, false><<<g, 256, 0, st>>>(A);
+  } else {
+    if (excl) k_nl_build<float, true><<<g, 256, 0, st>>>(A);
+    else k_nl_build<float, false><<<g, 256, 0, st>>>(A);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pair(const DevArrays& A, int precision, int has_pairs, int bonds, int walls, int excl,
                         cudaStream_t st) {
   if (A.n == 0) return cudaSuccess;
+  if (has_pairs && A.nl_dirty) {
+    if (precision == 0) pair_dispatch_nl<double>(A, bonds, walls, st);
+    else pair_dispatch_nl<float>(A, bonds, walls, st);
+    return cudaGetLastError();
+  }
   if (!has_pairs) {
     const int b = block_for(A.n);
     if (precision == 0) k_nopair<double><<<grid_for(A.n, b), b, 0, st>>>(A, bonds, walls);
@@ -2776,7 +2992,10 @@ cudaError_t launch_integrate(const DevArrays& A, int precision, int has_pairs, c
   if (A.n == 0) return cudaSuccess;
   const int b = block_for(A.n);
   const unsigned g = grid_for(A.n, b);
-  if (precision == 0) {
+  if (A.nl_dirty && has_pairs) {
+    if (precision == 0) k_integrate_nl<double><<<g, b, 0, st>>>(A);
+    else k_integrate_nl<float><<<g, b, 0, st>>>(A);
+  } else if (precision == 0) {
     if (has_pairs) k_integrate<double, true><<<g, b, 0, st>>>(A);
     else k_integrate<double, false><<<g, b, 0, st>>>(A);
   } else {

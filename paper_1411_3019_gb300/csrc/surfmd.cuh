@@ -14,6 +14,7 @@ constexpr uint32_t kFlagRattle = 0x1u;
 constexpr uint32_t kFlagNonfinite = 0x2u;
 constexpr uint32_t kFlagOutOfGrid = 0x4u;
 constexpr uint32_t kFlagTimeout = 0x8u;
+constexpr uint32_t kFlagNlistFull = 0x10u;  // a particle had more neighbours than the list holds
 constexpr uint32_t kFlagOffSurface = 0x100u;  // set-state validation only
 
 enum SurfKind : int32_t {
@@ -132,6 +133,18 @@ struct DevArrays {
   int32_t log_t;
   int32_t pair_lanes;   // lanes per particle in the pair kernel (1, 2, 4 or 8)
   int32_t pair_tile;    // 0, or particles per warp (8, 16, 32) of the cell-tiled pair kernel (needs hashed == 0)
+  // Verlet neighbour list (nl_dirty == null: off). Built from the cell list
+  // with every pair within r_c + skin; between builds the integrator moves
+  // the records in place and raises *nl_dirty when a particle has moved more
+  // than skin / 2, and the cell list and the list are rebuilt in that step.
+  uint32_t* nl_dirty;   // device flag: 1 = rebuild the cell list and the neighbour list
+  uint32_t* nl;         // [nl_max][n] neighbour entries by sorted slot: slot << 5 | stencil cell (0..26)
+  uint32_t* nl_cnt;     // [n] entries per sorted slot
+  void* rec0;           // [n] records at the last build
+  double* xb;           // [3][n] positions at the last build (user order)
+  int32_t nl_max;
+  float nl_half_skin2;  // (skin / 2)^2
+  double nl_skin;
   int32_t rec_cell;     // 1: a record's w word holds type | cell << 3 (no exclusions,
                         // cells < 2^29), so the pair kernel needs no sorted-cell load;
                         // 0: type | molecule << 3

@@ -25,6 +25,7 @@ SURF_KINDS = {"none": 0, "plane": 1, "sphere": 2, "ellipsoid": 3, "torus": 4, "g
 PRECISION = {"fp64": 0, "mixed": 1}
 MD_OK, MD_ERR_INVALID_ARG, MD_ERR_CUDA, MD_ERR_RATTLE_DIVERGED = 0, 1, 2, 3
 MD_ERR_NONFINITE, MD_ERR_OUT_OF_GRID, MD_ERR_TIMEOUT, MD_ERR_NO_DEVICE = 4, 5, 6, 7
+MD_ERR_NLIST_FULL = 8
 MD_FLAG_RATTLE_DIVERGED, MD_FLAG_NONFINITE, MD_FLAG_OUT_OF_GRID, MD_FLAG_TIMEOUT = 1, 2, 4, 8
 MD_OPT_PAIR_LANES = 1
 MD_PAIR_TRUNC_SHIFT, MD_PAIR_LINEAR_SMOOTH = 0, 1
@@ -35,7 +36,8 @@ MD_OPT_RESIDENT_THREADS = 4
 MD_OPT_RESIDENT_STEPS = 5
 MD_OPT_PAIR_TILE = 6
 ERROR_NAMES = {0: "MD_OK", 1: "MD_ERR_INVALID_ARG", 2: "MD_ERR_CUDA", 3: "MD_ERR_RATTLE_DIVERGED",
-               4: "MD_ERR_NONFINITE", 5: "MD_ERR_OUT_OF_GRID", 6: "MD_ERR_TIMEOUT", 7: "MD_ERR_NO_DEVICE"}
+               4: "MD_ERR_NONFINITE", 5: "MD_ERR_OUT_OF_GRID", 6: "MD_ERR_TIMEOUT", 7: "MD_ERR_NO_DEVICE",
+               8: "MD_ERR_NLIST_FULL"}
 
 
 class MdError(RuntimeError):
@@ -120,6 +122,7 @@ def lib():
                 "md_forces_noalloc": ([C.POINTER(md_surface), C.POINTER(md_params), i64, dp, dp, dp, dp, dp,
                                        dp, vp], C.c_int),
                 "md_set_option": ([vp, i32, i64], C.c_int),
+                "md_set_neighbor_list": ([vp, C.c_double, i32], C.c_int),
                 "md_check_conversions": ([vp, i64, vp, vp], C.c_int),
                 "md_get_option": ([vp, i32, C.POINTER(i64)], C.c_int),
                 "md_last_error": ([vp], C.c_char_p),
@@ -384,6 +387,12 @@ def md_check_conversions(values) -> tuple[np.ndarray, np.ndarray]:
 
 def md_set_option(h, key: int, value: int) -> None:
     _check(h, lib().md_set_option(h, int(key), int(value)))
+
+
+def md_set_neighbor_list(h, skin: float, max_neighbors: int = 64) -> None:
+    """Verlet neighbour list with the given skin (<= 0: off); the handle's
+    cell edge must be at least the largest cutoff + skin."""
+    _check(h, lib().md_set_neighbor_list(h, float(skin), int(max_neighbors)))
 
 
 def md_get_option(h, key: int) -> int:

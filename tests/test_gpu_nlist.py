@@ -1,0 +1,117 @@
+"""Verlet neighbour list (md_set_neighbor_list) against the oracle, which
+always searches a fresh cell list: trajectories and forces in both
+precisions with a small skin (a rebuild every few steps) and a large one (a
+rebuild every few tens), across md_step calls. Workloads: replicas on spheres,
+bead molecules (bonds, exclusions, r_c = 2.5), a Gaussian bump with free
+crowders between walls in a box periodic in x and y (particles cross the
+boundary between builds). Also: a list too small for a particle's neighbours
+is reported, a cell edge below r_c + skin is refused, the list can be
+switched off mid-run, and a run repeats bit for bit."""
+import numpy as np
+import pytest
+
+from paper_1411_3019_gb300 import inputs as I
+from paper_1411_3019_gb300 import md
+
+from parity_util import POS_100, assert_forces, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+def _tol(precision):
+    return 1e-12 if precision == "fp64" else 1e-10
+
+
+def _cells(systems, skin):
+    """Cell edge r_c + skin, as the list needs."""
+    for s in systems:
+        rc = float(np.max(s["params"]["rcut"]))
+        s["params"] = dict(s["params"], cell_size=rc + skin)
+    return systems
+
+
+def _run(systems, skin, chunks, maxnb=64):
+    sim = md.Simulation(systems)
+    md.md_set_neighbor_list(sim.h, skin, maxnb)
+    sim.set_state()
+    for k in chunks:
+        sim.step(k)
+    sim.sync()
+    st = sim.state()
+    f, u = sim.forces()
+    res = sim.residual()
+    sim.close()
+    return st, f, u, res
+
+
+def _check(systems, precision, chunks, skin):
+    st, f, _, res = _run(systems, skin, chunks)
+    ref = oracle_run(systems, sum(chunks))[0]
+    assert np.abs(st["x"] - ref["x"]).max() <= POS_100[precision]
+    assert_forces(systems, st["x"], f, precision)
+    return res
+
+
+@pytest.mark.parametrize("skin", [0.05, 0.5])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_replicas_small_and_large_skin(precision, skin):
+    systems = _cells(I.c4_replicas(nrep=3, seed=8, nmin=200, nmax=600, rmin=6.0, rmax=10.0, precision=precision,
+                                   dt=0.002, tol=_tol(precision)), skin)
+    res = _check(systems, precision, [37, 63], skin)
+    assert res["max_g_over_gradg"] < 10 * _tol(precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_bead_molecules(precision):
+    systems = _cells(I.c5_bead_molecules(nmol=300, beads=5, R=10.0, seed=4, precision=precision,
+                                         tol=_tol(precision)), 0.4)
+    _check(systems, precision, [60], 0.4)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_bump_with_crowders_periodic_and_walls(precision):
+    systems = _cells(I.c3_bump_crowders(n_surf=600, n_free=1500, seed=5, precision=precision,
+                                        tol=_tol(precision)), 0.3)
+    _check(systems, precision, [20, 20], 0.3)
+
+
+def test_list_too_small_is_reported():
+    systems = _cells(I.lj_lattice(12, rc=2.5, seed=3, precision="mixed"), 0.3)
+    sim = md.Simulation(systems)
+    md.md_set_neighbor_list(sim.h, 0.3, 8)  # about 70 partners within 2.8 at density 0.79
+    with pytest.raises(md.MdError) as e:
+        sim.set_state()
+        sim.step(1)
+        sim.sync()
+    assert e.value.code == md.MD_ERR_NLIST_FULL
+    sim.close()
+
+
+def test_cell_edge_below_cutoff_plus_skin_is_refused():
+    systems = I.c4_replicas(nrep=2, seed=8, nmin=200, nmax=300, rmin=6.0, rmax=8.0, precision="mixed")
+    sim = md.Simulation(systems)  # cell edge = the WCA cutoff
+    with pytest.raises(md.MdError) as e:
+        md.md_set_neighbor_list(sim.h, 0.3, 64)
+    assert e.value.code == md.MD_ERR_INVALID_ARG
+    sim.close()
+
+
+def test_switch_off_mid_run_and_repeat_bit_for_bit():
+    skin = 0.3
+    systems = _cells(I.c4_replicas(nrep=2, seed=9, nmin=300, nmax=500, rmin=6.0, rmax=9.0, precision="mixed",
+                                   dt=0.002, tol=1e-10), skin)
+    a = _run(systems, skin, [25, 25])
+    b = _run(systems, skin, [25, 25])
+    for key in ("x", "v", "p_half"):
+        assert np.array_equal(a[0][key], b[0][key]), key
+    sim = md.Simulation(systems)
+    md.md_set_neighbor_list(sim.h, skin, 64)
+    sim.set_state()
+    sim.step(25)
+    md.md_set_neighbor_list(sim.h, 0.0, 64)
+    sim.step(25)
+    sim.sync()
+    st = sim.state()
+    sim.close()
+    ref = oracle_run(systems, 50)[0]
+    assert np.abs(st["x"] - ref["x"]).max() <= POS_100["mixed"]
