@@ -50,7 +50,7 @@ SM_MAX_MHZ = 2070.0
 def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="surfmd", choices=["surfmd", "reference"])
     ap.add_argument("--workload", default="ellipsoid_torus", choices=WORKLOADS)
@@ -66,7 +66,7 @@ def parse(argv=None):
     ap.add_argument("--skin", type=float, default=-1.0,
                     help="> 0: Verlet neighbour list with this skin (cell edge r_c + skin), rebuilt when a "
                          "particle has moved skin / 2; 0: cell list every step; < 0: the workload's default")
-    ap.add_argument("--max-neighbors", type=int, default=64)
+    ap.add_argument("--max-neighbors", type=int, default=-1, help="< 0: the workload's default")
     ap.add_argument("--nrep", type=int, default=4096, help="systems of the replicas workload")
     ap.add_argument("--pair-form", type=int, default=1, choices=[0, 1],
                     help="nve_surfaces: 0 truncated-shifted, 1 linearly smoothed Lennard-Jones")
@@ -120,13 +120,20 @@ def workload(name: str, rank: int, precision: str, nrep: int = 4096, pair_form: 
     raise ValueError(name)
 
 
-# Verlet-list skin per workload when --skin is not given (0: cell list every
-# step): the list where systems are large and the global engine runs them.
-DEFAULT_SKIN = {}
+# Verlet list (skin, entries per particle) per workload when --skin is not
+# given: the list where systems are large and the global engine runs them
+# (measured 1.7-2.2x over a cell list every step); the resident engine's
+# batches and the small float64 systems keep the per-step cell list.
+DEFAULT_NLIST = {"ellipsoid_torus": (0.4, 64), "bump_crowders": (0.4, 64), "bead_molecules": (0.4, 128),
+                 "sphere_vs_2d": (0.5, 64), "lj_lattice": (0.3, 128)}
 
 
 def workload_skin(args) -> float:
-    return DEFAULT_SKIN.get(args.workload, 0.0) if args.skin < 0 else args.skin
+    return DEFAULT_NLIST.get(args.workload, (0.0, 0))[0] if args.skin < 0 else args.skin
+
+
+def workload_max_neighbors(args) -> int:
+    return DEFAULT_NLIST.get(args.workload, (0.0, 64))[1] if args.max_neighbors < 0 else args.max_neighbors
 
 
 def cells_for_skin(systems, skin: float):
@@ -175,7 +182,7 @@ def reduce_over_ranks(dist, ms_local: float, n_local: float, device=None):
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
 class ClockSampler:
-    """nvidia-smi sampling every 200 ms from construction to stop(); only the
+    """nvidia-smi sampling every 50 ms from construction to stop(); only the
     samples whose timestamps fall inside [mark_start, mark_end] are kept."""
     FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -188,7 +195,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(device_index)], stdout=self.file, stderr=subprocess.DEVNULL)
+                 "-lms", "50", "-i", str(device_index)], stdout=self.file, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
 
@@ -242,11 +249,23 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # rooflines
 # ---------------------------------------------------------------------------
-def algorithmic_bytes(kernel: str, n: int, nbucket: int, precision: str) -> float:
+def algorithmic_bytes(kernel: str, n: int, nbucket: int, precision: str, nlist: bool = False) -> float:
     """Bytes each kernel must move per launch if every datum is read or written
-    once (per step for the resident engine's entry)."""
+    once (per step for the resident engine's entry). With the neighbour list
+    the pair kernel's list entries and repeated neighbour records are not
+    counted (a lower bound), and the cell-list kernels and the list build,
+    which work only on rebuild steps, count no bytes."""
     v4 = 16 if precision == "mixed" else 32
     tiles = math.ceil(nbucket / 8192)
+    if nlist:
+        per = {
+            # sorted id, meta, own record, entry count; force vec4
+            "pair": n * (4 + 4 + v4 + 4 + v4),
+            # meta, x, p_half, force vec4; x, p_half written; slot, build position and
+            # build record read, record written
+            "integrate": n * (4 + 24 + 24 + v4 + 24 + 24 + 4 + 24 + v4 + v4),
+        }
+        return float(per.get(kernel, 0))
     per = {
         # sorted id, cell id, own record, meta; force vec4; bucket starts once
         "pair": n * (4 + 4 + v4 + 4 + v4) + 4 * (nbucket + 1),
@@ -271,11 +290,13 @@ def kernels_source_hash() -> str:
         return hashlib.sha256(fh.read()).hexdigest()
 
 
-def ncu_counts(workload_name: str, precision: str):
+def ncu_counts(workload_name: str, precision: str, nlist: bool = False):
     """Per-launch ncu counters (float64-pipe thread instructions, DRAM bytes)
-    recorded in profiles/ for this workload, if they were taken from the
-    current kernel source (else {})."""
-    path = os.path.join(ROOT, "profiles", f"ncu_counts_{workload_name}_{precision}.txt")
+    recorded in profiles/ for this workload (and step form: neighbour list or
+    cell list every step), if they were taken from the current kernel source
+    (else {})."""
+    suffix = "_nlist" if nlist else ""
+    path = os.path.join(ROOT, "profiles", f"ncu_counts_{workload_name}_{precision}{suffix}.txt")
     if not os.path.exists(path):
         return {}
     out, sha = {}, None
@@ -291,11 +312,11 @@ def ncu_counts(workload_name: str, precision: str):
     return out if sha == kernels_source_hash() else {}
 
 
-def rooflines(prof_ms, n, nbucket, precision, hbm_peak, counts, sm_mhz):
+def rooflines(prof_ms, n, nbucket, precision, hbm_peak, counts, sm_mhz, nlist=False):
     fp64_peak = SMS * FP64_OPS_PER_SM_CLK * (sm_mhz or SM_MAX_MHZ) * 1e6  # float64 ops/s
     table = {}
     for k, ms in prof_ms.items():
-        b = algorithmic_bytes(k, n, nbucket, precision)
+        b = algorithmic_bytes(k, n, nbucket, precision, nlist)
         row = {"ms": round(ms, 5), "bytes_per_launch": b, "hbm_gbs": b / (ms / 1e3) / 1e9,
                "hbm_frac": b / (ms / 1e3) / 1e9 / hbm_peak}
         c = counts.get(k, {})
@@ -387,7 +408,7 @@ def main(argv=None):
     n_local = int(sum(s["n"] for s in systems))
     sim = md.Simulation(systems, stream=stream)
     if skin > 0:
-        md.md_set_neighbor_list(sim.h, skin, args.max_neighbors)
+        md.md_set_neighbor_list(sim.h, skin, workload_max_neighbors(args))
     sim.set_state()
     sim.step(args.warmup)
     sim.sync()
@@ -399,7 +420,7 @@ def main(argv=None):
         md.md_set_option(sim.h, md.MD_OPT_ENGINE, 1)
         tuned = {"options": {"engine": 1, "resident_threads": md.md_get_option(sim.h, md.MD_OPT_RESIDENT_THREADS)}}
     elif skin > 0:
-        tuned = {"options": {"neighbor_list_skin": skin, "max_neighbors": args.max_neighbors}}
+        tuned = {"options": {"neighbor_list_skin": skin, "max_neighbors": workload_max_neighbors(args)}}
     elif args.pair_tile is not None:
         md.md_set_option(sim.h, md.MD_OPT_PAIR_TILE, args.pair_tile)
         tuned = {"options": {**tuned["options"], "pair_tile": args.pair_tile}}
@@ -408,6 +429,7 @@ def main(argv=None):
             tuned = tune.autotune(sim.h, trials=3, flush=lambda: flush.add_(1.0))
     sim.step(2)
     sim.sync()
+    builds0 = md.md_get_option(sim.h, md.MD_OPT_NLIST_BUILDS) if skin > 0 else 0
 
     barrier()
     torch.cuda.synchronize()
@@ -416,6 +438,8 @@ def main(argv=None):
     t_wall0 = time.perf_counter()
     resident = md.md_get_option(sim.h, md.MD_OPT_ENGINE) == 1
     durs, launches = (timed_resident if resident else timed_steps)(sim, args.steps)
+    if skin > 0:  # list builds in the timed steps (the rebuild kernels exit at once in the others)
+        tuned["options"]["rebuilds_in_timed_steps"] = md.md_get_option(sim.h, md.MD_OPT_NLIST_BUILDS) - builds0
     torch.cuda.synchronize()
     barrier()
     t_wall = time.perf_counter() - t_wall0
@@ -456,8 +480,8 @@ def main(argv=None):
     except OSError:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    roofline = rooflines(prof, n_local, nbucket, precision, hbm_peak, ncu_counts(args.workload, precision),
-                         clk["sm_mhz"] if clk else None)
+    roofline = rooflines(prof, n_local, nbucket, precision, hbm_peak, ncu_counts(args.workload, precision, skin > 0),
+                         clk["sm_mhz"] if clk else None, nlist=skin > 0)
     if "hbm_gbs" not in peaks and roofline["bound"] == "hbm":
         roofline["peak_source"] = "fallback"
 
@@ -495,7 +519,7 @@ def main(argv=None):
         systems64 = cells_for_skin(workload(args.workload, rank, "fp64", args.nrep, args.pair_form), skin)
         sim64 = md.Simulation(systems64, stream=stream)
         if skin > 0:
-            md.md_set_neighbor_list(sim64.h, skin, args.max_neighbors)
+            md.md_set_neighbor_list(sim64.h, skin, workload_max_neighbors(args))
         sim64.set_state()
         sim64.step(args.warmup)
         sim64.sync()
@@ -520,7 +544,7 @@ def main(argv=None):
                                skin)
         simp = md.Simulation(plane, stream=stream)
         if skin > 0:
-            md.md_set_neighbor_list(simp.h, skin, args.max_neighbors)
+            md.md_set_neighbor_list(simp.h, skin, workload_max_neighbors(args))
         simp.set_state()
         simp.step(args.warmup)
         simp.sync()

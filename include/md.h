@@ -299,6 +299,10 @@ int md_step(md_handle* h, int64_t nsteps);
  * max(2^20, 4N) cells; else MD_ERR_INVALID_ARG). Forces agree with the other
  * settings to float rounding (summation order differs). */
 #define MD_OPT_PAIR_TILE 6
+/* MD_OPT_NLIST_BUILDS (md_get_option only; waits for the stream): how many
+ * times the Verlet list has been built since it was first switched on (by
+ * the steps, and by md_set_state, md_restore and switching the list on). */
+#define MD_OPT_NLIST_BUILDS 7
 /* Verlet neighbour list (the LAMMPS-style list the paper's simulations
  * ran with; the cell list is how it is built). With skin > 0 every pair
  * within r_c + skin is listed from the cell list, and the pair kernel walks
@@ -314,8 +318,10 @@ int md_step(md_handle* h, int64_t nsteps);
  * skin <= 0 switches the list off. Used by the global engine (md_step,
  * md_forces); the resident engine keeps its own per-step cell lists.
  * Cost: one pair pass over about (r_c + skin)^d / r_c^d times the partners
- * in range, and the cell-list kernels return at once on steps without a
- * rebuild. */
+ * in range. The rebuild kernels (cell list and list) are launched every
+ * step and return at once unless a particle has moved skin / 2 (a graph
+ * with a conditional rebuild node measured slower: the node and its gate
+ * cost more than four early exits). */
 int md_set_neighbor_list(md_handle* h, double skin, int32_t max_neighbors);
 int md_set_option(md_handle* h, int32_t key, int64_t value);
 int md_get_option(md_handle* h, int32_t key, int64_t* value);

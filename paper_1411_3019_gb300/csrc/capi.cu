@@ -1117,6 +1117,10 @@ int md_set_neighbor_list(md_handle* h, double skin, int32_t max_neighbors) {
       if (e == cudaSuccess) e = dalloc(h, &A.nl, (size_t)max_neighbors * n);
       if (e == cudaSuccess) e = dalloc(h, &A.nl_cnt, n);
       if (e == cudaSuccess) e = dalloc(h, &A.xb, 3 * n);
+      if (e == cudaSuccess && !A.nl_builds) {
+        e = dalloc(h, &A.nl_builds, 1);
+        if (e == cudaSuccess) e = cudaMemsetAsync(A.nl_builds, 0, sizeof(unsigned long long), h->stream());
+      }
       if (e == cudaSuccess)
         e = h->precision == MD_PREC_FP64 ? dalloc(h, reinterpret_cast<double4_32a**>(&A.rec0), n)
                                          : dalloc(h, reinterpret_cast<float4**>(&A.rec0), n);
@@ -1208,6 +1212,15 @@ int md_get_option(md_handle* h, int32_t key, int64_t* value) {
     case MD_OPT_RESIDENT_THREADS: *value = h->res_threads; return MD_OK;
     case MD_OPT_RESIDENT_STEPS: *value = h->res_steps_per_launch; return MD_OK;
     case MD_OPT_PAIR_TILE: *value = h->A.pair_tile; return MD_OK;
+    case MD_OPT_NLIST_BUILDS: {
+      unsigned long long b = 0;
+      if (h->A.nl_builds) {
+        CK(h, cudaMemcpyAsync(&b, h->A.nl_builds, sizeof(b), cudaMemcpyDeviceToHost, h->stream()));
+        CK(h, cudaStreamSynchronize(h->stream()));
+      }
+      *value = (int64_t)b;
+      return MD_OK;
+    }
     default: return fail(h, MD_ERR_INVALID_ARG, "unknown option");
   }
 }

@@ -1274,6 +1274,7 @@ template <typename R, bool EXCL>
 __global__ void __launch_bounds__(256) k_nl_build(DevArrays A) {
   __shared__ PairTab<R> tab;
   if (*A.nl_dirty == 0u) return;  // uniform: nothing moved far enough
+  if (blockIdx.x == 0 && threadIdx.x == 0) *A.nl_builds += 1ull;
   load_tab<R>(tab, A.types);
   __syncthreads();
   using Rec = typename RecT<R>::T;

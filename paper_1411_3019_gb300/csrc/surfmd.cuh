@@ -142,6 +142,7 @@ struct DevArrays {
   uint32_t* nl_cnt;     // [n] entries per sorted slot
   void* rec0;           // [n] records at the last build
   double* xb;           // [3][n] positions at the last build (user order)
+  unsigned long long* nl_builds;  // list builds so far (counter)
   int32_t nl_max;
   float nl_half_skin2;  // (skin / 2)^2
   double nl_skin;

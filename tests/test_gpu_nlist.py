@@ -115,3 +115,22 @@ def test_switch_off_mid_run_and_repeat_bit_for_bit():
     sim.close()
     ref = oracle_run(systems, 50)[0]
     assert np.abs(st["x"] - ref["x"]).max() <= POS_100["mixed"]
+
+
+def test_rebuild_counts():
+    """The list is rebuilt only in steps where a particle has moved skin / 2:
+    many rebuilds with a tiny skin, none in a few steps with a large one; the
+    seven kernels of a step are launched every step."""
+    counts = {}
+    for skin, steps in ((0.02, 40), (0.6, 5)):
+        systems = _cells(I.c4_replicas(nrep=2, seed=9, nmin=300, nmax=500, rmin=6.0, rmax=9.0,
+                                       precision="mixed", dt=0.002, tol=1e-10), skin)
+        sim = md.Simulation(systems)
+        md.md_set_neighbor_list(sim.h, skin, 64)
+        sim.set_state()
+        b0 = md.md_get_option(sim.h, md.MD_OPT_NLIST_BUILDS)
+        sim.step(steps)
+        assert md.md_last_launch_count(sim.h) == 7 * steps
+        counts[skin] = md.md_get_option(sim.h, md.MD_OPT_NLIST_BUILDS) - b0
+        sim.close()
+    assert counts[0.02] >= 5 and counts[0.6] == 0, counts
