@@ -50,3 +50,31 @@ def test_reference_arm_prints_one_json_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     assert line["config"]["workload"].startswith("plain_sphere")
+
+
+def test_neighbour_list_defaults_and_cell_edge():
+    """Per-workload Verlet-list defaults, explicit skins, and the cell edge
+    the list needs (largest cutoff + skin)."""
+    import numpy as np
+
+    args = bench.parse(["--workload", "ellipsoid_torus"])
+    assert bench.workload_skin(args) == 0.4 and bench.workload_max_neighbors(args) == 64
+    args = bench.parse(["--workload", "bead_molecules"])
+    assert bench.workload_max_neighbors(args) == 128
+    args = bench.parse(["--workload", "replicas"])  # the resident engine's batch keeps the cell list
+    assert bench.workload_skin(args) == 0.0
+    args = bench.parse(["--workload", "ellipsoid_torus", "--skin", "0", "--max-neighbors", "32"])
+    assert bench.workload_skin(args) == 0.0 and bench.workload_max_neighbors(args) == 32
+    rc = np.array([[1.12, 2.5], [2.5, 1.12]])
+    systems = [{"params": {"rcut": rc, "cell_size": 0.0}}]
+    assert bench.cells_for_skin(systems, 0.3)[0]["params"]["cell_size"] == 2.8
+    systems = [{"params": {"rcut": rc, "cell_size": 0.0}}]
+    assert bench.cells_for_skin(systems, 0.0)[0]["params"]["cell_size"] == 0.0
+
+
+def test_neighbour_list_algorithmic_bytes():
+    """With the list, the integrator moves 176 bytes per particle in mixed
+    precision, and the rebuild kernels count no bytes per step."""
+    assert bench.algorithmic_bytes("integrate", 1000, 4096, "mixed", nlist=True) == 176_000
+    assert bench.algorithmic_bytes("scan", 1000, 4096, "mixed", nlist=True) == 0
+    assert bench.algorithmic_bytes("integrate", 1000, 4096, "mixed") == 1000 * 124 + 8 * 4096
