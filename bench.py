@@ -121,11 +121,14 @@ def workload(name: str, rank: int, precision: str, nrep: int = 4096, pair_form: 
 
 
 # Verlet list (skin, entries per particle) per workload when --skin is not
-# given: the list where systems are large and the global engine runs them
-# (measured 1.7-2.2x over a cell list every step); the resident engine's
-# batches and the small float64 systems keep the per-step cell list.
+# given. On every workload measured the list on the global engine is faster
+# than a cell list every step (1.7-2.2x) and than the resident engine's
+# batches (replicas 5.8e9 vs 4.6e9, capsids 1.5e9 vs 1.3e9, thylakoids 1.4e9
+# vs 1.1e9 particle-steps/s); --skin 0 restores the per-step cell list (and
+# with it the autotuner's engine choice). The NVE study keeps the cell list.
 DEFAULT_NLIST = {"ellipsoid_torus": (0.4, 64), "bump_crowders": (0.4, 64), "bead_molecules": (0.4, 128),
-                 "sphere_vs_2d": (0.5, 64), "lj_lattice": (0.3, 128)}
+                 "sphere_vs_2d": (0.5, 64), "lj_lattice": (0.3, 128), "replicas": (0.4, 64),
+                 "capsids": (0.4, 256), "thylakoids": (0.4, 64), "plain_sphere": (0.4, 64)}
 
 
 def workload_skin(args) -> float:

@@ -61,7 +61,9 @@ def test_neighbour_list_defaults_and_cell_edge():
     assert bench.workload_skin(args) == 0.4 and bench.workload_max_neighbors(args) == 64
     args = bench.parse(["--workload", "bead_molecules"])
     assert bench.workload_max_neighbors(args) == 128
-    args = bench.parse(["--workload", "replicas"])  # the resident engine's batch keeps the cell list
+    args = bench.parse(["--workload", "capsids"])
+    assert bench.workload_skin(args) == 0.4 and bench.workload_max_neighbors(args) == 256
+    args = bench.parse(["--workload", "nve_surfaces"])  # the energy study keeps the cell list
     assert bench.workload_skin(args) == 0.0
     args = bench.parse(["--workload", "ellipsoid_torus", "--skin", "0", "--max-neighbors", "32"])
     assert bench.workload_skin(args) == 0.0 and bench.workload_max_neighbors(args) == 32
