@@ -134,3 +134,33 @@ def test_rebuild_counts():
         counts[skin] = md.md_get_option(sim.h, md.MD_OPT_NLIST_BUILDS) - b0
         sim.close()
     assert counts[0.02] >= 5 and counts[0.6] == 0, counts
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_forces_after_set_state_and_resume_from_checkpoint(precision):
+    """The headline workload's shape (ellipsoid + torus) with the list: forces
+    straight after md_set_state come from a fresh list; a checkpoint restored
+    with md_restore (which rebuilds both lists) continues within the parity
+    tolerance of the uninterrupted run, and its forces match the oracle."""
+    skin = 0.3
+    systems = _cells(I.c2_ellipsoid_torus(n_ell=4000, n_tor=1500, seed=8, precision=precision,
+                                          tol=_tol(precision)), skin)
+    with md.Simulation(systems) as a:
+        md.md_set_neighbor_list(a.h, skin, 64)
+        a.set_state()
+        f0, _ = a.forces()
+        assert_forces(systems, a.state()["x"], f0, precision)
+        a.step(30)
+        ck = a.state()
+        a.step(30)
+        xa = a.state()
+    with md.Simulation(systems) as c:
+        md.md_set_neighbor_list(c.h, skin, 64)
+        c.set_state()
+        md.md_restore(c.h, ck["x"], ck["p_half"], ck["step"])
+        c.step(30)
+        xc = c.state()
+        fc, _ = c.forces()
+    assert xc["step"] == 60
+    assert np.abs(xa["x"] - xc["x"]).max() <= POS_100[precision]
+    assert_forces(systems, xc["x"], fc, precision)
