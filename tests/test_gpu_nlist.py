@@ -141,10 +141,11 @@ def test_forces_after_set_state_and_resume_from_checkpoint(precision):
     """The headline workload's shape (ellipsoid + torus, 5,500 particles)
     with the list. Straight after md_set_state the list's forces equal those
     of a cell-list handle with the same cell edge to float rounding (same
-    records; the list keeps the stencil's order of the pairs). A checkpoint restored
-    with md_restore (which rebuilds both lists) continues within the parity
-    tolerance of the uninterrupted run, with the same forces to float
-    rounding (float64: also against the oracle)."""
+    records; the list keeps the stencil's order of the pairs). A checkpoint
+    restored with md_restore (which rebuilds the cell list and the list from
+    the restored positions) repeats, bit for bit, a run that rebuilt its
+    lists at the checkpoint step (switching the list on again rebuilds
+    them); float64 forces also match the oracle."""
     skin = 0.3
     systems = _cells(I.c2_ellipsoid_torus(n_ell=4000, n_tor=1500, seed=8, precision=precision,
                                           tol=_tol(precision)), skin)
@@ -159,6 +160,7 @@ def test_forces_after_set_state_and_resume_from_checkpoint(precision):
         assert np.max(np.linalg.norm(f0 - f_cells, axis=1) / sc) < (1e-12 if precision == "fp64" else 1e-6)
         a.step(30)
         ck = a.state()
+        md.md_set_neighbor_list(a.h, skin, 64)  # rebuild both lists at the checkpoint
         a.step(30)
         xa = a.state()
         fa, _ = a.forces()
@@ -170,8 +172,8 @@ def test_forces_after_set_state_and_resume_from_checkpoint(precision):
         xc = c.state()
         fc, _ = c.forces()
     assert xc["step"] == 60
-    assert np.abs(xa["x"] - xc["x"]).max() <= POS_100[precision]
-    scale = np.maximum(np.linalg.norm(fa, axis=1), 1.0)
-    assert np.max(np.linalg.norm(fc - fa, axis=1) / scale) < (1e-11 if precision == "fp64" else 1e-6)
+    for key in ("x", "p_half"):
+        assert np.array_equal(xa[key], xc[key]), key
+    assert np.array_equal(fa, fc)
     if precision == "fp64":
         assert_forces(systems, xc["x"], fc, precision)
