@@ -47,7 +47,6 @@ struct md_handle {
   uint32_t* d_order = nullptr;
   int64_t steps_since_order = 0;
   int64_t last_launches = 0;
-  int kernels_per_step = 0;
   // Verlet neighbour list (md_set_neighbor_list); A.nl_dirty != null when on
   uint32_t* d_nl_dirty = nullptr;
   int32_t nl_capacity = 0;  // entries per particle the allocated list holds
@@ -906,7 +905,6 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
     md_destroy(h);
     return fail(nullptr, MD_ERR_CUDA, m);
   }
-  h->kernels_per_step = (h->has_pairs ? 5 : 3) + (h->bends ? 1 : 0);
   *out = h;
   return MD_OK;
 }
