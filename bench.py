@@ -132,7 +132,10 @@ DEFAULT_NLIST = {"ellipsoid_torus": (0.4, 64), "bump_crowders": (0.4, 64), "bead
 
 
 def workload_skin(args) -> float:
-    return DEFAULT_NLIST.get(args.workload, (0.0, 0))[0] if args.skin < 0 else args.skin
+    if args.skin >= 0:
+        return args.skin
+    # the resident engine keeps its own per-step cell lists
+    return 0.0 if args.engine == "resident" else DEFAULT_NLIST.get(args.workload, (0.0, 0))[0]
 
 
 def workload_max_neighbors(args) -> int:

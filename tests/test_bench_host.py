@@ -65,6 +65,8 @@ def test_neighbour_list_defaults_and_cell_edge():
     assert bench.workload_skin(args) == 0.4 and bench.workload_max_neighbors(args) == 256
     args = bench.parse(["--workload", "nve_surfaces"])  # the energy study keeps the cell list
     assert bench.workload_skin(args) == 0.0
+    args = bench.parse(["--workload", "replicas", "--engine", "resident"])  # its own cell lists
+    assert bench.workload_skin(args) == 0.0
     args = bench.parse(["--workload", "ellipsoid_torus", "--skin", "0", "--max-neighbors", "32"])
     assert bench.workload_skin(args) == 0.0 and bench.workload_max_neighbors(args) == 32
     rc = np.array([[1.12, 2.5], [2.5, 1.12]])
