@@ -112,3 +112,21 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(mdmod, "library_path", lambda: str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="missing"):
         mdmod.lib()
+
+
+def test_binding_constants_match_the_header():
+    """Every status code, flag, option, pair form and wall kind the header
+    defines has the same value in the binding, and so do the surface kinds
+    and precisions."""
+    from paper_1411_3019_gb300 import md as binding
+
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    defines = {k: int(v.rstrip("uU"), 0) for k, v in
+               re.findall(r"#define\s+(MD_[A-Z0-9_]+)\s+(0x[0-9a-fA-F]+u?|\d+)\b", text)}
+    wanted = [k for k in defines if k.startswith(("MD_OK", "MD_ERR_", "MD_FLAG_", "MD_OPT_", "MD_PAIR_", "MD_WALL_"))]
+    assert len(wanted) >= 24
+    for k in wanted:
+        assert getattr(binding, k) == defines[k], k
+    kinds = dict(re.findall(r"\bMD_SURF_([A-Z0-9_]+)\s*=\s*(\d+)", text))
+    assert {k.lower(): int(v) for k, v in kinds.items()} == binding.SURF_KINDS
+    assert binding.PRECISION == {"fp64": defines["MD_PREC_FP64"], "mixed": defines["MD_PREC_MIXED"]}
