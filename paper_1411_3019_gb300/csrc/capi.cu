@@ -217,6 +217,27 @@ int check_system(const md_surface& s, const md_params& p, SysDev& S, std::string
   S.tol_f = (float)p.rattle_tol;
   if (s.kind == MD_SURF_SPHERE || s.kind == MD_SURF_CYLINDER) S.gconst = -s.p[0] * s.p[0];
   if (s.kind == MD_SURF_TORUS) S.gconst = -s.p[1] * s.p[1];
+  // double-float copies (h = v rounded to float32, l = the rest rounded)
+  auto split = [](double v) {
+    DF r;
+    r.h = (float)v;
+    r.l = (float)(v - (double)r.h);
+    return r;
+  };
+  S.c_zero = (S.c[0] == 0.0 && S.c[1] == 0.0 && S.c[2] == 0.0) ? 1 : 0;
+  for (int d = 0; d < 3; ++d) {
+    S.c_df[d] = split(S.c[d]);
+    S.inv_a2_df[d] = split(S.inv_a2[d]);
+    S.pn_df[d] = split(s.kind == MD_SURF_PLANE ? s.p[d] : 0.0);
+  }
+  S.gconst_df = split(S.gconst);
+  S.R_df = split(s.kind == MD_SURF_TORUS ? s.p[0] : 0.0);
+  S.dt_df = split(S.dt);
+  S.half_dt_df = split(S.half_dt);
+  for (int t = 0; t < kMaxTypes; ++t) {
+    S.dtm_df[t] = split(S.dtm[t]);
+    S.inv_dtm_df[t] = split(S.inv_dtm[t]);
+  }
   for (int d = 0; d < 3; ++d) {
     S.box_lo[d] = p.box_lo[d];
     S.box_len[d] = p.box_hi[d] - p.box_lo[d];

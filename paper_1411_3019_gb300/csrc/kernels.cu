@@ -19,6 +19,7 @@
 #include <type_traits>
 #include <cmath>
 
+#include "df.cuh"
 #include "engine.h"
 
 namespace surfmd {
@@ -87,21 +88,28 @@ __device__ __forceinline__ void gauss3(uint32_t seed, uint32_t rep, uint32_t pid
 // are formed here; binary32 subnormal results, overflow, infinities and NaN
 // take the hardware conversion, so the result is bit-identical to it always.
 //
-// binary64 -> binary32, round to nearest, ties to even: rebias the exponent
-// field in place (1023 - 127 = 896), then drop the low 29 fraction bits with
-// the rounding increment 2^28 - 1 plus the lowest kept bit; a carry out of the
-// fraction moves into the exponent, as rounding up to the next binade must.
+// binary64 -> binary32, round to nearest, ties to even, with 32-bit integer
+// operations on the two words of the binary64 value: the high word's
+// exponent and fraction bits shifted up by 3 with the top 3 bits of the low
+// word shifted in give (exponent << 23 | top 23 fraction bits) modulo 2^32;
+// rebiasing subtracts 896 << 23; the 29 dropped bits round it (half-way cases
+// to the even result), and a carry out of the fraction moves into the
+// exponent, as rounding up to the next binade must.
+__device__ __forceinline__ uint32_t d2f_bits_rn(uint32_t hi, uint32_t lo, uint32_t& up, uint32_t& rest) {
+  const uint32_t t = __funnelshift_l(lo, hi & 0x7fffffffu, 3) - 0xC0000000u;  // 896 << 23 modulo 2^32
+  rest = lo & 0x1fffffffu;
+  up = (rest + (t & 1u) + 0x0fffffffu) >> 29;
+  return t + up;
+}
+
 __device__ __forceinline__ float d2f_rn(double v) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const unsigned long long a = b & 0x7fffffffffffffffull;
-  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
   // biased binary64 exponent in [897, 1150] <=> binary32 exponent in [1, 254]
-  if (a - (897ull << 52) < (254ull << 52)) {
-    const unsigned long long r = a - (896ull << 52);
-    const unsigned long long q = (r + 0x0fffffffull + ((r >> 29) & 1ull)) >> 29;
-    return __uint_as_float(sign | (uint32_t)q);
+  if (((hi >> 20) & 0x7ffu) - 897u < 254u) {
+    uint32_t up, rest;
+    return __uint_as_float((hi & 0x80000000u) | d2f_bits_rn(hi, lo, up, rest));
   }
-  if (a == 0ull) return __uint_as_float(sign);
+  if (((hi & 0x7fffffffu) | lo) == 0u) return __uint_as_float(hi);
   return __double2float_rn(v);
 }
 
@@ -2073,8 +2081,11 @@ __device__ __forceinline__ void integrate_particle_fp64(const DevArrays& A, int6
 }
 
 // ---------------------------------------------------------------------------
-// Mixed path: float32 forces, noise, surface direction, Newton denominator and
-// stopping tests; float64 positions, momenta, constraint values and updates.
+// Mixed path: float32 forces, noise and force combination; the position
+// half, the momentum update and the surface normal of constrained particles
+// in double-float arithmetic (df.cuh, about 48 significant bits, on the
+// float32 pipe) from the float64 masters, which are read and written as
+// float64.
 //
 // Algorithm 1 in multiplier form. The momentum half at x^k and the kick of the
 // position half give q = p^{k-1/2} + dt F^k - s n0, s = n0.(p^{k-1/2} + h F^k)
@@ -2088,55 +2099,18 @@ __device__ __forceinline__ void integrate_particle_fp64(const DevArrays& A, int6
 //
 // The position-half Newton update lambda += g / (a n1.n0) of Algorithm 1 reads
 // mu += g(x(mu)) / (n1.n0) on the line x(mu) = y - mu n0 (mu = a lambda,
-// n1 = grad g(x(mu)); n1 = n0 in the frozen-normal variant), and g along that
-// line is evaluated by the surface's line form below. The full-step momentum
-// p^k is not needed by the step and is formed only on read-out.
+// n1 = grad g(x(mu)); n1 = n0 in the frozen-normal variant). g along the line
+// is evaluated in double-float: for the quadrics (plane, sphere, ellipsoid,
+// cylinder) by its exact line form g(y) - b mu + c mu^2 (b = grad g(y).n0,
+// c = n0.H n0 / 2, H the constant Hessian), for the torus at the point
+// itself; the Newton denominator n1.n0 is float32 (it scales the step, not
+// the root). The other surfaces (Gaussian bump, thylakoid) take the float64
+// form below. The full-step momentum p^k is not needed by the step and is
+// formed only on read-out, with the float64 normal.
 // ---------------------------------------------------------------------------
 
-// Quadric surfaces (plane, sphere, ellipsoid, cylinder): g along the line is
-// exactly g(y) - b mu + c mu^2 with b = grad g(y).n0 and c = n0.H n0 / 2 (H the
-// constant Hessian), so n1.n0 = -dg/dmu = b - 2 c mu.
-struct LineQuadric {
-  double g0, b, c;
-  float bf, cf;
-  __device__ __forceinline__ double g(double mu) { return fma(mu, fma(mu, c, -b), g0); }
-  __device__ __forceinline__ float n1n0(float mu) const { return fmaf(-2.f * mu, cf, bf); }
-};
-
-// Torus: with d = y - centre, rho the in-plane radius and z = d_z - mu n0_z,
-// g = (rho - R)^2 + z^2 - r^2 and rho(mu)^2 = rho_y^2 + D(mu), D = -2 A1 mu +
-// A2 mu^2 (A1 = d_xy.n0_xy, A2 = |n0_xy|^2). rho(mu) is advanced from rho_y by
-// the series sqrt(rho_y^2 + D) = rho_y + w - w^2 / (2 rho_y) + ..., w = D /
-// (2 rho_y), whose next term, w^3 / (2 rho_y^2), is below 1e-15 rho_y while
-// |w| < 1e-5 rho_y (a time step moves a particle far less); beyond that bound
-// rho(mu) is taken from its square root directly.
-struct LineTorus {
-  double dz, tY, rho2, a1x2, a2, inv2rho, n0z, R, mr2;
-  float rhoyf, inv2rhof, a1f, a2f, n0zf, Rf;
-  float ttf, zf;  // rho - R and z at the last evaluation (for n1.n0)
-  __device__ __forceinline__ double g(double mu) {
-    const double D = mu * fma(mu, a2, -a1x2);
-    const double w = D * inv2rho;
-    const float wf = d2f_rn(w);
-    double tt;
-    if (fabsf(wf) < 1e-5f * rhoyf) {
-      tt = (tY + w) - f2d(wf * wf * inv2rhof);
-    } else {
-      const double q2 = rho2 + D;
-      tt = q2 * nr_rsqrt(q2) - R;
-    }
-    const double z = fma(-mu, n0z, dz);
-    ttf = d2f_rn(tt);
-    zf = d2f_rn(z);
-    return fma(tt, tt, fma(z, z, mr2));
-  }
-  // n1 = (2 (rho - R) / rho) (d_xy - mu n0_xy, 0) + (0, 0, 2 z)
-  __device__ __forceinline__ float n1n0(float mu) const {
-    return 2.f * ttf / (ttf + Rf) * fmaf(-mu, a2f, a1f) + 2.f * zf * n0zf;
-  }
-};
-
-// Any other surface: g re-evaluated at x(mu).
+// Any surface by re-evaluation of g at x(mu) in float64 (Gaussian bump,
+// thylakoid composite).
 struct LineGeneric {
   const SysDev* S;
   double yx, yy, yz, n0x, n0y, n0z;
@@ -2175,6 +2149,173 @@ __device__ __forceinline__ bool newton_line(L& line, int max_newton, bool frozen
   return false;
 }
 
+// float64 -> double-float on the integer pipe: h = v rounded to float32 (as
+// d2f_rn), l = the remainder v - h. The remainder is an integer number rem of
+// units 2^(E-1075) of v's binade (E = v's biased exponent; rem is the low
+// bits of the fraction field minus the rounding, |rem| <= 2^28); l keeps its
+// leading bits, rem >> 6 (<= 2^22 in magnitude, so converted exactly by the
+// 1.5 * 2^23 bias), times 2^(E-1069). h + l = v within 2^-46 |v|. Outside
+// 2^-80 <= |v| < 2^128 (zero, tiny or huge values) the split takes one
+// float64 subtraction instead.
+__device__ __forceinline__ DF df_from(double v) {
+  const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
+  const uint32_t e = (hi >> 20) & 0x7ffu;
+  if (e - 943u < 208u) {  // biased exponent in [943, 1150]
+    uint32_t up, rest;
+    const uint32_t q = d2f_bits_rn(hi, lo, up, rest);
+    const int32_t rem = (int32_t)rest - (int32_t)(up << 29);  // dropped bits, less 2^29 if rounded up
+    const float k = __fsub_rn(__int_as_float(0x4B400000 + (rem >> 6)), 12582912.0f);
+    const float l = __fmul_rn(k, __uint_as_float((e - 942u) << 23));
+    const uint32_t sign = hi & 0x80000000u;
+    return {__uint_as_float(sign | q), sign ? -l : l};
+  }
+  const float h = d2f_rn(v);
+  return {h, d2f_rn(v - f2d(h))};
+}
+__device__ __forceinline__ double df_to(DF a) { return f2d(a.h) + f2d(a.l); }
+
+__device__ __forceinline__ bool df_surface(int32_t kind) {
+  return kind == kPlane || kind == kSphere || kind == kEllipsoid || kind == kCylinder || kind == kTorus;
+}
+
+// g on the line x(mu) = y - mu n0 in double-float, D = y - c, N = n0.
+// Quadrics: the line form g(y) - b mu + c mu^2. Torus: g at the point, with
+// rho - R, rho and x(mu) - c kept in float32 for the Newton denominator.
+struct DFTorusEval {
+  float ttf, rhof, e0, e1, e2;
+  __device__ __forceinline__ DF g(const SysDev& S, const DF D[3], const DF N[3], DF mu) {
+    DF E[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) E[d] = df_sub(D[d], df_mul(N[d], mu));
+    const DF rho = df_sqrt(df_add(df_mul(E[0], E[0]), df_mul(E[1], E[1])));
+    const DF t = df_sub(rho, S.R_df);
+    ttf = t.h;
+    rhof = rho.h;
+    e0 = E[0].h; e1 = E[1].h; e2 = E[2].h;
+    return df_add(df_add(df_mul(t, t), df_mul(E[2], E[2])), S.gconst_df);
+  }
+  // n1.n0 = 2 (rho - R)/rho (e_xy . n0_xy) + 2 e_z n0_z
+  __device__ __forceinline__ float n1n0(const DF N[3]) const {
+    return 2.f * ttf / rhof * fmaf(e0, N[0].h, e1 * N[1].h) + 2.f * e2 * N[2].h;
+  }
+};
+
+// Position half of a constrained particle on a plane, sphere, ellipsoid,
+// cylinder or torus (multiplier form above): reads x^k, p^{k-1/2} (or p^k on
+// the first step) and the combined force F, returns x^{k+1} and p^{k+1/2}.
+// y - c, n0 = grad g(x^k) and g in double-float. For the quadrics the Newton
+// iteration runs on the line form first in float32, which brings mu to
+// float32 resolution (about 1e-7 of mu n0, itself about 1e-4 sigma), then
+// continues in double-float until g, evaluated in double-float, meets the
+// tolerance; the torus iterates in double-float throughout. x^{k+1} =
+// c + (y - c) - mu n0 is rounded once to float64; p^{k+1/2} = p + (kick F -
+// (m/dt) mu n0) adds a float32 increment to the float64 momentum.
+__device__ __forceinline__ void position_half_df(const SysDev& S, uint32_t ty, int mode, const double xv[3],
+                                                 const double pv[3], const float pf[3], const float F[3],
+                                                 uint32_t* status, double xo[3], double qo[3]) {
+  DF D[3], N[3];
+  const DF kick = mode ? S.dt_df : S.half_dt_df;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const DF q0 = df_add(df_from(pv[d]), df_mul_f(kick, F[d]));  // q0 = p + kick F
+    const DF X = df_from(xv[d]);
+    N[d] = S.c_zero ? X : df_sub(X, S.c_df[d]);                   // x - c (n0 below)
+    D[d] = df_add(N[d], df_mul(S.dtm_df[ty], q0));               // y - c = x - c + (dt/m) q0
+  }
+  DF gy{0.f, 0.f}, b{0.f, 0.f};
+  float c = 0.f;
+  switch (S.kind) {
+    case kPlane:
+#pragma unroll
+      for (int d = 0; d < 3; ++d) N[d] = S.pn_df[d];
+      gy = df_dot3(S.pn_df, D);
+      b = df_dot3(S.pn_df, N);
+      break;
+    case kEllipsoid: {
+      DF U[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        N[d] = df_scale2(df_mul(N[d], S.inv_a2_df[d]), 2.f);
+        U[d] = df_mul(D[d], S.inv_a2_df[d]);
+        c = fmaf(N[d].h * N[d].h, S.inv_a2_df[d].h, c);
+      }
+      gy = df_add_f(df_dot3(U, D), -1.f);
+      b = df_scale2(df_dot3(U, N), 2.f);
+      break;
+    }
+    case kTorus: {
+      const DF rho = df_sqrt(df_add(df_mul(N[0], N[0]), df_mul(N[1], N[1])));
+      const DF q = df_scale2(df_div(df_sub(rho, S.R_df), rho), 2.f);  // 2 (rho - R) / rho
+      N[0] = df_mul(q, N[0]);
+      N[1] = df_mul(q, N[1]);
+      N[2] = df_scale2(N[2], 2.f);
+      break;
+    }
+    default: {  // sphere; cylinder without the axis component (n0 has none)
+      DF M[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const bool off = S.kind == kCylinder && d == S.axis;
+        M[d] = off ? DF{0.f, 0.f} : D[d];
+        N[d] = off ? DF{0.f, 0.f} : df_scale2(N[d], 2.f);
+      }
+      gy = df_add(df_dot3(M, M), S.gconst_df);
+      b = df_scale2(df_dot3(M, N), 2.f);
+      break;
+    }
+  }
+  const float nnf = fmaf(N[0].h, N[0].h, fmaf(N[1].h, N[1].h, N[2].h * N[2].h));
+  if (S.kind == kSphere || S.kind == kCylinder) c = nnf;
+  float mu0 = 0.f;
+  if (mode) {  // mu_0 = (dt/m) n0.(p + h F) / |n0|^2
+    float sp = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) sp = fmaf(N[d].h, fmaf(S.half_dt_f, F[d], pf[d]), sp);
+    mu0 = S.dtm_f[ty] * sp / nnf;
+  }
+  const float tol_n = 0.99f * S.tol_f * sqrtf(nnf);
+  // round-off floor: an update below 4 units of the double-float resolution of the position
+  const float dmax = fmaxf(fabsf(D[0].h), fmaxf(fabsf(D[1].h), fabsf(D[2].h)));
+  const float floor_mu = 4.f * 0x1p-47f * dmax / fmaxf(fabsf(N[0].h), fmaxf(fabsf(N[1].h), fabsf(N[2].h)));
+  const bool torus = S.kind == kTorus;
+  int it = 0;
+  if (!torus) {  // float32 Newton on the line form g(y) - b mu + c mu^2
+    for (; it < S.max_newton; ++it) {
+      const float gf = fmaf(fmaf(c, mu0, -b.h), mu0, gy.h);
+      if (fabsf(gf) < 0.5f * tol_n) break;
+      const float dmu = gf * __frcp_rn(S.frozen ? nnf : fmaf(-2.f * mu0, c, b.h));
+      mu0 += dmu;
+      if (fabsf(dmu) <= 0x1p-22f * fabsf(mu0)) {
+        ++it;
+        break;
+      }
+    }
+  }
+  DFTorusEval T;
+  DF mu = {mu0, 0.f};
+  DF g = torus ? T.g(S, D, N, mu) : df_add_f(df_sub(gy, df_mul(b, mu)), c * mu.h * mu.h);
+  bool ok = false;
+  for (;; ++it) {
+    if (fabsf(g.h) < tol_n) { ok = true; break; }
+    if (it >= S.max_newton) break;
+    const float den = S.frozen ? nnf : (torus ? T.n1n0(N) : fmaf(-2.f * mu.h, c, b.h));
+    const float dmu = g.h * __frcp_rn(den);
+    mu = df_add_f(mu, dmu);
+    if (it > 0 && fabsf(dmu) <= floor_mu) { ok = true; break; }
+    g = torus ? T.g(S, D, N, mu) : df_add_f(df_sub(gy, df_mul(b, mu)), c * mu.h * mu.h);
+  }
+  if (!ok) flag(status, kFlagRattle);
+  const float kickf = mode ? S.dt_df.h : S.half_dt_df.h;
+  const float cm = mu.h * S.inv_dtm_df[ty].h;  // (m/dt) mu
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    DF e = df_sub(D[d], df_mul(N[d], mu));  // (y - c) - mu n0
+    if (!S.c_zero) e = df_add(e, S.c_df[d]);
+    xo[d] = df_to(e);
+    qo[d] = pv[d] + f2d(fmaf(kickf, F[d], -cm * N[d].h));  // p + kick F - (m/dt) mu n0
+  }
+}
+
 template <class Bin>
 __device__ __forceinline__ void integrate_particle_mixed(const DevArrays& A, int64_t i, Force3<float> fr_in,
                                                          unsigned long long k, int mode, const Bin& bin) {
@@ -2187,101 +2328,55 @@ __device__ __forceinline__ void integrate_particle_mixed(const DevArrays& A, int
   const float pxf = d2f_rn(px), pyf = d2f_rn(py), pzf = d2f_rn(pz);
   Force3<float> F = combine<float>(S, A.types, ty, (uint32_t)(i - S.first), k, mode, fr_in, pxf, pyf, pzf);
   if (S.kind == kXY2D) F.z = 0.f;  // 2D plane: no z update
-  const double kick = mode ? S.dt : S.half_dt;
-  double qx = fma(kick, f2d(F.x), px), qy = fma(kick, f2d(F.y), py), qz = fma(kick, f2d(F.z), pz);
-  const double dtm = S.dtm[ty];
-  const double yx = fma(dtm, qx, x), yy = fma(dtm, qy, y), yz = fma(dtm, qz, z);
-  double xn = yx, yn = yy, zn = yz;
-  if (meta_con(m)) {
-    const float xf = d2f_rn(x), yf = d2f_rn(y), zf = d2f_rn(z);
-    float n0xf, n0yf, n0zf;
-    Piece q0{};
-    if (S.kind == kThylakoid) {  // composite surface: the piece at x^k, held for the solve
-      q0 = thyl_select(S, x, y, z);
-      double gx, gy, gz;
-      thyl_eval(S, q0, x, y, z, gx, gy, gz);
-      n0xf = d2f_rn(gx); n0yf = d2f_rn(gy); n0zf = d2f_rn(gz);
-    } else {
-      surf_grad_f(S, xf - S.c_f[0], yf - S.c_f[1], zf - S.c_f[2], n0xf, n0yf, n0zf);
-    }
-    const float nnf = fmaf(n0xf, n0xf, fmaf(n0yf, n0yf, n0zf * n0zf));
-    float mu0f = 0.f;
-    if (mode) {  // mu_0 = (dt/m) n0.(p + h F) / |n0|^2
-      const float hf = S.half_dt_f;
-      const float sp = fmaf(n0xf, fmaf(hf, F.x, pxf), fmaf(n0yf, fmaf(hf, F.y, pyf), n0zf * fmaf(hf, F.z, pzf)));
-      mu0f = S.dtm_f[ty] * sp / nnf;
-    }
-    const float tol_n = 0.99f * S.tol_f * sqrtf(nnf);
-    const float floor_mu = 4.f * (float)DBL_EPSILON * fmaxf(fabsf(xf), fmaxf(fabsf(yf), fabsf(zf))) /
-                           fmaxf(fabsf(n0xf), fmaxf(fabsf(n0yf), fabsf(n0zf)));
-    const double n0x = f2d(n0xf), n0y = f2d(n0yf), n0z = f2d(n0zf);
-    const double dx = yx - S.c[0], dy = yy - S.c[1], dz = yz - S.c[2];
-    double mu;
-    bool ok;
-    switch (S.kind) {
-      case kSphere:
-      case kCylinder:
-      case kEllipsoid:
-      case kPlane: {
-        LineQuadric L;
-        const double tx = f2d(2.f * n0xf), ty2 = f2d(2.f * n0yf), tz = f2d(2.f * n0zf);  // 2 n0, exact
-        if (S.kind == kEllipsoid) {
-          const double ux = dx * S.inv_a2[0], uy = dy * S.inv_a2[1], uz = dz * S.inv_a2[2];
-          L.g0 = fma(ux, dx, fma(uy, dy, fma(uz, dz, -1.0)));
-          L.b = fma(ux, tx, fma(uy, ty2, uz * tz));
-          L.cf = fmaf(n0xf * n0xf, S.inv_a2_f[0], fmaf(n0yf * n0yf, S.inv_a2_f[1], n0zf * n0zf * S.inv_a2_f[2]));
-        } else if (S.kind == kPlane) {
-          L.g0 = fma(S.p[0], dx, fma(S.p[1], dy, S.p[2] * dz));
-          L.b = fma(S.p[0], n0x, fma(S.p[1], n0y, S.p[2] * n0z));
-          L.cf = 0.f;
-        } else {  // sphere; cylinder with the axis component of d dropped (n0 has none)
-          const double ex = (S.kind == kCylinder && S.axis == 0) ? 0.0 : dx;
-          const double ey = (S.kind == kCylinder && S.axis == 1) ? 0.0 : dy;
-          const double ez = (S.kind == kCylinder && S.axis == 2) ? 0.0 : dz;
-          L.g0 = fma(ex, ex, fma(ey, ey, fma(ez, ez, S.gconst)));
-          L.b = fma(ex, tx, fma(ey, ty2, ez * tz));
-          L.cf = nnf;
-        }
-        L.c = f2d(L.cf);
-        L.bf = d2f_rn(L.b);
-        ok = newton_line(L, S.max_newton, S.frozen, nnf, tol_n, floor_mu, mu0f, mu);
-        break;
+  double xn, yn, zn, qx, qy, qz;
+  if (meta_con(m) && df_surface(S.kind)) {
+    const double xv[3] = {x, y, z}, pv[3] = {px, py, pz};
+    const float pf[3] = {pxf, pyf, pzf}, Fv[3] = {F.x, F.y, F.z};
+    double xo[3], qo[3];
+    position_half_df(S, ty, mode, xv, pv, pf, Fv, A.status, xo, qo);
+    xn = xo[0]; yn = xo[1]; zn = xo[2];
+    qx = qo[0]; qy = qo[1]; qz = qo[2];
+  } else {
+    const double kick = mode ? S.dt : S.half_dt;
+    qx = fma(kick, f2d(F.x), px); qy = fma(kick, f2d(F.y), py); qz = fma(kick, f2d(F.z), pz);
+    const double dtm = S.dtm[ty];
+    const double yx = fma(dtm, qx, x), yy = fma(dtm, qy, y), yz = fma(dtm, qz, z);
+    xn = yx; yn = yy; zn = yz;
+    if (meta_con(m)) {  // Gaussian bump, thylakoid: float64 line
+      const float xf = d2f_rn(x), yf = d2f_rn(y), zf = d2f_rn(z);
+      float n0xf, n0yf, n0zf;
+      Piece q0{};
+      if (S.kind == kThylakoid) {  // composite surface: the piece at x^k, held for the solve
+        q0 = thyl_select(S, x, y, z);
+        double gx, gy, gz;
+        thyl_eval(S, q0, x, y, z, gx, gy, gz);
+        n0xf = d2f_rn(gx); n0yf = d2f_rn(gy); n0zf = d2f_rn(gz);
+      } else {
+        surf_grad_f(S, xf - S.c_f[0], yf - S.c_f[1], zf - S.c_f[2], n0xf, n0yf, n0zf);
       }
-      case kTorus: {
-        LineTorus L;
-        L.rho2 = fma(dx, dx, dy * dy);
-        const double ir = nr_rsqrt(L.rho2);
-        L.R = S.p[0];
-        L.mr2 = S.gconst;
-        L.tY = fma(L.rho2, ir, -L.R);
-        L.inv2rho = 0.5 * ir;
-        L.dz = dz;
-        L.n0z = n0z;
-        L.a1x2 = fma(dx, f2d(2.f * n0xf), dy * f2d(2.f * n0yf));
-        L.a2f = fmaf(n0xf, n0xf, n0yf * n0yf);
-        L.a2 = f2d(L.a2f);
-        L.a1f = 0.5f * d2f_rn(L.a1x2);
-        L.inv2rhof = d2f_rn(L.inv2rho);
-        L.Rf = S.p_f[0];
-        L.rhoyf = d2f_rn(L.tY) + L.Rf;
-        L.n0zf = n0zf;
-        ok = newton_line(L, S.max_newton, S.frozen, nnf, tol_n, floor_mu, mu0f, mu);
-        break;
+      const float nnf = fmaf(n0xf, n0xf, fmaf(n0yf, n0yf, n0zf * n0zf));
+      float mu0f = 0.f;
+      if (mode) {  // mu_0 = (dt/m) n0.(p + h F) / |n0|^2
+        const float hf = S.half_dt_f;
+        const float sp =
+            fmaf(n0xf, fmaf(hf, F.x, pxf), fmaf(n0yf, fmaf(hf, F.y, pyf), n0zf * fmaf(hf, F.z, pzf)));
+        mu0f = S.dtm_f[ty] * sp / nnf;
       }
-      default: {
-        LineGeneric L;
-        L.S = &S;
-        L.yx = yx; L.yy = yy; L.yz = yz;
-        L.n0x = n0x; L.n0y = n0y; L.n0z = n0z;
-        L.n0xf = n0xf; L.n0yf = n0yf; L.n0zf = n0zf;
-        L.q = q0;
-        ok = newton_line(L, S.max_newton, S.frozen, nnf, tol_n, floor_mu, mu0f, mu);
-      }
+      const float tol_n = 0.99f * S.tol_f * sqrtf(nnf);
+      const float floor_mu = 4.f * (float)DBL_EPSILON * fmaxf(fabsf(xf), fmaxf(fabsf(yf), fabsf(zf))) /
+                             fmaxf(fabsf(n0xf), fmaxf(fabsf(n0yf), fabsf(n0zf)));
+      LineGeneric L;
+      L.S = &S;
+      L.yx = yx; L.yy = yy; L.yz = yz;
+      L.n0x = f2d(n0xf); L.n0y = f2d(n0yf); L.n0z = f2d(n0zf);
+      L.n0xf = n0xf; L.n0yf = n0yf; L.n0zf = n0zf;
+      L.q = q0;
+      double mu;
+      if (!newton_line(L, S.max_newton, S.frozen, nnf, tol_n, floor_mu, mu0f, mu)) flag(A.status, kFlagRattle);
+      xn = fma(-mu, L.n0x, yx); yn = fma(-mu, L.n0y, yy); zn = fma(-mu, L.n0z, yz);
+      const double c = mu * S.inv_dtm[ty];
+      qx = fma(-c, L.n0x, qx); qy = fma(-c, L.n0y, qy); qz = fma(-c, L.n0z, qz);
     }
-    if (!ok) flag(A.status, kFlagRattle);
-    xn = fma(-mu, n0x, yx); yn = fma(-mu, n0y, yy); zn = fma(-mu, n0z, yz);
-    const double c = mu * S.inv_dtm[ty];
-    qx = fma(-c, n0x, qx); qy = fma(-c, n0y, qy); qz = fma(-c, n0z, qz);
   }
   if (!(finite_bits(xn) && finite_bits(yn) && finite_bits(zn) && finite_bits(qx) && finite_bits(qy) &&
         finite_bits(qz)))
@@ -2608,8 +2703,9 @@ __global__ void k_advance(unsigned long long* step, int32_t* mode) {
   *mode = 1;
 }
 
-// p^k = momentum half of Algorithm 1 from p^{k-1/2} and F^k (state unchanged),
-// with the same arithmetic as k_integrate.
+// p^k = momentum half of Algorithm 1 from p^{k-1/2} and F^k (state unchanged):
+// the force combination as in k_integrate, the projection with the float64
+// normal at x^k in both precisions.
 template <typename R>
 __global__ void k_finish(DevArrays A) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -2631,22 +2727,9 @@ __global__ void k_finish(DevArrays A) {
   if (S.kind == kXY2D) Fr.z = (R)0;
   const bool con = meta_con(m);
   double nx = 0.0, ny = 0.0, nz = 0.0, inv_nn = 0.0;
-  if (con) {
-    if (sizeof(R) == 4) {
-      float fx, fy, fz;
-      if (S.kind == kThylakoid) {
-        double gx, gy, gz;
-        surf_eval(S, x, y, z, gx, gy, gz);
-        fx = d2f_rn(gx); fy = d2f_rn(gy); fz = d2f_rn(gz);
-      } else {
-        surf_grad_f(S, (float)x - S.c_f[0], (float)y - S.c_f[1], (float)z - S.c_f[2], fx, fy, fz);
-      }
-      nx = fx; ny = fy; nz = fz;
-      inv_nn = (double)(1.0f / fmaf(fx, fx, fmaf(fy, fy, fz * fz)));
-    } else {
-      surf_n(S, surf_g(S, x, y, z), nx, ny, nz);
-      inv_nn = nr_rcp(fma(nx, nx, fma(ny, ny, nz * nz)));
-    }
+  if (con) {  // the float64 normal in both precisions: n.p^k = 0 to float64 rounding
+    surf_eval(S, x, y, z, nx, ny, nz);
+    inv_nn = 1.0 / fma(nx, nx, fma(ny, ny, nz * nz));
   }
   momentum_half(S.half_dt, (double)Fr.x, (double)Fr.y, (double)Fr.z, con, nx, ny, nz, inv_nn, px, py, pz);
   A.pk[i] = px; A.pk[n + i] = py; A.pk[2 * n + i] = pz;

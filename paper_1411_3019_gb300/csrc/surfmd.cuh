@@ -29,6 +29,12 @@ __host__ __device__ inline uint32_t meta_type(uint32_t m) { return m & 7u; }
 __host__ __device__ inline bool meta_con(uint32_t m) { return (m >> 3) & 1u; }
 __host__ __device__ inline uint32_t meta_sys(uint32_t m) { return m >> 4; }
 
+// A double-float value h + l (two float32 numbers, |l| <= ulp(h) / 2); the
+// arithmetic is in df.cuh.
+struct DF {
+  float h, l;
+};
+
 // One system's constants as the kernels read them.
 struct SysDev {
   // surface g(x) = 0
@@ -50,6 +56,13 @@ struct SysDev {
   float dtm_f[kMaxTypes];
   float half_dt_f, tol_f;
   double gconst;             // constant term of g: -R^2 (sphere, cylinder), -r^2 (torus)
+  // double-float copies for the mixed path's position half
+  DF c_df[3], inv_a2_df[3], pn_df[3];  // centre, ellipsoid 1/a_d^2, plane normal
+  DF gconst_df, R_df;                  // constant term of g; torus R
+  DF dt_df, half_dt_df;
+  DF dtm_df[kMaxTypes], inv_dtm_df[kMaxTypes];  // dt/m and m/dt per type
+  int32_t c_zero;            // 1: the centre is the origin
+  int32_t pad_df;
   // box and cell grid
   double box_lo[3], box_len[3], inv_box_len[3];
   int32_t periodic[3];

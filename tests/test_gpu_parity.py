@@ -42,8 +42,8 @@ def test_trajectory_matches_oracle(precision, nsteps):
     assert st["step"] == 7 + nsteps
     tol = systems[0]["params"]["rattle_tol"]
     assert res["max_g_over_gradg"] < tol
-    # mixed: the normal direction of the projection is float32 (n.v ~ 1e-7 |v|)
-    assert res["max_n_dot_v"] < (1e-9 if precision == "fp64" else 1e-6)
+    # both precisions project p^k with the float64 normal
+    assert res["max_n_dot_v"] < 1e-9
     assert_forces(systems, st["x"], f, precision)
     assert obs[0]["ndof"] == 2 * systems[0]["n"]
     assert obs[0]["kT"] == pytest.approx(obs_ref[0]["kT"], rel=1e-6)
