@@ -394,7 +394,7 @@ int md_cell_list(md_handle* h, uint32_t* sorted_ids, uint32_t* sorted_cells,
  * an application whose device memory is all owned by its own allocator.
  * It computes f = -grad V (pair, bond and wall terms) and the per-particle
  * energy u at positions d_x, exactly as md_forces does for a handle with the
- * same surface and parameters, using a scratch array of about 10 MB that the
+ * same surface and parameters, using a scratch array of about 11 MB that the
  * library reserves in device global memory when its device code is loaded
  * (each device that loads the library keeps it until the process exits).
  *   n <= 65536 particles (else MD_ERR_INVALID_ARG); cell grids larger than

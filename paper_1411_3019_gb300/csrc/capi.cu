@@ -104,6 +104,14 @@ cudaError_t dalloc(md_handle* h, T** p, size_t count) {
   return e;
 }
 
+// double-float copy of a float64 constant: h = v rounded to float32, l = the rest rounded
+DF df_split(double v) {
+  DF r;
+  r.h = (float)v;
+  r.l = (float)(v - (double)r.h);
+  return r;
+}
+
 bool symmetric_ok(const double t[MD_MAX_TYPES][MD_MAX_TYPES], int nt) {
   for (int a = 0; a < nt; ++a)
     for (int b = 0; b < nt; ++b)
@@ -217,26 +225,19 @@ int check_system(const md_surface& s, const md_params& p, SysDev& S, std::string
   S.tol_f = (float)p.rattle_tol;
   if (s.kind == MD_SURF_SPHERE || s.kind == MD_SURF_CYLINDER) S.gconst = -s.p[0] * s.p[0];
   if (s.kind == MD_SURF_TORUS) S.gconst = -s.p[1] * s.p[1];
-  // double-float copies (h = v rounded to float32, l = the rest rounded)
-  auto split = [](double v) {
-    DF r;
-    r.h = (float)v;
-    r.l = (float)(v - (double)r.h);
-    return r;
-  };
   S.c_zero = (S.c[0] == 0.0 && S.c[1] == 0.0 && S.c[2] == 0.0) ? 1 : 0;
   for (int d = 0; d < 3; ++d) {
-    S.c_df[d] = split(S.c[d]);
-    S.inv_a2_df[d] = split(S.inv_a2[d]);
-    S.pn_df[d] = split(s.kind == MD_SURF_PLANE ? s.p[d] : 0.0);
+    S.c_df[d] = df_split(S.c[d]);
+    S.inv_a2_df[d] = df_split(S.inv_a2[d]);
+    S.pn_df[d] = df_split(s.kind == MD_SURF_PLANE ? s.p[d] : 0.0);
   }
-  S.gconst_df = split(S.gconst);
-  S.R_df = split(s.kind == MD_SURF_TORUS ? s.p[0] : 0.0);
-  S.dt_df = split(S.dt);
-  S.half_dt_df = split(S.half_dt);
+  S.gconst_df = df_split(S.gconst);
+  S.R_df = df_split(s.kind == MD_SURF_TORUS ? s.p[0] : 0.0);
+  S.dt_df = df_split(S.dt);
+  S.half_dt_df = df_split(S.half_dt);
   for (int t = 0; t < kMaxTypes; ++t) {
-    S.dtm_df[t] = split(S.dtm[t]);
-    S.inv_dtm_df[t] = split(S.inv_dtm[t]);
+    S.dtm_df[t] = df_split(S.dtm[t]);
+    S.inv_dtm_df[t] = df_split(S.inv_dtm[t]);
   }
   for (int d = 0; d < 3; ++d) {
     S.box_lo[d] = p.box_lo[d];
@@ -345,6 +346,14 @@ void fill_types(const md_params& p, TypeTable& T) {
       T.shift_f[a][b] = (float)shift;
       T.lin_f[a][b] = (float)lin;
       T.rc_f[a][b] = (float)rc;
+      // mixed path, pair terms from double-float displacements
+      const double sg6 = std::pow(sg * sg, 3.0);
+      T.rc2m_f[a][b] = (float)(rc * rc * (1.0 + std::ldexp(1.0, -18)));
+      T.rc2_df[a][b] = df_split(rc * rc);
+      T.s6x2_df[a][b] = df_split(2.0 * sg6);
+      T.c24_f[a][b] = (float)(24.0 * ep * sg6);
+      T.c4_f[a][b] = (float)(4.0 * ep * sg6);
+      T.s6_f[a][b] = (float)sg6;
     }
   }
 }
@@ -792,6 +801,7 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
   }
   if (!h->has_pairs) A.nbucket = 1;
   A.pair_lanes = 1;
+  A.ntypes = prms[0].ntypes;
   A.rec_cell = (!h->excl && cell_total < (uint64_t(1) << 29)) ? 1 : 0;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
@@ -818,6 +828,7 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
     al(h->precision == MD_PREC_FP64 ? dalloc(h, reinterpret_cast<double4_32a**>(&r), n)
                                     : dalloc(h, reinterpret_cast<float4**>(&r), n));
     A.rec = r;
+    if (h->precision != MD_PREC_FP64) al(dalloc(h, &A.rec_lo, n));
   }
   al(dalloc(h, &A.meta, n));
   if (h->excl) al(dalloc(h, &A.mol, n));
@@ -1143,6 +1154,7 @@ int md_set_neighbor_list(md_handle* h, double skin, int32_t max_neighbors) {
       if (e == cudaSuccess)
         e = h->precision == MD_PREC_FP64 ? dalloc(h, reinterpret_cast<double4_32a**>(&A.rec0), n)
                                          : dalloc(h, reinterpret_cast<float4**>(&A.rec0), n);
+      if (e == cudaSuccess && h->precision != MD_PREC_FP64) e = dalloc(h, &A.rec0_lo, n);
       if (e != cudaSuccess) return cuda_fail(h, e, "neighbour list allocation");
       h->nl_capacity = max_neighbors;
     }
@@ -1474,7 +1486,8 @@ struct NaLayout {
   static constexpr size_t x = 0;
   static constexpr size_t f = x + na_align(3 * N * sizeof(double));
   static constexpr size_t rec = f + na_align(N * sizeof(double4_32a));
-  static constexpr size_t meta = rec + na_align(N * sizeof(double4_32a));
+  static constexpr size_t rec_lo = rec + na_align(N * sizeof(double4_32a));
+  static constexpr size_t meta = rec_lo + na_align(N * sizeof(float4));
   static constexpr size_t mol = meta + na_align(N * 4);
   static constexpr size_t cell = mol + na_align(N * 4);
   static constexpr size_t rank = cell + na_align(N * 4);
@@ -1498,7 +1511,7 @@ struct NaLayout {
 
 }  // namespace
 
-// The scratch array (about 10 MB). In host code its name is only a stand-in
+// The scratch array (about 11 MB). In host code its name is only a stand-in
 // for the device symbol; its device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_forces_scratch[NaLayout::total];
 
@@ -1612,6 +1625,8 @@ extern "C" int md_forces_noalloc(const md_surface* surf, const md_params* prm, i
   A.x = reinterpret_cast<double*>(base + NaLayout::x);
   A.f = base + NaLayout::f;
   A.rec = base + NaLayout::rec;
+  A.rec_lo = prm->precision == MD_PREC_FP64 ? nullptr : reinterpret_cast<float4*>(base + NaLayout::rec_lo);
+  A.ntypes = prm->ntypes;
   A.meta = reinterpret_cast<uint32_t*>(base + NaLayout::meta);
   A.mol = excl ? reinterpret_cast<int32_t*>(base + NaLayout::mol) : nullptr;
   A.cell = reinterpret_cast<uint32_t*>(base + NaLayout::cell);

@@ -125,6 +125,31 @@ __device__ __forceinline__ double f2d(float v) {
   return (double)v;
 }
 
+// float64 -> double-float on the integer pipe: h = v rounded to float32 (as
+// d2f_rn), l = the remainder v - h. The remainder is an integer number rem of
+// units 2^(E-1075) of v's binade (E = v's biased exponent; rem is the low
+// bits of the fraction field minus the rounding, |rem| <= 2^28); l keeps its
+// leading bits, rem >> 6 (<= 2^22 in magnitude, so converted exactly by the
+// 1.5 * 2^23 bias), times 2^(E-1069). h + l = v within 2^-46 |v|. Outside
+// 2^-80 <= |v| < 2^128 (zero, tiny or huge values) the split takes one
+// float64 subtraction instead.
+__device__ __forceinline__ DF df_from(double v) {
+  const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
+  const uint32_t e = (hi >> 20) & 0x7ffu;
+  if (e - 943u < 208u) {  // biased exponent in [943, 1150]
+    uint32_t up, rest;
+    const uint32_t q = d2f_bits_rn(hi, lo, up, rest);
+    const int32_t rem = (int32_t)rest - (int32_t)(up << 29);  // dropped bits, less 2^29 if rounded up
+    const float k = __fsub_rn(__int_as_float(0x4B400000 + (rem >> 6)), 12582912.0f);
+    const float l = __fmul_rn(k, __uint_as_float((e - 942u) << 23));
+    const uint32_t sign = hi & 0x80000000u;
+    return {__uint_as_float(sign | q), sign ? -l : l};
+  }
+  const float h = d2f_rn(v);
+  return {h, d2f_rn(v - f2d(h))};
+}
+__device__ __forceinline__ double df_to(DF a) { return f2d(a.h) + f2d(a.l); }
+
 // ---------------------------------------------------------------------------
 // Surfaces: g(x) and n = grad g (unnormalised), float64.
 // ---------------------------------------------------------------------------
@@ -377,7 +402,7 @@ __global__ void k_build_meta(DevArrays A, const int64_t* __restrict__ first, int
   }
   const SysDev& S = A.sys[lo];
   int t = type ? type[i] : 0;
-  if (t < 0 || t >= kMaxTypes) {
+  if (t < 0 || t >= A.ntypes) {
     flag(A.status, kFlagOffSurface);
     t = 0;
   }
@@ -624,13 +649,17 @@ __global__ void k_scatter(DevArrays A) {
   A.stag_tmp[A.start[b] + A.rank[i]] = (uint32_t)i;
 }
 
-template <typename R> __device__ __forceinline__ void put_rec(void* rec, uint32_t s, double ox, double oy,
-                                                              double oz, uint32_t bits);
-template <> __device__ __forceinline__ void put_rec<float>(void* rec, uint32_t s, double ox, double oy,
-                                                           double oz, uint32_t bits) {
-  reinterpret_cast<float4*>(rec)[s] = make_float4(d2f_rn(ox), d2f_rn(oy), d2f_rn(oz), __uint_as_float(bits));
+// Record of slot s. Mixed path: the offset rounded to float32 (the high
+// part) and the remainder (the low part, in lo[s]); float64 path: the offset.
+template <typename R> __device__ __forceinline__ void put_rec(void* rec, float4* lo, uint32_t s, double ox,
+                                                              double oy, double oz, uint32_t bits);
+template <> __device__ __forceinline__ void put_rec<float>(void* rec, float4* lo, uint32_t s, double ox,
+                                                           double oy, double oz, uint32_t bits) {
+  const DF x = df_from(ox), y = df_from(oy), z = df_from(oz);
+  reinterpret_cast<float4*>(rec)[s] = make_float4(x.h, y.h, z.h, __uint_as_float(bits));
+  lo[s] = make_float4(x.l, y.l, z.l, 0.f);
 }
-template <> __device__ __forceinline__ void put_rec<double>(void* rec, uint32_t s, double ox, double oy,
+template <> __device__ __forceinline__ void put_rec<double>(void* rec, float4*, uint32_t s, double ox, double oy,
                                                             double oz, uint32_t bits) {
   reinterpret_cast<double4_32a*>(rec)[s] =
       make_double4_32a(ox, oy, oz, __longlong_as_double((long long)bits));
@@ -683,7 +712,7 @@ __global__ void k_bucket_build(DevArrays A) {
   A.stag[d] = tag;
   A.scell[d] = cell;
   if (A.slot_of) A.slot_of[tag] = d;
-  put_rec<R>(A.rec, d, o[0], o[1], o[2], meta_type(m) | ((A.rec_cell ? cell : mol) << 3));
+  put_rec<R>(A.rec, A.rec_lo, d, o[0], o[1], o[2], meta_type(m) | ((A.rec_cell ? cell : mol) << 3));
 }
 
 // float64 reciprocal and inverse square root without the long divide/sqrt
@@ -803,9 +832,19 @@ template <> struct RecT<double> {
   }
 };
 
+// Tables of the mixed path's pair terms from double-float displacements
+// (lj_term_acc); not loaded on the float64 path.
+struct PairAcc {
+  float rc2m[kMaxTypes * kMaxTypes];  // screen bound r_c^2 (1 + 2^-18)
+  DF rc2[kMaxTypes * kMaxTypes];
+  DF s6x2[kMaxTypes * kMaxTypes];     // 2 sigma^6
+  float c24[kMaxTypes * kMaxTypes], c4[kMaxTypes * kMaxTypes], s6[kMaxTypes * kMaxTypes];
+};
+
 template <typename R> struct PairTab {
   R eps[kMaxTypes * kMaxTypes], sig2[kMaxTypes * kMaxTypes], rc2[kMaxTypes * kMaxTypes],
       shift[kMaxTypes * kMaxTypes], lin[kMaxTypes * kMaxTypes], rc[kMaxTypes * kMaxTypes];
+  PairAcc acc;
 };
 
 template <typename R> __device__ __forceinline__ void load_tab(PairTab<R>& t, const TypeTable* T);
@@ -818,6 +857,12 @@ template <> __device__ __forceinline__ void load_tab<float>(PairTab<float>& t, c
     t.shift[q] = T->shift_f[a][b];
     t.lin[q] = T->lin_f[a][b];
     t.rc[q] = T->rc_f[a][b];
+    t.acc.rc2m[q] = T->rc2m_f[a][b];
+    t.acc.rc2[q] = T->rc2_df[a][b];
+    t.acc.s6x2[q] = T->s6x2_df[a][b];
+    t.acc.c24[q] = T->c24_f[a][b];
+    t.acc.c4[q] = T->c4_f[a][b];
+    t.acc.s6[q] = T->s6_f[a][b];
   }
 }
 template <> __device__ __forceinline__ void load_tab<double>(PairTab<double>& t, const TypeTable* T) {
@@ -863,6 +908,94 @@ __device__ __forceinline__ void lj_term(const PairTab<R>& tab, uint32_t qt, R r2
   }
   fx += fr * ddx; fy += fr * ddy; fz += fr * ddz;
   u += (R)0.5 * v;
+}
+
+// Mixed path: the pair term of a candidate that the float32 screen found
+// near or inside the cutoff, from the records' high parts (offsets from the
+// cell centre rounded to float32) and low parts (the rounding remainders).
+// Per axis the displacement d = (o_i - o_j - shift) is formed exactly as a
+// double-float: two error-free sums (two_sum) of the high parts and the
+// shift, plus the difference of the low parts. r^2 is then a double-float by
+// Ogita, Rump and Oishi's compensated dot product (Dot2: exact squares by
+// two_prod, exact partial sums by two_sum, the cross terms 2 d_h d_l), the
+// cutoff test compares it with r_c^2 held as a double-float, and r^6 is a
+// double-float product. The Lennard-Jones factor of Eq. S1 is written as
+//   f(r)/r = 24 eps s6 (2 s6 - 1) / r^2 = 24 eps sigma^6 (2 sigma^6 - r^6) / (r^6 r^6 r^2),
+// with 2 sigma^6 - r^6 formed from the double-float r^6 (exact cancellation
+// near the WCA cutoff) and 1/r^6, 1/r^2 from a float32 reciprocal corrected
+// by the low part. Only float32 products of well-conditioned factors remain,
+// so the pair force carries a few float32 roundings relative to itself,
+// while a float32 r^2 (relative error 2^-24) would move it by up to 22 of
+// them near contact (d ln f / d ln r = -22 at r = 1.03 sigma) and by up to
+// 6e-6 eps/sigma absolute near the WCA cutoff.
+__device__ __forceinline__ DF pair_disp(float a, float b, float sh, float dl) {
+  const DF s1 = df_two_sum(a, -b);
+  const DF s2 = df_two_sum(s1.h, -sh);
+  return {s2.h, __fadd_rn(__fadd_rn(s1.l, s2.l), dl)};
+}
+
+__device__ __forceinline__ void lj_term_acc(const PairTab<float>& tab, uint32_t qt, const float4& ri,
+                                            const float4& li, const float4& rj, const float4& lj, float shx,
+                                            float shy, float shz, float& fx, float& fy, float& fz, float& u) {
+  const DF dx = pair_disp(ri.x, rj.x, shx, __fsub_rn(li.x, lj.x));
+  const DF dy = pair_disp(ri.y, rj.y, shy, __fsub_rn(li.y, lj.y));
+  const DF dz = pair_disp(ri.z, rj.z, shz, __fsub_rn(li.z, lj.z));
+  const DF px = df_two_prod(dx.h, dx.h), py = df_two_prod(dy.h, dy.h), pz = df_two_prod(dz.h, dz.h);
+  const DF s1 = df_two_sum(px.h, py.h);
+  const DF s2 = df_two_sum(s1.h, pz.h);
+  float lo = __fadd_rn(__fadd_rn(__fadd_rn(px.l, py.l), pz.l), __fadd_rn(s1.l, s2.l));
+  lo = __fmaf_rn(2.f * dx.h, dx.l, lo);
+  lo = __fmaf_rn(2.f * dy.h, dy.l, lo);
+  lo = __fmaf_rn(2.f * dz.h, dz.l, lo);
+  const DF r2 = df_fast_sum(s2.h, lo);
+  const DF rc2 = tab.acc.rc2[qt];
+  if (!(__fadd_rn(__fsub_rn(r2.h, rc2.h), __fsub_rn(r2.l, rc2.l)) < 0.f)) return;  // r >= r_c
+  const float iR0 = __frcp_rn(r2.h);
+  const float iR = __fmaf_rn(-__fmul_rn(r2.l, iR0), iR0, iR0);  // 1 / r^2
+  DF r4 = df_two_prod(r2.h, r2.h);
+  r4.l = __fmaf_rn(2.f * r2.h, r2.l, r4.l);
+  DF r6 = df_two_prod(r4.h, r2.h);
+  r6.l = __fmaf_rn(r4.h, r2.l, __fmaf_rn(r4.l, r2.h, r6.l));
+  const DF s = tab.acc.s6x2[qt];
+  const float num = __fadd_rn(__fsub_rn(s.h, r6.h), __fsub_rn(s.l, r6.l));  // 2 sigma^6 - r^6
+  const float iq0 = __frcp_rn(r6.h);
+  const float iq = __fmaf_rn(-__fmul_rn(r6.l, iq0), iq0, iq0);  // 1 / r^6
+  float fr = tab.acc.c24[qt] * num * (iq * iq) * iR;
+  const float s6 = tab.acc.s6[qt] * iq;
+  float v = tab.acc.c4[qt] * iq * (s6 - 1.f) - tab.shift[qt];
+  const float lin = tab.lin[qt];
+  if (lin != 0.f) {
+    const float ir = rsqrtf(r2.h);
+    fr += lin * ir;
+    v -= (r2.h * ir - tab.rc[qt]) * lin;
+  }
+  fx = __fmaf_rn(fr, dx.h, __fmaf_rn(fr, dx.l, fx));
+  fy = __fmaf_rn(fr, dy.h, __fmaf_rn(fr, dy.l, fy));
+  fz = __fmaf_rn(fr, dz.h, __fmaf_rn(fr, dz.l, fz));
+  u += 0.5f * v;
+}
+
+// One candidate pair: float64 path as lj_term; mixed path a float32 screen on
+// the records' high parts (r^2 < r_c^2 (1 + 2^-18); the screen's own error is
+// below 2e-6 relative) and lj_term_acc for what passes, with the low part of
+// the candidate's record loaded only then.
+template <typename R>
+__device__ __forceinline__ void pair_term(const PairTab<R>& tab, uint32_t qt, const typename RecT<R>::T& ri,
+                                          const float4& li, const typename RecT<R>::T& rj,
+                                          const float4* __restrict__ lo, uint32_t t, R shx, R shy, R shz, R& fx,
+                                          R& fy, R& fz, R& u) {
+  const R ddx = ri.x - rj.x - shx, ddy = ri.y - rj.y - shy, ddz = ri.z - rj.z - shz;
+  const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+  if constexpr (sizeof(R) == 4) {
+    if (r2 < tab.acc.rc2m[qt]) lj_term_acc(tab, qt, ri, li, rj, lo[t], shx, shy, shz, fx, fy, fz, u);
+  } else {
+    if (r2 < tab.rc2[qt]) lj_term<R>(tab, qt, r2, ddx, ddy, ddz, fx, fy, fz, u);
+  }
+}
+
+template <typename R> __device__ __forceinline__ float4 rec_lo_at(const float4* lo, uint32_t s) {
+  if constexpr (sizeof(R) == 4) return lo[s];
+  return make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 template <typename R> __device__ __forceinline__ void store_f(void* f, uint32_t i, R fx, R fy, R fz, R u);
@@ -1144,13 +1277,15 @@ __device__ __forceinline__ void bonded_terms(const DevArrays& A, const SysDev& S
 template <typename R> struct GlobalCells {
   using Rec = typename RecT<R>::T;
   const Rec* __restrict__ rec_;
+  const float4* __restrict__ lo_;
   const uint32_t* __restrict__ scell_;
   const uint32_t* __restrict__ start_;
   const uint32_t* __restrict__ stag_;
   int hashed, log_t;
   __device__ __forceinline__ explicit GlobalCells(const DevArrays& A)
-      : rec_(reinterpret_cast<const Rec*>(A.rec)), scell_(A.scell), start_(A.start), stag_(A.stag),
+      : rec_(reinterpret_cast<const Rec*>(A.rec)), lo_(A.rec_lo), scell_(A.scell), start_(A.start), stag_(A.stag),
         hashed(A.hashed), log_t(A.log_t) {}
+  __device__ __forceinline__ const float4* lo() const { return lo_; }
   __device__ __forceinline__ uint32_t tag(uint32_t s) const { return stag_[s]; }
   __device__ __forceinline__ uint32_t scell(uint32_t t) const { return scell_[t]; }
   __device__ __forceinline__ Rec rec(uint32_t t) const { return rec_[t]; }
@@ -1165,6 +1300,7 @@ __device__ __forceinline__ uint32_t pair_slot(const DevArrays& A, const Cells& C
   const uint32_t tag = C.tag(s);
   const uint32_t cell = C.scell(s);
   const Rec ri = C.rec(s);
+  const float4 li = rec_lo_at<R>(C.lo(), s);
   const uint32_t bi = RecT<R>::bits(ri);
   const uint32_t ti = bi & 7u, moli = bi >> 3;
   const uint32_t m = A.meta[tag];
@@ -1240,9 +1376,7 @@ __device__ __forceinline__ uint32_t pair_slot(const DevArrays& A, const Cells& C
           const uint32_t bj = RecT<R>::bits(rj);
           if (EXCL && (bj >> 3) == moli) continue;
           const uint32_t qt = ti * kMaxTypes + (bj & 7u);
-          const R ddx = ri.x - rj.x - shx, ddy = ri.y - rj.y - shy, ddz = ri.z - rj.z - shz;
-          const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-          if (r2 < tab.rc2[qt]) lj_term<R>(tab, qt, r2, ddx, ddy, ddz, fx, fy, fz, u);
+          pair_term<R>(tab, qt, ri, li, rj, C.lo(), t, shx, shy, shz, fx, fy, fz, u);
         }
       }
     }
@@ -1349,6 +1483,7 @@ __global__ void __launch_bounds__(256) k_nl_build(DevArrays A) {
   if (cnt > cap) flag(A.status, kFlagNlistFull);
   A.nl_cnt[s] = min(cnt, cap);
   reinterpret_cast<Rec*>(A.rec0)[s] = ri;
+  if (sizeof(R) == 4) A.rec0_lo[s] = A.rec_lo[s];
   A.xb[tag] = A.x[tag];
   A.xb[n + tag] = A.x[n + tag];
   A.xb[2 * n + tag] = A.x[2 * n + tag];
@@ -1369,6 +1504,8 @@ __global__ void __launch_bounds__(256) k_pair_nl(DevArrays A) {
   const uint32_t m = A.meta[tag];
   const SysDev& S = A.sys[meta_sys(m)];
   const Rec ri = rec[s];
+  const float4* __restrict__ lo = A.rec_lo;
+  const float4 li = rec_lo_at<R>(lo, s);
   const uint32_t ti = RecT<R>::bits(ri) & 7u;
   const R csx = sizeof(R) == 4 ? (R)S.cs_f[0] : (R)S.cs[0];
   const R csy = sizeof(R) == 4 ? (R)S.cs_f[1] : (R)S.cs[1];
@@ -1382,9 +1519,7 @@ __global__ void __launch_bounds__(256) k_pair_nl(DevArrays A) {
     const Rec rj = rec[e >> 5];
     const int dz = (int)(code / 9u) - 1, dy = (int)(code / 3u % 3u) - 1, dx = (int)(code % 3u) - 1;
     const uint32_t qt = ti * kMaxTypes + (RecT<R>::bits(rj) & 7u);
-    const R ddx = ri.x - rj.x - (R)dx * csx, ddy = ri.y - rj.y - (R)dy * csy, ddz = ri.z - rj.z - (R)dz * csz;
-    const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-    if (r2 < tab.rc2[qt]) lj_term<R>(tab, qt, r2, ddx, ddy, ddz, fx, fy, fz, u);
+    pair_term<R>(tab, qt, ri, li, rj, lo, e >> 5, (R)dx * csx, (R)dy * csy, (R)dz * csz, fx, fy, fz, u);
   }
   if (BONDS || WALLS) bonded_terms<R>(A, S, tag, m, BONDS, WALLS, fx, fy, fz, u);
   store_f<R>(A.f, tag, fx, fy, fz, u);
@@ -1430,6 +1565,7 @@ __global__ void __launch_bounds__(256) k_pair_lanes(DevArrays A) {
     tag = A.stag[s];
     const uint32_t cell = scell[s];
     const Rec ri = rec[s];
+    const float4 li = rec_lo_at<R>(A.rec_lo, s);
     const uint32_t bi = RecT<R>::bits(ri);
     const uint32_t ti = bi & 7u, moli = bi >> 3;
     m = A.meta[tag];
@@ -1490,9 +1626,7 @@ __global__ void __launch_bounds__(256) k_pair_lanes(DevArrays A) {
         const uint32_t bj = RecT<R>::bits(rj);
         if (EXCL && (bj >> 3) == moli) continue;
         const uint32_t qt = ti * kMaxTypes + (bj & 7u);
-        const R ddx = ri.x - rj.x - shx, ddy = ri.y - rj.y - shy, ddz = ri.z - rj.z - shz;
-        const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-        if (r2 < tab.rc2[qt]) lj_term<R>(tab, qt, r2, ddx, ddy, ddz, fx, fy, fz, u);
+        pair_term<R>(tab, qt, ri, li, rj, A.rec_lo, t, shx, shy, shz, fx, fy, fz, u);
       }
     }
   }
@@ -1543,13 +1677,14 @@ template <typename R> constexpr int tile_cap() { return sizeof(R) == 4 ? 256 : 1
 // flight before their stores. All 32 lanes call this.
 template <typename R>
 __device__ __forceinline__ void tile_stage(const typename RecT<R>::T* __restrict__ rec, typename RecT<R>::T* stage,
-                                           uint32_t t0, uint32_t pre, R csx, R csy, R csz, uint32_t w0,
-                                           uint32_t len, int lane) {
+                                           uint32_t* code, uint32_t t0, uint32_t pre, R csx, R csy, R csz,
+                                           uint32_t w0, uint32_t len, int lane) {
   using Rec = typename RecT<R>::T;
   constexpr int U = 4;
   for (uint32_t e0 = 0; e0 < len; e0 += 32u * U) {
     Rec r[U];
     int kk[U];
+    uint32_t ts[U];
 #pragma unroll
     for (int v = 0; v < U; ++v) {
       const uint32_t e = e0 + 32u * v + (uint32_t)lane, g = w0 + e;
@@ -1562,7 +1697,8 @@ __device__ __forceinline__ void tile_stage(const typename RecT<R>::T* __restrict
       }
       kk[v] = k;
       const uint32_t tk = __shfl_sync(0xffffffffu, t0, k), pk = __shfl_sync(0xffffffffu, pre, k);
-      if (e < len) r[v] = rec[tk + (g - pk)];
+      ts[v] = tk + (g - pk);
+      if (e < len) r[v] = rec[ts[v]];
     }
 #pragma unroll
     for (int v = 0; v < U; ++v) {
@@ -1574,6 +1710,7 @@ __device__ __forceinline__ void tile_stage(const typename RecT<R>::T* __restrict
         q.y += (R)((k / 3) % 3 - 1) * csy;
         q.z += (R)(k / 9 - 1) * csz;
         stage[e] = q;
+        code[e] = ts[v] << 5 | (uint32_t)k;  // the candidate's slot and stencil cell
       }
     }
   }
@@ -1584,7 +1721,7 @@ __device__ __forceinline__ void tile_stage(const typename RecT<R>::T* __restrict
 template <typename R, bool EXCL>
 __device__ __forceinline__ void tile_piece(const DevArrays& A, const PairTab<R>& tab,
                                            const typename RecT<R>::T* __restrict__ rec, typename RecT<R>::T* stage,
-                                           typename V4<R>::T* fw, uint32_t home, uint32_t lo,
+                                           uint32_t* code, typename V4<R>::T* fw, uint32_t home, uint32_t lo,
                                            uint32_t hi, int lane) {
   using Rec = typename RecT<R>::T;
   const uint32_t* __restrict__ start = A.start;
@@ -1634,17 +1771,19 @@ __device__ __forceinline__ void tile_piece(const DevArrays& A, const PairTab<R>&
   const bool act = g < p;
   const uint32_t s = lo + (act ? g : 0u);
   const Rec ri = rec[s];
+  const float4 li = rec_lo_at<R>(A.rec_lo, s);
   const uint32_t bi = RecT<R>::bits(ri);
   const uint32_t ti = bi & 7u, moli = bi >> 3;
   const uint32_t self = self0 + g;
-  R rcm = 0;  // largest squared cutoff of the particle's type
+  R rcm = 0;  // largest squared cutoff of the particle's type (the mixed path's screen bound)
 #pragma unroll
-  for (int b = 0; b < kMaxTypes; ++b) rcm = max(rcm, tab.rc2[ti * kMaxTypes + b]);
+  for (int b = 0; b < kMaxTypes; ++b)
+    rcm = max(rcm, sizeof(R) == 4 ? (R)tab.acc.rc2m[ti * kMaxTypes + b] : tab.rc2[ti * kMaxTypes + b]);
   R fx = 0, fy = 0, fz = 0, u = 0;
   for (uint32_t w0 = 0; w0 < M; w0 += (uint32_t)tile_cap<R>()) {
     const uint32_t len = min(M - w0, (uint32_t)tile_cap<R>());
     __syncwarp();
-    tile_stage<R>(rec, stage, t0, pre, csx, csy, csz, w0, len, lane);
+    tile_stage<R>(rec, stage, code, t0, pre, csx, csy, csz, w0, len, lane);
     __syncwarp();
     if (act) {
       // the lane's candidates are e = lj + i L, i < ne
@@ -1669,7 +1808,18 @@ __device__ __forceinline__ void tile_piece(const DevArrays& A, const PairTab<R>&
           const uint32_t qt = ti * kMaxTypes + (bj & 7u);
           const R ddx = ri.x - rj.x, ddy = ri.y - rj.y, ddz = ri.z - rj.z;
           const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-          if (r2 < tab.rc2[qt]) lj_term<R>(tab, qt, r2, ddx, ddy, ddz, fx, fy, fz, u);
+          if constexpr (sizeof(R) == 4) {
+            // the screen passed on the staged (shifted) record: the candidate's own record, low
+            // part and stencil shift give the pair term
+            if (r2 < tab.acc.rc2m[qt]) {
+              const uint32_t cd = code[e], t = cd >> 5;
+              const int k = (int)(cd & 31u);
+              lj_term_acc(tab, qt, ri, li, rec[t], A.rec_lo[t], (float)(k % 3 - 1) * csx,
+                          (float)((k / 3) % 3 - 1) * csy, (float)(k / 9 - 1) * csz, fx, fy, fz, u);
+            }
+          } else {
+            if (r2 < tab.rc2[qt]) lj_term<R>(tab, qt, r2, ddx, ddy, ddz, fx, fy, fz, u);
+          }
         }
       }
     }
@@ -1702,6 +1852,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, sizeof(R) == 4 ? 6 : 4) k_pai
   using Rec = typename RecT<R>::T;
   __shared__ PairTab<R> tab;
   __shared__ Rec stage_all[kTileWarps][tile_cap<R>()];
+  __shared__ uint32_t code_all[kTileWarps][tile_cap<R>()];
   __shared__ typename V4<R>::T f_all[kTileWarps][kTileSlots];
   load_tab<R>(tab, A.types);
   __syncthreads();
@@ -1728,7 +1879,8 @@ __global__ void __launch_bounds__(kTileWarps * 32, sizeof(R) == 4 ? 6 : 4) k_pai
     const uint32_t lo = (uint32_t)r0 + (uint32_t)a;
     const uint32_t hi = cut ? (uint32_t)r0 + (uint32_t)(__ffs(cut) - 1) : r1;
     const uint32_t home = __shfl_sync(0xffffffffu, c, a);
-    tile_piece<R, EXCL>(A, tab, rec, stage_all[wib], f_all[wib] + (lo - (uint32_t)r0), home, lo, hi, lane);
+    tile_piece<R, EXCL>(A, tab, rec, stage_all[wib], code_all[wib], f_all[wib] + (lo - (uint32_t)r0), home, lo,
+                        hi, lane);
   }
   if (mine) {  // the pieces' leaders wrote f_all before the last __syncwarp
     const typename V4<R>::T q = f_all[wib][lane];
@@ -1956,21 +2108,25 @@ struct GlobalBin {
 
 // Neighbour-list mode: the particle keeps its cell until the next rebuild;
 // its record moves with it (record at the build + the float64 displacement
-// since the build, rounded once), and a displacement beyond skin / 2 raises
-// the rebuild flag for this step's cell-list kernels.
+// since the build; on the mixed path the sum is formed as a double-float and
+// split again into the high and low parts), and a displacement beyond skin / 2
+// raises the rebuild flag for this step's cell-list kernels.
 template <typename R> struct NlSink {
   static constexpr bool kOn = false, kPos = true;
   using Rec = typename RecT<R>::T;
   const uint32_t* slot_of;
   const double* xb;
   const Rec* rec0;
+  const float4* rec0_lo;
   Rec* rec;
+  float4* rec_lo;
   uint32_t* dirty;
   float half_skin2;
   int64_t n;
   __device__ __forceinline__ explicit NlSink(const DevArrays& A)
-      : slot_of(A.slot_of), xb(A.xb), rec0(reinterpret_cast<const Rec*>(A.rec0)),
-        rec(reinterpret_cast<Rec*>(A.rec)), dirty(A.nl_dirty), half_skin2(A.nl_half_skin2), n(A.n) {}
+      : slot_of(A.slot_of), xb(A.xb), rec0(reinterpret_cast<const Rec*>(A.rec0)), rec0_lo(A.rec0_lo),
+        rec(reinterpret_cast<Rec*>(A.rec)), rec_lo(A.rec_lo), dirty(A.nl_dirty), half_skin2(A.nl_half_skin2),
+        n(A.n) {}
   __device__ __forceinline__ void put(int64_t, uint32_t) const {}
   __device__ __forceinline__ void pos(int64_t i, double xn, double yn, double zn) const {
     const uint32_t s = slot_of[i];
@@ -1978,9 +2134,12 @@ template <typename R> struct NlSink {
     Rec r = rec0[s];
     float d2;
     if constexpr (sizeof(R) == 4) {
-      const float fx = d2f_rn(dx), fy = d2f_rn(dy), fz = d2f_rn(dz);
-      r.x += fx; r.y += fy; r.z += fz;
-      d2 = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+      const float4 l = rec0_lo[s];
+      const DF ex = df_from(dx), ey = df_from(dy), ez = df_from(dz);
+      const DF ox = df_add(DF{r.x, l.x}, ex), oy = df_add(DF{r.y, l.y}, ey), oz = df_add(DF{r.z, l.z}, ez);
+      r.x = ox.h; r.y = oy.h; r.z = oz.h;
+      rec_lo[s] = make_float4(ox.l, oy.l, oz.l, 0.f);
+      d2 = fmaf(ex.h, ex.h, fmaf(ey.h, ey.h, ez.h * ez.h));
     } else {
       r.x += dx; r.y += dy; r.z += dz;
       d2 = d2f_rn(fma(dx, dx, fma(dy, dy, dz * dz)));
@@ -2148,31 +2307,6 @@ __device__ __forceinline__ bool newton_line(L& line, int max_newton, bool frozen
   }
   return false;
 }
-
-// float64 -> double-float on the integer pipe: h = v rounded to float32 (as
-// d2f_rn), l = the remainder v - h. The remainder is an integer number rem of
-// units 2^(E-1075) of v's binade (E = v's biased exponent; rem is the low
-// bits of the fraction field minus the rounding, |rem| <= 2^28); l keeps its
-// leading bits, rem >> 6 (<= 2^22 in magnitude, so converted exactly by the
-// 1.5 * 2^23 bias), times 2^(E-1069). h + l = v within 2^-46 |v|. Outside
-// 2^-80 <= |v| < 2^128 (zero, tiny or huge values) the split takes one
-// float64 subtraction instead.
-__device__ __forceinline__ DF df_from(double v) {
-  const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
-  const uint32_t e = (hi >> 20) & 0x7ffu;
-  if (e - 943u < 208u) {  // biased exponent in [943, 1150]
-    uint32_t up, rest;
-    const uint32_t q = d2f_bits_rn(hi, lo, up, rest);
-    const int32_t rem = (int32_t)rest - (int32_t)(up << 29);  // dropped bits, less 2^29 if rounded up
-    const float k = __fsub_rn(__int_as_float(0x4B400000 + (rem >> 6)), 12582912.0f);
-    const float l = __fmul_rn(k, __uint_as_float((e - 942u) << 23));
-    const uint32_t sign = hi & 0x80000000u;
-    return {__uint_as_float(sign | q), sign ? -l : l};
-  }
-  const float h = d2f_rn(v);
-  return {h, d2f_rn(v - f2d(h))};
-}
-__device__ __forceinline__ double df_to(DF a) { return f2d(a.h) + f2d(a.l); }
 
 __device__ __forceinline__ bool df_surface(int32_t kind) {
   return kind == kPlane || kind == kSphere || kind == kEllipsoid || kind == kCylinder || kind == kTorus;
@@ -2429,11 +2563,13 @@ __global__ void __launch_bounds__(256, 4) k_integrate(DevArrays A) {
 template <typename R> struct SharedCells {
   using Rec = typename RecT<R>::T;
   const Rec* rec_;
+  const float4* lo_;
   const uint32_t* scell_;
   const uint32_t* start_;
   const uint16_t* stag_;
   uint32_t first, base;
   int hashed, log_t;
+  __device__ __forceinline__ const float4* lo() const { return lo_; }
   __device__ __forceinline__ uint32_t tag(uint32_t s) const { return first + stag_[s]; }
   __device__ __forceinline__ uint32_t scell(uint32_t t) const { return scell_[t]; }
   __device__ __forceinline__ Rec rec(uint32_t t) const { return rec_[t]; }
@@ -2467,7 +2603,7 @@ template <typename R>
 __device__ __forceinline__ void resident_cells(const DevArrays& A, const SysDev& S, int64_t first, uint32_t n,
                                                uint32_t T, uint32_t* s_start, const uint32_t* s_cell,
                                                uint32_t cstride, const uint16_t* s_rank, uint16_t* s_tmp,
-                                               uint16_t* s_stag, uint32_t* s_scell, void* s_rec,
+                                               uint16_t* s_stag, uint32_t* s_scell, void* s_rec, float4* s_lo,
                                                uint32_t* warp_tot) {
   const uint32_t tid = threadIdx.x, bd = blockDim.x;
   {
@@ -2505,7 +2641,7 @@ __device__ __forceinline__ void resident_cells(const DevArrays& A, const SysDev&
     const uint32_t mol = A.mol ? (uint32_t)A.mol[i] : 0u;
     s_stag[dd] = (uint16_t)li;
     s_scell[dd] = c;
-    put_rec<R>(s_rec, dd, o[0], o[1], o[2], meta_type(m) | ((A.rec_cell ? c : mol) << 3));
+    put_rec<R>(s_rec, s_lo, dd, o[0], o[1], o[2], meta_type(m) | ((A.rec_cell ? c : mol) << 3));
   }
   __syncthreads();
 }
@@ -2517,7 +2653,8 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 2) k_resident(DevArrays A
   __shared__ uint32_t warp_tot[33];
   __shared__ int s_job;
   extern __shared__ __align__(32) unsigned char smem[];
-  // Layout (nmax particles, tmax buckets): records, then the force components
+  // Layout (nmax particles, tmax buckets): records (mixed path: then their
+  // low parts), then the force components
   // (each nmax R; the x-forces double as the particles' cells and the
   // y-forces as the scatter's slot list, which are live only while the
   // forces are not), sorted cells, bucket counters / starts, sorted ids,
@@ -2525,7 +2662,9 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 2) k_resident(DevArrays A
   // size carries 32 bytes of slack for this).
   const uint32_t mis = (uint32_t)__cvta_generic_to_shared(smem) & 31u;
   Rec* s_rec = reinterpret_cast<Rec*>(smem + (mis ? 32u - mis : 0u));
-  R* s_fx = reinterpret_cast<R*>(s_rec + J.nmax);
+  float4* s_lo = reinterpret_cast<float4*>(s_rec + J.nmax);
+  R* s_fx = reinterpret_cast<R*>(sizeof(R) == 4 ? reinterpret_cast<unsigned char*>(s_lo + J.nmax)
+                                                : reinterpret_cast<unsigned char*>(s_rec + J.nmax));
   R* s_fy = s_fx + J.nmax;
   R* s_fz = s_fy + J.nmax;
   uint32_t* s_cell = reinterpret_cast<uint32_t*>(s_fx);
@@ -2551,7 +2690,7 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 2) k_resident(DevArrays A
     const uint32_t n = (uint32_t)S.n;
     const uint32_t T = S.res_t;
     const SharedBin bin{s_cell, cstride, s_rank, s_start, first, S.cell_base, S.res_hashed, S.res_log_t};
-    const SharedCells<R> C{s_rec, s_scell, s_start, s_stag, (uint32_t)first, S.cell_base, S.res_hashed,
+    const SharedCells<R> C{s_rec, s_lo, s_scell, s_start, s_stag, (uint32_t)first, S.cell_base, S.res_hashed,
                            S.res_log_t};
     // cell list of the positions the launch starts from
     for (uint32_t e = tid; e <= T; e += bd) s_start[e] = 0u;
@@ -2564,7 +2703,7 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 2) k_resident(DevArrays A
       bin.put(i, cell);
     }
     __syncthreads();
-    resident_cells<R>(A, S, first, n, T, s_start, s_cell, cstride, s_rank, s_tmp, s_stag, s_scell, s_rec,
+    resident_cells<R>(A, S, first, n, T, s_start, s_cell, cstride, s_rank, s_tmp, s_stag, s_scell, s_rec, s_lo,
                       warp_tot);
     for (int j = 0; j < J.nsteps; ++j) {
       for (uint32_t s = tid; s < n; s += bd) {
@@ -2597,7 +2736,7 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 2) k_resident(DevArrays A
       // the last step's list would only be rebuilt by the next launch
       if (j + 1 < J.nsteps)
         resident_cells<R>(A, S, first, n, T, s_start, s_cell, cstride, s_rank, s_tmp, s_stag, s_scell, s_rec,
-                          warp_tot);
+                          s_lo, warp_tot);
     }
   }
 }
@@ -2608,7 +2747,7 @@ __global__ void k_advance_n(unsigned long long* step, int32_t* mode, int32_t nst
 }
 
 size_t resident_smem_bytes(int precision, uint32_t nmax, uint32_t tmax) {
-  const size_t rec = precision == 0 ? sizeof(double4_32a) : sizeof(float4);
+  const size_t rec = precision == 0 ? sizeof(double4_32a) : 2 * sizeof(float4);  // mixed: record + low part
   const size_t r = precision == 0 ? sizeof(double) : sizeof(float);
   return (size_t)nmax * (rec + 3 * r + sizeof(uint32_t) + 2 * sizeof(uint16_t)) +
          sizeof(uint32_t) * ((size_t)tmax + 1) + 32;

@@ -111,6 +111,13 @@ struct TypeTable {
   double bond_r0_mix[kMaxTypes][kMaxTypes];  // 2^(1/6) sigma_ij / 2
   double mass[kMaxTypes], inv_mass[kMaxTypes], sqrt_mass[kMaxTypes];
   float sqrt_mass_f[kMaxTypes];
+  // mixed path, pair terms from double-float displacements (kernels.cu, lj_term_acc)
+  float rc2m_f[kMaxTypes][kMaxTypes];  // screen: r_c^2 (1 + 2^-18) in float32
+  DF rc2_df[kMaxTypes][kMaxTypes];     // r_c^2
+  DF s6x2_df[kMaxTypes][kMaxTypes];    // 2 sigma^6
+  float c24_f[kMaxTypes][kMaxTypes];   // 24 eps sigma^6
+  float c4_f[kMaxTypes][kMaxTypes];    // 4 eps sigma^6
+  float s6_f[kMaxTypes][kMaxTypes];    // sigma^6
 };
 
 template <typename R> struct V4;
@@ -182,6 +189,9 @@ struct DevArrays {
   uint32_t* stag_tmp;   // [n] slot -> particle in atomic order (before the canonical sort)
   uint32_t* scell;      // [n] sorted slot -> cell id
   void* rec;            // [n] float4 / double4_32a cell-relative offsets + type/mol bits
+  float4* rec_lo;       // [n] mixed path: offset - record (the low parts; w unused), else null
+  float4* rec0_lo;      // [n] mixed path with the neighbour list: rec_lo at the last build
+  int32_t ntypes;       // particle types in use (a type must lie in [0, ntypes))
   const SysDev* sys;    // [nsys]
   const TypeTable* types;  // pair and mass tables shared by the systems
   int32_t* sys_free;    // [nsys] unconstrained particles per system (set with the state)

@@ -1,8 +1,15 @@
-"""Full-size workloads in the configuration the benchmark times, checked on
-sampled particles that the oracle computes one by one: the force on each
-sampled particle (all pairs with it), the first step after the state is set
-and a later step (Algorithm S1 for that particle, its neighbours at the
-GPU's positions), plus the constraint residual of every particle."""
+"""Full-size workloads in the launch configuration the benchmark times (the
+Verlet neighbour list with the benchmark's skin and list size, cell edge
+r_c + skin), and with the cell list every step:
+
+- the forces of every particle at x^0 and again after at least one list
+  rebuild, against the oracle's forces at the same positions (its cell list,
+  which its pins check against all pairs), per particle as
+  |df| / max(|f|, 1 eps/sigma);
+- per sampled particle, one step of Algorithm S1 from the GPU's state at
+  k = 0 and at a step after the rebuild (the oracle advances that particle
+  with its neighbours at the GPU's positions);
+- the constraint residual of every particle after every checked step."""
 import numpy as np
 import pytest
 
@@ -10,20 +17,25 @@ import oracle
 from paper_1411_3019_gb300 import inputs as I
 from paper_1411_3019_gb300 import md
 
-from parity_util import FORCE_REL
+from parity_util import FORCE_REL, force_errors
 
 pytestmark = pytest.mark.gpu
 
 _cache = {}
+SKIN, MAX_NB = 0.4, 64  # the benchmark's list for both workloads
 
 
-def _workload(name):
+def _workload(name, skin):
     if name not in _cache:
         if name == "ellipsoid_torus_250k":
             _cache[name] = I.c2_ellipsoid_torus()
         elif name == "replicas_4096":
             _cache[name] = I.c4_replicas()
-    return _cache[name]
+    systems = [dict(s) for s in _cache[name]]
+    if skin > 0:
+        for s in systems:
+            s["params"] = dict(s["params"], cell_size=float(np.max(s["params"]["rcut"])) + skin)
+    return systems
 
 
 def _sample(n, k, seed):
@@ -31,38 +43,7 @@ def _sample(n, k, seed):
     return np.unique(np.concatenate([[0, n - 1], g.choice(n, size=min(k, n), replace=False)]))
 
 
-def _check_system(sy, x0, f0, x1, ph1, x2, sample_k, seed, dx_tol):
-    prm, surf = sy["params"], sy["surface"]
-    idx = _sample(sy["n"], sample_k, seed)
-    small = sy["n"] <= 5000
-    scale_all = oracle.force_scale(prm, x0, sy["type"], None, sy["constrained"], surf) if small else None
-    for i in idx:
-        f_ref, _ = oracle.force_on(prm, x0, i, sy["type"], None, sy["constrained"], surf)
-        sc = scale_all[i] if small else _scale_on(prm, x0, i, sy)
-        assert np.linalg.norm(f0[i] - f_ref) / max(sc, 1.0) <= FORCE_REL["mixed"]
-        m = prm["mass"][sy["type"][i]]
-        _, xa, pha, st = oracle.particle_advance(surf, prm, x0, i, sy_p0(sy, i), 0, 1, sy["type"], None,
-                                                 sy["constrained"])
-        assert st >= 0
-        assert np.abs(xa - x1[i]).max() <= dx_tol
-        _, xb, _, st = oracle.particle_advance(surf, prm, x1, i, ph1[i], 1, 0, sy["type"], None,
-                                               sy["constrained"])
-        assert st >= 0
-        assert np.abs(xb - x2[i]).max() <= dx_tol
-        del m
-
-
-def _scale_on(prm, x, i, sy):
-    """Force scale of particle i alone: its neighbours within the largest cutoff
-    (a superset of its interacting pairs) as a small system."""
-    rc = float(np.max(prm["rcut"]))
-    near = np.nonzero(np.sum((x - x[i]) ** 2, axis=1) < (rc + 1e-9) ** 2)[0]
-    j = int(np.nonzero(near == i)[0][0])
-    return oracle.force_scale(prm, x[near], sy["type"][near], None, sy["constrained"][near],
-                              sy["surface"])[j]
-
-
-def sy_p0(sy, i):
+def _p0(sy, i):
     """p^0 of particle i as md_set_state stores it: m v projected on the
     tangent plane (the projection is the oracle's, at x^0)."""
     x, v = sy["x"][i], sy["v"][i]
@@ -73,26 +54,57 @@ def sy_p0(sy, i):
     return m * v
 
 
-@pytest.mark.parametrize("name,sample_k", [("ellipsoid_torus_250k", 150), ("replicas_4096", 40)])
-def test_full_size_sampled_parity(name, sample_k):
-    systems = _workload(name)
+def _advance_ok(sy, x, p_in, k, first, x_next, idx, tol):
+    """Algorithm S1 for each sampled particle from (x, p_in) at step k equals
+    the GPU's x^{k+1} within tol."""
+    worst = 0.0
+    for i in idx:
+        p = _p0(sy, i) if first else p_in[i]
+        _, xa, _, st = oracle.particle_advance(sy["surface"], sy["params"], x, int(i), p, k, int(first),
+                                               sy["type"], None, sy["constrained"])
+        assert st >= 0
+        worst = max(worst, float(np.abs(xa - x_next[i]).max()))
+    assert worst <= tol, worst
+    return worst
+
+
+@pytest.mark.parametrize("mode", ["neighbor_list", "cell_list"])
+@pytest.mark.parametrize("name,sample_k", [("ellipsoid_torus_250k", 300), ("replicas_4096", 6)])
+def test_full_size_parity(name, sample_k, mode):
+    skin = SKIN if mode == "neighbor_list" else 0.0
+    systems = _workload(name, skin)
+    k_late = 40  # the list (skin 0.4) is rebuilt about every 20 steps on these workloads
     with md.Simulation(systems) as sim:
+        if skin > 0:
+            md.md_set_neighbor_list(sim.h, skin, MAX_NB)
         sim.set_state()
         f0, _ = sim.forces()
+        b0 = md.md_get_option(sim.h, md.MD_OPT_NLIST_BUILDS) if skin > 0 else 0
         sim.step(1)
         sim.sync()
         s1 = sim.state()
+        assert sim.residual()["max_g_over_gradg"] <= 1e-10
+        sim.step(k_late - 1)
+        sim.sync()
+        sk = sim.state()
+        fk, _ = sim.forces()
+        assert sim.residual()["max_g_over_gradg"] <= 1e-10
+        if skin > 0:
+            assert md.md_get_option(sim.h, md.MD_OPT_NLIST_BUILDS) > b0  # a rebuild inside the window
         sim.step(1)
         sim.sync()
-        s2 = sim.state()
-        res = sim.residual()
-    assert res["max_g_over_gradg"] <= 1e-10
-    off = 0
-    picks = range(len(systems)) if len(systems) <= 2 else np.linspace(0, len(systems) - 1, 5).astype(int)
+        sk1 = sim.state()
+        assert sim.residual()["max_g_over_gradg"] <= 1e-10
+    assert sk["step"] == k_late
+    x0 = np.concatenate([s["x"] for s in systems])
+    for x, f in ((x0, f0), (sk["x"], fk)):
+        net, _ = force_errors(systems, x, f)
+        assert float(net.max()) <= FORCE_REL["mixed"], (float(net.max()), int(np.argmax(net)))
     offs = np.concatenate([[0], np.cumsum([s["n"] for s in systems])])
+    picks = range(len(systems)) if len(systems) <= 2 else np.linspace(0, len(systems) - 1, 40).astype(int)
     for k in picks:
         sy = systems[k]
-        off = offs[k]
-        sl = slice(off, off + sy["n"])
-        _check_system(sy, sy["x"], f0[sl], s1["x"][sl], s1["p_half"][sl], s2["x"][sl], sample_k,
-                      seed=int(k), dx_tol=1e-9)
+        sl = slice(offs[k], offs[k + 1])
+        idx = _sample(sy["n"], sample_k, seed=int(k))
+        _advance_ok(sy, sy["x"], None, 0, True, s1["x"][sl], idx, 1e-9)
+        _advance_ok(sy, sk["x"][sl], sk["p_half"][sl], k_late, False, sk1["x"][sl], idx, 1e-9)
