@@ -31,6 +31,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -41,10 +43,6 @@ UNIT = "particle-steps/s"
 L2_FLUSH_BYTES = 256 << 20  # larger than the 129 MB L2
 WORKLOADS = ("ellipsoid_torus", "plain_sphere", "replicas", "bead_molecules", "bump_crowders", "nve_surfaces",
              "capsids", "sphere_vs_2d", "thylakoids", "lj_lattice")
-# float64 pipe of one GB300: 152 SMs x 2 float64 operations per SM per clock
-FP64_OPS_PER_SM_CLK = 2
-SMS = 152
-SM_MAX_MHZ = 2070.0
 
 
 def parse(argv=None):
@@ -255,28 +253,29 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # rooflines
 # ---------------------------------------------------------------------------
+# Algorithmic bytes per particle of the two kernels every step runs, as the
+# survey of the method counts them (each datum read or written once):
+#   integrate: x (24) + p^{k-1/2} (24) + f (12, float32; 24 on the float64
+#              path) + type/flags (4) read, x + p^{k-1/2} (48) written, the
+#              cell key (4)  -> 116 B (128 B float64 path)
+#   pair:      the particle's float4 record once (16; double4 32), its cell
+#              start (4) and the force written (16; 32)  -> 36 B (68 B float64)
+SURVEY_BYTES = {"mixed": {"integrate": 116, "pair": 36}, "fp64": {"integrate": 128, "pair": 68}}
+
+
 def algorithmic_bytes(kernel: str, n: int, nbucket: int, precision: str, nlist: bool = False) -> float:
-    """Bytes each kernel must move per launch if every datum is read or written
-    once (per step for the resident engine's entry). With the neighbour list
-    the pair kernel's list entries and repeated neighbour records are not
-    counted (a lower bound), and the cell-list kernels and the list build,
-    which work only on rebuild steps, count no bytes."""
+    """Algorithmic bytes of one launch: the per-particle figure above times
+    the particles for the integrator and the pair kernel (either step form);
+    for the cell-list kernels (cell list every step) the bytes they move if
+    every datum is read or written once; the list build and, with the
+    neighbour list, the cell-list kernels (rebuild steps only) count none."""
+    if kernel in ("integrate", "pair"):
+        return float(SURVEY_BYTES[precision][kernel] * n)
+    if nlist:
+        return 0.0
     v4 = 16 if precision == "mixed" else 32
     tiles = math.ceil(nbucket / 8192)
-    if nlist:
-        per = {
-            # sorted id, meta, own record, entry count; force vec4
-            "pair": n * (4 + 4 + v4 + 4 + v4),
-            # meta, x, p_half, force vec4; x, p_half written; slot, build position and
-            # build record read, record written
-            "integrate": n * (4 + 24 + 24 + v4 + 24 + 24 + 4 + 24 + v4 + v4),
-        }
-        return float(per.get(kernel, 0))
     per = {
-        # sorted id, cell id, own record, meta; force vec4; bucket starts once
-        "pair": n * (4 + 4 + v4 + 4 + v4) + 4 * (nbucket + 1),
-        # meta, x, p_half, force vec4; x, p_half, cell, rank; counters read-modify-write
-        "integrate": n * (4 + 24 + 24 + v4 + 24 + 24 + 4 + 4) + 8 * nbucket,
         # counters read and cleared, starts written, tile states
         "scan": 12 * nbucket + 16 * tiles,
         # cell id, rank, bucket start; slot written
@@ -288,6 +287,20 @@ def algorithmic_bytes(kernel: str, n: int, nbucket: int, precision: str, nlist: 
         "resident": n * (4 + 24 + 24 + 24 + 24),
     }
     return float(per.get(kernel, 0))
+
+
+def impl_bytes(kernel: str, n: int, precision: str, nlist: bool) -> float:
+    """Bytes the implementation's launch reads and writes once each (beyond
+    the algorithmic count: the list step's slot map, build position and the
+    records it moves; the float4 force's energy word)."""
+    v4 = 16 if precision == "mixed" else 32
+    lo = 16 if precision == "mixed" else 0
+    if kernel == "integrate":
+        base = 4 + 24 + 24 + v4 + 24 + 24
+        return float(n * (base + (4 + 24 + v4 + lo + v4 + lo if nlist else 4 + 4)))
+    if kernel == "pair":
+        return float(n * (4 + 4 + v4 + lo + 4 + v4))
+    return 0.0
 
 
 def kernels_source_hash() -> str:
@@ -318,17 +331,24 @@ def ncu_counts(workload_name: str, precision: str, nlist: bool = False):
     return out if sha == kernels_source_hash() else {}
 
 
-def rooflines(prof_ms, n, nbucket, precision, hbm_peak, counts, sm_mhz, nlist=False):
-    fp64_peak = SMS * FP64_OPS_PER_SM_CLK * (sm_mhz or SM_MAX_MHZ) * 1e6  # float64 ops/s
+def rooflines(prof_ms, n, nbucket, precision, hbm_peak, counts, fma_peaks, nlist=False):
+    """Per-kernel achieved bandwidth against the measured HBM copy peak, and
+    the float64 / float32 pipe fractions where ncu counts of the current
+    kernel source are recorded (instructions per launch / duration / the FMA
+    instruction rate measured in this run). The headline roofline is the
+    dominant (longest) kernel's HBM fraction on its algorithmic bytes."""
     table = {}
     for k, ms in prof_ms.items():
         b = algorithmic_bytes(k, n, nbucket, precision, nlist)
         row = {"ms": round(ms, 5), "bytes_per_launch": b, "hbm_gbs": b / (ms / 1e3) / 1e9,
                "hbm_frac": b / (ms / 1e3) / 1e9 / hbm_peak}
+        ib = impl_bytes(k, n, precision, nlist)
+        if ib:
+            row["impl_bytes_per_launch"] = ib
         c = counts.get(k, {})
-        if "fp64_inst" in c:
+        if "fp64_inst" in c and fma_peaks.get("fp64"):
             row["fp64_inst_per_launch"] = c["fp64_inst"]
-            row["fp64_frac"] = c["fp64_inst"] / (ms / 1e3) / fp64_peak
+            row["fp64_pipe_frac"] = c["fp64_inst"] / (ms / 1e3) / fma_peaks["fp64"]
         if "dram_bytes" in c:
             row["traffic"] = c["dram_bytes"]
         if "fma_pct" in c:  # sm__pipe_fma_cycles_active: the float32 pipe's busy fraction (ncu)
@@ -336,16 +356,13 @@ def rooflines(prof_ms, n, nbucket, precision, hbm_peak, counts, sm_mhz, nlist=Fa
         table[k] = row
     top = max(prof_ms, key=prof_ms.get)
     r = table[top]
-    if r.get("fp64_frac", 0.0) > r["hbm_frac"]:
-        main = {"bound": "alu", "kernel": top, "achieved": r["fp64_inst_per_launch"] / (prof_ms[top] / 1e3),
-                "peak": fp64_peak, "unit": "FP64 ops/s", "frac": r["fp64_frac"],
-                "traffic": r.get("traffic"),
-                "peak_source": "derived: 152 SMs x 2 float64 ops/clk x SM clock"}
-    else:
-        main = {"bound": "hbm", "kernel": top, "achieved": r["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                "frac": r["hbm_frac"], "traffic": r.get("traffic"), "peak_source": "measured"}
-    if "fp32_pipe_frac" in r:
-        main["fp32_pipe_frac"] = r["fp32_pipe_frac"]
+    main = {"bound": "hbm", "kernel": top, "achieved": r["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
+            "frac": r["hbm_frac"], "traffic": r.get("traffic"),
+            "bytes_per_unit": SURVEY_BYTES[precision].get(top), "units_per_launch": n,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, copy)"}
+    for key in ("fp64_pipe_frac", "fp32_pipe_frac"):
+        if key in r:
+            main[key] = r[key]
     main["per_kernel"] = table
     return main
 
@@ -486,10 +503,12 @@ def main(argv=None):
     except OSError:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    fma_peaks = {"fp64": md.md_measure_fma_peak("fp64"), "fp32": md.md_measure_fma_peak("mixed")}
     roofline = rooflines(prof, n_local, nbucket, precision, hbm_peak, ncu_counts(args.workload, precision, skin > 0),
-                         clk["sm_mhz"] if clk else None, nlist=skin > 0)
-    if "hbm_gbs" not in peaks and roofline["bound"] == "hbm":
-        roofline["peak_source"] = "fallback"
+                         fma_peaks, nlist=skin > 0)
+    roofline["fma_peaks_measured"] = {"fp64_fma_per_s": fma_peaks["fp64"], "fp32_fma_per_s": fma_peaks["fp32"]}
+    if "hbm_gbs" not in peaks:
+        roofline["peak_source"] = "fallback (6.8 TB/s)"
 
     # end to end through the C ABI with host buffers (pinned): restore the
     # checkpoint state from the host, one step, read the state back
@@ -518,7 +537,16 @@ def main(argv=None):
     e2e = {"value": total_particles / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 24 * n_local,
            "d2h_bytes_per_step": 2 * 24 * n_local + 8, "ms_per_step": e2e_s * 1e3,
            "path": "md_restore(host x, p_half) + md_step(1) + md_get_state(host x, p_half)"}
+    # the state the accuracy report starts from (the benched launch configuration), and one more step
+    snap = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not resident:
+        s_k = sim.state()
+        f_k, _ = sim.forces()
+        sim.step(1)
+        sim.sync()
+        snap = {"state": s_k, "forces": f_k, "next": sim.state()}
     sim.close()
+    diffusion = diffusion_check(md, stream) if precision == "mixed" and rank == 0 else None
 
     plain = None
     if not args.no_plain and precision == "mixed":
@@ -565,9 +593,10 @@ def main(argv=None):
                 "workload": "250000 WCA in a periodic 2D plane (z updates not evaluated) at the sphere's "
                             "area fraction 0.4", "rattle_over_2d": ms / msp}
 
-    cpu = None
+    cpu, accuracy = None, {"residual_max_g_over_gradg": res["max_g_over_gradg"], "diffusion": diffusion}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(systems, args.cpu_seconds)
+        cpu, acc = oracle_leg(systems, args.cpu_seconds, snap, precision)
+        accuracy.update(acc)
 
     if rank == 0:
         line = {
@@ -582,7 +611,7 @@ def main(argv=None):
             "residual_max_g_over_gradg": res["max_g_over_gradg"],
             "l2_resident": {"value": total_particles / (ms_resident / 1e3), "ms_per_step": ms_resident},
             "wall_s_timed_region": t_wall,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "roofline": roofline, "cpu_baseline": cpu, "accuracy": accuracy, "e2e": e2e, "clocks": clk,
             "gpu_launches": launches, "plain_fp64": plain, "unconstrained_2d": flat,
             "tuned": {"options": tuned["options"], "trials": tuned.get("trials")},
         }
@@ -602,9 +631,36 @@ def _oracle_systems(systems):
     return sims
 
 
-def cpu_baseline(systems, seconds: float):
-    """The oracle, as it stands, on the host cores: whole time steps of the same
-    workload for about `seconds` of CPU time (single thread)."""
+def cpu_info() -> dict:
+    """Host cores and CPU model (lscpu, else /proc/cpuinfo)."""
+    cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"cores": cores, "model": model}
+
+
+def time_oracle(systems, seconds: float, threads: int):
+    """Whole time steps of the oracle on `threads` host threads for about
+    `seconds`; returns (particle-steps/s, steps, elapsed, threads used)."""
+    import oracle
+
+    used = oracle.set_threads(threads)
     sims = _oracle_systems(systems)
     n = sum(s["n"] for s in systems)
     steps = 0
@@ -616,16 +672,133 @@ def cpu_baseline(systems, seconds: float):
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    return {"value": n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} whole time steps of the {n}-particle workload ({len(systems)} system(s)), "
-                      f"{el:.1f} s, single-threaded float64 C oracle with a cell list"}
+    oracle.set_threads(1)
+    return n * steps / el, steps, el, used
+
+
+def oracle_leg(systems, seconds: float, snap, precision: str):
+    """The oracle on the host cores (the CPU baseline: single-threaded and
+    with OpenMP over the particle loops on every core, whole time steps of the
+    same workload, about `seconds` each) and the accuracy of the GPU run
+    against it: forces of every particle at the benched state, and one step of
+    Algorithm S1 (position half with its multiplier) for sampled particles."""
+    import oracle
+
+    info = cpu_info()
+    n = sum(s["n"] for s in systems)
+    v1, k1, e1, _ = time_oracle(systems, seconds, 1)
+    vm, km, em, used = time_oracle(systems, seconds, info["cores"])
+    cpu = {"value": vm, "unit": UNIT, "cores": used, "kind": "oracle", "model": info["model"],
+           "sample": f"{km} whole time steps of the {n}-particle workload ({len(systems)} system(s)), {em:.1f} s, "
+                     f"float64 C oracle with a cell list, OpenMP over the per-particle loops on {used} threads",
+           "single_thread": {"value": v1, "cores": 1, "sample": f"{k1} whole time steps, {e1:.1f} s"}}
+    acc = {}
+    if snap is not None:
+        acc.update(force_accuracy(systems, snap))
+        acc.update(step_accuracy(systems, snap))
+    return cpu, acc
+
+
+def _oracle_forces(systems, x):
+    import oracle
+
+    out, off = [], 0
+    for s in systems:
+        xs = x[off:off + s["n"]]
+        mol = s.get("mol")
+        if mol is None:
+            bpm = s["params"].get("beads_per_mol", 0)
+            mol = (np.arange(s["n"]) // bpm if bpm > 1 else np.arange(s["n"])).astype(np.int32)
+        f, _ = oracle.pair_forces(s["params"], xs, s["type"], mol, mode="cells")
+        fb, _, _ = oracle.bond_wall_forces(s["params"], xs, s["constrained"], s["type"])
+        out.append(f + fb)
+        off += s["n"]
+    return np.concatenate(out)
+
+
+def force_accuracy(systems, snap):
+    """|df| / max(|f|, 1 eps/sigma) of every particle's force at the benched state."""
+    x, f = snap["state"]["x"], snap["forces"]
+    ref = _oracle_forces(systems, x)
+    rel = np.linalg.norm(f - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1.0)
+    return {"force_rel_err": {"max": float(rel.max()), "p99_99": float(np.quantile(rel, 0.9999)),
+                              "above_1e-5": int((rel > 1e-5).sum()), "particles": int(rel.size),
+                              "metric": "|f_gpu - f_oracle| / max(|f_oracle|, 1 eps/sigma), all particles",
+                              "step": int(snap["state"]["step"])}}
+
+
+def step_accuracy(systems, snap, per_system: int = 200):
+    """One step of Algorithm S1 from the GPU's state for sampled constrained
+    particles (the oracle advances each with its neighbours at the GPU's
+    positions): the largest |x^{k+1}_gpu - x^{k+1}_oracle| and the multiplier
+    difference it implies, as the normal constraint force |dlambda n0| =
+    |dx . n0| / (a |n0|) with a = dt^2 / (2m) (eps/sigma)."""
+    import oracle
+
+    st, nxt = snap["state"], snap["next"]
+    k = int(st["step"])
+    g = np.random.default_rng(7)
+    dx_max, dlam_max, count = 0.0, 0.0, 0
+    off = 0
+    for s in systems:
+        sl = slice(off, off + s["n"])
+        off += s["n"]
+        x, ph, xn = st["x"][sl], st["p_half"][sl], nxt["x"][sl]
+        con = np.nonzero(s["constrained"])[0]
+        if con.size == 0:
+            continue
+        m = s["params"]["mass"][0]
+        a = s["params"]["dt"] ** 2 / (2 * m)
+        for i in g.choice(con, size=min(per_system, con.size), replace=False):
+            _, xa, _, _ = oracle.particle_advance(s["surface"], s["params"], x, int(i), ph[i], k, 0, s["type"],
+                                                   None, s["constrained"])
+            _, n0 = oracle.surface_g(s["surface"], s["params"], x[i])
+            d = xn[i] - xa
+            dx_max = max(dx_max, float(np.abs(d).max()))
+            dlam_max = max(dlam_max, abs(float(d @ n0)) / (a * float(np.linalg.norm(n0))))
+            count += 1
+    return {"position_half": {"max_abs_dx": dx_max, "max_abs_dlambda_n0": dlam_max, "particles": count,
+                              "step": k,
+                              "metric": "one step of Algorithm S1 from the GPU's (x^k, p^{k-1/2}) per sampled "
+                                        "constrained particle; |dlambda n0| = |dx . n0| / (a |n0|), "
+                                        "a = dt^2/(2m), in eps/sigma"}}
+
+
+def diffusion_check(md, stream):
+    """Diffusion coefficient of 40,000 non-interacting particles on a sphere of
+    radius 10 (mixed path, same library): <r(0).r(t)>/R^2 = exp(-2 D t'/R^2),
+    t' = t - tau(1 - e^{-t/tau}) (SI S1.3 with the Langevin inertia; tau = 1),
+    fitted through the origin in ln c over t = 10, 25, 50, 80; D = kT/(m gamma) = 1."""
+    from paper_1411_3019_gb300 import inputs
+
+    R, dt = 10.0, 0.002
+    surf = {"kind": "sphere", "center": (0.0, 0.0, 0.0), "p": (R, 0.0, 0.0, 0.0)}
+    sim = md.Simulation(inputs.free_on_surface(surf, 40_000, seed=3, dt=dt), stream=stream)
+    sim.set_state()
+    ts, cs, t = [], [], 0.0
+    for tc in (10.0, 25.0, 50.0, 80.0):
+        k = int(round((tc - t) / dt))
+        sim.step(k)
+        t += k * dt
+        ts.append(t - (1 - math.exp(-t)))
+        cs.append(sim.observables()[0]["r0_dot_rt"])
+    sim.close()
+    ts, lc = np.array(ts), np.log(np.array(cs))
+    d_fit = float(-(ts @ lc) / (ts @ ts) * R ** 2 / 2)
+    return {"D_fit": d_fit, "D_theory": 1.0, "rel_err": d_fit - 1.0,
+            "setup": "40000 non-interacting particles on a sphere R=10, mixed, dt=0.002, t up to 80 tau"}
 
 
 def reference_arm(args, rank: int, world: int, precision: str):
-    """The reference arm is the oracle on the host cores: rank 0 only, whole
-    time steps of the same workload (at most 60 timed steps)."""
+    """The reference arm is the oracle on the host cores (OpenMP over its
+    per-particle loops on every core): rank 0 only, whole time steps of the
+    same workload (at most 60 timed steps)."""
     if rank != 0:
         return
+    import oracle
+
+    info = cpu_info()
+    threads = oracle.set_threads(info["cores"])
     systems = workload(args.workload, 0, precision, args.nrep, args.pair_form)
     sims = _oracle_systems(systems)
     n = sum(s["n"] for s in systems)
@@ -642,9 +815,13 @@ def reference_arm(args, rank: int, world: int, precision: str):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
             "warmup": args.warmup, "ms_per_step": el / steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.workload, systems, precision), "impl": "reference",
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
-                             "sample": f"{steps} whole time steps of the {n}-particle workload"},
+            "config": dict(workload_config(args.workload, systems, precision),
+                           engine="resident" if args.engine == "resident" else "global"),
+            "impl": "reference",
+            "cpu_baseline": {"kind": "oracle", "cores": threads, "model": info["model"], "value": value,
+                             "unit": UNIT,
+                             "sample": f"{steps} whole time steps of the {n}-particle workload, OpenMP over the "
+                                       f"per-particle loops on {threads} threads"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

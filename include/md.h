@@ -303,6 +303,16 @@ int md_step(md_handle* h, int64_t nsteps);
  * times the Verlet list has been built since it was first switched on (by
  * the steps, and by md_set_state, md_restore and switching the list on). */
 #define MD_OPT_NLIST_BUILDS 7
+/* MD_OPT_SPIN_LIMIT: the one bounded wait on the device, the scan of the
+ * bucket counters waiting for its predecessor tiles (decoupled look-back),
+ * reads a predecessor's word at most `limit` times (0..2^31-1, default
+ * 2^22). When the limit runs out the kernel latches MD_FLAG_TIMEOUT, gives its
+ * tile a zero prefix (the cell list of that step is then wrong, every access
+ * stays in bounds) and returns; the next synchronising call reports
+ * MD_ERR_TIMEOUT and the next md_step rebuilds the cell list from the
+ * positions before it steps. With 0 the wait gives up without reading, so a
+ * scan of more than one tile (more than 8192 buckets) always times out. */
+#define MD_OPT_SPIN_LIMIT 8
 /* Verlet neighbour list (the LAMMPS-style list the paper's simulations
  * ran with; the cell list is how it is built). With skin > 0 every pair
  * within r_c + skin is listed from the cell list, and the pair kernel walks
@@ -389,25 +399,31 @@ int md_cell_list(md_handle* h, uint32_t* sorted_ids, uint32_t* sorted_cells,
 
 /* Forces of one system without allocating device memory. The paper has no
  * counterpart: this entry point exists for callers that cannot allocate at
- * the point where they need forces, e.g. a thread working while a CUDA graph
- * is captured in global mode (device allocation is not permitted then), or
- * an application whose device memory is all owned by its own allocator.
+ * the point where they need forces, e.g. an application whose device memory
+ * all belongs to its own pool allocator (nothing is left for the driver to
+ * hand out), or a caller on a latency-critical path that must not wait on
+ * the driver's allocator.
  * It computes f = -grad V (pair, bond and wall terms) and the per-particle
- * energy u at positions d_x, exactly as md_forces does for a handle with the
- * same surface and parameters, using a scratch array of about 11 MB that the
- * library reserves in device global memory when its device code is loaded
- * (each device that loads the library keeps it until the process exits).
+ * energy u at positions d_x, as md_forces does for a handle with the same
+ * surface and parameters (within the force tolerance of md_forces: its cell
+ * grid and bucket layout may differ, so float32 sums can differ in their
+ * last bits), using a scratch array of about 11 MB that the library
+ * reserves in device global memory when its device code is loaded (each
+ * device that loads the library keeps it until the process exits).
  *   n <= 65536 particles (else MD_ERR_INVALID_ARG); cell grids larger than
  *   2^18 cells use 2^18 hashed buckets.
  *   d_x [n][3] float64, d_f [n][3] float64 (required); d_type, d_mol,
  *   d_constrained, d_u may be NULL (defaults of md_set_state). All pointers
  *   are device memory owned by the caller.
- *   cuda_stream: the stream to work on (NULL = legacy stream). The call
- *   waits for the stream before it returns and reports a particle outside
- *   the grid as MD_ERR_OUT_OF_GRID.
+ *   cuda_stream: the stream to work on (NULL = legacy stream, which waits
+ *   for every blocking stream of the context: pass a non-blocking stream when
+ *   other threads work on the device at the same time). The call waits for
+ *   the stream before it returns and reports a particle outside the grid as
+ *   MD_ERR_OUT_OF_GRID.
  * The first call on a device resolves the scratch address on that device
  * (and loads the device code if it is not loaded yet); make that first call
- * before any stream capture. Every call shares the one array: calls that
+ * before any stream capture. Every call shares the one array, which keeps the
+ * last call's contents (each call resets what must start at zero): calls that
  * overlap on the GPU (other threads, other streams) race and must be
  * serialised by the caller. Errors of this entry point are read with
  * md_last_error(NULL). */
@@ -427,6 +443,17 @@ int md_forces_noalloc(const md_surface* surf, const md_params* prm, int64_t n,
  * Synchronous; allocates and frees its own device buffers. Errors are read
  * with md_last_error(NULL). */
 int md_check_conversions(const double* in, int64_t n, float* out_f32, double* out_f64);
+
+/* Diagnostic (no counterpart in the paper): measured fused multiply-add
+ * throughput of the current device, the denominator of the arithmetic
+ * rooflines. precision: MD_PREC_FP64 (float64 FMA) or MD_PREC_MIXED (float32
+ * FMA). A kernel of 16 CTAs per SM, 256 threads each, runs 8 independent FMA
+ * chains per thread; the best of `trials` (>= 1) launches timed with CUDA
+ * events gives *fma_per_s (thread FMA instructions per second; 2 flops
+ * each). Synchronous; allocates nothing. Errors: MD_ERR_INVALID_ARG for a
+ * bad precision, trials or NULL output; MD_ERR_CUDA for a failed launch (read
+ * with md_last_error(NULL)). */
+int md_measure_fma_peak(int32_t precision, int32_t trials, double* fma_per_s);
 
 /* Description of the last error on h (or of the last md_create failure
  * when h is NULL). Never NULL. */

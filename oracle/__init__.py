@@ -42,7 +42,9 @@ def build(force: bool = False) -> str:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
                "-fno-fast-math", "-Wall", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        # OpenMP over the independent per-particle loops where the compiler has it
+        if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True).returncode != 0:
+            subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -128,8 +130,17 @@ def lib():
             L.orc_particle_advance.argtypes = [C.POINTER(Surface), C.POINTER(Params), C.c_int64, _dp,
                                                _ip, _ip, C.c_void_p, C.c_int64, _dp, C.c_uint64,
                                                C.c_int, _dp, _dp, _dp]
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_set_threads.restype = C.c_int
+            L.orc_set_threads(1)  # one thread unless set_threads asks for more
             _lib = L
     return _lib
+
+
+def set_threads(k: int) -> int:
+    """Threads of the oracle's per-particle loops (OpenMP; 1 if it was built
+    without). Results are the same at any count. Returns the count in use."""
+    return int(lib().orc_set_threads(int(k)))
 
 
 # ---------------------------------------------------------------------------

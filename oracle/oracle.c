@@ -65,6 +65,9 @@
  *       continuous at r_c, which holds for "- (r - r_c) phi'(r_c)", the form
  *       used here.
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -620,6 +623,7 @@ int orc_pair_forces_cells(const orc_params* P, int64_t n, const double* x,
     free(cell);
     return -1;
   }
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     int64_t c[3];
     for (int k = 0; k < 3; ++k) {
@@ -638,6 +642,7 @@ int orc_pair_forces_cells(const orc_params* P, int64_t n, const double* x,
     kv[i].idx = i;
   }
   qsort(kv, (size_t)n, sizeof(orc_kv), kv_cmp);
+#pragma omp parallel for schedule(dynamic, 256)
   for (int64_t i = 0; i < n; ++i) {
     int64_t seen[27];
     int nseen = 0;
@@ -877,6 +882,7 @@ int orc_sys_forces(orc_sys* s) {
 /* Random force f_r^k of every particle (Algorithm S1):
  * sqrt(2 m kT / (tau dt)) * N(0,1)^3 with 1/tau = gamma. */
 static void random_forces(orc_sys* s, uint64_t k, double* out) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < s->n; ++i) {
     double m = mass_of(s, i);
     double amp = sqrt(2.0 * m * s->P.kT * s->P.gamma / s->P.dt);
@@ -937,7 +943,10 @@ int64_t orc_step(orc_sys* s, int64_t nsteps) {
   if (!frn) return -1;
   const double dt = s->P.dt, gam = s->P.gamma;
   for (int64_t st = 0; st < nsteps; ++st) {
-    /* 1. position update of Algorithm 1 for every particle */
+    /* 1. position update of Algorithm 1 for every particle (the particles
+     * are independent: OpenMP threads take disjoint ranges) */
+    int64_t n_iters = 0, n_fail = 0, n_floor = 0;
+#pragma omp parallel for schedule(static) reduction(+ : n_iters, n_fail, n_floor)
     for (int64_t i = 0; i < n; ++i) {
       double m = mass_of(s, i);
       double* xi = &s->x[3 * i];
@@ -947,12 +956,11 @@ int64_t orc_step(orc_sys* s, int64_t nsteps) {
         double xn[3], phn[3];
         int32_t its = 0;
         int rc = orc_position_half(&s->S, &s->P, xi, pi, Fi, m, xn, phn, NULL, &its);
-        s->newton_iters += its;
+        n_iters += its;
         if (rc < 0) {
-          fails++;
-          s->newton_fail++;
+          n_fail++;
         } else if (rc == 1) {
-          s->newton_floor++;
+          n_floor++;
         }
         for (int k = 0; k < 3; ++k) {
           xi[k] = xn[k];
@@ -967,6 +975,10 @@ int64_t orc_step(orc_sys* s, int64_t nsteps) {
         }
       }
     }
+    s->newton_iters += n_iters;
+    s->newton_fail += n_fail;
+    s->newton_floor += n_floor;
+    fails += n_fail;
     s->step += 1;
     /* 2. new conservative forces f^{m+1} = -grad V */
     if (orc_sys_forces(s)) {
@@ -975,30 +987,44 @@ int64_t orc_step(orc_sys* s, int64_t nsteps) {
     }
     /* 3. new random force and the combination of Algorithm S1 */
     random_forces(s, s->step, frn);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < 3 * n; ++i) {
       s->F[i] = (s->fc[i] - gam * s->ph[i] + 0.5 * (frn[i] + s->fr[i])) / (1.0 + 0.5 * dt * gam);
       s->fr[i] = frn[i];
     }
     /* 4. momentum update of Algorithm 1 */
+    int64_t m_fail = 0;
+#pragma omp parallel for schedule(static) reduction(+ : m_fail)
     for (int64_t i = 0; i < n; ++i) {
       double m = mass_of(s, i);
       if (s->con[i]) {
         double pn[3];
         int rc = orc_momentum_half(&s->S, &s->P, &s->x[3 * i], &s->ph[3 * i],
                                    &s->F[3 * i], m, pn, NULL, NULL);
-        if (rc < 0) {
-          fails++;
-          s->newton_fail++;
-        }
+        if (rc < 0) m_fail++;
         for (int k = 0; k < 3; ++k) s->p[3 * i + k] = pn[k];
       } else {
         int dims = s->S.kind == 7 ? 2 : 3;
         for (int k = 0; k < dims; ++k) s->p[3 * i + k] = s->ph[3 * i + k] + 0.5 * dt * s->F[3 * i + k];
       }
     }
+    s->newton_fail += m_fail;
+    fails += m_fail;
   }
   free(frn);
   return fails;
+}
+
+/* Threads of the per-particle loops (1 without OpenMP). The particles'
+ * arithmetic, and every sum's order, is the same at any count. */
+int orc_set_threads(int k) {
+#ifdef _OPENMP
+  if (k >= 1) omp_set_num_threads(k);
+  return omp_get_max_threads();
+#else
+  (void)k;
+  return 1;
+#endif
 }
 
 void orc_get_state(const orc_sys* s, double* x, double* v, double* p_half,

@@ -18,8 +18,11 @@
 
 using namespace surfmd;
 
+constexpr uint32_t kDefaultSpinLimit = 1u << 22;  // reads of one scan word before the wait gives up
+
 struct md_handle {
   int dev = 0;
+  bool cells_stale = false;  // a step's cell list was not completed (a bounded wait ran out)
   cudaStream_t user_stream = nullptr;  // set by md_set_stream (nullptr: own stream)
   cudaStream_t own_stream = nullptr;
   cudaStream_t cap_stream = nullptr;
@@ -381,7 +384,10 @@ int check_device_status(md_handle* h) {
   if (st & kFlagRattle) return fail(h, MD_ERR_RATTLE_DIVERGED, "RATTLE Newton iteration missed the tolerance");
   if (st & kFlagNonfinite) return fail(h, MD_ERR_NONFINITE, "non-finite position or momentum");
   if (st & kFlagOutOfGrid) return fail(h, MD_ERR_OUT_OF_GRID, "a particle left its cell grid or crossed a wall");
-  if (st & kFlagTimeout) return fail(h, MD_ERR_TIMEOUT, "a bounded device wait ran out");
+  if (st & kFlagTimeout) {  // the cell list of that step is not valid: rebuild it before the next step
+    h->cells_stale = true;
+    return fail(h, MD_ERR_TIMEOUT, "a bounded device wait ran out (the cell list is rebuilt before the next step)");
+  }
   if (st & kFlagNlistFull)
     return fail(h, MD_ERR_NLIST_FULL, "a particle has more neighbours than the neighbour list holds");
   if (st & kFlagOffSurface)
@@ -802,6 +808,7 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
   if (!h->has_pairs) A.nbucket = 1;
   A.pair_lanes = 1;
   A.ntypes = prms[0].ntypes;
+  A.spin_limit = kDefaultSpinLimit;
   A.rec_cell = (!h->excl && cell_total < (uint64_t(1) << 29)) ? 1 : 0;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
@@ -1016,6 +1023,11 @@ int md_step(md_handle* h, int64_t nsteps) {
   if (nsteps < 0) return fail(h, MD_ERR_INVALID_ARG, "nsteps must be >= 0");
   h->last_launches = 0;
   if (nsteps == 0) return MD_OK;
+  if (h->cells_stale) {  // the previous step's cell list did not complete
+    rc = rebuild_cells(h);
+    if (rc) return rc;
+    h->cells_stale = false;
+  }
   if (h->engine == 1) return resident_steps(h, nsteps);
   rc = build_graph(h);
   if (rc) return rc;
@@ -1217,6 +1229,10 @@ int md_set_option(md_handle* h, int32_t key, int64_t value) {
       if (value < 1 || value > 100000) return fail(h, MD_ERR_INVALID_ARG, "steps per launch must be in 1..100000");
       h->res_steps_per_launch = value;
       break;
+    case MD_OPT_SPIN_LIMIT:
+      if (value < 0 || value > 0x7fffffff) return fail(h, MD_ERR_INVALID_ARG, "spin limit must be in 0..2^31-1");
+      h->A.spin_limit = (uint32_t)value;
+      break;
     case MD_OPT_PAIR_TILE:
       if (value != 0 && value != 8 && value != 16 && value != 32)
         return fail(h, MD_ERR_INVALID_ARG, "pair tile must be 0, 8, 16 or 32");
@@ -1243,6 +1259,7 @@ int md_get_option(md_handle* h, int32_t key, int64_t* value) {
     case MD_OPT_RESIDENT_THREADS: *value = h->res_threads; return MD_OK;
     case MD_OPT_RESIDENT_STEPS: *value = h->res_steps_per_launch; return MD_OK;
     case MD_OPT_PAIR_TILE: *value = h->A.pair_tile; return MD_OK;
+    case MD_OPT_SPIN_LIMIT: *value = h->A.spin_limit; return MD_OK;
     case MD_OPT_NLIST_BUILDS: {
       unsigned long long b = 0;
       if (h->A.nl_builds) {
@@ -1441,6 +1458,38 @@ int md_check_conversions(const double* in, int64_t n, float* out_f32, double* ou
   return MD_OK;
 }
 
+int md_measure_fma_peak(int32_t precision, int32_t trials, double* fma_per_s) {
+  if ((precision != MD_PREC_FP64 && precision != MD_PREC_MIXED) || trials < 1 || !fma_per_s)
+    return fail(nullptr, MD_ERR_INVALID_ARG, "precision must be MD_PREC_FP64 or MD_PREC_MIXED, trials >= 1");
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // long enough to time (~ms), short enough to stay a probe
+  const int blocks = 16 * std::max(sms, 1), iters = precision == MD_PREC_FP64 ? 256 : 16384;
+  cudaStream_t st = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) e = launch_fma_probe(precision == MD_PREC_FP64 ? 0 : 1, blocks, iters, st);  // warm-up
+  double best = 0.0;
+  for (int t = 0; t < trials && e == cudaSuccess; ++t) {
+    e = cudaEventRecord(a, st);
+    if (e == cudaSuccess) e = launch_fma_probe(precision == MD_PREC_FP64 ? 0 : 1, blocks, iters, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e == cudaSuccess && ms > 0.f) best = std::max(best, (double)blocks * 256.0 * 8.0 * iters / (ms * 1e-3));
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (st) cudaStreamDestroy(st);
+  if (e != cudaSuccess) return fail(nullptr, MD_ERR_CUDA, std::string("peak probe: ") + cudaGetErrorString(e));
+  *fma_per_s = best;
+  return MD_OK;
+}
+
 const char* md_last_error(md_handle* h) {
   if (!h) return g_create_err.c_str();
   return h->err.c_str();
@@ -1627,6 +1676,7 @@ extern "C" int md_forces_noalloc(const md_surface* surf, const md_params* prm, i
   A.rec = base + NaLayout::rec;
   A.rec_lo = prm->precision == MD_PREC_FP64 ? nullptr : reinterpret_cast<float4*>(base + NaLayout::rec_lo);
   A.ntypes = prm->ntypes;
+  A.spin_limit = kDefaultSpinLimit;
   A.meta = reinterpret_cast<uint32_t*>(base + NaLayout::meta);
   A.mol = excl ? reinterpret_cast<int32_t*>(base + NaLayout::mol) : nullptr;
   A.cell = reinterpret_cast<uint32_t*>(base + NaLayout::cell);

@@ -80,6 +80,10 @@ int resident_blocks_per_sm(int precision, int bonds, int walls, int excl, uint32
 // by the integer-pipe conversions of the mixed path.
 cudaError_t launch_check_conversions(const double* in, int64_t n, float* out_f, double* out_d, cudaStream_t st);
 
+// Peak probe: blocks x 256 threads, each 8 independent FMA chains of iters
+// steps, in float64 (precision 0) or float32 (1).
+cudaError_t launch_fma_probe(int precision, int blocks, int iters, cudaStream_t st);
+
 // Residuals: out[0] = max |g|/|grad g|, out[1] = max |g|, out[2] = max |n.v|/|n|
 // (stored as the bit patterns of non-negative doubles; zeroed inside).
 cudaError_t launch_residual(const DevArrays& A, unsigned long long* d_out, cudaStream_t st);

@@ -509,12 +509,14 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
 // aggregate, then walks back over its predecessors' published values until it
 // meets an inclusive prefix. Tile states are 64-bit words
 // (epoch:30 | flag:2 | value:32); a state from an earlier launch (older epoch)
-// reads as "not ready". Every wait is bounded: after kScanSpinLimit polls the
-// kernel sets the timeout flag and carries on. The last CTA to finish resets
-// the tile counter and advances the epoch. Optionally the kernel also moves
-// the step counter on (nothing in it reads the step).
+// reads as "not ready". Every wait is bounded: a predecessor's word is read at
+// most A.spin_limit times; if it is still not ready the kernel sets the
+// timeout flag and takes a zero prefix for its tile, so every bucket start
+// stays within [0, n] (the list is wrong, every later access stays in bounds,
+// and the host rebuilds the list before the next step). The last CTA to
+// finish resets the tile counter and advances the epoch. Optionally the
+// kernel also moves the step counter on (nothing in it reads the step).
 constexpr uint32_t kTileAgg = 1u, kTileIncl = 2u;
-constexpr int kScanSpinLimit = 1 << 22;
 
 __device__ __forceinline__ unsigned long long tile_word(uint32_t epoch, uint32_t flag, uint32_t value) {
   return ((unsigned long long)(epoch & 0x3fffffffu) << 34) | ((unsigned long long)flag << 32) | value;
@@ -575,14 +577,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_onepass(DevArrays A, int 
         unsigned long long w = 0ull;
         uint32_t flag = kTileIncl;  // lanes beyond tile 0 act as an empty inclusive prefix
         if (j >= 0) {
-          int spins = 0;
-          w = st[j];
           // ready: written in this launch (epoch) with a flag (zeroed words carry none)
-          while (((uint32_t)(w >> 34) != ep || ((w >> 32) & 3u) == 0u) && spins < kScanSpinLimit) {
-            ++spins;
+          bool ready = false;
+          for (uint32_t reads = 0; reads < A.spin_limit && !ready; ++reads) {
             w = st[j];
+            ready = (uint32_t)(w >> 34) == ep && ((w >> 32) & 3u) != 0u;
           }
-          if (spins >= kScanSpinLimit) timed_out = true;
+          if (!ready) timed_out = true;
           flag = (uint32_t)((w >> 32) & 3u);
         }
         // the nearest inclusive prefix among the 32 (lowest lane holding one)
@@ -591,11 +592,12 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_onepass(DevArrays A, int 
         uint32_t part = (lane <= stop && j >= 0) ? (uint32_t)w : 0u;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        prefix += part;
-        if (__any_sync(0xffffffffu, timed_out)) {
+        if (__any_sync(0xffffffffu, timed_out)) {  // give up: a zero prefix keeps the starts in [0, n]
           if (lane == 0) atomicOr(A.status, kFlagTimeout);
+          prefix = 0;
           break;
         }
+        prefix += part;
         if (incl) break;
         hi -= 32;
       }
@@ -704,6 +706,7 @@ __global__ void k_bucket_build(DevArrays A) {
   uint32_t rank = 0;
   for (uint32_t t = s0; t < s1; ++t) rank += (A.stag_tmp[t] < tag) ? 1u : 0u;
   const uint32_t d = s0 + rank;
+  if (d >= (uint32_t)n) return;  // only after a scan that timed out (its starts are not a partition)
   const uint32_t m = A.meta[tag];
   const SysDev& S = A.sys[meta_sys(m)];
   double o[3];
@@ -2903,6 +2906,32 @@ __global__ void k_get_forces(DevArrays A, double* fa, double* ua) {
   if (ua) ua[i] = (double)v.w;
 }
 
+
+// Arithmetic peak probe: every thread runs 8 independent fused multiply-add
+// chains of `iters` steps each in R; one result per thread is kept in a
+// device sink so the chains cannot be dropped.
+__device__ double g_peak_sink;
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_fma_probe(int iters, R b, R c) {
+  R a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = (R)(threadIdx.x + k);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+  }
+  R t = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t += a[k];
+  if (t == (R)-1.2345) g_peak_sink = (double)t;  // never true for these inputs; keeps the chains live
+}
+
+cudaError_t launch_fma_probe(int precision, int blocks, int iters, cudaStream_t st) {
+  if (precision == 0) k_fma_probe<double><<<blocks, 256, 0, st>>>(iters, 0.999999, 1e-7);
+  else k_fma_probe<float><<<blocks, 256, 0, st>>>(iters, 0.999999f, 1e-7f);
+  return cudaGetLastError();
+}
 
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* a, double v) {
   atomicMax(a, (unsigned long long)__double_as_longlong(v));

@@ -192,6 +192,7 @@ struct DevArrays {
   float4* rec_lo;       // [n] mixed path: offset - record (the low parts; w unused), else null
   float4* rec0_lo;      // [n] mixed path with the neighbour list: rec_lo at the last build
   int32_t ntypes;       // particle types in use (a type must lie in [0, ntypes))
+  uint32_t spin_limit;  // reads of a predecessor's scan word before the wait gives up
   const SysDev* sys;    // [nsys]
   const TypeTable* types;  // pair and mass tables shared by the systems
   int32_t* sys_free;    // [nsys] unconstrained particles per system (set with the state)

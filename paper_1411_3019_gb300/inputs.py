@@ -308,6 +308,16 @@ def sphere_system(n=1000, R=10.0, seed=1, dmin=0.8, precision="fp64", dt=0.001, 
     return _system(f"sphere_N{n}_R{R:g}", surf, prm, x, v)
 
 
+def free_on_surface(surf: dict, n: int, seed: int = 3, dt: float = 0.002, precision: str = "mixed", box=None):
+    """n non-interacting particles sampled uniformly by area on a surface with
+    Maxwell velocities at kT = 1 (gamma = m = 1, so D = kT/(m gamma) = 1): the
+    inputs of the diffusion laws of SI Section S1.3."""
+    prm = noninteracting(wca_params(dt=dt, seed=seed, precision=precision, rattle_tol=1e-10))
+    g = np.random.default_rng(seed)
+    x = sample_surface(surf, n, g, box=box)
+    return [_system("free", surf, prm, x, maxwell(n, 1.0, 1.0, g))]
+
+
 def c1_plain_sphere():
     """1,000 WCA particles on a sphere R = 10 sigma, float64 path, dt = 0.001,
     RATTLE tolerance 1e-12, seed 1; overlaps rejected below 0.8 sigma

@@ -36,6 +36,7 @@ MD_OPT_RESIDENT_THREADS = 4
 MD_OPT_RESIDENT_STEPS = 5
 MD_OPT_PAIR_TILE = 6
 MD_OPT_NLIST_BUILDS = 7
+MD_OPT_SPIN_LIMIT = 8
 ERROR_NAMES = {0: "MD_OK", 1: "MD_ERR_INVALID_ARG", 2: "MD_ERR_CUDA", 3: "MD_ERR_RATTLE_DIVERGED",
                4: "MD_ERR_NONFINITE", 5: "MD_ERR_OUT_OF_GRID", 6: "MD_ERR_TIMEOUT", 7: "MD_ERR_NO_DEVICE",
                8: "MD_ERR_NLIST_FULL"}
@@ -125,6 +126,7 @@ def lib():
                 "md_set_option": ([vp, i32, i64], C.c_int),
                 "md_set_neighbor_list": ([vp, C.c_double, i32], C.c_int),
                 "md_check_conversions": ([vp, i64, vp, vp], C.c_int),
+                "md_measure_fma_peak": ([i32, i32, C.POINTER(C.c_double)], C.c_int),
                 "md_get_option": ([vp, i32, C.POINTER(i64)], C.c_int),
                 "md_last_error": ([vp], C.c_char_p),
                 "md_destroy": ([vp], None),
@@ -342,6 +344,17 @@ def md_grid_info(h, sys: int = 0):
     _check(h, lib().md_grid_info(h, int(sys), lo, cs, nc, C.byref(base), C.byref(hashed)))
     return {"lo": np.array(lo[:]), "cs": np.array(cs[:]), "nc": np.array(nc[:]), "base": base.value,
             "hashed": hashed.value}
+
+
+def md_measure_fma_peak(precision: str = "fp64", trials: int = 5) -> float:
+    """Measured FMA instructions per second of the current device
+    (float64 for "fp64", float32 for "mixed")."""
+    out = C.c_double()
+    rc = lib().md_measure_fma_peak(PRECISION[precision] if isinstance(precision, str) else int(precision),
+                                   int(trials), C.byref(out))
+    if rc:
+        raise MdError(rc, md_last_error(None))
+    return out.value
 
 
 def md_cell_list(h):

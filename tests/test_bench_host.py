@@ -48,6 +48,7 @@ def test_reference_arm_prints_one_json_line():
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 2
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["cores"] >= 1 and line["config"]["engine"] == "global"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     assert line["config"]["workload"].startswith("plain_sphere")
 
@@ -76,9 +77,37 @@ def test_neighbour_list_defaults_and_cell_edge():
     assert bench.cells_for_skin(systems, 0.0)[0]["params"]["cell_size"] == 0.0
 
 
-def test_neighbour_list_algorithmic_bytes():
-    """With the list, the integrator moves 176 bytes per particle in mixed
-    precision, and the rebuild kernels count no bytes per step."""
-    assert bench.algorithmic_bytes("integrate", 1000, 4096, "mixed", nlist=True) == 176_000
+def test_algorithmic_bytes_follow_the_survey_figures():
+    """The integrator and the pair kernel count the per-particle algorithmic
+    bytes of the method's survey (116 and 36 B in mixed precision, 128 and
+    68 B in float64) in both step forms; with the neighbour list the rebuild
+    kernels count no bytes per step; the implementation's own bytes are
+    reported beside them."""
+    assert bench.algorithmic_bytes("integrate", 1000, 4096, "mixed", nlist=True) == 116_000
+    assert bench.algorithmic_bytes("integrate", 1000, 4096, "mixed") == 116_000
+    assert bench.algorithmic_bytes("pair", 1000, 4096, "mixed", nlist=True) == 36_000
+    assert bench.algorithmic_bytes("integrate", 1000, 4096, "fp64") == 128_000
     assert bench.algorithmic_bytes("scan", 1000, 4096, "mixed", nlist=True) == 0
-    assert bench.algorithmic_bytes("integrate", 1000, 4096, "mixed") == 1000 * 124 + 8 * 4096
+    assert bench.algorithmic_bytes("scan", 1000, 4096, "mixed") == 12 * 4096 + 16
+    assert bench.impl_bytes("integrate", 1000, "mixed", True) > bench.algorithmic_bytes("integrate", 1000, 0,
+                                                                                         "mixed")
+
+
+def test_roofline_recomputes_from_kernel_times_bytes_and_peaks():
+    """roofline.frac = (survey bytes per particle x particles) / dominant
+    kernel's duration / measured HBM peak; the float64-pipe fraction uses the
+    measured FMA rate."""
+    prof = {"pair": 0.020, "integrate": 0.030, "scan": 0.006}
+    counts = {"integrate": {"fp64_inst": 2.5e6, "dram_bytes": 3e7}}
+    r = bench.rooflines(prof, 250_000, 1 << 20, "mixed", 6766.7, counts, {"fp64": 6.0e11, "fp32": 4.0e13},
+                        nlist=True)
+    assert r["kernel"] == "integrate" and r["bound"] == "hbm"
+    achieved = 116 * 250_000 / 30e-6 / 1e9
+    assert abs(r["achieved"] - achieved) < 1e-9 and abs(r["frac"] - achieved / 6766.7) < 1e-12
+    assert abs(r["fp64_pipe_frac"] - 2.5e6 / 30e-6 / 6.0e11) < 1e-12
+    assert r["traffic"] == 3e7 and r["bytes_per_unit"] == 116 and r["units_per_launch"] == 250_000
+
+
+def test_cpu_info_reports_cores():
+    info = bench.cpu_info()
+    assert info["cores"] >= 1

@@ -107,3 +107,38 @@ def test_empty_and_single_particle_systems():
         f, _ = sim.forces()
         assert np.abs(f).max() == 0.0
         assert sim.residual()["max_g_over_gradg"] < 1e-10
+
+
+def test_scan_wait_limit_reports_timeout_and_the_next_step_recovers():
+    """The scan's bounded look-back wait (the one device-side wait): with a
+    limit of 0 reads every tile after the first gives up, latches the
+    timeout flag and returns (no wait, every access in bounds); the next
+    synchronising call reports MD_ERR_TIMEOUT, and the next md_step rebuilds
+    the cell list, so the run then repeats a run that never timed out bit
+    for bit."""
+    systems = I.c2_ellipsoid_torus(n_ell=4000, n_tor=1500, seed=8, precision="mixed")
+    with md.Simulation(systems) as ref:
+        ref.set_state()
+        ref.step(4)
+        ref.sync()
+        want = ref.state()
+    with md.Simulation(systems) as sim:
+        sim.set_state()
+        assert md.md_get_option(sim.h, md.MD_OPT_SPIN_LIMIT) == 1 << 22
+        assert md.md_cell_list(sim.h)["bucket_start"].shape[0] - 1 > 8192  # more than one scan tile
+        md.md_set_option(sim.h, md.MD_OPT_SPIN_LIMIT, 0)
+        sim.step(1)
+        with pytest.raises(md.MdError) as e:
+            sim.sync()
+        assert e.value.code == md.MD_ERR_TIMEOUT
+        sim.sync()  # reported once, then cleared
+        md.md_set_option(sim.h, md.MD_OPT_SPIN_LIMIT, 1 << 22)
+        sim.step(3)
+        sim.sync()
+        got = sim.state()
+        assert sim.residual()["max_g_over_gradg"] < 1e-10
+    assert got["step"] == want["step"] == 4
+    for key in ("x", "p_half"):
+        assert np.array_equal(got[key], want[key]), key
+    with md.Simulation(systems) as sim, pytest.raises(md.MdError):
+        md.md_set_option(sim.h, md.MD_OPT_SPIN_LIMIT, -1)
