@@ -313,6 +313,21 @@ int md_step(md_handle* h, int64_t nsteps);
  * positions before it steps. With 0 the wait gives up without reading, so a
  * scan of more than one tile (more than 8192 buckets) always times out. */
 #define MD_OPT_SPIN_LIMIT 8
+/* MD_OPT_PAIR_QUEUE (mixed precision with the Verlet list): 1 (default) = a
+ * warp screens its 32 particles' list entries round by round and queues the
+ * pairs near or inside the cutoff, then evaluates 32 queued pairs at a time
+ * on all lanes; 0 = each lane walks its particle's list alone. Both add every
+ * particle's terms in list order with the same arithmetic: the same bits. */
+#define MD_OPT_PAIR_QUEUE 9
+/* MD_OPT_FUSED_REBUILD (Verlet-list step form): 1 (default) = the cell-list
+ * and list rebuild of a step is one cooperative launch that returns at once
+ * unless the rebuild flag is up (three launches per step: pair, integrate,
+ * rebuild); 0 = five separate launches (bin, scan, scatter, bucket build,
+ * list build), each returning at once without a rebuild. The same lists and
+ * the same bits either way. Where a cooperative launch cannot be captured or
+ * run, md_step falls back to the separate launches (md_get_option then
+ * reads 0). */
+#define MD_OPT_FUSED_REBUILD 10
 /* Verlet neighbour list (the LAMMPS-style list the paper's simulations
  * ran with; the cell list is how it is built). With skin > 0 every pair
  * within r_c + skin is listed from the cell list, and the pair kernel walks

@@ -22,6 +22,8 @@ constexpr uint32_t kDefaultSpinLimit = 1u << 22;  // reads of one scan word befo
 
 struct md_handle {
   int dev = 0;
+  int fused_rebuild = 1;     // Verlet-list step: the cell-list and list rebuild as one cooperative launch
+  int rebuild_ctas = 0;      // CTAs of that launch (0: not computed yet)
   bool cells_stale = false;  // a step's cell list was not completed (a bounded wait ran out)
   cudaStream_t user_stream = nullptr;  // set by md_set_stream (nullptr: own stream)
   cudaStream_t own_stream = nullptr;
@@ -398,6 +400,8 @@ int check_device_status(md_handle* h) {
 // Cell list of the current positions (no step advance).
 int rebuild_cells(md_handle* h) {
   if (!h->has_pairs) return MD_OK;
+  // the fused rebuild's grid barrier starts from zero (a timed-out launch may have left arrivals)
+  CK(h, cudaMemsetAsync(h->A.gbar, 0, sizeof(GridBar), h->stream()));
   if (h->A.nl_dirty) {  // neighbour-list mode: raise the flag so every rebuild kernel runs
     const uint32_t one = 1u;
     CK(h, cudaMemcpyAsync(h->A.nl_dirty, &one, sizeof(one), cudaMemcpyHostToDevice, h->stream()));
@@ -459,12 +463,22 @@ const StepKernel kStepNl[] = {{"pair", k_pair_step},       {"integrate", k_integ
                               {"bin", k_bin_step},         {"scan", k_scan_step},
                               {"scatter", k_scatter_step}, {"bucket_build", k_bucket_step},
                               {"nl_build", k_nl_build_step}};
+cudaError_t k_rebuild_step(md_handle* h, cudaStream_t st) {
+  return launch_rebuild(h->A, h->precision, h->excl, h->rebuild_ctas, st);
+}
+const StepKernel kStepNlFused[] = {{"pair", k_pair_step}, {"integrate", k_integrate_step}, {"rebuild", k_rebuild_step}};
+const StepKernel kStepNlFusedBends[] = {
+    {"pair", k_pair_step}, {"bend", k_bend_step}, {"integrate", k_integrate_step}, {"rebuild", k_rebuild_step}};
 const StepKernel kStepNlBends[] = {{"pair", k_pair_step},       {"bend", k_bend_step},
                                    {"integrate", k_integrate_step}, {"bin", k_bin_step},
                                    {"scan", k_scan_step},       {"scatter", k_scatter_step},
                                    {"bucket_build", k_bucket_step}, {"nl_build", k_nl_build_step}};
 
 int step_kernels(const md_handle* h, const StepKernel** list) {
+  if (h->has_pairs && h->A.nl_dirty && h->fused_rebuild && h->rebuild_ctas > 0) {
+    *list = h->bends ? kStepNlFusedBends : kStepNlFused;
+    return h->bends ? 4 : 3;
+  }
   if (h->has_pairs && h->A.nl_dirty) {
     *list = h->bends ? kStepNlBends : kStepNl;
     return h->bends ? 8 : 7;
@@ -490,15 +504,30 @@ cudaError_t enqueue_step(md_handle* h, cudaStream_t st) {
 
 int build_graph(md_handle* h) {
   if (h->graph) return MD_OK;
+  if (h->has_pairs && h->A.nl_dirty && h->fused_rebuild && h->rebuild_ctas == 0) {
+    h->rebuild_ctas = rebuild_blocks(h->precision, h->excl, h->n);
+    if (h->rebuild_ctas <= 0) h->fused_rebuild = 0;  // not launchable here: five separate launches
+  }
   cudaGraph_t g = nullptr;
   CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = enqueue_step(h, h->cap_stream);
   cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
-  if (e != cudaSuccess) return cuda_fail(h, e, "capture of one step");
-  if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&h->graph, g, 0);
-  cudaGraphDestroy(g);
-  if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+  if (e == cudaSuccess && e2 == cudaSuccess) {
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+  } else if (g) {
+    cudaGraphDestroy(g);
+  }
+  const cudaError_t failed = e != cudaSuccess ? e : e2;
+  if (failed != cudaSuccess && h->A.nl_dirty && h->fused_rebuild) {
+    // a cooperative launch that cannot be captured here: the separate rebuild kernels instead
+    cudaGetLastError();
+    h->graph = nullptr;
+    h->fused_rebuild = 0;
+    return build_graph(h);
+  }
+  if (e2 != cudaSuccess) return cuda_fail(h, e2, "capture of one step");
+  if (e != cudaSuccess) return cuda_fail(h, e, "capture or instantiation of one step");
   return MD_OK;
 }
 
@@ -807,6 +836,7 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
   }
   if (!h->has_pairs) A.nbucket = 1;
   A.pair_lanes = 1;
+  A.pair_queue = 1;
   A.ntypes = prms[0].ntypes;
   A.spin_limit = kDefaultSpinLimit;
   A.rec_cell = (!h->excl && cell_total < (uint64_t(1) << 29)) ? 1 : 0;
@@ -846,6 +876,8 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
   al(dalloc(h, &A.blocksum, (size_t)nblk));
   al(dalloc(h, &A.tile_state, (size_t)nblk));
   al(dalloc(h, &A.scan, 1));
+  al(dalloc(h, &A.gbar, 1));
+  al(dalloc(h, &A.rb_sum, (size_t)kRebuildMaxBlocks));
   // order keys: (system, Morton code of the cell) packed into at most 2^20 keys
   {
     int maxnc = 1;
@@ -905,6 +937,7 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
   if (e == cudaSuccess) e = cudaMemset(A.count, 0, sizeof(uint32_t) * std::max<size_t>(A.nbucket, 1));
   if (e == cudaSuccess) e = cudaMemset(A.tile_state, 0, sizeof(unsigned long long) * (size_t)nblk);
   if (e == cudaSuccess) e = cudaMemset(A.scan, 0, sizeof(ScanCtl));
+  if (e == cudaSuccess) e = cudaMemset(A.gbar, 0, sizeof(GridBar));
   if (e == cudaSuccess) e = cudaMemset(h->O.count, 0, sizeof(uint32_t) * h->O.nbucket);
   if (e == cudaSuccess)
     e = cudaMemset(h->O.tile_state, 0,
@@ -1229,6 +1262,15 @@ int md_set_option(md_handle* h, int32_t key, int64_t value) {
       if (value < 1 || value > 100000) return fail(h, MD_ERR_INVALID_ARG, "steps per launch must be in 1..100000");
       h->res_steps_per_launch = value;
       break;
+    case MD_OPT_PAIR_QUEUE:
+      if (value != 0 && value != 1) return fail(h, MD_ERR_INVALID_ARG, "pair queue must be 0 or 1");
+      h->A.pair_queue = (int32_t)value;
+      break;
+    case MD_OPT_FUSED_REBUILD:
+      if (value != 0 && value != 1) return fail(h, MD_ERR_INVALID_ARG, "fused rebuild must be 0 or 1");
+      h->fused_rebuild = (int)value;
+      h->rebuild_ctas = 0;
+      break;
     case MD_OPT_SPIN_LIMIT:
       if (value < 0 || value > 0x7fffffff) return fail(h, MD_ERR_INVALID_ARG, "spin limit must be in 0..2^31-1");
       h->A.spin_limit = (uint32_t)value;
@@ -1260,6 +1302,8 @@ int md_get_option(md_handle* h, int32_t key, int64_t* value) {
     case MD_OPT_RESIDENT_STEPS: *value = h->res_steps_per_launch; return MD_OK;
     case MD_OPT_PAIR_TILE: *value = h->A.pair_tile; return MD_OK;
     case MD_OPT_SPIN_LIMIT: *value = h->A.spin_limit; return MD_OK;
+    case MD_OPT_PAIR_QUEUE: *value = h->A.pair_queue; return MD_OK;
+    case MD_OPT_FUSED_REBUILD: *value = h->fused_rebuild; return MD_OK;
     case MD_OPT_NLIST_BUILDS: {
       unsigned long long b = 0;
       if (h->A.nl_builds) {

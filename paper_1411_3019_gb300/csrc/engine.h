@@ -42,6 +42,11 @@ cudaError_t launch_scatter(const DevArrays& A, cudaStream_t st);
 // Conservative forces at the current positions into A.f.
 // Neighbour-list build (only when *A.nl_dirty; every pair within r_c + skin).
 cudaError_t launch_nl_build(const DevArrays& A, int precision, int excl, cudaStream_t st);
+// Fused rebuild of the Verlet-list step (cooperative launch of `blocks` CTAs of
+// 256 threads; rebuild_blocks gives the count, 0 if it cannot be launched):
+// returns at once unless the rebuild flag is up, advances the step counter.
+int rebuild_blocks(int precision, int excl, int64_t n);
+cudaError_t launch_rebuild(const DevArrays& A, int precision, int excl, int blocks, cudaStream_t st);
 cudaError_t launch_pair(const DevArrays& A, int precision, int has_pairs, int bonds, int walls,
                         int excl, cudaStream_t st);
 

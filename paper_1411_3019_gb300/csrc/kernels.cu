@@ -459,17 +459,21 @@ __global__ void k_restore(DevArrays A, const double* __restrict__ xa, const doub
 // cell list
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void k_bin(DevArrays A) {
-  if (A.nl_dirty && *A.nl_dirty == 0u) return;  // neighbour-list mode, no rebuild this step
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void bin_one(const DevArrays& A, int64_t i) {
   const int64_t n = A.n;
-  if (i >= n) return;
   const SysDev& S = A.sys[meta_sys(A.meta[i])];
   bool out = false;
   const uint32_t cell = cell_of<R>(S, A.x[i], A.x[n + i], A.x[2 * n + i], out);
   if (out) flag(A.status, kFlagOutOfGrid);
   A.cell[i] = cell;
   A.rank[i] = atomicAdd(&A.count[bucket_of(cell, A.hashed, A.log_t)], 1u);
+}
+
+template <typename R>
+__global__ void k_bin(DevArrays A) {
+  if (A.nl_dirty && *A.nl_dirty == 0u) return;  // neighbour-list mode, no rebuild this step
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < A.n) bin_one<R>(A, i);
 }
 
 constexpr int kScanThreads = 512;
@@ -643,12 +647,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_onepass(DevArrays A, int 
   }
 }
 
+__device__ __forceinline__ void scatter_one(const DevArrays& A, int64_t i) {
+  const uint32_t b = bucket_of(A.cell[i], A.hashed, A.log_t);
+  A.stag_tmp[A.start[b] + A.rank[i]] = (uint32_t)i;
+}
+
 __global__ void k_scatter(DevArrays A) {
   if (A.nl_dirty && *A.nl_dirty == 0u) return;  // neighbour-list mode, no rebuild this step
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.n) return;
-  const uint32_t b = bucket_of(A.cell[i], A.hashed, A.log_t);
-  A.stag_tmp[A.start[b] + A.rank[i]] = (uint32_t)i;
+  if (i < A.n) scatter_one(A, i);
 }
 
 // Record of slot s. Mixed path: the offset rounded to float32 (the high
@@ -694,11 +701,8 @@ __device__ __forceinline__ void cell_offsets(const SysDev& S, uint32_t cell, dou
 // The thread writes the slot's particle id, cell id and its offset from the
 // cell centre (formed in float64, stored in R).
 template <typename R>
-__global__ void k_bucket_build(DevArrays A) {
-  if (A.nl_dirty && *A.nl_dirty == 0u) return;  // neighbour-list mode, no rebuild this step
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void bucket_build_one(const DevArrays& A, int64_t s) {
   const int64_t n = A.n;
-  if (s >= n) return;
   const uint32_t tag = A.stag_tmp[s];
   const uint32_t cell = A.cell[tag];
   const uint32_t b = bucket_of(cell, A.hashed, A.log_t);
@@ -716,6 +720,13 @@ __global__ void k_bucket_build(DevArrays A) {
   A.scell[d] = cell;
   if (A.slot_of) A.slot_of[tag] = d;
   put_rec<R>(A.rec, A.rec_lo, d, o[0], o[1], o[2], meta_type(m) | ((A.rec_cell ? cell : mol) << 3));
+}
+
+template <typename R>
+__global__ void k_bucket_build(DevArrays A) {
+  if (A.nl_dirty && *A.nl_dirty == 0u) return;  // neighbour-list mode, no rebuild this step
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < A.n) bucket_build_one<R>(A, s);
 }
 
 // float64 reciprocal and inverse square root without the long divide/sqrt
@@ -937,22 +948,29 @@ __device__ __forceinline__ DF pair_disp(float a, float b, float sh, float dl) {
   return {s2.h, __fadd_rn(__fadd_rn(s1.l, s2.l), dl)};
 }
 
-__device__ __forceinline__ void lj_term_acc(const PairTab<float>& tab, uint32_t qt, const float4& ri,
-                                            const float4& li, const float4& rj, const float4& lj, float shx,
-                                            float shy, float shz, float& fx, float& fy, float& fz, float& u) {
-  const DF dx = pair_disp(ri.x, rj.x, shx, __fsub_rn(li.x, lj.x));
-  const DF dy = pair_disp(ri.y, rj.y, shy, __fsub_rn(li.y, lj.y));
-  const DF dz = pair_disp(ri.z, rj.z, shz, __fsub_rn(li.z, lj.z));
-  const DF px = df_two_prod(dx.h, dx.h), py = df_two_prod(dy.h, dy.h), pz = df_two_prod(dz.h, dz.h);
+// One accurate pair term: the factor fr = f(r)/r, the displacement d and the
+// pair energy v; false when r >= r_c.
+struct AccTerm {
+  float fr, v;
+  DF dx, dy, dz;
+};
+
+__device__ __forceinline__ bool acc_pair(const PairTab<float>& tab, uint32_t qt, const float4& ri, const float4& li,
+                                         const float4& rj, const float4& lj, float shx, float shy, float shz,
+                                         AccTerm& t) {
+  t.dx = pair_disp(ri.x, rj.x, shx, __fsub_rn(li.x, lj.x));
+  t.dy = pair_disp(ri.y, rj.y, shy, __fsub_rn(li.y, lj.y));
+  t.dz = pair_disp(ri.z, rj.z, shz, __fsub_rn(li.z, lj.z));
+  const DF px = df_two_prod(t.dx.h, t.dx.h), py = df_two_prod(t.dy.h, t.dy.h), pz = df_two_prod(t.dz.h, t.dz.h);
   const DF s1 = df_two_sum(px.h, py.h);
   const DF s2 = df_two_sum(s1.h, pz.h);
   float lo = __fadd_rn(__fadd_rn(__fadd_rn(px.l, py.l), pz.l), __fadd_rn(s1.l, s2.l));
-  lo = __fmaf_rn(2.f * dx.h, dx.l, lo);
-  lo = __fmaf_rn(2.f * dy.h, dy.l, lo);
-  lo = __fmaf_rn(2.f * dz.h, dz.l, lo);
+  lo = __fmaf_rn(2.f * t.dx.h, t.dx.l, lo);
+  lo = __fmaf_rn(2.f * t.dy.h, t.dy.l, lo);
+  lo = __fmaf_rn(2.f * t.dz.h, t.dz.l, lo);
   const DF r2 = df_fast_sum(s2.h, lo);
   const DF rc2 = tab.acc.rc2[qt];
-  if (!(__fadd_rn(__fsub_rn(r2.h, rc2.h), __fsub_rn(r2.l, rc2.l)) < 0.f)) return;  // r >= r_c
+  if (!(__fadd_rn(__fsub_rn(r2.h, rc2.h), __fsub_rn(r2.l, rc2.l)) < 0.f)) return false;  // r >= r_c
   const float iR0 = __frcp_rn(r2.h);
   const float iR = __fmaf_rn(-__fmul_rn(r2.l, iR0), iR0, iR0);  // 1 / r^2
   DF r4 = df_two_prod(r2.h, r2.h);
@@ -963,19 +981,32 @@ __device__ __forceinline__ void lj_term_acc(const PairTab<float>& tab, uint32_t 
   const float num = __fadd_rn(__fsub_rn(s.h, r6.h), __fsub_rn(s.l, r6.l));  // 2 sigma^6 - r^6
   const float iq0 = __frcp_rn(r6.h);
   const float iq = __fmaf_rn(-__fmul_rn(r6.l, iq0), iq0, iq0);  // 1 / r^6
-  float fr = tab.acc.c24[qt] * num * (iq * iq) * iR;
+  t.fr = tab.acc.c24[qt] * num * (iq * iq) * iR;
   const float s6 = tab.acc.s6[qt] * iq;
-  float v = tab.acc.c4[qt] * iq * (s6 - 1.f) - tab.shift[qt];
+  t.v = tab.acc.c4[qt] * iq * (s6 - 1.f) - tab.shift[qt];
   const float lin = tab.lin[qt];
   if (lin != 0.f) {
     const float ir = rsqrtf(r2.h);
-    fr += lin * ir;
-    v -= (r2.h * ir - tab.rc[qt]) * lin;
+    t.fr += lin * ir;
+    t.v -= (r2.h * ir - tab.rc[qt]) * lin;
   }
+  return true;
+}
+
+// f += fr d (low part first), u += v / 2
+__device__ __forceinline__ void acc_add(float fr, DF dx, DF dy, DF dz, float v, float& fx, float& fy, float& fz,
+                                        float& u) {
   fx = __fmaf_rn(fr, dx.h, __fmaf_rn(fr, dx.l, fx));
   fy = __fmaf_rn(fr, dy.h, __fmaf_rn(fr, dy.l, fy));
   fz = __fmaf_rn(fr, dz.h, __fmaf_rn(fr, dz.l, fz));
   u += 0.5f * v;
+}
+
+__device__ __forceinline__ void lj_term_acc(const PairTab<float>& tab, uint32_t qt, const float4& ri,
+                                            const float4& li, const float4& rj, const float4& lj, float shx,
+                                            float shy, float shz, float& fx, float& fy, float& fz, float& u) {
+  AccTerm t;
+  if (acc_pair(tab, qt, ri, li, rj, lj, shx, shy, shz, t)) acc_add(t.fr, t.dx, t.dy, t.dz, t.v, fx, fy, fz, u);
 }
 
 // One candidate pair: float64 path as lj_term; mixed path a float32 screen on
@@ -1000,6 +1031,26 @@ template <typename R> __device__ __forceinline__ float4 rec_lo_at(const float4* 
   if constexpr (sizeof(R) == 4) return lo[s];
   return make_float4(0.f, 0.f, 0.f, 0.f);
 }
+
+// pair_term with the candidate's low part already loaded (lj; unused on the
+// float64 path)
+template <typename R>
+__device__ __forceinline__ void pair_term_v(const PairTab<R>& tab, uint32_t qt, const typename RecT<R>::T& ri,
+                                            const float4& li, const typename RecT<R>::T& rj, const float4& lj,
+                                            R shx, R shy, R shz, R& fx, R& fy, R& fz, R& u) {
+  const R ddx = ri.x - rj.x - shx, ddy = ri.y - rj.y - shy, ddz = ri.z - rj.z - shz;
+  const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+  if constexpr (sizeof(R) == 4) {
+    if (r2 < tab.acc.rc2m[qt]) lj_term_acc(tab, qt, ri, li, rj, lj, shx, shy, shz, fx, fy, fz, u);
+  } else {
+    if (r2 < tab.rc2[qt]) lj_term<R>(tab, qt, r2, ddx, ddy, ddz, fx, fy, fz, u);
+  }
+}
+
+#ifndef SURFMD_NL_BATCH
+#define SURFMD_NL_BATCH 2
+#endif
+constexpr int kNlBatch = SURFMD_NL_BATCH;  // list entries whose loads are in flight together
 
 template <typename R> __device__ __forceinline__ void store_f(void* f, uint32_t i, R fx, R fy, R fz, R u);
 template <> __device__ __forceinline__ void store_f<float>(void* f, uint32_t i, float fx, float fy, float fz,
@@ -1416,15 +1467,8 @@ __global__ void __launch_bounds__(256) k_pair_row(DevArrays A) {
 // position is still within r_c + skin of any partner it had).
 // ---------------------------------------------------------------------------
 template <typename R, bool EXCL>
-__global__ void __launch_bounds__(256) k_nl_build(DevArrays A) {
-  __shared__ PairTab<R> tab;
-  if (*A.nl_dirty == 0u) return;  // uniform: nothing moved far enough
-  if (blockIdx.x == 0 && threadIdx.x == 0) *A.nl_builds += 1ull;
-  load_tab<R>(tab, A.types);
-  __syncthreads();
+__device__ __forceinline__ void nl_build_one(const DevArrays& A, const PairTab<R>& tab, uint32_t s) {
   using Rec = typename RecT<R>::T;
-  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= (uint32_t)A.n) return;
   const GlobalCells<R> C(A);
   const int64_t n = A.n;
   const uint32_t tag = C.tag(s);
@@ -1492,8 +1536,164 @@ __global__ void __launch_bounds__(256) k_nl_build(DevArrays A) {
   A.xb[2 * n + tag] = A.x[2 * n + tag];
 }
 
+template <typename R, bool EXCL>
+__global__ void __launch_bounds__(256) k_nl_build(DevArrays A) {
+  __shared__ PairTab<R> tab;
+  if (*A.nl_dirty == 0u) return;  // uniform: nothing moved far enough
+  if (blockIdx.x == 0 && threadIdx.x == 0) *A.nl_builds += 1ull;
+  load_tab<R>(tab, A.types);
+  __syncthreads();
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < (uint32_t)A.n) nl_build_one<R, EXCL>(A, tab, s);
+}
+
+// ---------------------------------------------------------------------------
+// Fused rebuild (Verlet-list step form): one cooperative launch per step that
+// returns at once unless a particle has moved skin / 2 since the last build;
+// then it runs the cell-list build (binning, exclusive scan of the bucket
+// counters, scatter, canonical order and records) and the list build, with a
+// grid barrier between phases, in place of five launches of which four would
+// exit at once. Every CTA of a cooperative launch is resident, so the barrier
+// cannot wait for a CTA that never runs; its wait is bounded all the same
+// (spin_limit polls; on running out the CTA latches the timeout flag and the
+// whole grid leaves, the host rebuilding the list before the next step).
+// Each phase's per-item work is the separate kernels' own (bin_one,
+// scatter_one, bucket_build_one, nl_build_one): the same list, bit for bit.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool grid_barrier(GridBar* b, uint32_t nblocks, uint32_t limit, uint32_t* status,
+                                             int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile uint32_t* gen = &b->gen;
+    const uint32_t g0 = *gen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&b->count, 1u) == nblocks - 1) {  // last to arrive: release the others
+      b->count = 0u;
+      __threadfence();
+      atomicAdd(&b->gen, 1u);
+    } else {
+      uint32_t polls = 0;
+      while (*gen == g0 && polls < limit) ++polls;
+      if (*gen == g0) {
+        ok = 0;
+        atomicOr(status, kFlagTimeout);
+      }
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+template <typename R, bool EXCL>
+__global__ void __launch_bounds__(256) k_rebuild(DevArrays A) {
+  __shared__ PairTab<R> tab;
+  __shared__ uint32_t warp_tot[33];
+  __shared__ int s_ok;
+  __shared__ uint32_t s_pre;
+  const uint32_t G = gridDim.x, tid = threadIdx.x, bd = blockDim.x;
+  const bool lead = blockIdx.x == 0 && tid == 0;
+  if (*A.nl_dirty == 0u) {  // uniform: nothing moved far enough; only the step advances
+    if (lead) {
+      *A.step += 1ull;
+      *A.mode = 1;
+    }
+    return;
+  }
+  load_tab<R>(tab, A.types);
+  const int64_t n = A.n;
+  const int64_t stride = (int64_t)G * bd;
+  const int64_t first = (int64_t)blockIdx.x * bd + tid;
+  const uint32_t T = A.nbucket, lim = A.spin_limit;
+  // 1. cell of every particle and its rank in the bucket counter
+  for (int64_t i = first; i < n; i += stride) bin_one<R>(A, i);
+  if (!grid_barrier(A.gbar, G, lim, A.status, &s_ok)) return;
+  // 2. exclusive scan of the counters: each CTA a contiguous range, its sum,
+  //    then (after the barrier) the sums of the CTAs before it as its prefix
+  const uint32_t chunk = (T + G - 1) / G;
+  const uint32_t b0 = min(blockIdx.x * chunk, T), b1 = min(b0 + chunk, T);
+  uint32_t part = 0;
+  for (uint32_t b = b0 + tid; b < b1; b += bd) part += A.count[b];
+  uint32_t total;
+  block_exclusive_scan(part, warp_tot, total);
+  if (tid == 0) A.rb_sum[blockIdx.x] = total;
+  if (!grid_barrier(A.gbar, G, lim, A.status, &s_ok)) return;
+  part = 0;
+  for (uint32_t j = tid; j < blockIdx.x; j += bd) part += A.rb_sum[j];
+  block_exclusive_scan(part, warp_tot, total);
+  if (tid == 0) s_pre = total;
+  __syncthreads();
+  uint32_t run = s_pre;
+  for (uint32_t base = b0; base < b1; base += bd) {  // bd counters at a time, in order
+    const uint32_t b = base + tid;
+    const uint32_t v = b < b1 ? A.count[b] : 0u;
+    const uint32_t ex = block_exclusive_scan(v, warp_tot, total);
+    if (b < b1) {
+      A.start[b] = run + ex;
+      A.count[b] = 0u;
+    }
+    run += total;
+    __syncthreads();  // every thread has read this round's totals before the next round writes them
+  }
+  if (!grid_barrier(A.gbar, G, lim, A.status, &s_ok)) return;
+  // 3. particles to their slots (atomic order), 4. canonical order and records
+  for (int64_t i = first; i < n; i += stride) scatter_one(A, i);
+  if (!grid_barrier(A.gbar, G, lim, A.status, &s_ok)) return;
+  for (int64_t s = first; s < n; s += stride) bucket_build_one<R>(A, s);
+  if (!grid_barrier(A.gbar, G, lim, A.status, &s_ok)) return;
+  // 5. the Verlet list of the new cell list
+  for (int64_t s = first; s < n; s += stride) nl_build_one<R, EXCL>(A, tab, (uint32_t)s);
+  if (lead) {
+    *A.nl_builds += 1ull;
+    *A.step += 1ull;
+    *A.mode = 1;
+  }
+}
+
+// CTAs of the fused rebuild: at most what is resident at once on the device
+// (a cooperative launch needs it), at most kRebuildMaxBlocks, no more than
+// the particles need.
+int rebuild_blocks(int precision, int excl, int64_t n) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))
+    return 0;
+  cudaError_t e;
+  if (precision == 0) {
+    e = excl ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rebuild<double, true>, 256, 0)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rebuild<double, false>, 256, 0);
+  } else {
+    e = excl ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rebuild<float, true>, 256, 0)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rebuild<float, false>, 256, 0);
+  }
+  if (e != cudaSuccess || per_sm < 1) return 0;
+  const int64_t want = std::max<int64_t>(1, (n + 255) / 256);
+  return (int)std::min<int64_t>({want, (int64_t)per_sm * sms, (int64_t)kRebuildMaxBlocks});
+}
+
+cudaError_t launch_rebuild(const DevArrays& A, int precision, int excl, int blocks, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (precision == 0) {
+    return excl ? cudaLaunchKernelEx(&cfg, k_rebuild<double, true>, A) : cudaLaunchKernelEx(&cfg, k_rebuild<double, false>, A);
+  }
+  return excl ? cudaLaunchKernelEx(&cfg, k_rebuild<float, true>, A) : cudaLaunchKernelEx(&cfg, k_rebuild<float, false>, A);
+}
+
+#ifndef SURFMD_PAIR_NL_MINB
+#define SURFMD_PAIR_NL_MINB 1
+#endif
+
 template <typename R, bool BONDS, bool WALLS>
-__global__ void __launch_bounds__(256) k_pair_nl(DevArrays A) {
+__global__ void __launch_bounds__(256, SURFMD_PAIR_NL_MINB) k_pair_nl(DevArrays A) {
   __shared__ PairTab<R> tab;
   load_tab<R>(tab, A.types);
   if (blockIdx.x == 0 && threadIdx.x == 0) *A.nl_dirty = 0u;  // the previous step's rebuild is done
@@ -1516,7 +1716,31 @@ __global__ void __launch_bounds__(256) k_pair_nl(DevArrays A) {
   const uint32_t cnt = A.nl_cnt[s];
   const uint32_t* __restrict__ nl = A.nl + s;
   R fx = 0, fy = 0, fz = 0, u = 0;
-  for (uint32_t k = 0; k < cnt; ++k) {
+  // batches of kNlBatch entries: the batch's entries, then its records (and,
+  // mixed, their low parts) are all loaded before any term is evaluated, so
+  // the gathers of a batch are in flight together; the terms are added in
+  // list order, as one entry at a time would add them
+  uint32_t k = 0;
+  for (; k + kNlBatch <= cnt; k += kNlBatch) {
+    uint32_t e[kNlBatch];
+    Rec rj[kNlBatch];
+    float4 lj[kNlBatch];
+#pragma unroll
+    for (int q = 0; q < kNlBatch; ++q) e[q] = nl[(int64_t)(k + q) * n];
+#pragma unroll
+    for (int q = 0; q < kNlBatch; ++q) {
+      rj[q] = rec[e[q] >> 5];
+      lj[q] = rec_lo_at<R>(lo, e[q] >> 5);
+    }
+#pragma unroll
+    for (int q = 0; q < kNlBatch; ++q) {
+      const uint32_t code = e[q] & 31u;
+      const int dz = (int)(code / 9u) - 1, dy = (int)(code / 3u % 3u) - 1, dx = (int)(code % 3u) - 1;
+      const uint32_t qt = ti * kMaxTypes + (RecT<R>::bits(rj[q]) & 7u);
+      pair_term_v<R>(tab, qt, ri, li, rj[q], lj[q], (R)dx * csx, (R)dy * csy, (R)dz * csz, fx, fy, fz, u);
+    }
+  }
+  for (; k < cnt; ++k) {
     const uint32_t e = nl[(int64_t)k * n];
     const uint32_t code = e & 31u;
     const Rec rj = rec[e >> 5];
@@ -1526,6 +1750,154 @@ __global__ void __launch_bounds__(256) k_pair_nl(DevArrays A) {
   }
   if (BONDS || WALLS) bonded_terms<R>(A, S, tag, m, BONDS, WALLS, fx, fy, fz, u);
   store_f<R>(A.f, tag, fx, fy, fz, u);
+}
+
+// Mixed path with the Verlet list: the warp's 32 particles (one per lane)
+// screen their list entries round by round (round r: every lane's entry r,
+// float32 screen on the records' high parts) and append the entries that pass
+// to a per-warp queue in shared memory (a ballot gives each its place: by
+// round, then lane). Whenever 32 are queued, all lanes evaluate one queued
+// pair each with the double-float arithmetic of lj_term_acc, so that
+// arithmetic runs on full warps instead of on the few lanes whose entry of a
+// round passed. The terms are then added to their particles round by round:
+// a particle has at most one entry per round, so each round's terms go to
+// distinct particles, and every particle adds its terms in list order, as
+// k_pair_nl does (the same bits).
+constexpr int kQueueWarps = 8;
+#ifndef SURFMD_QUEUE_ROUNDS
+#define SURFMD_QUEUE_ROUNDS 4
+#endif
+constexpr int kQueueRounds = SURFMD_QUEUE_ROUNDS;  // list rounds whose loads are in flight together
+
+struct QueueWarp {
+  float4 ri[32], li[32];          // the lanes' own records and low parts
+  float4 hit_a[32], hit_b[32];    // one round's terms by particle: (fr, dx.h, dy.h, dz.h), (dx.l, dy.l, dz.l, v)
+  float csx[32], csy[32], csz[32];  // the lanes' cell edges (their systems')
+  uint32_t e[64];                 // queued list entries (slot << 5 | stencil cell)
+  uint16_t r[64];                 // their rounds
+  uint8_t o[64];                  // their particles (lanes)
+  uint8_t flag[32];               // a term waits for particle (lane) in this round
+};
+
+template <bool BONDS, bool WALLS>
+__global__ void __launch_bounds__(kQueueWarps * 32) k_pair_nlq(DevArrays A) {
+  __shared__ PairTab<float> tab;
+  __shared__ QueueWarp qw_all[kQueueWarps];
+  load_tab<float>(tab, A.types);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *A.nl_dirty = 0u;  // the previous step's rebuild is done
+  const int lane = (int)(threadIdx.x & 31u);
+  QueueWarp& Q = qw_all[threadIdx.x >> 5];
+  Q.flag[lane] = 0;
+  __syncthreads();
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = s < (uint32_t)A.n;
+  const int64_t n = A.n;
+  const float4* __restrict__ rec = reinterpret_cast<const float4*>(A.rec);
+  const float4* __restrict__ lo = A.rec_lo;
+  uint32_t tag = 0, m = 0, cnt = 0, ti = 0;
+  float4 ri = make_float4(0.f, 0.f, 0.f, 0.f);
+  float csx = 0.f, csy = 0.f, csz = 0.f;
+  if (valid) {
+    tag = A.stag[s];
+    m = A.meta[tag];
+    const SysDev& S = A.sys[meta_sys(m)];
+    ri = rec[s];
+    Q.ri[lane] = ri;
+    Q.li[lane] = lo[s];
+    ti = RecT<float>::bits(ri) & 7u;
+    csx = S.cs_f[0]; csy = S.cs_f[1]; csz = S.cs_f[2];
+    cnt = A.nl_cnt[s];
+  }
+  Q.csx[lane] = csx; Q.csy[lane] = csy; Q.csz[lane] = csz;
+  const uint32_t rounds = __reduce_max_sync(0xffffffffu, cnt);
+  const uint32_t* __restrict__ nl = A.nl + s;
+  float fx = 0.f, fy = 0.f, fz = 0.f, u = 0.f;
+  uint32_t qn = 0;  // queued entries (warp-uniform)
+  // evaluate the first k queued entries (k <= 32) and add their terms
+  auto drain = [&](uint32_t k) {
+    __syncwarp();
+    const bool have = (uint32_t)lane < k;
+    AccTerm t;
+    bool in = false;
+    uint32_t rr = 0, own = 0;
+    if (have) {
+      const uint32_t e = Q.e[lane];
+      rr = Q.r[lane];
+      own = Q.o[lane];
+      const float4 ro = Q.ri[own], lio = Q.li[own];
+      const uint32_t j = e >> 5, code = e & 31u;
+      const float4 rj = rec[j];
+      const float4 lj = lo[j];
+      const int dz = (int)(code / 9u) - 1, dy = (int)(code / 3u % 3u) - 1, dx = (int)(code % 3u) - 1;
+      const uint32_t qt = (RecT<float>::bits(ro) & 7u) * kMaxTypes + (RecT<float>::bits(rj) & 7u);
+      in = acc_pair(tab, qt, ro, lio, rj, lj, (float)dx * Q.csx[own], (float)dy * Q.csy[own],
+                    (float)dz * Q.csz[own], t);
+    }
+    const uint32_t r0 = Q.r[0], r1 = Q.r[k - 1];  // the queue is in round order
+    for (uint32_t q = r0; q <= r1; ++q) {
+      if (have && in && rr == q) {
+        Q.hit_a[own] = make_float4(t.fr, t.dx.h, t.dy.h, t.dz.h);
+        Q.hit_b[own] = make_float4(t.dx.l, t.dy.l, t.dz.l, t.v);
+        Q.flag[own] = 1;
+      }
+      __syncwarp();
+      if (Q.flag[lane]) {
+        const float4 a = Q.hit_a[lane], b = Q.hit_b[lane];
+        acc_add(a.x, DF{a.y, b.x}, DF{a.z, b.y}, DF{a.w, b.z}, b.w, fx, fy, fz, u);
+        Q.flag[lane] = 0;
+      }
+      __syncwarp();
+    }
+  };
+  // kQueueRounds rounds at a time: their entries, then their records, are
+  // loaded together (independent loads in flight), then screened and queued
+  // round by round
+  for (uint32_t r0 = 0; r0 < rounds; r0 += kQueueRounds) {
+    uint32_t e[kQueueRounds];
+    float4 rj[kQueueRounds];
+#pragma unroll
+    for (int q = 0; q < kQueueRounds; ++q) e[q] = r0 + q < cnt ? nl[(int64_t)(r0 + q) * n] : 0u;
+#pragma unroll
+    for (int q = 0; q < kQueueRounds; ++q)
+      if (r0 + q < cnt) rj[q] = rec[e[q] >> 5];
+#pragma unroll
+    for (int q = 0; q < kQueueRounds; ++q) {
+      const uint32_t r = r0 + q;
+      if (r >= rounds) break;  // warp-uniform
+      bool hit = false;
+      if (r < cnt) {
+        const uint32_t code = e[q] & 31u;
+        const int dz = (int)(code / 9u) - 1, dy = (int)(code / 3u % 3u) - 1, dx = (int)(code % 3u) - 1;
+        const float ddx = ri.x - rj[q].x - (float)dx * csx, ddy = ri.y - rj[q].y - (float)dy * csy,
+                    ddz = ri.z - rj[q].z - (float)dz * csz;
+        const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+        hit = r2 < tab.acc.rc2m[ti * kMaxTypes + (RecT<float>::bits(rj[q]) & 7u)];
+      }
+      const uint32_t mask = __ballot_sync(0xffffffffu, hit);
+      if (hit) {
+        const uint32_t pos = qn + __popc(mask & ((1u << lane) - 1u));
+        Q.e[pos] = e[q];
+        Q.r[pos] = (uint16_t)r;
+        Q.o[pos] = (uint8_t)lane;
+      }
+      qn += __popc(mask);
+      if (qn >= 32) {
+        drain(32);
+        // move the rest (qn - 32 < 32 entries) to the front
+        uint32_t e2 = 0, o2 = 0, rr2 = 0;
+        const bool mv = (uint32_t)lane < qn - 32;
+        if (mv) { e2 = Q.e[32 + lane]; rr2 = Q.r[32 + lane]; o2 = Q.o[32 + lane]; }
+        __syncwarp();
+        if (mv) { Q.e[lane] = e2; Q.r[lane] = (uint16_t)rr2; Q.o[lane] = (uint8_t)o2; }
+        __syncwarp();
+        qn -= 32;
+      }
+    }
+  }
+  if (qn) drain(qn);
+  if (!valid) return;
+  if (BONDS || WALLS) bonded_terms<float>(A, A.sys[meta_sys(m)], tag, m, BONDS, WALLS, fx, fy, fz, u);
+  store_f<float>(A.f, tag, fx, fy, fz, u);
 }
 
 // Bend-angle forces (and energy shares) added to the pair kernel's output.
@@ -3191,6 +3563,18 @@ static void pair_dispatch(const DevArrays& A, int bonds, int walls, int excl, in
 template <typename R>
 static void pair_dispatch_nl(const DevArrays& A, int bonds, int walls, cudaStream_t st) {
   const unsigned g = grid_for(A.n, 256);
+  if constexpr (sizeof(R) == 4) {
+    if (A.pair_queue) {
+      const unsigned gq = grid_for(A.n, kQueueWarps * 32);
+      switch ((bonds ? 2 : 0) | (walls ? 1 : 0)) {
+        case 0: k_pair_nlq<false, false><<<gq, kQueueWarps * 32, 0, st>>>(A); break;
+        case 1: k_pair_nlq<false, true><<<gq, kQueueWarps * 32, 0, st>>>(A); break;
+        case 2: k_pair_nlq<true, false><<<gq, kQueueWarps * 32, 0, st>>>(A); break;
+        default: k_pair_nlq<true, true><<<gq, kQueueWarps * 32, 0, st>>>(A); break;
+      }
+      return;
+    }
+  }
   switch ((bonds ? 2 : 0) | (walls ? 1 : 0)) {
     case 0: k_pair_nl<R, false, false><<<g, 256, 0, st>>>(A); break;
     case 1: k_pair_nl<R, false, true><<<g, 256, 0, st>>>(A); break;

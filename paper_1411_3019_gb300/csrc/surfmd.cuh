@@ -137,6 +137,14 @@ struct ResidentJob {
   uint32_t nmax, tmax;
 };
 
+// Grid barrier of the fused rebuild kernel (zero at creation): arrivals and
+// the generation the waiting CTAs watch.
+struct GridBar {
+  uint32_t count;
+  uint32_t gen;
+};
+constexpr int kRebuildMaxBlocks = 4096;  // CTAs of the fused rebuild kernel at most
+
 struct ScanCtl {
   uint32_t tile;   // next tile index
   uint32_t done;   // tiles finished in this launch
@@ -153,6 +161,7 @@ struct DevArrays {
   int32_t log_t;
   int32_t pair_lanes;   // lanes per particle in the pair kernel (1, 2, 4 or 8)
   int32_t pair_tile;    // 0, or particles per warp (8, 16, 32) of the cell-tiled pair kernel (needs hashed == 0)
+  int32_t pair_queue;   // mixed path with the Verlet list: 1 = warp-queued list walk (k_pair_nlq), 0 = per-lane walk
   // Verlet neighbour list (nl_dirty == null: off). Built from the cell list
   // with every pair within r_c + skin; between builds the integrator moves
   // the records in place and raises *nl_dirty when a particle has moved more
@@ -193,6 +202,8 @@ struct DevArrays {
   float4* rec0_lo;      // [n] mixed path with the neighbour list: rec_lo at the last build
   int32_t ntypes;       // particle types in use (a type must lie in [0, ntypes))
   uint32_t spin_limit;  // reads of a predecessor's scan word before the wait gives up
+  GridBar* gbar;        // fused rebuild: grid barrier
+  uint32_t* rb_sum;     // fused rebuild: [kRebuildMaxBlocks] bucket-counter sums of the CTAs' ranges
   const SysDev* sys;    // [nsys]
   const TypeTable* types;  // pair and mass tables shared by the systems
   int32_t* sys_free;    // [nsys] unconstrained particles per system (set with the state)

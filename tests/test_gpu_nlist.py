@@ -119,8 +119,9 @@ def test_switch_off_mid_run_and_repeat_bit_for_bit():
 
 def test_rebuild_counts():
     """The list is rebuilt only in steps where a particle has moved skin / 2:
-    many rebuilds with a tiny skin, none in a few steps with a large one; the
-    seven kernels of a step are launched every step."""
+    many rebuilds with a tiny skin, none in a few steps with a large one; a
+    step is three launches (pair, integrate, the fused rebuild that returns
+    at once without a rebuild), or seven with the separate rebuild kernels."""
     counts = {}
     for skin, steps in ((0.02, 40), (0.6, 5)):
         systems = _cells(I.c4_replicas(nrep=2, seed=9, nmin=300, nmax=500, rmin=6.0, rmax=9.0,
@@ -130,7 +131,9 @@ def test_rebuild_counts():
         sim.set_state()
         b0 = md.md_get_option(sim.h, md.MD_OPT_NLIST_BUILDS)
         sim.step(steps)
-        assert md.md_last_launch_count(sim.h) == 7 * steps
+        fused = md.md_get_option(sim.h, md.MD_OPT_FUSED_REBUILD)
+        assert fused == 1  # the cooperative launch is available on this GPU
+        assert md.md_last_launch_count(sim.h) == 3 * steps
         counts[skin] = md.md_get_option(sim.h, md.MD_OPT_NLIST_BUILDS) - b0
         sim.close()
     assert counts[0.02] >= 5 and counts[0.6] == 0, counts
@@ -178,3 +181,60 @@ def test_forces_after_set_state_and_resume_from_checkpoint(precision):
         assert np.array_equal(xa[key], xc[key]), key
     assert np.array_equal(fa, fc)
     assert_forces(systems, xc["x"], fc, precision)
+
+
+@pytest.mark.parametrize("workload", ["ellipsoid_torus", "bead_molecules"])
+def test_queued_list_walk_gives_the_same_bits(workload):
+    """The warp-queued list walk (default) and the per-lane walk add each
+    particle's terms in list order with the same arithmetic: forces and a
+    trajectory across rebuilds agree bit for bit."""
+    skin = 0.4
+    if workload == "ellipsoid_torus":
+        systems = _cells(I.c2_ellipsoid_torus(n_ell=4000, n_tor=1500, seed=8, precision="mixed"), skin)
+    else:
+        systems = _cells(I.c5_bead_molecules(nmol=400, beads=5, R=12.0, seed=6, precision="mixed"), skin)
+    out = {}
+    for queue in (1, 0):
+        with md.Simulation(systems) as sim:
+            md.md_set_option(sim.h, md.MD_OPT_PAIR_QUEUE, queue)
+            assert md.md_get_option(sim.h, md.MD_OPT_PAIR_QUEUE) == queue
+            md.md_set_neighbor_list(sim.h, skin, 128)
+            sim.set_state()
+            f0, u0 = sim.forces()
+            sim.step(40)
+            sim.sync()
+            out[queue] = (f0, u0, sim.state(), md.md_get_option(sim.h, md.MD_OPT_NLIST_BUILDS))
+    assert out[1][3] > 1  # rebuilds inside the run
+    assert np.array_equal(out[1][0], out[0][0]) and np.array_equal(out[1][1], out[0][1])
+    for key in ("x", "p_half"):
+        assert np.array_equal(out[1][2][key], out[0][2][key]), key
+
+
+@pytest.mark.parametrize("workload", ["ellipsoid_torus", "bead_molecules"])
+def test_fused_rebuild_gives_the_same_bits(workload):
+    """The fused rebuild (one cooperative launch with grid barriers) and the
+    five separate rebuild kernels build the same cell list and Verlet list:
+    trajectories across many rebuilds agree bit for bit, and so do the build
+    counts; the separate form launches seven kernels per step."""
+    skin = 0.1
+    if workload == "ellipsoid_torus":
+        systems = _cells(I.c2_ellipsoid_torus(n_ell=4000, n_tor=1500, seed=8, precision="mixed"), skin)
+    else:
+        systems = _cells(I.c5_bead_molecules(nmol=400, beads=5, R=12.0, seed=6, precision="mixed"), skin)
+    out = {}
+    for fused in (1, 0):
+        with md.Simulation(systems) as sim:
+            md.md_set_option(sim.h, md.MD_OPT_FUSED_REBUILD, fused)
+            md.md_set_neighbor_list(sim.h, skin, 128)
+            sim.set_state()
+            b0 = md.md_get_option(sim.h, md.MD_OPT_NLIST_BUILDS)
+            sim.step(60)
+            launches = md.md_last_launch_count(sim.h)
+            sim.sync()
+            out[fused] = (sim.state(), sim.forces()[0], md.md_get_option(sim.h, md.MD_OPT_NLIST_BUILDS) - b0)
+            assert md.md_get_option(sim.h, md.MD_OPT_FUSED_REBUILD) == fused
+            assert launches == (3 if fused else 7) * 60
+    assert out[1][2] == out[0][2] > 5
+    assert np.array_equal(out[1][1], out[0][1])
+    for key in ("x", "p_half"):
+        assert np.array_equal(out[1][0][key], out[0][0][key]), key
