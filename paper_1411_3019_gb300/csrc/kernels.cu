@@ -1529,8 +1529,8 @@ __device__ __forceinline__ void nl_build_one(const DevArrays& A, const PairTab<R
   }
   if (cnt > cap) flag(A.status, kFlagNlistFull);
   A.nl_cnt[s] = min(cnt, cap);
-  reinterpret_cast<Rec*>(A.rec0)[s] = ri;
-  if (sizeof(R) == 4) A.rec0_lo[s] = A.rec_lo[s];
+  reinterpret_cast<Rec*>(A.rec0)[tag] = ri;  // by particle: the integrator reads it in particle order
+  if (sizeof(R) == 4) A.rec0_lo[tag] = A.rec_lo[s];
   A.xb[tag] = A.x[tag];
   A.xb[n + tag] = A.x[n + tag];
   A.xb[2 * n + tag] = A.x[2 * n + tag];
@@ -2506,10 +2506,10 @@ template <typename R> struct NlSink {
   __device__ __forceinline__ void pos(int64_t i, double xn, double yn, double zn) const {
     const uint32_t s = slot_of[i];
     const double dx = xn - xb[i], dy = yn - xb[n + i], dz = zn - xb[2 * n + i];
-    Rec r = rec0[s];
+    Rec r = rec0[i];
     float d2;
     if constexpr (sizeof(R) == 4) {
-      const float4 l = rec0_lo[s];
+      const float4 l = rec0_lo[i];
       const DF ex = df_from(dx), ey = df_from(dy), ez = df_from(dz);
       const DF ox = df_add(DF{r.x, l.x}, ex), oy = df_add(DF{r.y, l.y}, ey), oz = df_add(DF{r.z, l.z}, ez);
       r.x = ox.h; r.y = oy.h; r.z = oz.h;

@@ -169,7 +169,7 @@ struct DevArrays {
   uint32_t* nl_dirty;   // device flag: 1 = rebuild the cell list and the neighbour list
   uint32_t* nl;         // [nl_max][n] neighbour entries by sorted slot: slot << 5 | stencil cell (0..26)
   uint32_t* nl_cnt;     // [n] entries per sorted slot
-  void* rec0;           // [n] records at the last build
+  void* rec0;           // [n] records at the last build, by particle
   double* xb;           // [3][n] positions at the last build (user order)
   unsigned long long* nl_builds;  // list builds so far (counter)
   int32_t nl_max;
@@ -199,7 +199,7 @@ struct DevArrays {
   uint32_t* scell;      // [n] sorted slot -> cell id
   void* rec;            // [n] float4 / double4_32a cell-relative offsets + type/mol bits
   float4* rec_lo;       // [n] mixed path: offset - record (the low parts; w unused), else null
-  float4* rec0_lo;      // [n] mixed path with the neighbour list: rec_lo at the last build
+  float4* rec0_lo;      // [n] mixed path with the neighbour list: rec_lo at the last build, by particle
   int32_t ntypes;       // particle types in use (a type must lie in [0, ntypes))
   uint32_t spin_limit;  // reads of a predecessor's scan word before the wait gives up
   GridBar* gbar;        // fused rebuild: grid barrier
