@@ -1520,7 +1520,7 @@ __device__ __forceinline__ void nl_build_one(const DevArrays& A, const PairTab<R
           const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
           const R rs = tab.rc[qt] + skin;
           if (r2 < rs * rs) {
-            if (cnt < cap) A.nl[(int64_t)cnt * n + s] = t << 5 | code;
+            if (cnt < cap) A.nl[(int64_t)s * cap + cnt] = t << 5 | code;
             ++cnt;
           }
         }
@@ -1714,7 +1714,7 @@ __global__ void __launch_bounds__(256, SURFMD_PAIR_NL_MINB) k_pair_nl(DevArrays 
   const R csy = sizeof(R) == 4 ? (R)S.cs_f[1] : (R)S.cs[1];
   const R csz = sizeof(R) == 4 ? (R)S.cs_f[2] : (R)S.cs[2];
   const uint32_t cnt = A.nl_cnt[s];
-  const uint32_t* __restrict__ nl = A.nl + s;
+  const uint32_t* __restrict__ nl = A.nl + (int64_t)s * A.nl_max;
   R fx = 0, fy = 0, fz = 0, u = 0;
   // batches of kNlBatch entries: the batch's entries, then its records (and,
   // mixed, their low parts) are all loaded before any term is evaluated, so
@@ -1726,7 +1726,7 @@ __global__ void __launch_bounds__(256, SURFMD_PAIR_NL_MINB) k_pair_nl(DevArrays 
     Rec rj[kNlBatch];
     float4 lj[kNlBatch];
 #pragma unroll
-    for (int q = 0; q < kNlBatch; ++q) e[q] = nl[(int64_t)(k + q) * n];
+    for (int q = 0; q < kNlBatch; ++q) e[q] = nl[k + q];
 #pragma unroll
     for (int q = 0; q < kNlBatch; ++q) {
       rj[q] = rec[e[q] >> 5];
@@ -1741,7 +1741,7 @@ __global__ void __launch_bounds__(256, SURFMD_PAIR_NL_MINB) k_pair_nl(DevArrays 
     }
   }
   for (; k < cnt; ++k) {
-    const uint32_t e = nl[(int64_t)k * n];
+    const uint32_t e = nl[k];
     const uint32_t code = e & 31u;
     const Rec rj = rec[e >> 5];
     const int dz = (int)(code / 9u) - 1, dy = (int)(code / 3u % 3u) - 1, dx = (int)(code % 3u) - 1;
@@ -1752,31 +1752,29 @@ __global__ void __launch_bounds__(256, SURFMD_PAIR_NL_MINB) k_pair_nl(DevArrays 
   store_f<R>(A.f, tag, fx, fy, fz, u);
 }
 
-// Mixed path with the Verlet list: the warp's 32 particles (one per lane)
-// screen their list entries round by round (round r: every lane's entry r,
-// float32 screen on the records' high parts) and append the entries that pass
-// to a per-warp queue in shared memory (a ballot gives each its place: by
-// round, then lane). Whenever 32 are queued, all lanes evaluate one queued
-// pair each with the double-float arithmetic of lj_term_acc, so that
-// arithmetic runs on full warps instead of on the few lanes whose entry of a
-// round passed. The terms are then added to their particles round by round:
-// a particle has at most one entry per round, so each round's terms go to
-// distinct particles, and every particle adds its terms in list order, as
-// k_pair_nl does (the same bits).
+// Mixed path with the Verlet list, one warp per 32 consecutive slots. The
+// warp walks its particles' list entries as one flat sequence (particle by
+// particle, each particle's entries in list order; its list is contiguous, so
+// 32 consecutive positions are a few contiguous runs): lane q takes position
+// c + q, finds its particle by a binary search over the warp's prefix sums
+// of the list lengths, and screens the pair in float32 on the records' high
+// parts. The pairs that pass are queued in shared memory in the same flat
+// order (a ballot gives each its place), and every 32 of them are evaluated
+// on all lanes with the double-float arithmetic of lj_term_acc. A particle's
+// queued pairs are consecutive, so after each evaluation the particle's lane
+// adds its run of terms in order: every particle adds its terms in list
+// order with the same arithmetic as k_pair_nl (the same bits), while no lane
+// idles on a short list or on a pair that fails the screen.
 constexpr int kQueueWarps = 8;
-#ifndef SURFMD_QUEUE_ROUNDS
-#define SURFMD_QUEUE_ROUNDS 4
-#endif
-constexpr int kQueueRounds = SURFMD_QUEUE_ROUNDS;  // list rounds whose loads are in flight together
 
 struct QueueWarp {
   float4 ri[32], li[32];          // the lanes' own records and low parts
-  float4 hit_a[32], hit_b[32];    // one round's terms by particle: (fr, dx.h, dy.h, dz.h), (dx.l, dy.l, dz.l, v)
+  float4 ta[32], tb[32];          // evaluated terms: (fr, dx.h, dy.h, dz.h), (dx.l, dy.l, dz.l, v)
   float csx[32], csy[32], csz[32];  // the lanes' cell edges (their systems')
   uint32_t e[64];                 // queued list entries (slot << 5 | stencil cell)
-  uint16_t r[64];                 // their rounds
   uint8_t o[64];                  // their particles (lanes)
-  uint8_t flag[32];               // a term waits for particle (lane) in this round
+  uint8_t in[32];                 // evaluated term is inside the cutoff
+  uint8_t run0[32], runn[32];     // per particle: first queue position and length of its run
 };
 
 template <bool BONDS, bool WALLS>
@@ -1787,42 +1785,45 @@ __global__ void __launch_bounds__(kQueueWarps * 32) k_pair_nlq(DevArrays A) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *A.nl_dirty = 0u;  // the previous step's rebuild is done
   const int lane = (int)(threadIdx.x & 31u);
   QueueWarp& Q = qw_all[threadIdx.x >> 5];
-  Q.flag[lane] = 0;
   __syncthreads();
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t s0 = s - (uint32_t)lane;  // the warp's first slot
   const bool valid = s < (uint32_t)A.n;
-  const int64_t n = A.n;
   const float4* __restrict__ rec = reinterpret_cast<const float4*>(A.rec);
   const float4* __restrict__ lo = A.rec_lo;
-  uint32_t tag = 0, m = 0, cnt = 0, ti = 0;
-  float4 ri = make_float4(0.f, 0.f, 0.f, 0.f);
+  const uint32_t* __restrict__ nl = A.nl;
+  const uint32_t cap = (uint32_t)A.nl_max;
+  uint32_t tag = 0, m = 0, cnt = 0;
   float csx = 0.f, csy = 0.f, csz = 0.f;
   if (valid) {
     tag = A.stag[s];
     m = A.meta[tag];
     const SysDev& S = A.sys[meta_sys(m)];
-    ri = rec[s];
-    Q.ri[lane] = ri;
+    Q.ri[lane] = rec[s];
     Q.li[lane] = lo[s];
-    ti = RecT<float>::bits(ri) & 7u;
     csx = S.cs_f[0]; csy = S.cs_f[1]; csz = S.cs_f[2];
     cnt = A.nl_cnt[s];
   }
   Q.csx[lane] = csx; Q.csy[lane] = csy; Q.csz[lane] = csz;
-  const uint32_t rounds = __reduce_max_sync(0xffffffffu, cnt);
-  const uint32_t* __restrict__ nl = A.nl + s;
+  // prefix sums of the list lengths over the warp
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const uint32_t pre = incl - cnt;
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
   float fx = 0.f, fy = 0.f, fz = 0.f, u = 0.f;
-  uint32_t qn = 0;  // queued entries (warp-uniform)
-  // evaluate the first k queued entries (k <= 32) and add their terms
+  uint32_t qn = 0;  // queued pairs (warp-uniform)
+  // evaluate the first k queued pairs (k <= 32); each particle adds its run in order
   auto drain = [&](uint32_t k) {
     __syncwarp();
     const bool have = (uint32_t)lane < k;
-    AccTerm t;
+    uint32_t own = 0;
     bool in = false;
-    uint32_t rr = 0, own = 0;
     if (have) {
       const uint32_t e = Q.e[lane];
-      rr = Q.r[lane];
       own = Q.o[lane];
       const float4 ro = Q.ri[own], lio = Q.li[own];
       const uint32_t j = e >> 5, code = e & 31u;
@@ -1830,68 +1831,76 @@ __global__ void __launch_bounds__(kQueueWarps * 32) k_pair_nlq(DevArrays A) {
       const float4 lj = lo[j];
       const int dz = (int)(code / 9u) - 1, dy = (int)(code / 3u % 3u) - 1, dx = (int)(code % 3u) - 1;
       const uint32_t qt = (RecT<float>::bits(ro) & 7u) * kMaxTypes + (RecT<float>::bits(rj) & 7u);
+      AccTerm t;
       in = acc_pair(tab, qt, ro, lio, rj, lj, (float)dx * Q.csx[own], (float)dy * Q.csy[own],
                     (float)dz * Q.csz[own], t);
+      Q.ta[lane] = make_float4(t.fr, t.dx.h, t.dy.h, t.dz.h);
+      Q.tb[lane] = make_float4(t.dx.l, t.dy.l, t.dz.l, t.v);
+      Q.in[lane] = in ? 1 : 0;
     }
-    const uint32_t r0 = Q.r[0], r1 = Q.r[k - 1];  // the queue is in round order
-    for (uint32_t q = r0; q <= r1; ++q) {
-      if (have && in && rr == q) {
-        Q.hit_a[own] = make_float4(t.fr, t.dx.h, t.dy.h, t.dz.h);
-        Q.hit_b[own] = make_float4(t.dx.l, t.dy.l, t.dz.l, t.v);
-        Q.flag[own] = 1;
-      }
-      __syncwarp();
-      if (Q.flag[lane]) {
-        const float4 a = Q.hit_a[lane], b = Q.hit_b[lane];
+    // runs: a queue position starts one where its particle differs from the previous position's
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, own, 1);
+    const bool start = have && (lane == 0 || prev != own);
+    const uint32_t starts = __ballot_sync(0xffffffffu, start);
+    Q.runn[lane] = 0;
+    __syncwarp();
+    if (start) {
+      const uint32_t after = starts & ~((2u << lane) - 1u);  // starts above this one
+      const uint32_t next = after ? (uint32_t)(__ffs(after) - 1) : k;
+      Q.run0[own] = (uint8_t)lane;
+      Q.runn[own] = (uint8_t)(next - lane);
+    }
+    __syncwarp();
+    const uint32_t r0 = Q.run0[lane], rn = Q.runn[lane];
+    const uint32_t longest = __reduce_max_sync(0xffffffffu, rn);
+    for (uint32_t q = 0; q < longest; ++q) {
+      if (q < rn && Q.in[r0 + q]) {
+        const float4 a = Q.ta[r0 + q], b = Q.tb[r0 + q];
         acc_add(a.x, DF{a.y, b.x}, DF{a.z, b.y}, DF{a.w, b.z}, b.w, fx, fy, fz, u);
-        Q.flag[lane] = 0;
       }
-      __syncwarp();
     }
+    __syncwarp();
   };
-  // kQueueRounds rounds at a time: their entries, then their records, are
-  // loaded together (independent loads in flight), then screened and queued
-  // round by round
-  for (uint32_t r0 = 0; r0 < rounds; r0 += kQueueRounds) {
-    uint32_t e[kQueueRounds];
-    float4 rj[kQueueRounds];
+  for (uint32_t c = 0; c < total; c += 32) {
+    const uint32_t p = c + (uint32_t)lane;
+    bool hit = false;
+    uint32_t e = 0, own = 0;
+    // the particle of position p: the highest lane whose prefix is <= p
 #pragma unroll
-    for (int q = 0; q < kQueueRounds; ++q) e[q] = r0 + q < cnt ? nl[(int64_t)(r0 + q) * n] : 0u;
-#pragma unroll
-    for (int q = 0; q < kQueueRounds; ++q)
-      if (r0 + q < cnt) rj[q] = rec[e[q] >> 5];
-#pragma unroll
-    for (int q = 0; q < kQueueRounds; ++q) {
-      const uint32_t r = r0 + q;
-      if (r >= rounds) break;  // warp-uniform
-      bool hit = false;
-      if (r < cnt) {
-        const uint32_t code = e[q] & 31u;
-        const int dz = (int)(code / 9u) - 1, dy = (int)(code / 3u % 3u) - 1, dx = (int)(code % 3u) - 1;
-        const float ddx = ri.x - rj[q].x - (float)dx * csx, ddy = ri.y - rj[q].y - (float)dy * csy,
-                    ddz = ri.z - rj[q].z - (float)dz * csz;
-        const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-        hit = r2 < tab.acc.rc2m[ti * kMaxTypes + (RecT<float>::bits(rj[q]) & 7u)];
-      }
-      const uint32_t mask = __ballot_sync(0xffffffffu, hit);
-      if (hit) {
-        const uint32_t pos = qn + __popc(mask & ((1u << lane) - 1u));
-        Q.e[pos] = e[q];
-        Q.r[pos] = (uint16_t)r;
-        Q.o[pos] = (uint8_t)lane;
-      }
-      qn += __popc(mask);
-      if (qn >= 32) {
-        drain(32);
-        // move the rest (qn - 32 < 32 entries) to the front
-        uint32_t e2 = 0, o2 = 0, rr2 = 0;
-        const bool mv = (uint32_t)lane < qn - 32;
-        if (mv) { e2 = Q.e[32 + lane]; rr2 = Q.r[32 + lane]; o2 = Q.o[32 + lane]; }
-        __syncwarp();
-        if (mv) { Q.e[lane] = e2; Q.r[lane] = (uint16_t)rr2; Q.o[lane] = (uint8_t)o2; }
-        __syncwarp();
-        qn -= 32;
-      }
+    for (int step = 16; step > 0; step >>= 1) {
+      const uint32_t cand = own + (uint32_t)step;
+      const uint32_t pc = __shfl_sync(0xffffffffu, pre, (int)(cand & 31u));
+      if (cand < 32u && pc <= p) own = cand;
+    }
+    const uint32_t k = p - __shfl_sync(0xffffffffu, pre, (int)own);
+    if (p < total) {
+      e = nl[(int64_t)(s0 + own) * cap + k];
+      const float4 rj = rec[e >> 5];
+      const float4 ro = Q.ri[own];
+      const uint32_t code = e & 31u;
+      const int dz = (int)(code / 9u) - 1, dy = (int)(code / 3u % 3u) - 1, dx = (int)(code % 3u) - 1;
+      const float ddx = ro.x - rj.x - (float)dx * Q.csx[own], ddy = ro.y - rj.y - (float)dy * Q.csy[own],
+                  ddz = ro.z - rj.z - (float)dz * Q.csz[own];
+      const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+      hit = r2 < tab.acc.rc2m[(RecT<float>::bits(ro) & 7u) * kMaxTypes + (RecT<float>::bits(rj) & 7u)];
+    }
+    const uint32_t mask = __ballot_sync(0xffffffffu, hit);
+    if (hit) {
+      const uint32_t pos = qn + __popc(mask & ((1u << lane) - 1u));
+      Q.e[pos] = e;
+      Q.o[pos] = (uint8_t)own;
+    }
+    qn += __popc(mask);
+    if (qn >= 32) {
+      drain(32);
+      // move the rest (qn - 32 < 32 pairs) to the front
+      uint32_t e2 = 0, o2 = 0;
+      const bool mv = (uint32_t)lane < qn - 32;
+      if (mv) { e2 = Q.e[32 + lane]; o2 = Q.o[32 + lane]; }
+      __syncwarp();
+      if (mv) { Q.e[lane] = e2; Q.o[lane] = (uint8_t)o2; }
+      __syncwarp();
+      qn -= 32;
     }
   }
   if (qn) drain(qn);

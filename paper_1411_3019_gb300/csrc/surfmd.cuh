@@ -167,7 +167,7 @@ struct DevArrays {
   // the records in place and raises *nl_dirty when a particle has moved more
   // than skin / 2, and the cell list and the list are rebuilt in that step.
   uint32_t* nl_dirty;   // device flag: 1 = rebuild the cell list and the neighbour list
-  uint32_t* nl;         // [nl_max][n] neighbour entries by sorted slot: slot << 5 | stencil cell (0..26)
+  uint32_t* nl;         // [n][nl_max] neighbour entries by sorted slot: slot << 5 | stencil cell (0..26)
   uint32_t* nl_cnt;     // [n] entries per sorted slot
   void* rec0;           // [n] records at the last build, by particle
   double* xb;           // [3][n] positions at the last build (user order)
