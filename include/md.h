@@ -328,6 +328,12 @@ int md_step(md_handle* h, int64_t nsteps);
  * run, md_step falls back to the separate launches (md_get_option then
  * reads 0). */
 #define MD_OPT_FUSED_REBUILD 10
+/* MD_OPT_LIST_WARP (mixed precision with the Verlet list, MD_OPT_PAIR_QUEUE =
+ * 1): particles per warp of the list walk, 32 (default), 16 or 8. The warp
+ * walks its particles' lists as one sequence, 32 entries at a time, so long
+ * lists (long cutoffs, dense systems) spread over more warps with fewer
+ * particles each. The same bits for every setting. */
+#define MD_OPT_LIST_WARP 11
 /* Verlet neighbour list (the LAMMPS-style list the paper's simulations
  * ran with; the cell list is how it is built). With skin > 0 every pair
  * within r_c + skin is listed from the cell list, and the pair kernel walks

@@ -837,6 +837,7 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
   if (!h->has_pairs) A.nbucket = 1;
   A.pair_lanes = 1;
   A.pair_queue = 1;
+  A.list_warp = 32;
   A.ntypes = prms[0].ntypes;
   A.spin_limit = kDefaultSpinLimit;
   A.rec_cell = (!h->excl && cell_total < (uint64_t(1) << 29)) ? 1 : 0;
@@ -1266,6 +1267,11 @@ int md_set_option(md_handle* h, int32_t key, int64_t value) {
       if (value != 0 && value != 1) return fail(h, MD_ERR_INVALID_ARG, "pair queue must be 0 or 1");
       h->A.pair_queue = (int32_t)value;
       break;
+    case MD_OPT_LIST_WARP:
+      if (value != 8 && value != 16 && value != 32)
+        return fail(h, MD_ERR_INVALID_ARG, "particles per warp of the list walk must be 8, 16 or 32");
+      h->A.list_warp = (int32_t)value;
+      break;
     case MD_OPT_FUSED_REBUILD:
       if (value != 0 && value != 1) return fail(h, MD_ERR_INVALID_ARG, "fused rebuild must be 0 or 1");
       h->fused_rebuild = (int)value;
@@ -1304,6 +1310,7 @@ int md_get_option(md_handle* h, int32_t key, int64_t* value) {
     case MD_OPT_SPIN_LIMIT: *value = h->A.spin_limit; return MD_OK;
     case MD_OPT_PAIR_QUEUE: *value = h->A.pair_queue; return MD_OK;
     case MD_OPT_FUSED_REBUILD: *value = h->fused_rebuild; return MD_OK;
+    case MD_OPT_LIST_WARP: *value = h->A.list_warp; return MD_OK;
     case MD_OPT_NLIST_BUILDS: {
       unsigned long long b = 0;
       if (h->A.nl_builds) {

@@ -1752,7 +1752,8 @@ __global__ void __launch_bounds__(256, SURFMD_PAIR_NL_MINB) k_pair_nl(DevArrays 
   store_f<R>(A.f, tag, fx, fy, fz, u);
 }
 
-// Mixed path with the Verlet list, one warp per 32 consecutive slots. The
+// Mixed path with the Verlet list, one warp per list_warp (8, 16 or 32)
+// consecutive slots (fewer for long lists, so more warps share the work). The
 // warp walks its particles' list entries as one flat sequence (particle by
 // particle, each particle's entries in list order; its list is contiguous, so
 // 32 consecutive positions are a few contiguous runs): lane q takes position
@@ -1786,9 +1787,11 @@ __global__ void __launch_bounds__(kQueueWarps * 32) k_pair_nlq(DevArrays A) {
   const int lane = (int)(threadIdx.x & 31u);
   QueueWarp& Q = qw_all[threadIdx.x >> 5];
   __syncthreads();
-  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t s0 = s - (uint32_t)lane;  // the warp's first slot
-  const bool valid = s < (uint32_t)A.n;
+  // the warp's particles: list_warp (8, 16 or 32) consecutive slots, one per lane from lane 0
+  const uint32_t P = (uint32_t)A.list_warp;
+  const uint32_t s0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * P;  // the warp's first slot
+  const uint32_t s = s0 + (uint32_t)lane;
+  const bool valid = (uint32_t)lane < P && s < (uint32_t)A.n;
   const float4* __restrict__ rec = reinterpret_cast<const float4*>(A.rec);
   const float4* __restrict__ lo = A.rec_lo;
   const uint32_t* __restrict__ nl = A.nl;
@@ -3574,7 +3577,8 @@ static void pair_dispatch_nl(const DevArrays& A, int bonds, int walls, cudaStrea
   const unsigned g = grid_for(A.n, 256);
   if constexpr (sizeof(R) == 4) {
     if (A.pair_queue) {
-      const unsigned gq = grid_for(A.n, kQueueWarps * 32);
+      const int64_t warps = (A.n + A.list_warp - 1) / A.list_warp;
+      const unsigned gq = (unsigned)((warps + kQueueWarps - 1) / kQueueWarps);
       switch ((bonds ? 2 : 0) | (walls ? 1 : 0)) {
         case 0: k_pair_nlq<false, false><<<gq, kQueueWarps * 32, 0, st>>>(A); break;
         case 1: k_pair_nlq<false, true><<<gq, kQueueWarps * 32, 0, st>>>(A); break;

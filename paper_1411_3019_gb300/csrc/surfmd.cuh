@@ -162,6 +162,7 @@ struct DevArrays {
   int32_t pair_lanes;   // lanes per particle in the pair kernel (1, 2, 4 or 8)
   int32_t pair_tile;    // 0, or particles per warp (8, 16, 32) of the cell-tiled pair kernel (needs hashed == 0)
   int32_t pair_queue;   // mixed path with the Verlet list: 1 = warp-queued list walk (k_pair_nlq), 0 = per-lane walk
+  int32_t list_warp;    // particles per warp of the warp-queued list walk (8, 16 or 32)
   // Verlet neighbour list (nl_dirty == null: off). Built from the cell list
   // with every pair within r_c + skin; between builds the integrator moves
   // the records in place and raises *nl_dirty when a particle has moved more

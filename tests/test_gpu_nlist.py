@@ -185,29 +185,34 @@ def test_forces_after_set_state_and_resume_from_checkpoint(precision):
 
 @pytest.mark.parametrize("workload", ["ellipsoid_torus", "bead_molecules"])
 def test_queued_list_walk_gives_the_same_bits(workload):
-    """The warp-queued list walk (default) and the per-lane walk add each
-    particle's terms in list order with the same arithmetic: forces and a
-    trajectory across rebuilds agree bit for bit."""
+    """The warp-queued list walk (default, at 32, 16 and 8 particles per
+    warp) and the per-lane walk add each particle's terms in list order with
+    the same arithmetic: forces and a trajectory across rebuilds agree bit for
+    bit."""
     skin = 0.4
     if workload == "ellipsoid_torus":
         systems = _cells(I.c2_ellipsoid_torus(n_ell=4000, n_tor=1500, seed=8, precision="mixed"), skin)
     else:
         systems = _cells(I.c5_bead_molecules(nmol=400, beads=5, R=12.0, seed=6, precision="mixed"), skin)
     out = {}
-    for queue in (1, 0):
+    for queue, per_warp in ((1, 32), (0, 32), (1, 16), (1, 8)):
         with md.Simulation(systems) as sim:
             md.md_set_option(sim.h, md.MD_OPT_PAIR_QUEUE, queue)
+            md.md_set_option(sim.h, md.MD_OPT_LIST_WARP, per_warp)
             assert md.md_get_option(sim.h, md.MD_OPT_PAIR_QUEUE) == queue
+            assert md.md_get_option(sim.h, md.MD_OPT_LIST_WARP) == per_warp
             md.md_set_neighbor_list(sim.h, skin, 128)
             sim.set_state()
             f0, u0 = sim.forces()
             sim.step(40)
             sim.sync()
-            out[queue] = (f0, u0, sim.state(), md.md_get_option(sim.h, md.MD_OPT_NLIST_BUILDS))
-    assert out[1][3] > 1  # rebuilds inside the run
-    assert np.array_equal(out[1][0], out[0][0]) and np.array_equal(out[1][1], out[0][1])
-    for key in ("x", "p_half"):
-        assert np.array_equal(out[1][2][key], out[0][2][key]), key
+            out[(queue, per_warp)] = (f0, u0, sim.state(), md.md_get_option(sim.h, md.MD_OPT_NLIST_BUILDS))
+    ref = out[(0, 32)]
+    assert ref[3] > 1  # rebuilds inside the run
+    for key_run, run in out.items():
+        assert np.array_equal(run[0], ref[0]) and np.array_equal(run[1], ref[1]), key_run
+        for key in ("x", "p_half"):
+            assert np.array_equal(run[2][key], ref[2][key]), (key_run, key)
 
 
 @pytest.mark.parametrize("workload", ["ellipsoid_torus", "bead_molecules"])
