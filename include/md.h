@@ -334,6 +334,15 @@ int md_step(md_handle* h, int64_t nsteps);
  * lists (long cutoffs, dense systems) spread over more warps with fewer
  * particles each. The same bits for every setting. */
 #define MD_OPT_LIST_WARP 11
+/* MD_OPT_STORE_NOISE (mixed precision with the Verlet list): 1 (default) =
+ * the integrator stores the unit normals xi^k it draws for step k (16 bytes
+ * per particle) and the next step's force combination, which needs xi^k
+ * again beside xi^(k+1), reads them instead of drawing them a second time;
+ * 0 = both steps' normals are drawn every step. The stored values are the
+ * ones the generator gives, so trajectories are the same bit for bit either
+ * way. After md_set_state or md_restore (and after switching the option) the
+ * first step draws both. */
+#define MD_OPT_STORE_NOISE 12
 /* Verlet neighbour list (the LAMMPS-style list the paper's simulations
  * ran with; the cell list is how it is built). With skin > 0 every pair
  * within r_c + skin is listed from the cell list, and the pair kernel walks

@@ -838,6 +838,7 @@ int md_create_batch(int32_t nsys, const md_surface* surfs, const md_params* prms
   A.pair_lanes = 1;
   A.pair_queue = 1;
   A.list_warp = 32;
+  A.store_noise = 1;
   A.ntypes = prms[0].ntypes;
   A.spin_limit = kDefaultSpinLimit;
   A.rec_cell = (!h->excl && cell_total < (uint64_t(1) << 29)) ? 1 : 0;
@@ -997,6 +998,7 @@ static int set_state_common(md_handle* h, const double* d_x, const double* d_v, 
   const unsigned long long k = step0;
   CK(h, cudaMemcpyAsync(h->A.step, &k, sizeof(k), cudaMemcpyHostToDevice, st));
   CK(h, cudaMemsetAsync(h->A.mode, 0, sizeof(int32_t), st));
+  if (h->A.noise_k) CK(h, cudaMemsetAsync(h->A.noise_k, 0xff, sizeof(unsigned long long), st));  // none stored
   int rc = rebuild_cells(h);
   if (rc) return rc;
   h->state_set = true;
@@ -1046,6 +1048,7 @@ int md_restore(md_handle* h, const double* x, const double* p_half, uint64_t ste
   const int32_t one = 1;
   CK(h, cudaMemcpyAsync(h->A.step, &k, sizeof(k), cudaMemcpyHostToDevice, st));
   CK(h, cudaMemcpyAsync(h->A.mode, &one, sizeof(one), cudaMemcpyHostToDevice, st));
+  if (h->A.noise_k) CK(h, cudaMemsetAsync(h->A.noise_k, 0xff, sizeof(unsigned long long), st));  // none stored
   rc = rebuild_cells(h);
   if (rc) return rc;
   return check_device_status(h);
@@ -1192,6 +1195,7 @@ int md_set_neighbor_list(md_handle* h, double skin, int32_t max_neighbors) {
       if (!h->d_nl_dirty) e = dalloc(h, &h->d_nl_dirty, 1);
       if (e == cudaSuccess) e = dalloc(h, &A.nl, (size_t)max_neighbors * n);
       if (e == cudaSuccess) e = dalloc(h, &A.nl_cnt, n);
+      if (e == cudaSuccess) e = dalloc(h, &A.smeta, n);
       if (e == cudaSuccess) e = dalloc(h, &A.xb, 3 * n);
       if (e == cudaSuccess && !A.nl_builds) {
         e = dalloc(h, &A.nl_builds, 1);
@@ -1201,6 +1205,11 @@ int md_set_neighbor_list(md_handle* h, double skin, int32_t max_neighbors) {
         e = h->precision == MD_PREC_FP64 ? dalloc(h, reinterpret_cast<double4_32a**>(&A.rec0), n)
                                          : dalloc(h, reinterpret_cast<float4**>(&A.rec0), n);
       if (e == cudaSuccess && h->precision != MD_PREC_FP64) e = dalloc(h, &A.rec0_lo, n);
+      if (e == cudaSuccess && h->precision != MD_PREC_FP64) e = dalloc(h, &A.noise, n);
+      if (e == cudaSuccess && h->precision != MD_PREC_FP64 && !A.noise_k) {
+        e = dalloc(h, &A.noise_k, 1);
+        if (e == cudaSuccess) e = cudaMemsetAsync(A.noise_k, 0xff, sizeof(unsigned long long), h->stream());
+      }
       if (e != cudaSuccess) return cuda_fail(h, e, "neighbour list allocation");
       h->nl_capacity = max_neighbors;
     }
@@ -1272,6 +1281,11 @@ int md_set_option(md_handle* h, int32_t key, int64_t value) {
         return fail(h, MD_ERR_INVALID_ARG, "particles per warp of the list walk must be 8, 16 or 32");
       h->A.list_warp = (int32_t)value;
       break;
+    case MD_OPT_STORE_NOISE:
+      if (value != 0 && value != 1) return fail(h, MD_ERR_INVALID_ARG, "store noise must be 0 or 1");
+      h->A.store_noise = (int32_t)value;
+      if (h->A.noise_k) CK(h, cudaMemsetAsync(h->A.noise_k, 0xff, sizeof(unsigned long long), h->stream()));
+      break;
     case MD_OPT_FUSED_REBUILD:
       if (value != 0 && value != 1) return fail(h, MD_ERR_INVALID_ARG, "fused rebuild must be 0 or 1");
       h->fused_rebuild = (int)value;
@@ -1311,6 +1325,7 @@ int md_get_option(md_handle* h, int32_t key, int64_t* value) {
     case MD_OPT_PAIR_QUEUE: *value = h->A.pair_queue; return MD_OK;
     case MD_OPT_FUSED_REBUILD: *value = h->fused_rebuild; return MD_OK;
     case MD_OPT_LIST_WARP: *value = h->A.list_warp; return MD_OK;
+    case MD_OPT_STORE_NOISE: *value = h->A.store_noise; return MD_OK;
     case MD_OPT_NLIST_BUILDS: {
       unsigned long long b = 0;
       if (h->A.nl_builds) {

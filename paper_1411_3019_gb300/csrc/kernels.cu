@@ -537,6 +537,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_onepass(DevArrays A, int 
     if (threadIdx.x == 0 && atomicAdd(&ctl->done, 1u) == gridDim.x - 1) {
       ctl->done = 0u;
       if (advance) {
+        if (A.nl_dirty && A.noise_k) *A.noise_k = *A.step;  // list mode: this step's normals are stored
         *A.step += 1ull;
         *A.mode = 1;
       }
@@ -640,6 +641,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_onepass(DevArrays A, int 
       ctl->tile = 0u;
       ctl->epoch = epoch + 1u;
       if (advance) {
+        if (A.nl_dirty && A.noise_k) *A.noise_k = *A.step;  // list mode: this step's normals are stored
         *A.step += 1ull;
         *A.mode = 1;
       }
@@ -719,6 +721,7 @@ __device__ __forceinline__ void bucket_build_one(const DevArrays& A, int64_t s) 
   A.stag[d] = tag;
   A.scell[d] = cell;
   if (A.slot_of) A.slot_of[tag] = d;
+  if (A.smeta) A.smeta[d] = m;
   put_rec<R>(A.rec, A.rec_lo, d, o[0], o[1], o[2], meta_type(m) | ((A.rec_cell ? cell : mol) << 3));
 }
 
@@ -1597,6 +1600,7 @@ __global__ void __launch_bounds__(256) k_rebuild(DevArrays A) {
   const bool lead = blockIdx.x == 0 && tid == 0;
   if (*A.nl_dirty == 0u) {  // uniform: nothing moved far enough; only the step advances
     if (lead) {
+      if (A.noise_k) *A.noise_k = *A.step;  // the integrator has stored this step's normals
       *A.step += 1ull;
       *A.mode = 1;
     }
@@ -1647,6 +1651,7 @@ __global__ void __launch_bounds__(256) k_rebuild(DevArrays A) {
   for (int64_t s = first; s < n; s += stride) nl_build_one<R, EXCL>(A, tab, (uint32_t)s);
   if (lead) {
     *A.nl_builds += 1ull;
+    if (A.noise_k) *A.noise_k = *A.step;
     *A.step += 1ull;
     *A.mode = 1;
   }
@@ -1756,30 +1761,54 @@ __global__ void __launch_bounds__(256, SURFMD_PAIR_NL_MINB) k_pair_nl(DevArrays 
 // consecutive slots (fewer for long lists, so more warps share the work). The
 // warp walks its particles' list entries as one flat sequence (particle by
 // particle, each particle's entries in list order; its list is contiguous, so
-// 32 consecutive positions are a few contiguous runs): lane q takes position
-// c + q, finds its particle by a binary search over the warp's prefix sums
-// of the list lengths, and screens the pair in float32 on the records' high
-// parts. The pairs that pass are queued in shared memory in the same flat
-// order (a ballot gives each its place), and every 32 of them are evaluated
-// on all lanes with the double-float arithmetic of lj_term_acc. A particle's
-// queued pairs are consecutive, so after each evaluation the particle's lane
-// adds its run of terms in order: every particle adds its terms in list
-// order with the same arithmetic as k_pair_nl (the same bits), while no lane
-// idles on a short list or on a pair that fails the screen.
+// 32 consecutive positions are a few contiguous runs), kNlqGroup chunks of 32
+// positions at a time: lane q takes positions c + q, c + 32 + q, ..., finds
+// each one's particle by a binary search over the warp's prefix sums of the
+// list lengths and loads the entries; the entries' records and low parts are
+// then copied to shared memory with cp.async, all of the group's copies in
+// flight together and no register held for them. The pairs are screened in
+// float32 on the staged high parts; those that pass are queued (a ballot
+// gives each its place, in the flat order) and evaluated 32 at a time on all
+// lanes with the double-float arithmetic of lj_term_acc. A particle's queued
+// pairs are consecutive, so after each evaluation the particle's lane adds its
+// run of terms in order: every particle adds its terms in list order with the
+// same arithmetic as k_pair_nl (the same bits), while no lane idles on a short
+// list or on a pair that fails the screen.
 constexpr int kQueueWarps = 8;
+#ifndef SURFMD_NLQ_GROUP
+#define SURFMD_NLQ_GROUP 3
+#endif
+#ifndef SURFMD_NLQ_MINB
+#define SURFMD_NLQ_MINB 1
+#endif
+constexpr int kNlqGroup = SURFMD_NLQ_GROUP;
+constexpr int kNlqStage = 32 * kNlqGroup;  // staged positions per warp
 
 struct QueueWarp {
-  float4 ri[32], li[32];          // the lanes' own records and low parts
-  float4 ta[32], tb[32];          // evaluated terms: (fr, dx.h, dy.h, dz.h), (dx.l, dy.l, dz.l, v)
+  float4 ri[32], li[32];  // the lanes' own records and low parts
+  // staged pairs: the neighbour's record and low part; an evaluation
+  // overwrites a staged pair with its term, (fr, dx.h, dy.h, dz.h) and
+  // (dx.l, dy.l, dz.l, v)
+  float4 sr[kNlqStage], sl[kNlqStage];
   float csx[32], csy[32], csz[32];  // the lanes' cell edges (their systems')
-  uint32_t e[64];                 // queued list entries (slot << 5 | stencil cell)
-  uint8_t o[64];                  // their particles (lanes)
-  uint8_t in[32];                 // evaluated term is inside the cutoff
-  uint8_t run0[32], runn[32];     // per particle: first queue position and length of its run
+  uint8_t code[kNlqStage];          // staged pair: stencil cell of the neighbour
+  uint8_t own[kNlqStage];           // staged pair: its particle (lane)
+  uint8_t in[kNlqStage];            // staged pair: evaluated term is inside the cutoff
+  uint8_t q[kNlqStage];             // queue: staged pairs that passed the screen, in order
+  uint8_t run0[32], runn[32];       // per particle: first queue position and length of its run
 };
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <bool BONDS, bool WALLS>
-__global__ void __launch_bounds__(kQueueWarps * 32) k_pair_nlq(DevArrays A) {
+__global__ void __launch_bounds__(kQueueWarps * 32, SURFMD_NLQ_MINB) k_pair_nlq(DevArrays A) {
   __shared__ PairTab<float> tab;
   __shared__ QueueWarp qw_all[kQueueWarps];
   load_tab<float>(tab, A.types);
@@ -1796,11 +1825,10 @@ __global__ void __launch_bounds__(kQueueWarps * 32) k_pair_nlq(DevArrays A) {
   const float4* __restrict__ lo = A.rec_lo;
   const uint32_t* __restrict__ nl = A.nl;
   const uint32_t cap = (uint32_t)A.nl_max;
-  uint32_t tag = 0, m = 0, cnt = 0;
+  uint32_t m = 0, cnt = 0;
   float csx = 0.f, csy = 0.f, csz = 0.f;
   if (valid) {
-    tag = A.stag[s];
-    m = A.meta[tag];
+    m = A.smeta[s];  // sorted copy: no gather through the particle's tag
     const SysDev& S = A.sys[meta_sys(m)];
     Q.ri[lane] = rec[s];
     Q.li[lane] = lo[s];
@@ -1818,96 +1846,106 @@ __global__ void __launch_bounds__(kQueueWarps * 32) k_pair_nlq(DevArrays A) {
   const uint32_t pre = incl - cnt;
   const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
   float fx = 0.f, fy = 0.f, fz = 0.f, u = 0.f;
-  uint32_t qn = 0;  // queued pairs (warp-uniform)
-  // evaluate the first k queued pairs (k <= 32); each particle adds its run in order
-  auto drain = [&](uint32_t k) {
+  // evaluate the k queued pairs from queue position q0 (k <= 32); each particle adds its run in order
+  auto drain = [&](uint32_t q0, uint32_t k) {
     __syncwarp();
     const bool have = (uint32_t)lane < k;
-    uint32_t own = 0;
-    bool in = false;
+    uint32_t ow = 0;
     if (have) {
-      const uint32_t e = Q.e[lane];
-      own = Q.o[lane];
-      const float4 ro = Q.ri[own], lio = Q.li[own];
-      const uint32_t j = e >> 5, code = e & 31u;
-      const float4 rj = rec[j];
-      const float4 lj = lo[j];
+      const uint32_t x = Q.q[q0 + lane];
+      ow = Q.own[x];
+      const uint32_t code = Q.code[x];
+      const float4 ro = Q.ri[ow], lio = Q.li[ow];
+      const float4 rj = Q.sr[x], lj = Q.sl[x];
       const int dz = (int)(code / 9u) - 1, dy = (int)(code / 3u % 3u) - 1, dx = (int)(code % 3u) - 1;
       const uint32_t qt = (RecT<float>::bits(ro) & 7u) * kMaxTypes + (RecT<float>::bits(rj) & 7u);
       AccTerm t;
-      in = acc_pair(tab, qt, ro, lio, rj, lj, (float)dx * Q.csx[own], (float)dy * Q.csy[own],
-                    (float)dz * Q.csz[own], t);
-      Q.ta[lane] = make_float4(t.fr, t.dx.h, t.dy.h, t.dz.h);
-      Q.tb[lane] = make_float4(t.dx.l, t.dy.l, t.dz.l, t.v);
-      Q.in[lane] = in ? 1 : 0;
+      const bool in = acc_pair(tab, qt, ro, lio, rj, lj, (float)dx * Q.csx[ow], (float)dy * Q.csy[ow],
+                               (float)dz * Q.csz[ow], t);
+      Q.sr[x] = make_float4(t.fr, t.dx.h, t.dy.h, t.dz.h);
+      Q.sl[x] = make_float4(t.dx.l, t.dy.l, t.dz.l, t.v);
+      Q.in[x] = in ? 1 : 0;
     }
     // runs: a queue position starts one where its particle differs from the previous position's
-    const uint32_t prev = __shfl_up_sync(0xffffffffu, own, 1);
-    const bool start = have && (lane == 0 || prev != own);
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, ow, 1);
+    const bool start = have && (lane == 0 || prev != ow);
     const uint32_t starts = __ballot_sync(0xffffffffu, start);
     Q.runn[lane] = 0;
     __syncwarp();
     if (start) {
       const uint32_t after = starts & ~((2u << lane) - 1u);  // starts above this one
       const uint32_t next = after ? (uint32_t)(__ffs(after) - 1) : k;
-      Q.run0[own] = (uint8_t)lane;
-      Q.runn[own] = (uint8_t)(next - lane);
+      Q.run0[ow] = (uint8_t)lane;
+      Q.runn[ow] = (uint8_t)(next - lane);
     }
     __syncwarp();
     const uint32_t r0 = Q.run0[lane], rn = Q.runn[lane];
     const uint32_t longest = __reduce_max_sync(0xffffffffu, rn);
-    for (uint32_t q = 0; q < longest; ++q) {
-      if (q < rn && Q.in[r0 + q]) {
-        const float4 a = Q.ta[r0 + q], b = Q.tb[r0 + q];
-        acc_add(a.x, DF{a.y, b.x}, DF{a.z, b.y}, DF{a.w, b.z}, b.w, fx, fy, fz, u);
+    for (uint32_t j = 0; j < longest; ++j) {
+      if (j < rn) {
+        const uint32_t x = Q.q[q0 + r0 + j];
+        if (Q.in[x]) {
+          const float4 a = Q.sr[x], b = Q.sl[x];
+          acc_add(a.x, DF{a.y, b.x}, DF{a.z, b.y}, DF{a.w, b.z}, b.w, fx, fy, fz, u);
+        }
       }
     }
     __syncwarp();
   };
-  for (uint32_t c = 0; c < total; c += 32) {
-    const uint32_t p = c + (uint32_t)lane;
-    bool hit = false;
-    uint32_t e = 0, own = 0;
-    // the particle of position p: the highest lane whose prefix is <= p
+  for (uint32_t c = 0; c < total; c += (uint32_t)kNlqStage) {
+    // the particle of each position p (the highest lane whose prefix is <= p) and its list entry
+    uint32_t e[kNlqGroup];
 #pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-      const uint32_t cand = own + (uint32_t)step;
-      const uint32_t pc = __shfl_sync(0xffffffffu, pre, (int)(cand & 31u));
-      if (cand < 32u && pc <= p) own = cand;
+    for (int g = 0; g < kNlqGroup; ++g) {
+      const uint32_t p = c + 32u * g + (uint32_t)lane;
+      uint32_t ow = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t cand = ow + (uint32_t)step;
+        const uint32_t pc = __shfl_sync(0xffffffffu, pre, (int)(cand & 31u));
+        if (cand < 32u && pc <= p) ow = cand;
+      }
+      const uint32_t k = p - __shfl_sync(0xffffffffu, pre, (int)ow);
+      Q.own[32 * g + lane] = (uint8_t)ow;
+      e[g] = p < total ? nl[(int64_t)(s0 + ow) * cap + k] : 0u;
     }
-    const uint32_t k = p - __shfl_sync(0xffffffffu, pre, (int)own);
-    if (p < total) {
-      e = nl[(int64_t)(s0 + own) * cap + k];
-      const float4 rj = rec[e >> 5];
-      const float4 ro = Q.ri[own];
-      const uint32_t code = e & 31u;
-      const int dz = (int)(code / 9u) - 1, dy = (int)(code / 3u % 3u) - 1, dx = (int)(code % 3u) - 1;
-      const float ddx = ro.x - rj.x - (float)dx * Q.csx[own], ddy = ro.y - rj.y - (float)dy * Q.csy[own],
-                  ddz = ro.z - rj.z - (float)dz * Q.csz[own];
-      const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-      hit = r2 < tab.acc.rc2m[(RecT<float>::bits(ro) & 7u) * kMaxTypes + (RecT<float>::bits(rj) & 7u)];
+    // the entries' records and low parts to shared memory, all in flight together
+    __syncwarp();  // the previous group's evaluations have read their staged pairs
+#pragma unroll
+    for (int g = 0; g < kNlqGroup; ++g) {
+      const uint32_t p = c + 32u * g + (uint32_t)lane;
+      if (p < total) {
+        const uint32_t x = 32u * g + (uint32_t)lane;
+        Q.code[x] = (uint8_t)(e[g] & 31u);
+        cp_async16(&Q.sr[x], &rec[e[g] >> 5]);
+        cp_async16(&Q.sl[x], &lo[e[g] >> 5]);
+      }
     }
-    const uint32_t mask = __ballot_sync(0xffffffffu, hit);
-    if (hit) {
-      const uint32_t pos = qn + __popc(mask & ((1u << lane) - 1u));
-      Q.e[pos] = e;
-      Q.o[pos] = (uint8_t)own;
+    cp_async_wait_all();
+    // screen on the high parts; queue the pairs that pass, in order
+    uint32_t qn = 0;
+#pragma unroll
+    for (int g = 0; g < kNlqGroup; ++g) {
+      const uint32_t p = c + 32u * g + (uint32_t)lane;
+      const uint32_t x = 32u * g + (uint32_t)lane;
+      bool hit = false;
+      if (p < total) {
+        const uint32_t ow = Q.own[x], code = Q.code[x];
+        const float4 ro = Q.ri[ow], rj = Q.sr[x];
+        const int dz = (int)(code / 9u) - 1, dy = (int)(code / 3u % 3u) - 1, dx = (int)(code % 3u) - 1;
+        const float ddx = ro.x - rj.x - (float)dx * Q.csx[ow], ddy = ro.y - rj.y - (float)dy * Q.csy[ow],
+                    ddz = ro.z - rj.z - (float)dz * Q.csz[ow];
+        const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+        hit = r2 < tab.acc.rc2m[(RecT<float>::bits(ro) & 7u) * kMaxTypes + (RecT<float>::bits(rj) & 7u)];
+      }
+      const uint32_t mask = __ballot_sync(0xffffffffu, hit);
+      if (hit) Q.q[qn + __popc(mask & ((1u << lane) - 1u))] = (uint8_t)x;
+      qn += __popc(mask);
     }
-    qn += __popc(mask);
-    if (qn >= 32) {
-      drain(32);
-      // move the rest (qn - 32 < 32 pairs) to the front
-      uint32_t e2 = 0, o2 = 0;
-      const bool mv = (uint32_t)lane < qn - 32;
-      if (mv) { e2 = Q.e[32 + lane]; o2 = Q.o[32 + lane]; }
-      __syncwarp();
-      if (mv) { Q.e[lane] = e2; Q.o[lane] = (uint8_t)o2; }
-      __syncwarp();
-      qn -= 32;
-    }
+    for (uint32_t q0 = 0; q0 < qn; q0 += 32u) drain(q0, min(32u, qn - q0));
   }
-  if (qn) drain(qn);
   if (!valid) return;
+  const uint32_t tag = A.stag[s];
   if (BONDS || WALLS) bonded_terms<float>(A, A.sys[meta_sys(m)], tag, m, BONDS, WALLS, fx, fy, fz, u);
   store_f<float>(A.f, tag, fx, fy, fz, u);
 }
@@ -2421,10 +2459,14 @@ template <> __device__ __forceinline__ double noise_amp<double>(const SysDev& S,
 // Algorithm S1 force combination at step k for one particle, in R:
 //   first step after a set state:  F = f - gamma p + f_r^k
 //   otherwise:  F = [f - gamma p^{k-1/2} + (f_r^k + f_r^{k-1})/2] / (1 + gamma dt/2)
-// with f_r = sqrt(2 m kT gamma / dt) xi, xi drawn from Philox in R.
+// with f_r = sqrt(2 m kT gamma / dt) xi, xi drawn from Philox in R. Float32
+// only: with a slot xi, the normals of step k are stored there, and those of
+// step k-1 read from it when xi_prev (they were stored by the previous step:
+// the same values gauss3 would give again).
 template <typename R>
 __device__ __forceinline__ Force3<R> combine(const SysDev& S, const TypeTable* T, uint32_t ty, uint32_t pid,
-                                             unsigned long long k, int mode, Force3<R> f, R px, R py, R pz) {
+                                             unsigned long long k, int mode, Force3<R> f, R px, R py, R pz,
+                                             float4* xi = nullptr, bool xi_prev = false) {
   R nx = 0, ny = 0, nz = 0;
   const R amp = noise_amp<R>(S, T, ty);
   if (amp > (R)0) {
@@ -2434,9 +2476,21 @@ __device__ __forceinline__ Force3<R> combine(const SysDev& S, const TypeTable* T
       nx = amp * gx; ny = amp * gy; nz = amp * gz;
     } else {
       R hx, hy, hz;
-      gauss3(S.seed_lo, S.replica, pid, k - 1ull, hx, hy, hz);
+      if constexpr (sizeof(R) == 4) {
+        if (xi_prev) {
+          const float4 w = *xi;
+          hx = w.x; hy = w.y; hz = w.z;
+        } else {
+          gauss3(S.seed_lo, S.replica, pid, k - 1ull, hx, hy, hz);
+        }
+      } else {
+        gauss3(S.seed_lo, S.replica, pid, k - 1ull, hx, hy, hz);
+      }
       const R ha = (R)0.5 * amp;
       nx = ha * (gx + hx); ny = ha * (gy + hy); nz = ha * (gz + hz);
+    }
+    if constexpr (sizeof(R) == 4) {
+      if (xi) *xi = make_float4(gx, gy, gz, 0.f);
     }
   }
   const R gam = sys_gamma<R>(S);
@@ -2839,7 +2893,8 @@ __device__ __forceinline__ void position_half_df(const SysDev& S, uint32_t ty, i
 
 template <class Bin>
 __device__ __forceinline__ void integrate_particle_mixed(const DevArrays& A, int64_t i, Force3<float> fr_in,
-                                                         unsigned long long k, int mode, const Bin& bin) {
+                                                         unsigned long long k, int mode, const Bin& bin,
+                                                         float4* xi = nullptr, bool xi_prev = false) {
   const int64_t n = A.n;
   const uint32_t m = A.meta[i];
   const SysDev& S = A.sys[meta_sys(m)];
@@ -2847,7 +2902,8 @@ __device__ __forceinline__ void integrate_particle_mixed(const DevArrays& A, int
   const double x = A.x[i], y = A.x[n + i], z = A.x[2 * n + i];
   const double px = A.ph[i], py = A.ph[n + i], pz = A.ph[2 * n + i];
   const float pxf = d2f_rn(px), pyf = d2f_rn(py), pzf = d2f_rn(pz);
-  Force3<float> F = combine<float>(S, A.types, ty, (uint32_t)(i - S.first), k, mode, fr_in, pxf, pyf, pzf);
+  Force3<float> F =
+      combine<float>(S, A.types, ty, (uint32_t)(i - S.first), k, mode, fr_in, pxf, pyf, pzf, xi, xi_prev);
   if (S.kind == kXY2D) F.z = 0.f;  // 2D plane: no z update
   double xn, yn, zn, qx, qy, qz;
   if (meta_con(m) && df_surface(S.kind)) {
@@ -2920,8 +2976,14 @@ __global__ void __launch_bounds__(256, 4) k_integrate_nl(DevArrays A) {
   const unsigned long long k = *A.step;
   const int mode = *A.mode;
   const NlSink<R> bin(A);
-  if constexpr (sizeof(R) == 4) integrate_particle_mixed(A, i, load_f3<float>(A.f, i), k, mode, bin);
-  else integrate_particle_fp64(A, i, load_f3<double>(A.f, i), k, mode, bin);
+  if constexpr (sizeof(R) == 4) {
+    const bool store = A.noise && A.store_noise;
+    float4* xi = store ? A.noise + i : nullptr;
+    const bool xi_prev = store && k > 0ull && *A.noise_k == k - 1ull;  // ~0: none stored
+    integrate_particle_mixed(A, i, load_f3<float>(A.f, i), k, mode, bin, xi, xi_prev);
+  } else {
+    integrate_particle_fp64(A, i, load_f3<double>(A.f, i), k, mode, bin);
+  }
 }
 
 template <typename R, bool BIN>

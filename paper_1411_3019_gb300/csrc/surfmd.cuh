@@ -170,6 +170,13 @@ struct DevArrays {
   uint32_t* nl_dirty;   // device flag: 1 = rebuild the cell list and the neighbour list
   uint32_t* nl;         // [n][nl_max] neighbour entries by sorted slot: slot << 5 | stencil cell (0..26)
   uint32_t* nl_cnt;     // [n] entries per sorted slot
+  uint32_t* smeta;      // [n] meta of each sorted slot (written with the records at a rebuild), or null
+  // mixed path with the list: the unit normals xi^k of the last integrated
+  // step k (by particle; the next step's force combination needs them again)
+  // and that step, ~0 when none is stored (after a state is set)
+  float4* noise;
+  unsigned long long* noise_k;
+  int32_t store_noise;  // 1: store and reuse the normals (MD_OPT_STORE_NOISE), 0: draw both steps' again
   void* rec0;           // [n] records at the last build, by particle
   double* xb;           // [3][n] positions at the last build (user order)
   unsigned long long* nl_builds;  // list builds so far (counter)

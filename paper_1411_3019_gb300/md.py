@@ -40,6 +40,7 @@ MD_OPT_SPIN_LIMIT = 8
 MD_OPT_PAIR_QUEUE = 9
 MD_OPT_FUSED_REBUILD = 10
 MD_OPT_LIST_WARP = 11
+MD_OPT_STORE_NOISE = 12
 ERROR_NAMES = {0: "MD_OK", 1: "MD_ERR_INVALID_ARG", 2: "MD_ERR_CUDA", 3: "MD_ERR_RATTLE_DIVERGED",
                4: "MD_ERR_NONFINITE", 5: "MD_ERR_OUT_OF_GRID", 6: "MD_ERR_TIMEOUT", 7: "MD_ERR_NO_DEVICE",
                8: "MD_ERR_NLIST_FULL"}

@@ -243,3 +243,35 @@ def test_fused_rebuild_gives_the_same_bits(workload):
     assert np.array_equal(out[1][1], out[0][1])
     for key in ("x", "p_half"):
         assert np.array_equal(out[1][0][key], out[0][0][key]), key
+
+
+@pytest.mark.parametrize("fused", [1, 0])
+def test_stored_noise_gives_the_same_bits(fused):
+    """The integrator's stored unit normals (MD_OPT_STORE_NOISE = 1, read back
+    by the next step's force combination) against drawing both steps' normals
+    every step: the same trajectory bit for bit, through a restore from a
+    checkpoint (after which the first step draws both again), with the fused
+    rebuild and with the separate rebuild kernels (each advances the step
+    counter and records the stored step)."""
+    skin = 0.2
+    systems = _cells(I.c2_ellipsoid_torus(n_ell=4000, n_tor=1500, seed=9, precision="mixed"), skin)
+    out = {}
+    for store in (1, 0):
+        with md.Simulation(systems) as sim:
+            md.md_set_option(sim.h, md.MD_OPT_FUSED_REBUILD, fused)
+            md.md_set_option(sim.h, md.MD_OPT_STORE_NOISE, store)
+            assert md.md_get_option(sim.h, md.MD_OPT_STORE_NOISE) == store
+            md.md_set_neighbor_list(sim.h, skin, 128)
+            sim.set_state()
+            sim.step(25)
+            sim.sync()
+            chk = sim.state()
+            sim.step(15)
+            sim.sync()
+            md.md_restore(sim.h, chk["x"], chk["p_half"], chk["step"])
+            sim.step(30)
+            sim.sync()
+            out[store] = sim.state()
+    for key in ("x", "p_half"):
+        assert np.array_equal(out[1][key], out[0][key]), key
+    assert out[1]["step"] == 55
