@@ -1195,6 +1195,8 @@ int md_set_neighbor_list(md_handle* h, double skin, int32_t max_neighbors) {
       if (!h->d_nl_dirty) e = dalloc(h, &h->d_nl_dirty, 1);
       if (e == cudaSuccess) e = dalloc(h, &A.nl, (size_t)max_neighbors * n);
       if (e == cudaSuccess) e = dalloc(h, &A.nl_cnt, n);
+      if (e == cudaSuccess) e = dalloc(h, &A.nl_pk, (size_t)max_neighbors * n);
+      if (e == cudaSuccess) e = dalloc(h, &A.nl_off, n);
       if (e == cudaSuccess) e = dalloc(h, &A.smeta, n);
       if (e == cudaSuccess) e = dalloc(h, &A.xb, 3 * n);
       if (e == cudaSuccess && !A.nl_builds) {

@@ -1470,7 +1470,7 @@ __global__ void __launch_bounds__(256) k_pair_row(DevArrays A) {
 // position is still within r_c + skin of any partner it had).
 // ---------------------------------------------------------------------------
 template <typename R, bool EXCL>
-__device__ __forceinline__ void nl_build_one(const DevArrays& A, const PairTab<R>& tab, uint32_t s) {
+__device__ __forceinline__ uint32_t nl_build_one(const DevArrays& A, const PairTab<R>& tab, uint32_t s) {
   using Rec = typename RecT<R>::T;
   const GlobalCells<R> C(A);
   const int64_t n = A.n;
@@ -1488,6 +1488,32 @@ __device__ __forceinline__ void nl_build_one(const DevArrays& A, const PairTab<R
   const R skin = (R)A.nl_skin;
   const uint32_t cap = (uint32_t)A.nl_max;
   uint32_t cnt = 0;
+  // the candidates of a run of len cells with consecutive ids and consecutive
+  // buckets (x = x0 .. x0 + len - 1 of one row) are one contiguous range of
+  // slots, the cells' particles one after another: the same candidates in
+  // the same order as cell by cell, with one pair of bucket bounds per run
+  auto walk = [&](uint32_t cell0, uint32_t b0, uint32_t len, int dx0, int dy, int dz) {
+    const uint32_t t1 = C.start(b0 + len);
+    const R shy = (R)dy * csy, shz = (R)dz * csz;
+    for (uint32_t t = C.start(b0); t < t1; ++t) {
+      const Rec rj = C.rec(t);
+      const uint32_t cj = A.rec_cell ? RecT<R>::bits(rj) >> 3 : C.scell(t);
+      const uint32_t k = cj - cell0;  // which cell of the run (a hash collision: none)
+      if (k >= len || t == s) continue;
+      const uint32_t bj = RecT<R>::bits(rj);
+      if (EXCL && (bj >> 3) == moli) continue;
+      const uint32_t qt = ti * kMaxTypes + (bj & 7u);
+      if (!(tab.rc2[qt] > (R)0)) continue;
+      const int dx = dx0 + (int)k;
+      const R ddx = ri.x - rj.x - (R)dx * csx, ddy = ri.y - rj.y - shy, ddz = ri.z - rj.z - shz;
+      const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+      const R rs = tab.rc[qt] + skin;
+      if (r2 < rs * rs) {
+        if (cnt < cap) A.nl[(int64_t)s * cap + cnt] = t << 5 | (uint32_t)(9 * (dz + 1) + 3 * (dy + 1) + dx + 1);
+        ++cnt;
+      }
+    }
+  };
   for (int dz = -1; dz <= 1; ++dz) {
     int z = c[2] + dz;
     if (z < 0 || z >= S.nc[2]) {
@@ -1500,34 +1526,26 @@ __device__ __forceinline__ void nl_build_one(const DevArrays& A, const PairTab<R
         if (!S.periodic[1]) continue;
         y = (y + S.nc[1]) % S.nc[1];
       }
-      for (int dx = -1; dx <= 1; ++dx) {
-        int x = c[0] + dx;
-        if (x < 0 || x >= S.nc[0]) {
-          if (!S.periodic[0]) continue;
-          x = (x + S.nc[0]) % S.nc[0];
-        }
-        const uint32_t nb = cell_id(S, x, y, z);
-        const uint32_t b = C.bucket(nb);
-        const uint32_t t1 = C.start(b + 1);
-        const uint32_t code = (uint32_t)(9 * (dz + 1) + 3 * (dy + 1) + dx + 1);
-        const R shx = (R)dx * csx, shy = (R)dy * csy, shz = (R)dz * csz;
-        for (uint32_t t = C.start(b); t < t1; ++t) {
-          const Rec rj = C.rec(t);
-          const uint32_t cj = A.rec_cell ? RecT<R>::bits(rj) >> 3 : C.scell(t);
-          if (cj != nb || t == s) continue;
-          const uint32_t bj = RecT<R>::bits(rj);
-          if (EXCL && (bj >> 3) == moli) continue;
-          const uint32_t qt = ti * kMaxTypes + (bj & 7u);
-          if (!(tab.rc2[qt] > (R)0)) continue;
-          const R ddx = ri.x - rj.x - shx, ddy = ri.y - rj.y - shy, ddz = ri.z - rj.z - shz;
-          const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-          const R rs = tab.rc[qt] + skin;
-          if (r2 < rs * rs) {
-            if (cnt < cap) A.nl[(int64_t)s * cap + cnt] = t << 5 | code;
-            ++cnt;
-          }
-        }
+      // the row's three cells (dx = -1, 0, +1; the first and last may be
+      // missing on an open axis or wrapped on a periodic one)
+      int xm = c[0] - 1, xp = c[0] + 1;
+      bool hm = true, hp = true;
+      if (xm < 0) {
+        hm = S.periodic[0] != 0;
+        xm += S.nc[0];
       }
+      if (xp >= S.nc[0]) {
+        hp = S.periodic[0] != 0;
+        xp -= S.nc[0];
+      }
+      const uint32_t cc = cell_id(S, c[0], y, z), bc = C.bucket(cc);
+      const uint32_t cm = hm ? cell_id(S, xm, y, z) : 0u, bm = hm ? C.bucket(cm) : 0u;
+      const uint32_t cp = hp ? cell_id(S, xp, y, z) : 0u, bp = hp ? C.bucket(cp) : 0u;
+      const bool jm = hm && cc == cm + 1u && bc == bm + 1u;  // dx = -1 joins the centre's run
+      const bool jp = hp && cp == cc + 1u && bp == bc + 1u;  // dx = +1 joins it
+      if (hm && !jm) walk(cm, bm, 1u, -1, dy, dz);
+      walk(jm ? cm : cc, jm ? bm : bc, 1u + (jm ? 1u : 0u) + (jp ? 1u : 0u), jm ? -1 : 0, dy, dz);
+      if (hp && !jp) walk(cp, bp, 1u, 1, dy, dz);
     }
   }
   if (cnt > cap) flag(A.status, kFlagNlistFull);
@@ -1537,6 +1555,29 @@ __device__ __forceinline__ void nl_build_one(const DevArrays& A, const PairTab<R
   A.xb[tag] = A.x[tag];
   A.xb[n + tag] = A.x[n + tag];
   A.xb[2 * n + tag] = A.x[2 * n + tag];
+  return min(cnt, cap);
+}
+
+// Packs the lists of a warp's 32 consecutive slots s (group-aligned; lanes
+// past the end pass valid = false) into their group's run of nl_pk: a prefix
+// sum of the counts over the warp gives each slot's start, and each lane
+// copies its own entries from the scratch it has just written.
+__device__ __forceinline__ void nl_pack_warp(const DevArrays& A, uint32_t s, bool valid, uint32_t cnt) {
+  const int lane = (int)(threadIdx.x & 31u);
+  const uint32_t c = valid ? cnt : 0u;
+  uint32_t incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (!valid) return;
+  const uint32_t pre = incl - c;
+  const uint32_t cap = (uint32_t)A.nl_max;
+  A.nl_off[s] = pre;
+  const uint32_t* src = A.nl + (int64_t)s * cap;
+  uint32_t* dst = A.nl_pk + (int64_t)(s & ~31u) * cap + pre;
+  for (uint32_t k = 0; k < c; ++k) dst[k] = src[k];
 }
 
 template <typename R, bool EXCL>
@@ -1546,8 +1587,10 @@ __global__ void __launch_bounds__(256) k_nl_build(DevArrays A) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *A.nl_builds += 1ull;
   load_tab<R>(tab, A.types);
   __syncthreads();
-  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < (uint32_t)A.n) nl_build_one<R, EXCL>(A, tab, s);
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;  // whole warps: blockDim is a multiple of 32
+  const bool valid = s < (uint32_t)A.n;
+  const uint32_t cnt = valid ? nl_build_one<R, EXCL>(A, tab, s) : 0u;
+  nl_pack_warp(A, s, valid, cnt);
 }
 
 // ---------------------------------------------------------------------------
@@ -1647,8 +1690,13 @@ __global__ void __launch_bounds__(256) k_rebuild(DevArrays A) {
   if (!grid_barrier(A.gbar, G, lim, A.status, &s_ok)) return;
   for (int64_t s = first; s < n; s += stride) bucket_build_one<R>(A, s);
   if (!grid_barrier(A.gbar, G, lim, A.status, &s_ok)) return;
-  // 5. the Verlet list of the new cell list
-  for (int64_t s = first; s < n; s += stride) nl_build_one<R, EXCL>(A, tab, (uint32_t)s);
+  // 5. the Verlet list of the new cell list, packed by whole warps of 32 consecutive slots
+  for (int64_t w = first - (tid & 31u); w < n; w += stride) {
+    const int64_t s = w + (tid & 31u);
+    const bool valid = s < n;
+    const uint32_t cnt = valid ? nl_build_one<R, EXCL>(A, tab, (uint32_t)s) : 0u;
+    nl_pack_warp(A, (uint32_t)s, valid, cnt);
+  }
   if (lead) {
     *A.nl_builds += 1ull;
     if (A.noise_k) *A.noise_k = *A.step;
@@ -1706,7 +1754,6 @@ __global__ void __launch_bounds__(256, SURFMD_PAIR_NL_MINB) k_pair_nl(DevArrays 
   using Rec = typename RecT<R>::T;
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= (uint32_t)A.n) return;
-  const int64_t n = A.n;
   const Rec* __restrict__ rec = reinterpret_cast<const Rec*>(A.rec);
   const uint32_t tag = A.stag[s];
   const uint32_t m = A.meta[tag];
@@ -1719,7 +1766,7 @@ __global__ void __launch_bounds__(256, SURFMD_PAIR_NL_MINB) k_pair_nl(DevArrays 
   const R csy = sizeof(R) == 4 ? (R)S.cs_f[1] : (R)S.cs[1];
   const R csz = sizeof(R) == 4 ? (R)S.cs_f[2] : (R)S.cs[2];
   const uint32_t cnt = A.nl_cnt[s];
-  const uint32_t* __restrict__ nl = A.nl + (int64_t)s * A.nl_max;
+  const uint32_t* __restrict__ nl = A.nl_pk + (int64_t)(s & ~31u) * A.nl_max + A.nl_off[s];
   R fx = 0, fy = 0, fz = 0, u = 0;
   // batches of kNlBatch entries: the batch's entries, then its records (and,
   // mixed, their low parts) are all loaded before any term is evaluated, so
@@ -1823,11 +1870,10 @@ __global__ void __launch_bounds__(kQueueWarps * 32, SURFMD_NLQ_MINB) k_pair_nlq(
   const bool valid = (uint32_t)lane < P && s < (uint32_t)A.n;
   const float4* __restrict__ rec = reinterpret_cast<const float4*>(A.rec);
   const float4* __restrict__ lo = A.rec_lo;
-  const uint32_t* __restrict__ nl = A.nl;
-  const uint32_t cap = (uint32_t)A.nl_max;
-  uint32_t m = 0, cnt = 0;
+  uint32_t m = 0, cnt = 0, off = 0;
   float csx = 0.f, csy = 0.f, csz = 0.f;
   if (valid) {
+    off = A.nl_off[s];
     m = A.smeta[s];  // sorted copy: no gather through the particle's tag
     const SysDev& S = A.sys[meta_sys(m)];
     Q.ri[lane] = rec[s];
@@ -1845,6 +1891,9 @@ __global__ void __launch_bounds__(kQueueWarps * 32, SURFMD_NLQ_MINB) k_pair_nlq(
   }
   const uint32_t pre = incl - cnt;
   const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  // the warp's entries are one contiguous run of the packed lists (from its first slot's start)
+  const uint32_t* __restrict__ list =
+      A.nl_pk + (int64_t)(s0 & ~31u) * (uint32_t)A.nl_max + __shfl_sync(0xffffffffu, off, 0);
   float fx = 0.f, fy = 0.f, fz = 0.f, u = 0.f;
   // evaluate the k queued pairs from queue position q0 (k <= 32); each particle adds its run in order
   auto drain = [&](uint32_t q0, uint32_t k) {
@@ -1905,9 +1954,8 @@ __global__ void __launch_bounds__(kQueueWarps * 32, SURFMD_NLQ_MINB) k_pair_nlq(
         const uint32_t pc = __shfl_sync(0xffffffffu, pre, (int)(cand & 31u));
         if (cand < 32u && pc <= p) ow = cand;
       }
-      const uint32_t k = p - __shfl_sync(0xffffffffu, pre, (int)ow);
       Q.own[32 * g + lane] = (uint8_t)ow;
-      e[g] = p < total ? nl[(int64_t)(s0 + ow) * cap + k] : 0u;
+      e[g] = p < total ? list[p] : 0u;
     }
     // the entries' records and low parts to shared memory, all in flight together
     __syncwarp();  // the previous group's evaluations have read their staged pairs

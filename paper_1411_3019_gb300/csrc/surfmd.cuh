@@ -168,8 +168,14 @@ struct DevArrays {
   // the records in place and raises *nl_dirty when a particle has moved more
   // than skin / 2, and the cell list and the list are rebuilt in that step.
   uint32_t* nl_dirty;   // device flag: 1 = rebuild the cell list and the neighbour list
-  uint32_t* nl;         // [n][nl_max] neighbour entries by sorted slot: slot << 5 | stencil cell (0..26)
+  uint32_t* nl;         // [n][nl_max] build scratch: entries by sorted slot, slot << 5 | stencil cell (0..26)
   uint32_t* nl_cnt;     // [n] entries per sorted slot
+  // the lists packed by groups of 32 consecutive slots: group g = s & ~31 owns
+  // entries [g nl_max, (g + 32) nl_max), its slots' lists one after another
+  // in slot order, slot s's from nl_off[s]; the walks read these (nl is the
+  // build's scratch)
+  uint32_t* nl_pk;
+  uint32_t* nl_off;     // [n] start of a slot's entries within its group's run
   uint32_t* smeta;      // [n] meta of each sorted slot (written with the records at a rebuild), or null
   // mixed path with the list: the unit normals xi^k of the last integrated
   // step k (by particle; the next step's force combination needs them again)
