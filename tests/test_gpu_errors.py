@@ -36,6 +36,19 @@ def test_off_surface_state_is_rejected():
     _healthy()
 
 
+def test_type_outside_ntypes_is_rejected():
+    """A particle type equal to ntypes (inside the table's 8 slots, outside
+    the types the parameters define) is refused by md_set_state."""
+    s = _sphere()
+    s["type"] = np.asarray(s["type"]).copy()
+    s["type"][5] = s["params"]["ntypes"]
+    with md.Simulation([s]) as sim:
+        with pytest.raises(md.MdError) as e:
+            sim.set_state()
+        assert e.value.code == md.MD_ERR_INVALID_ARG
+    _healthy()
+
+
 def test_nan_state_is_rejected():
     s = _sphere()
     s["v"] = s["v"].copy()

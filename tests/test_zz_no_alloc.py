@@ -115,3 +115,20 @@ def test_noalloc_rejects_systems_beyond_its_limit():
         md.md_forces_noalloc(sy["surface"], sy["params"], 70000, d, d)
     assert e.value.code == md.MD_ERR_INVALID_ARG
     assert "65536" in md.md_last_error(None)
+
+
+def test_noalloc_rejects_a_type_outside_ntypes():
+    """A type equal to ntypes is reported as a bad input, and the next call
+    with valid types still matches md_forces."""
+    torch = pytest.importorskip("torch")
+    systems = [I.sphere_system(n=1000, R=10.0, seed=1, dmin=0.8, precision="mixed", dt=0.001)]
+    sy = dict(systems[0])
+    x, f_ref, _ = _reference(systems)
+    _load(torch)
+    bad = dict(sy, type=np.asarray(sy["type"]).copy())
+    bad["type"][7] = sy["params"]["ntypes"]
+    with pytest.raises(md.MdError) as e:
+        _noalloc(torch, bad, x)
+    assert e.value.code == md.MD_ERR_INVALID_ARG
+    f, _, _ = _noalloc(torch, sy, x)
+    assert _rel(f, f_ref) <= FORCE_REL["mixed"]
