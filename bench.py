@@ -55,7 +55,9 @@ def parse(argv=None):
     ap.add_argument("--precision", default=None, choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the float64 comparison leg")
-    ap.add_argument("--no-tune", action="store_true", help="keep the default launch options")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default launch options (with the Verlet list: the workload's skin and 32 "
+                         "particles per warp, no autotuning)")
     ap.add_argument("--engine", default="auto", choices=["auto", "global", "resident"],
                     help="auto: the autotuner picks the engine and its options")
     ap.add_argument("--pair-tile", type=int, default=None, choices=[0, 8, 16, 32],
@@ -436,11 +438,23 @@ def main(argv=None):
         return [a.elapsed_time(b) / k] * k, md.md_last_launch_count(sim.h)
 
     skin = workload_skin(args)
-    systems = cells_for_skin(workload(args.workload, rank, precision, args.nrep, args.pair_form), skin)
+    systems = workload(args.workload, rank, precision, args.nrep, args.pair_form)
+    list_tuned = None
+    if skin > 0 and args.skin < 0 and not args.no_tune and args.engine != "resident":
+        from paper_1411_3019_gb300 import tune
+
+        with torch.cuda.stream(stream):  # the skin (cell size r_c + skin) and the walk's warp width
+            list_tuned = tune.autotune_list(systems, workload_max_neighbors(args), flush=lambda: flush_l2(),
+                                            stream=stream)
+        if list_tuned:
+            skin = list_tuned["skin"]
+    systems = cells_for_skin(systems, skin)
     n_local = int(sum(s["n"] for s in systems))
     sim = md.Simulation(systems, stream=stream)
     if skin > 0:
         md.md_set_neighbor_list(sim.h, skin, workload_max_neighbors(args))
+        if list_tuned:
+            md.md_set_option(sim.h, md.MD_OPT_LIST_WARP, list_tuned["list_warp"])
     sim.set_state()
     sim.step(args.warmup)
     sim.sync()
@@ -452,7 +466,10 @@ def main(argv=None):
         md.md_set_option(sim.h, md.MD_OPT_ENGINE, 1)
         tuned = {"options": {"engine": 1, "resident_threads": md.md_get_option(sim.h, md.MD_OPT_RESIDENT_THREADS)}}
     elif skin > 0:
-        tuned = {"options": {"neighbor_list_skin": skin, "max_neighbors": workload_max_neighbors(args)}}
+        tuned = {"options": {"neighbor_list_skin": skin, "max_neighbors": workload_max_neighbors(args)},
+                 "trials": list_tuned["trials"] if list_tuned else None}
+        if precision != "fp64":
+            tuned["options"]["list_warp"] = md.md_get_option(sim.h, md.MD_OPT_LIST_WARP)
     elif args.pair_tile is not None:
         md.md_set_option(sim.h, md.MD_OPT_PAIR_TILE, args.pair_tile)
         tuned = {"options": {**tuned["options"], "pair_tile": args.pair_tile}}

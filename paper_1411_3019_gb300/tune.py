@@ -13,6 +13,10 @@ applies the fastest:
   trial (its cost per step, with its one cell-list rebuild per call spread
   over the run).
 
+With the Verlet list (`autotune_list`): the skin, which sets the cell size
+r_c + skin of a new handle, and the list walk's particles per warp, each
+timed over a run of steps that includes the rebuilds the skin causes.
+
 The visiting order and the resident engine change no bit of the results;
 the lanes per particle and the cell-tiled kernel add each particle's pair
 terms in another order, so their forces differ from the default's by float
@@ -115,3 +119,61 @@ def autotune(h, trials: int = 3, flush=None, cache: str | None = None, gpu_name:
             json.dump(known, fh, indent=1)
     return {"cached": False, "best_ms": best_ms, "options": {NAMES[k]: v for k, v in best.items()},
             "trials": [{"ms": ms, **{NAMES[k]: v for k, v in c.items()}} for ms, c in results]}
+
+
+LIST_SKINS = (0.3, 0.4, 0.5, 0.6)
+LIST_WARPS = (32, 16)
+LIST_NAMES = {md.MD_OPT_LIST_WARP: "list_warp"}
+
+
+def _with_cell_size(systems, skin: float):
+    """Copies of the system dicts with the cell edge r_c + skin (the list's
+    reach), the cell size a handle with that skin needs."""
+    out = []
+    for sy in systems:
+        rc = float(max(map(max, sy["params"]["rcut"])))
+        out.append(dict(sy, params=dict(sy["params"], cell_size=rc + skin)))
+    return out
+
+
+def autotune_list(systems, max_neighbors: int, skins=LIST_SKINS, list_warps=LIST_WARPS, steps: int = 100,
+                  warmup: int = 20, flush=None, stream=None):
+    """Verlet-list step form: the skin (hence the cell size r_c + skin, fixed
+    when a handle is created) and the list walk's particles per warp. For
+    each skin a handle of the systems is created with that cell size; each
+    setting is timed as the sum of the step kernels' mean times over `steps`
+    steps (which include the list rebuilds that skin causes), after `warmup`
+    steps and an optional L2 flush. Returns the best setting and the trials;
+    the handles are destroyed (the caller creates its own with the choice).
+    Skins whose list overflows max_neighbors are skipped."""
+    trials = []
+    if systems and systems[0]["params"].get("precision") in ("fp64", 0):
+        list_warps = list_warps[:1]  # the float64 path walks per lane: no warp width to choose
+    for skin in skins:
+        sim = md.Simulation(_with_cell_size(systems, skin), stream=stream)
+        try:
+            md.md_set_neighbor_list(sim.h, skin, max_neighbors)
+            sim.set_state()
+            sim.step(warmup)
+            sim.sync()
+            for lw in list_warps:
+                try:
+                    md.md_set_option(sim.h, md.MD_OPT_LIST_WARP, lw)
+                except md.MdError:
+                    continue  # the float64 path has no warp-queued walk
+                md.md_profile_step(sim.h, 2)  # capture and warm this setting
+                if flush is not None:
+                    flush()
+                b0 = md.md_get_option(sim.h, md.MD_OPT_NLIST_BUILDS)
+                ms = sum(md.md_profile_step(sim.h, steps).values())
+                builds = md.md_get_option(sim.h, md.MD_OPT_NLIST_BUILDS) - b0
+                trials.append({"ms": ms, "skin": skin, "list_warp": lw, "builds": int(builds), "steps": steps})
+        except md.MdError:
+            pass  # e.g. the list is too small at this skin
+        finally:
+            sim.close()
+    if not trials:
+        return None
+    trials.sort(key=lambda t: t["ms"])
+    best = trials[0]
+    return {"skin": best["skin"], "list_warp": best["list_warp"], "best_ms": best["ms"], "trials": trials}

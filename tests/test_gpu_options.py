@@ -114,3 +114,26 @@ def test_autotuner_applies_a_valid_choice_and_keeps_parity(tmp_path):
     ref = oracle_run(systems, 30)[0]
     assert np.abs(st["x"] - ref["x"]).max() <= POS_100["mixed"]
     assert_forces(systems, st["x"], f, "mixed")
+
+
+def test_list_autotuner_times_every_skin_and_warp_width():
+    """tune.autotune_list creates one handle per skin (cell edge r_c + skin),
+    times each particles-per-warp setting over steps that include its list
+    rebuilds, and returns the fastest; a handle with the chosen setting then
+    matches the oracle."""
+    systems = I.c2_ellipsoid_torus(n_ell=4000, n_tor=1500, seed=8, precision="mixed")
+    out = tune.autotune_list(systems, 128, skins=(0.2, 0.4), list_warps=(32, 16), steps=30, warmup=5)
+    assert out is not None and len(out["trials"]) == 4
+    assert {(t["skin"], t["list_warp"]) for t in out["trials"]} == {(0.2, 32), (0.2, 16), (0.4, 32), (0.4, 16)}
+    assert out["trials"][0]["ms"] == out["best_ms"] and all(t["builds"] >= 0 for t in out["trials"])
+    assert all("cell_size" not in s["params"] or s["params"]["cell_size"] == 0.0 for s in systems)  # inputs untouched
+    chosen = tune._with_cell_size(systems, out["skin"])
+    with md.Simulation(chosen) as sim:
+        md.md_set_neighbor_list(sim.h, out["skin"], 128)
+        md.md_set_option(sim.h, md.MD_OPT_LIST_WARP, out["list_warp"])
+        sim.set_state()
+        sim.step(20)
+        sim.sync()
+        x = sim.state()["x"]
+    ref = oracle_run(systems, 20)[0]
+    assert np.abs(x - ref["x"]).max() <= POS_100["mixed"]
