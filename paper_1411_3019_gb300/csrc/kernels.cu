@@ -1469,6 +1469,11 @@ __global__ void __launch_bounds__(256) k_pair_row(DevArrays A) {
 // edge is at least r_c + skin, so a particle within skin / 2 of its build
 // position is still within r_c + skin of any partner it had).
 // ---------------------------------------------------------------------------
+#ifndef SURFMD_NL_BUILD_BATCH
+#define SURFMD_NL_BUILD_BATCH 2
+#endif
+constexpr int kNlBuildBatch = SURFMD_NL_BUILD_BATCH;
+
 template <typename R, bool EXCL>
 __device__ __forceinline__ uint32_t nl_build_one(const DevArrays& A, const PairTab<R>& tab, uint32_t s) {
   using Rec = typename RecT<R>::T;
@@ -1492,25 +1497,40 @@ __device__ __forceinline__ uint32_t nl_build_one(const DevArrays& A, const PairT
   // buckets (x = x0 .. x0 + len - 1 of one row) are one contiguous range of
   // slots, the cells' particles one after another: the same candidates in
   // the same order as cell by cell, with one pair of bucket bounds per run
+  // (the candidates' records are loaded kNlBuildBatch at a time, so their
+  // loads are in flight together; they are tested in slot order)
   auto walk = [&](uint32_t cell0, uint32_t b0, uint32_t len, int dx0, int dy, int dz) {
     const uint32_t t1 = C.start(b0 + len);
     const R shy = (R)dy * csy, shz = (R)dz * csz;
-    for (uint32_t t = C.start(b0); t < t1; ++t) {
-      const Rec rj = C.rec(t);
-      const uint32_t cj = A.rec_cell ? RecT<R>::bits(rj) >> 3 : C.scell(t);
-      const uint32_t k = cj - cell0;  // which cell of the run (a hash collision: none)
-      if (k >= len || t == s) continue;
-      const uint32_t bj = RecT<R>::bits(rj);
-      if (EXCL && (bj >> 3) == moli) continue;
-      const uint32_t qt = ti * kMaxTypes + (bj & 7u);
-      if (!(tab.rc2[qt] > (R)0)) continue;
-      const int dx = dx0 + (int)k;
-      const R ddx = ri.x - rj.x - (R)dx * csx, ddy = ri.y - rj.y - shy, ddz = ri.z - rj.z - shz;
-      const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-      const R rs = tab.rc[qt] + skin;
-      if (r2 < rs * rs) {
-        if (cnt < cap) A.nl[(int64_t)s * cap + cnt] = t << 5 | (uint32_t)(9 * (dz + 1) + 3 * (dy + 1) + dx + 1);
-        ++cnt;
+    for (uint32_t t0 = C.start(b0); t0 < t1; t0 += kNlBuildBatch) {
+      Rec rb[kNlBuildBatch];
+      uint32_t cb[kNlBuildBatch];
+#pragma unroll
+      for (int q = 0; q < kNlBuildBatch; ++q) {
+        if (t0 + q < t1) {
+          rb[q] = C.rec(t0 + q);
+          cb[q] = A.rec_cell ? RecT<R>::bits(rb[q]) >> 3 : C.scell(t0 + q);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kNlBuildBatch; ++q) {
+        const uint32_t t = t0 + q;
+        if (t >= t1) break;
+        const Rec& rj = rb[q];
+        const uint32_t k = cb[q] - cell0;  // which cell of the run (a hash collision: none)
+        if (k >= len || t == s) continue;
+        const uint32_t bj = RecT<R>::bits(rj);
+        if (EXCL && (bj >> 3) == moli) continue;
+        const uint32_t qt = ti * kMaxTypes + (bj & 7u);
+        if (!(tab.rc2[qt] > (R)0)) continue;
+        const int dx = dx0 + (int)k;
+        const R ddx = ri.x - rj.x - (R)dx * csx, ddy = ri.y - rj.y - shy, ddz = ri.z - rj.z - shz;
+        const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+        const R rs = tab.rc[qt] + skin;
+        if (r2 < rs * rs) {
+          if (cnt < cap) A.nl[(int64_t)s * cap + cnt] = t << 5 | (uint32_t)(9 * (dz + 1) + 3 * (dy + 1) + dx + 1);
+          ++cnt;
+        }
       }
     }
   };
@@ -1543,9 +1563,15 @@ __device__ __forceinline__ uint32_t nl_build_one(const DevArrays& A, const PairT
       const uint32_t cp = hp ? cell_id(S, xp, y, z) : 0u, bp = hp ? C.bucket(cp) : 0u;
       const bool jm = hm && cc == cm + 1u && bc == bm + 1u;  // dx = -1 joins the centre's run
       const bool jp = hp && cp == cc + 1u && bp == bc + 1u;  // dx = +1 joins it
-      if (hm && !jm) walk(cm, bm, 1u, -1, dy, dz);
-      walk(jm ? cm : cc, jm ? bm : bc, 1u + (jm ? 1u : 0u) + (jp ? 1u : 0u), jm ? -1 : 0, dy, dz);
-      if (hp && !jp) walk(cp, bp, 1u, 1, dy, dz);
+      // the row's runs in dx order: [-1 alone], the centre's run, [+1 alone]
+#pragma unroll 1
+      for (int r = (hm && !jm) ? 0 : 1; r <= ((hp && !jp) ? 2 : 1); ++r) {
+        const uint32_t c0 = r == 0 ? cm : r == 2 ? cp : (jm ? cm : cc);
+        const uint32_t b0 = r == 0 ? bm : r == 2 ? bp : (jm ? bm : bc);
+        const uint32_t len = r == 1 ? 1u + (jm ? 1u : 0u) + (jp ? 1u : 0u) : 1u;
+        const int dx0 = r == 0 ? -1 : r == 2 ? 1 : (jm ? -1 : 0);
+        walk(c0, b0, len, dx0, dy, dz);
+      }
     }
   }
   if (cnt > cap) flag(A.status, kFlagNlistFull);
@@ -1633,8 +1659,13 @@ __device__ __forceinline__ bool grid_barrier(GridBar* b, uint32_t nblocks, uint3
   return *s_ok != 0;
 }
 
+#ifndef SURFMD_REBUILD_THREADS
+#define SURFMD_REBUILD_THREADS 256
+#endif
+constexpr int kRebuildThreads = SURFMD_REBUILD_THREADS;  // threads per CTA of the fused rebuild
+
 template <typename R, bool EXCL>
-__global__ void __launch_bounds__(256) k_rebuild(DevArrays A) {
+__global__ void __launch_bounds__(kRebuildThreads) k_rebuild(DevArrays A) {
   __shared__ PairTab<R> tab;
   __shared__ uint32_t warp_tot[33];
   __shared__ int s_ok;
@@ -1714,21 +1745,21 @@ int rebuild_blocks(int precision, int excl, int64_t n) {
     return 0;
   cudaError_t e;
   if (precision == 0) {
-    e = excl ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rebuild<double, true>, 256, 0)
-             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rebuild<double, false>, 256, 0);
+    e = excl ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rebuild<double, true>, kRebuildThreads, 0)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rebuild<double, false>, kRebuildThreads, 0);
   } else {
-    e = excl ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rebuild<float, true>, 256, 0)
-             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rebuild<float, false>, 256, 0);
+    e = excl ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rebuild<float, true>, kRebuildThreads, 0)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rebuild<float, false>, kRebuildThreads, 0);
   }
   if (e != cudaSuccess || per_sm < 1) return 0;
-  const int64_t want = std::max<int64_t>(1, (n + 255) / 256);
+  const int64_t want = std::max<int64_t>(1, (n + kRebuildThreads - 1) / kRebuildThreads);
   return (int)std::min<int64_t>({want, (int64_t)per_sm * sms, (int64_t)kRebuildMaxBlocks});
 }
 
 cudaError_t launch_rebuild(const DevArrays& A, int precision, int excl, int blocks, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(kRebuildThreads);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
