@@ -47,6 +47,15 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 // Three normals of particle pid at step k: key (seed, replica), counter
 // (pid, k_lo, k_hi, 0); Box-Muller on words (0,1) -> x, y and (2,3) -> z
 // (cosine branch); u = ((w >> 9) + 1/2) 2^-23 is exact in float and double.
+// Float32 (the mixed path's Langevin noise): the logarithm, sine and cosine
+// are the hardware's fast approximations (absolute error about 1e-6 in a
+// normal; the angle is taken as 2 pi (u - 1/2) in (-pi, pi), where their
+// error bound holds, with the signs of sin and cos of 2 pi u restored). The
+// float64 path (below) keeps the library functions: it matches the oracle's
+// normals to rounding.
+#ifndef SURFMD_FAST_NOISE
+#define SURFMD_FAST_NOISE 1
+#endif
 __device__ __forceinline__ void gauss3(uint32_t seed, uint32_t rep, uint32_t pid, uint64_t k,
                                        float& gx, float& gy, float& gz) {
   const uint4 w = philox4x32_10(make_uint4(pid, (uint32_t)k, (uint32_t)(k >> 32), 0u),
@@ -54,6 +63,17 @@ __device__ __forceinline__ void gauss3(uint32_t seed, uint32_t rep, uint32_t pid
   const float s = 1.0f / 8388608.0f;
   const float u0 = ((float)(w.x >> 9) + 0.5f) * s, u1 = ((float)(w.y >> 9) + 0.5f) * s;
   const float u2 = ((float)(w.z >> 9) + 0.5f) * s, u3 = ((float)(w.w >> 9) + 0.5f) * s;
+#if SURFMD_FAST_NOISE
+  const float two_pi = 6.28318530717958648f;
+  // (near u = 1 the fast logarithm's absolute error can exceed -ln u: clamp at 0)
+  const float r01 = sqrtf(fmaxf(-2.0f * __logf(u0), 0.0f));
+  const float r23 = sqrtf(fmaxf(-2.0f * __logf(u2), 0.0f));
+  float sn, cs;
+  __sincosf(two_pi * (u1 - 0.5f), &sn, &cs);
+  gx = -r01 * cs;
+  gy = -r01 * sn;
+  gz = -r23 * __cosf(two_pi * (u3 - 0.5f));
+#else
   const float r01 = sqrtf(-2.0f * logf(u0));
   const float r23 = sqrtf(-2.0f * logf(u2));
   float sn, cs;
@@ -61,6 +81,7 @@ __device__ __forceinline__ void gauss3(uint32_t seed, uint32_t rep, uint32_t pid
   gx = r01 * cs;
   gy = r01 * sn;
   gz = r23 * cospif(2.0f * u3);
+#endif
 }
 
 __device__ __forceinline__ void gauss3(uint32_t seed, uint32_t rep, uint32_t pid, uint64_t k,
