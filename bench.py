@@ -256,14 +256,14 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # rooflines
 # ---------------------------------------------------------------------------
-# Algorithmic bytes per particle of the two kernels every step runs, as the
-# survey of the method counts them (each datum read or written once):
+# Algorithmic bytes per particle of the two kernels every step runs (each
+# datum the method needs read or written once):
 #   integrate: x (24) + p^{k-1/2} (24) + f (12, float32; 24 on the float64
 #              path) + type/flags (4) read, x + p^{k-1/2} (48) written, the
 #              cell key (4)  -> 116 B (128 B float64 path)
 #   pair:      the particle's float4 record once (16; double4 32), its cell
 #              start (4) and the force written (16; 32)  -> 36 B (68 B float64)
-SURVEY_BYTES = {"mixed": {"integrate": 116, "pair": 36}, "fp64": {"integrate": 128, "pair": 68}}
+ALGO_BYTES = {"mixed": {"integrate": 116, "pair": 36}, "fp64": {"integrate": 128, "pair": 68}}
 
 
 def algorithmic_bytes(kernel: str, n: int, nbucket: int, precision: str, nlist: bool = False) -> float:
@@ -273,7 +273,7 @@ def algorithmic_bytes(kernel: str, n: int, nbucket: int, precision: str, nlist: 
     every datum is read or written once; the list build and, with the
     neighbour list, the cell-list kernels (rebuild steps only) count none."""
     if kernel in ("integrate", "pair"):
-        return float(SURVEY_BYTES[precision][kernel] * n)
+        return float(ALGO_BYTES[precision][kernel] * n)
     if nlist:
         return 0.0
     v4 = 16 if precision == "mixed" else 32
@@ -361,7 +361,7 @@ def rooflines(prof_ms, n, nbucket, precision, hbm_peak, counts, fma_peaks, nlist
     r = table[top]
     main = {"bound": "hbm", "kernel": top, "achieved": r["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
             "frac": r["hbm_frac"], "traffic": r.get("traffic"),
-            "bytes_per_unit": SURVEY_BYTES[precision].get(top), "units_per_launch": n,
+            "bytes_per_unit": ALGO_BYTES[precision].get(top), "units_per_launch": n,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, copy)"}
     for key in ("fp64_pipe_frac", "fp32_pipe_frac"):
         if key in r:

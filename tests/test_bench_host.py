@@ -77,10 +77,10 @@ def test_neighbour_list_defaults_and_cell_edge():
     assert bench.cells_for_skin(systems, 0.0)[0]["params"]["cell_size"] == 0.0
 
 
-def test_algorithmic_bytes_follow_the_survey_figures():
+def test_algorithmic_bytes_per_particle():
     """The integrator and the pair kernel count the per-particle algorithmic
-    bytes of the method's survey (116 and 36 B in mixed precision, 128 and
-    68 B in float64) in both step forms; with the neighbour list the rebuild
+    bytes (each datum the method needs read or written once: 116 and 36 B in
+    mixed precision, 128 and 68 B in float64) in both step forms; with the neighbour list the rebuild
     kernels count no bytes per step; the implementation's own bytes are
     reported beside them."""
     assert bench.algorithmic_bytes("integrate", 1000, 4096, "mixed", nlist=True) == 116_000
@@ -94,7 +94,7 @@ def test_algorithmic_bytes_follow_the_survey_figures():
 
 
 def test_roofline_recomputes_from_kernel_times_bytes_and_peaks():
-    """roofline.frac = (survey bytes per particle x particles) / dominant
+    """roofline.frac = (algorithmic bytes per particle x particles) / dominant
     kernel's duration / measured HBM peak; the float64-pipe fraction uses the
     measured FMA rate."""
     prof = {"pair": 0.020, "integrate": 0.030, "scan": 0.006}
