@@ -452,7 +452,11 @@ int md_cell_list(md_handle* h, uint32_t* sorted_ids, uint32_t* sorted_cells,
  *   MD_ERR_OUT_OF_GRID.
  * The first call on a device resolves the scratch address on that device
  * (and loads the device code if it is not loaded yet); make that first call
- * before any stream capture. Every call shares the one array, which keeps the
+ * before any stream capture. While another thread captures a CUDA graph in
+ * relaxed or thread-local capture mode, a call on a non-blocking stream runs
+ * and gives the same forces; a capture in global mode in another thread
+ * forbids the call's synchronising copies (the runtime refuses them and
+ * invalidates that capture). Every call shares the one array, which keeps the
  * last call's contents (each call resets what must start at zero): calls that
  * overlap on the GPU (other threads, other streams) race and must be
  * serialised by the caller. Errors of this entry point are read with

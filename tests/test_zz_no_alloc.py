@@ -132,3 +132,56 @@ def test_noalloc_rejects_a_type_outside_ntypes():
     assert e.value.code == md.MD_ERR_INVALID_ARG
     f, _, _ = _noalloc(torch, sy, x)
     assert _rel(f, f_ref) <= FORCE_REL["mixed"]
+
+
+@pytest.mark.parametrize("mode", ["relaxed", "thread_local"])
+def test_noalloc_while_another_thread_captures_a_graph(mode):
+    """Thread A captures a small torch graph (relaxed or thread-local capture
+    mode) and holds the capture open while this thread calls
+    md_forces_noalloc on a non-blocking stream: the call runs, its forces
+    equal md_forces', and A's capture completes and replays."""
+    import threading
+
+    torch = pytest.importorskip("torch")
+    systems = [I.sphere_system(n=1000, R=10.0, seed=1, dmin=0.8, precision="mixed", dt=0.001)]
+    sy = systems[0]
+    x, f_ref, _ = _reference(systems)
+    _load(torch)
+    dev = torch.device("cuda:0")
+    d_x = torch.tensor(x, dtype=torch.float64, device=dev)
+    d_type = torch.tensor(sy["type"], dtype=torch.int32, device=dev)
+    d_con = torch.tensor(sy["constrained"], dtype=torch.uint8, device=dev)
+    d_f = torch.zeros((sy["n"], 3), dtype=torch.float64, device=dev)
+    a = torch.zeros(1 << 20, device=dev)
+    s_cap, s_b = torch.cuda.Stream(), torch.cuda.Stream()  # torch streams are non-blocking
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    started, release, errors = threading.Event(), threading.Event(), []
+
+    def capture():
+        try:
+            with torch.cuda.stream(s_cap):
+                g.capture_begin(capture_error_mode=mode)
+                a.add_(1.0)
+                started.set()
+                release.wait(timeout=30)
+                a.mul_(2.0)
+                g.capture_end()
+        except Exception as e:  # reported below
+            errors.append(e)
+            started.set()
+
+    t = threading.Thread(target=capture)
+    t.start()
+    assert started.wait(30)
+    try:
+        md.md_forces_noalloc(sy["surface"], sy["params"], sy["n"], d_x, d_f, d_type=d_type, d_con=d_con,
+                             stream=s_b)
+    finally:
+        release.set()
+        t.join()
+    assert not errors, errors
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(a[0]) == 2.0
+    assert _rel(d_f.cpu().numpy(), f_ref) <= FORCE_REL["mixed"]
