@@ -314,9 +314,10 @@ int md_step(md_handle* h, int64_t nsteps);
  * scan of more than one tile (more than 8192 buckets) always times out. */
 #define MD_OPT_SPIN_LIMIT 8
 /* MD_OPT_PAIR_QUEUE (mixed precision with the Verlet list): 1 (default) = a
- * warp screens its 32 particles' list entries round by round and queues the
- * pairs near or inside the cutoff, then evaluates 32 queued pairs at a time
- * on all lanes; 0 = each lane walks its particle's list alone. Both add every
+ * warp walks its particles' packed list entries as one sequence (their
+ * records staged in shared memory a few chunks of 32 at a time), queues the
+ * pairs near or inside the cutoff and evaluates 32 queued pairs at a time on
+ * all lanes; 0 = each lane walks its particle's list alone. Both add every
  * particle's terms in list order with the same arithmetic: the same bits. */
 #define MD_OPT_PAIR_QUEUE 9
 /* MD_OPT_FUSED_REBUILD (Verlet-list step form): 1 (default) = the cell-list
