@@ -111,3 +111,19 @@ def test_roofline_recomputes_from_kernel_times_bytes_and_peaks():
 def test_cpu_info_reports_cores():
     info = bench.cpu_info()
     assert info["cores"] >= 1
+
+
+def test_list_autotuner_candidate_systems_leave_the_inputs_alone():
+    """tune._with_cell_size gives copies of the system dicts whose cell edge is
+    the largest cutoff + skin (the cell size a handle with that skin needs);
+    the caller's dicts keep their parameters."""
+    from paper_1411_3019_gb300 import inputs as I
+    from paper_1411_3019_gb300 import tune
+
+    systems = I.c5_bead_molecules(nmol=20, beads=5, R=6.0, seed=2)
+    before = [dict(s["params"]) for s in systems]
+    out = tune._with_cell_size(systems, 0.4)
+    assert [s["params"]["cell_size"] for s in out] == [2.5 + 0.4] * len(systems)  # r_c = 2.5 between type-3 beads
+    assert all(o is not s and o["params"] is not s["params"] for o, s in zip(out, systems))
+    assert [s["params"]["cell_size"] for s in systems] == [b["cell_size"] for b in before]
+    assert tune.LIST_SKINS == (0.3, 0.4, 0.5, 0.6) and tune.LIST_WARPS == (32, 16)
