@@ -76,18 +76,43 @@ def parse(argv=None):
 
 
 # ---------------------------------------------------------------------------
-# workloads and their sharding over ranks (independent, seeded per rank)
+# workloads and their sharding over ranks: the batched replicas are split
+# across the ranks (strong scaling: the same 4,096 systems for any number of
+# GPUs); every other workload is an independently seeded copy per rank (weak
+# scaling)
 # ---------------------------------------------------------------------------
 def rank_seed(rank: int) -> int:
     return 1 + rank
 
 
-def workload(name: str, rank: int, precision: str, nrep: int = 4096, pair_form: int = 1):
-    """The systems rank `rank` advances: an independently seeded copy of the
-    named workload (weak scaling)."""
+def scaling_of(name: str) -> str:
+    return "strong" if name == "replicas" else "weak"
+
+
+def partition_replicas(systems, rank: int, world: int):
+    """The replicas rank `rank` of `world` advances: largest first, each
+    replica to the rank with the fewest particles so far (ties to the lowest
+    rank), so every rank computes the same split; each keeps its systems in
+    their original order (and with their own replica index and noise)."""
+    load = [0] * world
+    own = [[] for _ in range(world)]
+    for k in sorted(range(len(systems)), key=lambda k: (-systems[k]["n"], k)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        own[r].append(k)
+        load[r] += systems[k]["n"]
+    return [systems[k] for k in sorted(own[rank])]
+
+
+def workload(name: str, rank: int, precision: str, nrep: int = 4096, pair_form: int = 1, world: int = 1):
+    """The systems rank `rank` of `world` advances: its share of the batched
+    replicas (the same batch on every rank, split by partition_replicas), or
+    an independently seeded copy of any other workload."""
     from paper_1411_3019_gb300 import inputs
 
     seed = rank_seed(rank)
+    if name == "replicas" and world > 1:
+        full = inputs.c4_replicas(nrep=nrep, seed=rank_seed(0), precision=precision)
+        return partition_replicas(full, rank, world)
     if name == "ellipsoid_torus":
         return inputs.c2_ellipsoid_torus(seed=seed, precision=precision)
     if name == "plain_sphere":
@@ -438,7 +463,7 @@ def main(argv=None):
         return [a.elapsed_time(b) / k] * k, md.md_last_launch_count(sim.h)
 
     skin = workload_skin(args)
-    systems = workload(args.workload, rank, precision, args.nrep, args.pair_form)
+    systems = workload(args.workload, rank, precision, args.nrep, args.pair_form, world)
     list_tuned = None
     if skin > 0 and args.skin < 0 and not args.no_tune and args.engine != "resident":
         from paper_1411_3019_gb300 import tune
@@ -576,7 +601,7 @@ def main(argv=None):
 
     plain = None
     if not args.no_plain and precision == "mixed":
-        systems64 = cells_for_skin(workload(args.workload, rank, "fp64", args.nrep, args.pair_form), skin)
+        systems64 = cells_for_skin(workload(args.workload, rank, "fp64", args.nrep, args.pair_form, world), skin)
         sim64 = md.Simulation(systems64, stream=stream)
         if skin > 0:
             md.md_set_neighbor_list(sim64.h, skin, workload_max_neighbors(args))
@@ -627,7 +652,8 @@ def main(argv=None):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": scaling_of(args.workload),
             "vs_baseline": None, "dtype": "f32+f64" if precision == "mixed" else "f64", "data": "synthetic",
             "config": dict(workload_config(args.workload, systems, precision),
                            **({"l2": f"one md_step({args.steps}) call (persistent resident launches), L2 flushed "
@@ -641,6 +667,10 @@ def main(argv=None):
             "gpu_launches": launches, "plain_fp64": plain, "unconstrained_2d": flat,
             "tuned": {"options": tuned["options"], "trials": tuned.get("trials")},
         }
+        if scaling_of(args.workload) == "strong" and world > 1:  # the whole batch, split over the ranks
+            line["config"].update(particles=int(total_particles), systems=args.nrep,
+                                  workload=f"replicas: {int(total_particles)} particles in {args.nrep} systems, "
+                                           f"split across {world} ranks by particle count, {precision}")
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -840,7 +870,7 @@ def reference_arm(args, rank: int, world: int, precision: str):
     value = n * steps / el
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
             "warmup": args.warmup, "ms_per_step": el / steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": scaling_of(args.workload), "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(workload_config(args.workload, systems, precision),
                            engine="resident" if args.engine == "resident" else "global"),
             "impl": "reference",
